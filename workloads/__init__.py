@@ -1,0 +1,114 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmarks.
+
+This module only draws numbers and lays out initial occupations; it holds none of
+the two-site update's arithmetic (no contraction, no SVD, no truncation), so the
+CUDA path and the float64 oracle can both take their inputs from it without
+sharing any of the method.
+
+Workloads follow the model families the paper names for U(1)-symmetric tensor
+networks (Sec. I: Bose-Hubbard chains, XXZ spin chains, boson-sampling
+circuits).  The paper prints no benchmark inputs, so every input here is
+synthetic and seeded (numpy PCG64).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "neel_occupations",
+    "mott_occupations",
+    "single_photon_occupations",
+    "haar_beam_splitter_angles",
+    "brickwork_pairs",
+    "random_complex",
+    "random_positive",
+    "random_occupations",
+    "serving_requests",
+]
+
+
+def neel_occupations(L: int) -> list[int]:
+    """Neel product state of an XXZ chain: up (occupation 1) on even 0-based sites."""
+    return [1 if s % 2 == 0 else 0 for s in range(L)]
+
+
+def mott_occupations(L: int, filling: int = 1) -> list[int]:
+    """Mott product state of a Bose-Hubbard chain: `filling` bosons on every site."""
+    return [filling] * L
+
+
+def single_photon_occupations(M: int, n_photons: int) -> list[int]:
+    """Boson-sampling input: one photon in each of modes 0..n_photons-1."""
+    return [1 if j < n_photons else 0 for j in range(M)]
+
+
+def brickwork_pairs(M: int, depth: int) -> list[list[int]]:
+    """Left-mode indices of the beam splitters of a brickwork interferometer.
+
+    Layer l (0-based) acts on pairs (0,1),(2,3),... when l is even and on
+    (1,2),(3,4),... when l is odd.
+    """
+    layers = []
+    for layer in range(depth):
+        start = layer % 2
+        layers.append(list(range(start, M - 1, 2)))
+    return layers
+
+
+def haar_beam_splitter_angles(n_gates: int, seed: int = 0) -> np.ndarray:
+    """(theta, phi) per beam splitter, Haar-distributed on U(2)/phases.
+
+    sin^2(theta) ~ U[0,1] and phi ~ U[0, 2 pi), drawn from numpy PCG64(seed).
+    Returns an (n_gates, 2) float64 array.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u = rng.random(n_gates)
+    phi = rng.random(n_gates) * 2.0 * np.pi
+    theta = np.arcsin(np.sqrt(u))
+    return np.stack([theta, phi], axis=1)
+
+
+def random_complex(shape, rng: np.random.Generator) -> np.ndarray:
+    """Complex normal entries (real and imaginary parts standard normal)."""
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def random_positive(n: int, rng: np.random.Generator) -> np.ndarray:
+    """Positive reals in (0.05, 1], sorted descending (stand-in Schmidt weights)."""
+    v = 0.05 + 0.95 * rng.random(n)
+    return np.sort(v)[::-1].copy()
+
+
+def random_occupations(L: int, d: int, N: int, rng: np.random.Generator) -> list[int]:
+    """A random product state of L sites, local dimension d, total charge N."""
+    if N > L * (d - 1):
+        raise ValueError("N too large for L sites of dimension d")
+    occ = [0] * L
+    left = N
+    while left:
+        s = int(rng.integers(L))
+        if occ[s] < d - 1:
+            occ[s] += 1
+            left -= 1
+    return occ
+
+
+def serving_requests(n: int, seed: int = 0, rate_hz: float = 1.0):
+    """Seeded request mix for the serving workload.
+
+    Each request is a dict: arrival time (Poisson process of `rate_hz`), model
+    ('xxz' with Delta ~ U[0,2], or 'bh' with U/J ~ U[1,10]), chain length L in
+    {32, 64, 128}, chi in {64, 256, 1024} and a Trotter step count in 50..500.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate_hz, size=n)
+    t = np.cumsum(gaps)
+    out = []
+    for k in range(n):
+        model = "xxz" if rng.random() < 0.5 else "bh"
+        L = int(rng.choice([32, 64, 128]))
+        chi = int(rng.choice([64, 256, 1024]))
+        steps = int(rng.integers(50, 501))
+        param = float(rng.uniform(0.0, 2.0)) if model == "xxz" else float(rng.uniform(1.0, 10.0))
+        out.append(dict(id=k, arrival=float(t[k]), model=model, L=L, chi=chi, steps=steps, param=param))
+    return out
