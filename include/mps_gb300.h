@@ -1,0 +1,268 @@
+/*
+ * mps_gb300.h - C ABI of the GB300 U(1)-symmetric MPS two-site update library.
+ *
+ * The library keeps a U(1)-symmetric matrix product state on one GPU and applies
+ * charge-conserving two-site gates to it by the block-sparse TEBD update of
+ * arXiv:2303.11409, Sec. II: every bond index carries a right-charge
+ * c^[k] = sum_{j>k} i_j, the Kronecker deltas of the U(1) amplitude formula force
+ * c^[k-1] - c^[k] = i_k with c^[0] = N and c^[M] = 0, so a site tensor is a block
+ * matrix without an explicit physical index, and a two-site update needs only
+ * block-sparse SVDs of the submatrices Theta(c), each at most chi x chi.
+ *
+ * Conventions used by every entry point
+ *   - Sites are 0-based, s = 0..L-1.  Bond b (b = 0..L) sits left of site b, so
+ *     site s joins bond s and bond s+1.  The charge of bond b is the number of
+ *     particles on sites b..L-1; bond 0 carries N, bond L carries 0.
+ *   - The state is stored right-canonical: B^[s] = Gamma^[s] lambda^[s+1] (the
+ *     paper's Gamma/lambda pair), plus the Schmidt values lambda of every bond.
+ *   - Block (l, m) of site s joins charge l of bond s and charge m of bond s+1;
+ *     it exists iff 0 <= l - m <= d - 1 (the occupation of site s is l - m).
+ *     Blocks are stored row-major, complex128 interleaved (re, im).
+ *   - A two-site gate is given by its charge blocks G_n, n = 0..2(d-1); block n
+ *     acts on the basis (i, n - i), i ascending over max(0, n-d+1)..min(d-1, n),
+ *     i being the occupation of the left site; rows are outputs, columns inputs;
+ *     blocks are concatenated in n order, each row-major complex128.
+ *   - Host pointers passed in are read before the call returns; the caller keeps
+ *     ownership.  The library owns all device memory of a handle.
+ *   - Work is ordered on the handle's CUDA stream.  Results written to host
+ *     pointers are complete when the call returns.
+ *   - A handle is not thread-safe.  Every call returns an int status (below);
+ *     mps_last_error() gives a message for the last failing call on a handle.
+ */
+#ifndef MPS_GB300_H
+#define MPS_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MPS_API __attribute__((visibility("default")))
+#else
+#define MPS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mps_s* mps_t;
+
+/* Status codes. */
+#define MPS_OK        0   /* success */
+#define MPS_EINVAL   -1   /* bad argument, size or state */
+#define MPS_ECHARGE  -2   /* a charge outside [0, d-1] or an inconsistent charge table */
+#define MPS_ENOMEM   -3   /* device or host allocation failed, or capacity exceeded */
+#define MPS_ENOCONV  -4   /* a Jacobi SVD hit its sweep limit; the state was updated anyway */
+#define MPS_ECUDA    -5   /* a CUDA runtime error */
+#define MPS_ETIMEOUT -6   /* a bounded device wait expired */
+
+/* Precision modes of the sector GEMMs.  SVD, truncation and renormalisation are FP64 in all modes. */
+#define MPS_FP64   0
+#define MPS_TF32   1
+#define MPS_BF16X3 2
+
+/* Largest local dimension the library accepts. */
+#define MPS_MAX_D 8
+
+/*
+ * mps_create - a product state |i_0 ... i_{L-1}> on the device.
+ *   L             number of sites, >= 2
+ *   d             local dimension, 2..MPS_MAX_D
+ *   site_charges  host array of L occupations, each in [0, d-1]; N = their sum
+ *                 (the paper's total charge, the boundary value c^[0] = N)
+ *   precision     MPS_FP64, MPS_TF32 or MPS_BF16X3
+ *   chi_max       largest bond dimension any later update may request, >= 1;
+ *                 sizes the device arena (per bond min(chi_max, Hilbert bound))
+ *   cuda_stream   cudaStream_t the handle works on (NULL = legacy default stream)
+ * Errors: MPS_EINVAL, MPS_ECHARGE, MPS_ENOMEM, MPS_ECUDA.
+ */
+MPS_API int mps_create(mps_t* out, int L, int d, const int32_t* site_charges,
+               int precision, int chi_max, void* cuda_stream);
+
+/* mps_destroy - frees the handle and its device memory (after its stream drains). */
+MPS_API int mps_destroy(mps_t h);
+
+/* mps_last_error - message of the last failing call on h ("" if none); owned by h. */
+MPS_API const char* mps_last_error(mps_t h);
+
+/* mps_info - L, d, N, chi_max and precision of a handle (any pointer may be NULL). */
+MPS_API int mps_info(mps_t h, int* L, int* d, int* N, int* chi_max, int* precision);
+
+/*
+ * mps_apply_gate2 - one two-site update on sites (site, site+1).
+ *   gate_blocks   host complex128 gate blocks (layout above)
+ *   chi           bond dimension cap for the new middle bond, 1..chi_max
+ *   cutoff        keep only singular values > cutoff * |sigma|_2 (>= 0)
+ *   trunc_err_out optional: discarded weight sum_disc sigma^2 / sum sigma^2
+ * The update follows Sec. II: Theta'(c) = G . B^[s] B^[s+1] for every allowed
+ * middle charge c, an FP64 SVD of diag(lambda^[s]) Theta'(c) per c, a global
+ * top-chi truncation across all c (ties within 1e-11 sigma_max at the cut go to
+ * the lower charge), then B^[s+1] = Y^dag_kept, B^[s] = Theta' Y_kept / |S_kept|
+ * and lambda^[s+1] = S_kept / |S_kept|.
+ * Errors: MPS_EINVAL, MPS_ENOMEM, MPS_ENOCONV (state updated), MPS_ECUDA.
+ */
+MPS_API int mps_apply_gate2(mps_t h, int site, const double* gate_blocks, int chi,
+                    double cutoff, double* trunc_err_out);
+
+/*
+ * mps_apply_layer - n independent two-site updates on one handle in one set of
+ * launches (the paper's "independent two-site updates ... processed in parallel",
+ * Sec. II).  sites[k] are left sites of pairwise disjoint pairs (no two differ by
+ * less than 2); gate_blocks[k] are host gate blocks; chi and cutoff as above;
+ * trunc_err_out (optional) receives n values.
+ */
+MPS_API int mps_apply_layer(mps_t h, int n, const int* sites, const double* const* gate_blocks,
+                    int chi, double cutoff, double* trunc_err_out);
+
+/*
+ * mps_apply_gate2_batch - updates on several handles merged into shared launches.
+ * Item k applies gates[k] at sites[k] of hs[k] with chis[k], cutoffs[k].  Items on
+ * one handle must touch disjoint site pairs.  All handles must live on the current
+ * device; work runs on hs[0]'s stream (the others' streams are joined first).
+ * status_out[k] receives the per-item status; the return value is the first
+ * non-OK item status, or MPS_OK.
+ */
+MPS_API int mps_apply_gate2_batch(int n, mps_t* hs, const int* sites, const double* const* gates,
+                          const int* chis, const double* cutoffs, double* trunc_err_out,
+                          int* status_out);
+
+/*
+ * mps_expect - <O_site> of a diagonal one-site operator (U(1)-conserving one-site
+ * operators are diagonal in the occupation basis).
+ *   diag_op  host array of d real values O(i)
+ *   out      host double: sum lambda^[s]_a^2 |B^[s]_{ab}|^2 O(l - m) over all blocks
+ *            (the local canonical formula; lambda are the Schmidt values of Sec. II)
+ */
+MPS_API int mps_expect(mps_t h, int site, const double* diag_op, double* out);
+
+/*
+ * mps_amplitude - <i_0 ... i_{L-1}|psi>, the product of the one block per site the
+ * charges select (the U(1) amplitude formula of Sec. II).
+ *   config       host array of L occupations
+ *   out_complex  host double[2] (re, im); 0 when sum(config) != N or an
+ *                occupation is outside [0, d-1]
+ */
+MPS_API int mps_amplitude(mps_t h, const int32_t* config, double out_complex[2]);
+
+/* mps_amplitude_batch - n amplitudes; configs is n x L row-major, out is n x 2. */
+MPS_API int mps_amplitude_batch(mps_t h, int n, const int32_t* configs, double* out);
+
+/*
+ * mps_bond_spectrum - the sectors of bond b (0..L): charges and dims ascending by
+ * charge, and lambda values sector by sector (each sector descending).
+ *   cap    capacity of charges/dims (sectors); lambda must hold the bond dimension
+ *   n_out  number of sectors; if cap is too small nothing else is written and
+ *          MPS_EINVAL is returned with n_out set
+ */
+MPS_API int mps_bond_spectrum(mps_t h, int bond, int32_t* charges, int32_t* dims, double* lambda,
+                      int cap, int* n_out);
+
+/*
+ * mps_get_site - the blocks of site s in (l ascending, m ascending) order.
+ *   lcharges, mcharges  block labels (capacity cap_blocks)
+ *   data                complex128 interleaved, blocks concatenated, each row-major
+ *                       D_l x D_m (capacity cap_values complex numbers)
+ *   n_blocks, n_values  sizes written (set even when a capacity is too small, in
+ *                       which case MPS_EINVAL is returned and nothing else written)
+ */
+MPS_API int mps_get_site(mps_t h, int site, int32_t* lcharges, int32_t* mcharges, int cap_blocks,
+                 double* data, int64_t cap_values, int* n_blocks, int64_t* n_values);
+
+/*
+ * mps_set_bond - replace the sector table and lambda of bond b (1..L-1).
+ * mps_set_site - replace the blocks of site s; the blocks must be exactly the
+ *   allowed (l, m) pairs of the current tables of bonds s and s+1, in (l, m)
+ *   ascending order, with data laid out as in mps_get_site.
+ * Together they load an arbitrary state (for checkpoints and tests); set every
+ * bond first, then every site whose neighbouring bonds changed.
+ */
+MPS_API int mps_set_bond(mps_t h, int bond, int n_sectors, const int32_t* charges, const int32_t* dims,
+                 const double* lambda);
+MPS_API int mps_set_site(mps_t h, int site, int n_blocks, const int32_t* lcharges, const int32_t* mcharges,
+                 const double* data);
+
+/*
+ * mps_last_update_stats - diagnostics of the last update on h: counts of sectors,
+ * (l,m,r) triples, Jacobi sweeps (max over sectors), ties resolved at the chi cut,
+ * and the pre-renormalisation norm |S_all| and kept norm |S_kept|.
+ * Any pointer may be NULL.
+ */
+MPS_API int mps_last_update_stats(mps_t h, int* n_sectors, int* n_triples, int* max_sweeps,
+                          int* tie_band, double* norm_all, double* norm_kept);
+
+/*
+ * Kernel kinds reported by mps_kernel_stats.
+ *   THETA   Theta'(c) build: sector GEMMs with the gate mixed in (Sec. II)
+ *   SVD     batched per-sector Jacobi SVD
+ *   SELECT  global top-chi truncation across sectors
+ *   LAMBDA, SCATTER, GEMM  reassembly of lambda, B^[s+1] and B^[s]
+ *   EXPECT, AMPLITUDE      measurements
+ */
+#define MPS_K_THETA 0
+#define MPS_K_SVD 1
+#define MPS_K_SELECT 2
+#define MPS_K_LAMBDA 3
+#define MPS_K_SCATTER 4
+#define MPS_K_GEMM 5
+#define MPS_K_EXPECT 6
+#define MPS_K_AMPLITUDE 7
+#define MPS_K_COUNT 8
+
+/*
+ * mps_set_profiling - when on, every kernel launch of h is bracketed by CUDA events
+ * on h's stream and its device time is accumulated per kind.
+ * mps_kernel_stats - for one kind since the last reset: launches, summed device
+ * milliseconds (0 unless profiling was on), and the algorithmic work of those
+ * launches: flops (complex multiply-add = 8; SVD counted by the nominal
+ * 4 (6 a b^2 + 20 b^3), a = max(m, n), b = min(m, n), per sector) and bytes
+ * (compulsory reads + writes).  Synchronises h's stream.
+ * mps_reset_kernel_stats - zeroes the counters of h.
+ * mps_launch_count - kernels launched by this library in this process so far.
+ */
+MPS_API int mps_set_profiling(mps_t h, int on);
+MPS_API int mps_kernel_stats(mps_t h, int kind, int64_t* launches, double* ms, double* flops, double* bytes);
+MPS_API int mps_reset_kernel_stats(mps_t h);
+MPS_API int64_t mps_launch_count(void);
+
+/*
+ * mps_plan_sectors - the integer sector planner alone (host code, no GPU needed).
+ * Given the charge tables of bonds s, s+1, s+2 (ascending charges), it lists every
+ * compatible (l, m, r) with 0 <= l-m <= d-1 and 0 <= m-r <= d-1, and every
+ * candidate middle charge c with its Theta(c) size: rows = sum of D_l over
+ * c <= l <= c+d-1, cols = sum of D_r over c-d+1 <= r <= c (Sec. II).
+ *   triples     out, 3 ints per triple (l, m, r), lexicographic ascending
+ *   sectors     out, 3 ints per sector (c, rows, cols), c ascending
+ *   n_triples, n_sectors  sizes written; MPS_EINVAL if a capacity is too small
+ */
+MPS_API int mps_plan_sectors(int d, int nl, const int32_t* lc, const int32_t* ld,
+                     int nm, const int32_t* mc, const int32_t* md,
+                     int nr, const int32_t* rc, const int32_t* rd,
+                     int32_t* triples, int cap_triples, int* n_triples,
+                     int32_t* sectors, int cap_sectors, int* n_sectors);
+
+/*
+ * mps_svd_sectors - the batched per-sector SVD kernel alone, on device memory
+ * (one-sided Jacobi in FP64; Sec. II "block-sparse SVDs on submatrices").
+ * For each sector k it decomposes M_k = diag(rowscale_k) A_k, A_k being the
+ * m_k x n_k row-major complex128 matrix at d_mats + mat_off[k] (in complex
+ * numbers), rowscale_k the m_k doubles at d_rowscale + row_off[k] (NULL = 1):
+ *   d_sigma + sig_off[k]   min(m_k, n_k) singular values, descending
+ *   d_y + y_off[k]         the right singular vectors as an n_k x min(m_k,n_k)
+ *                          column-major complex128 matrix Y (M = X S Y^dag)
+ *   d_status[k]            Jacobi sweeps used, or -1 if not converged
+ * mat_off, row_off, sig_off, y_off, m, n are host int64/int arrays of length
+ * n_sectors; d_work is device scratch of work_bytes bytes, at least
+ * mps_svd_work_bytes(...) for the same sizes.
+ */
+MPS_API int64_t mps_svd_work_bytes(int n_sectors, const int* m, const int* n);
+MPS_API int mps_svd_sectors(int n_sectors, const int* m, const int* n,
+                    const double* d_mats, const int64_t* mat_off,
+                    const double* d_rowscale, const int64_t* row_off,
+                    double* d_sigma, const int64_t* sig_off,
+                    double* d_y, const int64_t* y_off,
+                    int* d_status, void* d_work, int64_t work_bytes, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPS_GB300_H */

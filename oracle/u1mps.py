@@ -31,7 +31,10 @@ Readings where the paper is silent (each also listed in the design doc):
     (sigma descending, charge ascending, in-sector index ascending); values
     within TIE_REL * sigma_max of the chi-th value count as ties and are taken
     by (charge, index) order;
-  * lambda on the new bond is renormalised to unit 2-norm after every update.
+  * lambda on the new bond is renormalised to unit 2-norm after every update;
+  * a sector's singular values at or below NOISE_REL * |M(c)|_F (32 eps) are
+    rounding noise and count as exact zeros, so a zero cutoff keeps exactly the
+    numerically nonzero spectrum.
 """
 from __future__ import annotations
 
@@ -42,6 +45,7 @@ import numpy as np
 import scipy.linalg
 
 TIE_REL = 1e-11
+NOISE_REL = 32.0 * np.finfo(np.float64).eps
 
 
 # ---------------------------------------------------------------------------
@@ -259,6 +263,8 @@ class U1MPS:
             lam_rows = np.concatenate([lam_left[l] for l in plan.rows[c]])
             M = lam_rows[:, None] * theta[c]
             _, S, Yh = scipy.linalg.svd(M, full_matrices=False, lapack_driver="gesvd")
+            # rounding-level singular values are zero (noise floor 32 eps |M|_F)
+            S = np.where(S <= NOISE_REL * math.sqrt(float(np.sum(S * S))), 0.0, S)
             svals[c], vecs[c] = S, Yh
 
         kept, info = select_kept(svals, chi, cutoff)

@@ -1,0 +1,12 @@
+"""GB300-native U(1)-symmetric MPS two-site TEBD update (arXiv:2303.11409, Sec. II).
+
+The hot path is the C-ABI CUDA library built from csrc/ (declared in
+include/mps_gb300.h); this package is its ctypes binding plus host-side model
+set-up.  Importing it fails if the library has not been built.
+"""
+from ._binding import (EXPORTED, LIB_PATH, MPS, MPS_BF16X3, MPS_EINVAL, MPS_ECHARGE, MPS_ENOCONV,  # noqa: F401
+                       MPS_ENOMEM, MPS_ECUDA, MPS_ETIMEOUT, MPS_FP64, MPS_MAX_D, MPS_OK, MPS_TF32,
+                       JacobiNotConverged, KERNEL_KINDS, MPSError, apply_gate2_batch, gate_length, launch_count, lib,
+                       plan_sectors,
+                       svd_sectors, svd_work_bytes)
+from . import models, tebd  # noqa: F401

@@ -1,0 +1,393 @@
+"""ctypes binding of the C ABI in include/mps_gb300.h.
+
+Argument marshalling only: every step of the two-site update runs in the CUDA
+library.  The library must have been built (python -m paper_2303_11409_gb300.build);
+importing this module fails loudly otherwise.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import warnings
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmps_gb300.so")
+
+MPS_OK, MPS_EINVAL, MPS_ECHARGE, MPS_ENOMEM, MPS_ENOCONV, MPS_ECUDA, MPS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+MPS_FP64, MPS_TF32, MPS_BF16X3 = 0, 1, 2
+MPS_MAX_D = 8
+KERNEL_KINDS = ("theta", "svd", "select", "lambda", "scatter", "gemm", "expect", "amplitude")
+STATUS_NAMES = {0: "MPS_OK", -1: "MPS_EINVAL", -2: "MPS_ECHARGE", -3: "MPS_ENOMEM", -4: "MPS_ENOCONV",
+                -5: "MPS_ECUDA", -6: "MPS_ETIMEOUT"}
+
+
+class MPSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class JacobiNotConverged(UserWarning):
+    pass
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"CUDA library {LIB_PATH} is not built; run `python -m paper_2303_11409_gb300.build` "
+            "(there is no CPU fallback)")
+    return ctypes.CDLL(LIB_PATH)
+
+
+lib = _load()
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_intp = ctypes.POINTER(ctypes.c_int)
+_dblp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+_h = ctypes.c_void_p
+
+_SIGS = {
+    "mps_create": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int,
+                                  ctypes.c_int, _vp]),
+    "mps_destroy": (ctypes.c_int, [_h]),
+    "mps_last_error": (ctypes.c_char_p, [_h]),
+    "mps_info": (ctypes.c_int, [_h, _intp, _intp, _intp, _intp, _intp]),
+    "mps_apply_gate2": (ctypes.c_int, [_h, ctypes.c_int, _dblp, ctypes.c_int, ctypes.c_double, _dblp]),
+    "mps_apply_layer": (ctypes.c_int, [_h, ctypes.c_int, _intp, ctypes.POINTER(_dblp), ctypes.c_int,
+                                       ctypes.c_double, _dblp]),
+    "mps_apply_gate2_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_h), _intp, ctypes.POINTER(_dblp),
+                                             _intp, _dblp, _dblp, _intp]),
+    "mps_expect": (ctypes.c_int, [_h, ctypes.c_int, _dblp, _dblp]),
+    "mps_amplitude": (ctypes.c_int, [_h, _i32p, _dblp]),
+    "mps_amplitude_batch": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _dblp]),
+    "mps_bond_spectrum": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _i32p, _dblp, ctypes.c_int, _intp]),
+    "mps_get_site": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _i32p, ctypes.c_int, _dblp, ctypes.c_int64,
+                                    _intp, _i64p]),
+    "mps_set_bond": (ctypes.c_int, [_h, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _dblp]),
+    "mps_set_site": (ctypes.c_int, [_h, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _dblp]),
+    "mps_last_update_stats": (ctypes.c_int, [_h, _intp, _intp, _intp, _intp, _dblp, _dblp]),
+    "mps_plan_sectors": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.c_int, _i32p, _i32p,
+                                        ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_int, _intp, _i32p,
+                                        ctypes.c_int, _intp]),
+    "mps_set_profiling": (ctypes.c_int, [_h, ctypes.c_int]),
+    "mps_kernel_stats": (ctypes.c_int, [_h, ctypes.c_int, _i64p, _dblp, _dblp, _dblp]),
+    "mps_reset_kernel_stats": (ctypes.c_int, [_h]),
+    "mps_launch_count": (ctypes.c_int64, []),
+    "mps_svd_work_bytes": (ctypes.c_int64, [ctypes.c_int, _intp, _intp]),
+    "mps_svd_sectors": (ctypes.c_int, [ctypes.c_int, _intp, _intp, _vp, _i64p, _vp, _i64p, _vp, _i64p, _vp,
+                                       _i64p, _vp, _vp, ctypes.c_int64, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def _ptr(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _c128_flat(blocks) -> np.ndarray:
+    if isinstance(blocks, np.ndarray) and blocks.ndim == 1:
+        flat = blocks
+    else:
+        flat = np.concatenate([np.asarray(b, dtype=np.complex128).reshape(-1) for b in blocks])
+    return np.ascontiguousarray(flat, dtype=np.complex128)
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover - torch is optional plumbing
+        pass
+    return None
+
+
+def gate_length(d: int) -> int:
+    """Complex numbers in one flattened gate: sum over n of s_n^2."""
+    tot = 0
+    for n in range(2 * d - 1):
+        s = min(d - 1, n) - max(0, n - d + 1) + 1
+        tot += s * s
+    return tot
+
+
+class MPS:
+    """A U(1)-symmetric MPS living on the GPU (one handle of the C library)."""
+
+    def __init__(self, d: int, occupations, chi_max: int, precision: int = MPS_FP64, stream=None):
+        occ = _i32(occupations)
+        self.L, self.d, self.chi_max = len(occ), int(d), int(chi_max)
+        self.stream = _default_stream() if stream is None else stream
+        h = _h()
+        rc = lib.mps_create(ctypes.byref(h), self.L, self.d, _ptr(occ, _i32p), precision, self.chi_max,
+                            self.stream)
+        if rc != MPS_OK:
+            raise MPSError(rc, "mps_create failed")
+        self._h = h
+        self.N = int(occ.sum())
+
+    # -- lifetime ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mps_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check(self, rc: int, what: str):
+        if rc == MPS_OK:
+            return
+        msg = lib.mps_last_error(self._h).decode()
+        if rc == MPS_ENOCONV:
+            warnings.warn(f"{what}: {msg}", JacobiNotConverged)
+            return
+        raise MPSError(rc, f"{what}: {msg}")
+
+    # -- updates ----------------------------------------------------------------
+    def apply_gate2(self, site: int, gate, chi: int, cutoff: float) -> float:
+        g = _c128_flat(gate)
+        if g.size != gate_length(self.d):
+            raise ValueError("gate has the wrong number of entries")
+        te = ctypes.c_double(0.0)
+        rc = lib.mps_apply_gate2(self._h, site, g.ctypes.data_as(_dblp), chi, cutoff, ctypes.byref(te))
+        self._check(rc, "mps_apply_gate2")
+        return te.value
+
+    def apply_layer(self, sites, gates, chi: int, cutoff: float) -> np.ndarray:
+        sites = np.ascontiguousarray(np.asarray(sites, dtype=np.intc))
+        gs = [_c128_flat(g) for g in gates]
+        if len(gs) != len(sites):
+            raise ValueError("one gate per site")
+        arr = (_dblp * len(gs))(*[g.ctypes.data_as(_dblp) for g in gs])
+        te = np.zeros(len(gs))
+        rc = lib.mps_apply_layer(self._h, len(gs), _ptr(sites, _intp), arr, chi, cutoff, _ptr(te, _dblp))
+        self._check(rc, "mps_apply_layer")
+        return te
+
+    # -- measurements -----------------------------------------------------------
+    def expect(self, site: int, diag_op) -> float:
+        op = np.ascontiguousarray(np.asarray(diag_op, dtype=np.float64))
+        out = ctypes.c_double(0.0)
+        self._check(lib.mps_expect(self._h, site, _ptr(op, _dblp), ctypes.byref(out)), "mps_expect")
+        return out.value
+
+    def amplitude(self, config) -> complex:
+        c = _i32(config)
+        out = np.zeros(2)
+        self._check(lib.mps_amplitude(self._h, _ptr(c, _i32p), _ptr(out, _dblp)), "mps_amplitude")
+        return complex(out[0], out[1])
+
+    def amplitudes(self, configs) -> np.ndarray:
+        c = _i32(configs).reshape(-1, self.L)
+        out = np.zeros((len(c), 2))
+        self._check(lib.mps_amplitude_batch(self._h, len(c), _ptr(c, _i32p), _ptr(out, _dblp)),
+                    "mps_amplitude_batch")
+        return out[:, 0] + 1j * out[:, 1]
+
+    def bond(self, b: int):
+        """(charges, dims, lambda per charge) of bond b."""
+        n = ctypes.c_int(0)
+        cap = self.L * (self.d - 1) + 2
+        ch = np.zeros(cap, np.int32)
+        dm = np.zeros(cap, np.int32)
+        lam = np.zeros(max(1, self.chi_max) + 1)
+        self._check(lib.mps_bond_spectrum(self._h, b, _ptr(ch, _i32p), _ptr(dm, _i32p), _ptr(lam, _dblp), cap,
+                                          ctypes.byref(n)), "mps_bond_spectrum")
+        k = n.value
+        out, off = {}, 0
+        for c, D in zip(ch[:k], dm[:k]):
+            out[int(c)] = lam[off:off + D].copy()
+            off += int(D)
+        return out
+
+    def bond_dims(self, b: int) -> dict:
+        return {c: len(v) for c, v in self.bond(b).items()}
+
+    def entropy(self, b: int) -> float:
+        p = np.concatenate([v ** 2 for v in self.bond(b).values()])
+        p = p[p > 0]
+        return float(-np.sum(p * np.log(p)))
+
+    def site(self, s: int) -> dict:
+        """{(l, m): block} of site s (host copy)."""
+        nb, nv = ctypes.c_int(0), ctypes.c_int64(0)
+        lib.mps_get_site(self._h, s, None, None, 0, None, 0, ctypes.byref(nb), ctypes.byref(nv))
+        lc = np.zeros(max(1, nb.value), np.int32)
+        mc = np.zeros(max(1, nb.value), np.int32)
+        data = np.zeros(max(1, nv.value), np.complex128)
+        rc = lib.mps_get_site(self._h, s, _ptr(lc, _i32p), _ptr(mc, _i32p), nb.value,
+                              data.ctypes.data_as(_dblp), nv.value, ctypes.byref(nb), ctypes.byref(nv))
+        self._check(rc, "mps_get_site")
+        left = self.bond_dims(s)
+        right = self.bond_dims(s + 1)
+        out, off = {}, 0
+        for l, m in zip(lc[:nb.value], mc[:nb.value]):
+            Dl, Dm = left[int(l)], right[int(m)]
+            out[(int(l), int(m))] = data[off:off + Dl * Dm].reshape(Dl, Dm).copy()
+            off += Dl * Dm
+        return out
+
+    def set_bond(self, b: int, lam: dict):
+        ch = _i32(sorted(lam))
+        dm = _i32([len(lam[c]) for c in sorted(lam)])
+        vals = np.ascontiguousarray(np.concatenate([np.asarray(lam[c], np.float64) for c in sorted(lam)]))
+        self._check(lib.mps_set_bond(self._h, b, len(ch), _ptr(ch, _i32p), _ptr(dm, _i32p), _ptr(vals, _dblp)),
+                    "mps_set_bond")
+
+    def set_site(self, s: int, blocks: dict):
+        keys = sorted(blocks)
+        lc = _i32([k[0] for k in keys])
+        mc = _i32([k[1] for k in keys])
+        if keys:
+            data = np.ascontiguousarray(np.concatenate([np.asarray(blocks[k], np.complex128).reshape(-1)
+                                                        for k in keys]))
+        else:
+            data = np.zeros(1, np.complex128)
+        self._check(lib.mps_set_site(self._h, s, len(keys), _ptr(lc, _i32p), _ptr(mc, _i32p),
+                                     data.ctypes.data_as(_dblp)), "mps_set_site")
+
+    def set_profiling(self, on: bool = True):
+        self._check(lib.mps_set_profiling(self._h, int(bool(on))), "mps_set_profiling")
+
+    def kernel_stats(self) -> dict:
+        """{kind: dict(launches, ms, flops, bytes)} accumulated since the last reset."""
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            n = ctypes.c_int64()
+            ms, fl, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            self._check(lib.mps_kernel_stats(self._h, k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl),
+                                             ctypes.byref(by)), "mps_kernel_stats")
+            out[name] = dict(launches=n.value, ms=ms.value, flops=fl.value, bytes=by.value)
+        return out
+
+    def reset_kernel_stats(self):
+        self._check(lib.mps_reset_kernel_stats(self._h), "mps_reset_kernel_stats")
+
+    def stats(self) -> dict:
+        a, b, c, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        na, nk = ctypes.c_double(), ctypes.c_double()
+        lib.mps_last_update_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(t),
+                                  ctypes.byref(na), ctypes.byref(nk))
+        return dict(n_sectors=a.value, n_triples=b.value, max_sweeps=c.value, tie_band=t.value,
+                    norm_all=na.value, norm_kept=nk.value)
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib.mps_launch_count())
+
+
+def apply_gate2_batch(items, stream_owner: MPS | None = None):
+    """Merged updates across handles: items = [(mps, site, gate, chi, cutoff), ...]."""
+    n = len(items)
+    hs = (_h * n)(*[it[0].handle for it in items])
+    sites = np.array([it[1] for it in items], dtype=np.intc)
+    gs = [_c128_flat(it[2]) for it in items]
+    garr = (_dblp * n)(*[g.ctypes.data_as(_dblp) for g in gs])
+    chis = np.array([it[3] for it in items], dtype=np.intc)
+    cuts = np.array([it[4] for it in items], dtype=np.float64)
+    te = np.zeros(n)
+    st = np.zeros(n, dtype=np.intc)
+    rc = lib.mps_apply_gate2_batch(n, hs, _ptr(sites, _intp), garr, _ptr(chis, _intp), _ptr(cuts, _dblp),
+                                   _ptr(te, _dblp), _ptr(st, _intp))
+    if rc not in (MPS_OK, MPS_ENOCONV):
+        raise MPSError(rc, "mps_apply_gate2_batch: " + lib.mps_last_error(items[0][0].handle).decode())
+    return te, st
+
+
+def plan_sectors(d: int, left: dict, mid: dict, right: dict):
+    """The library's integer sector planner: (triples, sectors) as int arrays."""
+    def tab(t):
+        ks = sorted(t)
+        return _i32(ks), _i32([t[k] for k in ks])
+    (lc, ld), (mc, md), (rc, rd) = tab(left), tab(mid), tab(right)
+    cap_t = max(1, len(lc) * len(mc) * len(rc))
+    cap_s = max(1, len(lc) + len(rc) + 2 * d)
+    tri = np.zeros(3 * cap_t, np.int32)
+    sec = np.zeros(3 * cap_s, np.int32)
+    nt, ns = ctypes.c_int(), ctypes.c_int()
+    rcode = lib.mps_plan_sectors(d, len(lc), _ptr(lc, _i32p), _ptr(ld, _i32p), len(mc), _ptr(mc, _i32p),
+                                 _ptr(md, _i32p), len(rc), _ptr(rc, _i32p), _ptr(rd, _i32p), _ptr(tri, _i32p),
+                                 cap_t, ctypes.byref(nt), _ptr(sec, _i32p), cap_s, ctypes.byref(ns))
+    if rcode != MPS_OK:
+        raise MPSError(rcode, "mps_plan_sectors")
+    return tri[:3 * nt.value].reshape(-1, 3), sec[:3 * ns.value].reshape(-1, 3)
+
+
+def svd_work_bytes(ms, ns) -> int:
+    m = np.ascontiguousarray(np.asarray(ms, dtype=np.intc))
+    n = np.ascontiguousarray(np.asarray(ns, dtype=np.intc))
+    return int(lib.mps_svd_work_bytes(len(m), _ptr(m, _intp), _ptr(n, _intp)))
+
+
+def svd_sectors(mats, rowscales=None, stream=None):
+    """Batched sector SVD on the GPU through mps_svd_sectors (torch supplies device memory).
+
+    mats: list of complex128 host arrays (m_k x n_k).  Returns [(sigma, Y, sweeps)] with
+    M_k = diag(rowscale_k) mats_k = X S Y^dag.
+    """
+    import torch
+    dev = torch.device("cuda")
+    ms = [a.shape[0] for a in mats]
+    ns = [a.shape[1] for a in mats]
+    ks = [min(a, b) for a, b in zip(ms, ns)]
+    mat_off = np.cumsum([0] + [a * b for a, b in zip(ms, ns)])[:-1].astype(np.int64)
+    y_off = np.cumsum([0] + [n * k for n, k in zip(ns, ks)])[:-1].astype(np.int64)
+    s_off = np.cumsum([0] + ks)[:-1].astype(np.int64)
+    r_off = np.cumsum([0] + ms)[:-1].astype(np.int64)
+    flat = np.concatenate([np.ascontiguousarray(a, np.complex128).reshape(-1) for a in mats])
+    d_mats = torch.from_numpy(flat.view(np.float64).copy()).to(dev)
+    d_sig = torch.zeros(sum(ks), dtype=torch.float64, device=dev)
+    d_y = torch.zeros(2 * sum(n * k for n, k in zip(ns, ks)), dtype=torch.float64, device=dev)
+    d_st = torch.zeros(len(mats), dtype=torch.int32, device=dev)
+    wb = svd_work_bytes(ms, ns)
+    d_work = torch.zeros(max(wb, 256), dtype=torch.uint8, device=dev)
+    d_rs = None
+    if rowscales is not None:
+        d_rs = torch.from_numpy(np.concatenate([np.asarray(r, np.float64) for r in rowscales])).to(dev)
+    st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    m_a = np.asarray(ms, np.intc)
+    n_a = np.asarray(ns, np.intc)
+    rc = lib.mps_svd_sectors(len(mats), _ptr(m_a, _intp), _ptr(n_a, _intp), d_mats.data_ptr(),
+                             _ptr(mat_off, _i64p), d_rs.data_ptr() if d_rs is not None else None,
+                             _ptr(r_off, _i64p) if d_rs is not None else None,
+                             d_sig.data_ptr(), _ptr(s_off, _i64p), d_y.data_ptr(), _ptr(y_off, _i64p),
+                             d_st.data_ptr(), d_work.data_ptr(), d_work.numel(), st)
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_svd_sectors")
+    torch.cuda.synchronize()
+    sig = d_sig.cpu().numpy()
+    y = d_y.cpu().numpy().view(np.complex128)
+    sts = d_st.cpu().numpy()
+    out = []
+    for k in range(len(mats)):
+        Y = y[y_off[k]:y_off[k] + ns[k] * ks[k]].reshape(ks[k], ns[k]).T   # column-major n x k
+        out.append((sig[s_off[k]:s_off[k] + ks[k]].copy(), Y.copy(), int(sts[k])))
+    return out

@@ -1,0 +1,959 @@
+// C ABI of the GB300 U(1) MPS library: handles, the device arena, and the
+// batched two-site update executor.
+//
+// One update (Sec. II of arXiv:2303.11409) runs as
+//   host planner (K0) -> theta_kernel (K1: Theta'(c) for all middle charges)
+//   -> jacobi_svd_kernel (K2: one CTA per sector) -> select_kernel (K3: global
+//   top-chi) -> one device-to-host copy of the kept counts -> host layout of the
+//   new blocks -> gemm/scatter/lambda kernels (K4/K5: reassembly, renormalisation).
+// Any number of independent updates (disjoint site pairs, possibly of different
+// handles) share each launch, which is how a whole Trotter layer is one set of
+// launches with one host round trip.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "mps_internal.h"
+
+using namespace mps;
+
+namespace mps {
+
+cudaError_t DevBuf::reserve(size_t want) {
+  if (want <= bytes) return cudaSuccess;
+  if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+  size_t sz = want + want / 4 + (1 << 20);
+  cudaError_t e = cudaMalloc(&p, sz);
+  if (e != cudaSuccess) { p = nullptr; return e; }
+  bytes = sz;
+  return cudaSuccess;
+}
+void DevBuf::release() { if (p) cudaFree(p); p = nullptr; bytes = 0; }
+
+cudaError_t PinnedBuf::reserve(size_t want) {
+  if (want <= bytes) return cudaSuccess;
+  if (p) { cudaFreeHost(p); p = nullptr; bytes = 0; }
+  size_t sz = want + want / 4 + (1 << 16);
+  cudaError_t e = cudaMallocHost(&p, sz);
+  if (e != cudaSuccess) { p = nullptr; return e; }
+  bytes = sz;
+  return cudaSuccess;
+}
+void PinnedBuf::release() { if (p) cudaFreeHost(p); p = nullptr; bytes = 0; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+}  // namespace mps
+
+namespace {
+
+int fail(mps_s* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CUDA_OR_FAIL(h, x)                                                            \
+  do {                                                                                \
+    cudaError_t _e = (x);                                                             \
+    if (_e != cudaSuccess)                                                            \
+      return fail(h, MPS_ECUDA, std::string(#x) + ": " + cudaGetErrorString(_e));     \
+  } while (0)
+
+inline int64_t a256(int64_t x) { return (x + 255) & ~int64_t(255); }
+
+// ---- per-kernel device timing and algorithmic work ------------------------------------
+cudaEvent_t pool_event(mps_s* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Adds the device time of completed event pairs; call only when they have completed.
+void resolve_pending(mps_s* h) {
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) h->kstat[p.kind].ms += ms;
+    h->event_pool.push_back(p.a);
+    h->event_pool.push_back(p.b);
+  }
+  h->pending.clear();
+}
+
+template <class F>
+cudaError_t timed(mps_s* h, int kind, bool nonempty, double flops, double bytes, F&& launch) {
+  const bool prof = h->profiling && nonempty;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (prof) { a = pool_event(h); b = pool_event(h); cudaEventRecord(a, h->stream); }
+  cudaError_t e = launch();
+  if (prof) { cudaEventRecord(b, h->stream); h->pending.push_back(PendingTiming{kind, a, b}); }
+  if (nonempty) {
+    KStat& k = h->kstat[kind];
+    k.launches++;
+    k.flops += flops;
+    k.bytes += bytes;
+  }
+  return e;
+}
+
+int gate_sn(int n, int d) { return std::min(d - 1, n) - std::max(0, n - d + 1) + 1; }
+int64_t gate_len(int d) {          // complex numbers in one gate (all charge blocks)
+  int64_t t = 0;
+  for (int n = 0; n <= 2 * (d - 1); ++n) t += (int64_t)gate_sn(n, d) * gate_sn(n, d);
+  return t;
+}
+int64_t gate_block_off(int n, int d) {
+  int64_t t = 0;
+  for (int k = 0; k < n; ++k) t += (int64_t)gate_sn(k, d) * gate_sn(k, d);
+  return t;
+}
+
+// Number of occupation strings of n sites (0..d-1 each) summing to q, saturated.
+std::vector<std::vector<double>> config_counts(int L, int d, int N) {
+  std::vector<std::vector<double>> W(L + 1, std::vector<double>(N + 1, 0.0));
+  W[0][0] = 1.0;
+  for (int n = 1; n <= L; ++n)
+    for (int q = 0; q <= N; ++q) {
+      double s = 0.0;
+      for (int i = 0; i < d && i <= q; ++i) s += W[n - 1][q - i];
+      W[n][q] = std::min(s, 1e30);
+    }
+  return W;
+}
+
+// A host-side bump allocator over a staging buffer plus the matching device offsets.
+struct Stager {
+  char* host; int64_t size = 0;
+  template <typename T> int64_t put(const T* src, int64_t count) {
+    int64_t off = size;
+    std::memcpy(host + off, src, sizeof(T) * count);
+    size = a256(off + (int64_t)sizeof(T) * count);
+    return off;
+  }
+};
+
+struct Req {
+  mps_s* h; int site; const double* gate; int chi; double cutoff;
+  int status = MPS_OK; double trunc = 0.0;
+};
+
+// Per-update scratch bookkeeping of one batch.
+struct UpdWork {
+  UpdatePlan plan;
+  std::vector<int64_t> theta_off, y_off, sig_off;   // byte offsets into the workspace per sector
+  int sel_first = 0;                                // index of the first sector in the select arrays
+  int64_t gate_off = 0;                             // byte offset of this update's staged gate
+};
+
+int run_batch(std::vector<Req>& reqs, mps_s* owner) {
+  if (reqs.empty()) return MPS_OK;
+  cudaStream_t st = owner->stream;
+  const int nreq = (int)reqs.size();
+  std::vector<UpdWork> W(nreq);
+
+  // ---- K0: plan every update and size the workspace --------------------------------
+  int64_t ws = 0;
+  int n_sec_total = 0, n_tiles = 0, n_tasks = 0, max_tri = 0;
+  int64_t theta_bytes_begin = 0, theta_bytes_end = 0;
+  int64_t scatter_bound = 0, gemm_tiles_bound = 0, gemm_tasks_bound = 0, lam_bound = 0;
+  for (int u = 0; u < nreq; ++u) {
+    mps_s* h = reqs[u].h;
+    const int s = reqs[u].site;
+    plan_update(h->bonds[s], h->bonds[s + 1], h->bonds[s + 2], h->d, W[u].plan);
+    max_tri = std::max<int>(max_tri, (int)W[u].plan.triple_l.size());
+    n_sec_total += (int)W[u].plan.sectors.size();
+    if (W[u].plan.sectors.empty()) return fail(owner, MPS_EINVAL, "update has no charge sectors");
+  }
+  // Theta' region first (one memset), then Y, sigma, Jacobi scratch, gates.
+  theta_bytes_begin = 0;
+  for (int u = 0; u < nreq; ++u)
+    for (auto& e : W[u].plan.sectors) {
+      W[u].theta_off.push_back(ws);
+      ws = a256(ws + 16LL * e.rows * e.cols);
+    }
+  theta_bytes_end = ws;
+  for (int u = 0; u < nreq; ++u)
+    for (auto& e : W[u].plan.sectors) {
+      const int k = std::min(e.rows, e.cols);
+      W[u].y_off.push_back(ws);
+      ws = a256(ws + 16LL * e.cols * k);
+      W[u].sig_off.push_back(ws);
+      ws = a256(ws + 8LL * k);
+      scatter_bound += (e.r1 - e.r0);
+      gemm_tasks_bound += (e.l1 - e.l0);
+      lam_bound += 1;
+      for (int i = e.l0; i < e.l1; ++i) {
+        const int Dl = reqs[u].h->bonds[reqs[u].site].dim[i];
+        gemm_tiles_bound += (int64_t)((Dl + kTile - 1) / kTile) * ((k + kTile - 1) / kTile);
+      }
+    }
+  std::vector<int64_t> jac_work, jac_norm, jac_ord;
+  int svd_smem = 0;
+  for (int u = 0; u < nreq; ++u)
+    for (auto& e : W[u].plan.sectors) {
+      if (svd_smem_need(e.rows, e.cols) > kSvdSmemMax) {
+        jac_work.push_back(ws); ws = a256(ws + 16LL * e.rows * e.cols);
+        jac_norm.push_back(ws); ws = a256(ws + 8LL * e.rows);
+        jac_ord.push_back(ws); ws = a256(ws + 4LL * e.rows);
+      } else {
+        jac_work.push_back(-1); jac_norm.push_back(-1); jac_ord.push_back(-1);
+        svd_smem = std::max<int>(svd_smem, (int)svd_smem_need(e.rows, e.cols));
+      }
+    }
+  const int64_t glen = gate_len(owner->d);
+  for (int u = 0; u < nreq; ++u)
+    if (reqs[u].h->d != owner->d) return fail(owner, MPS_EINVAL, "batched handles must share d");
+  const int64_t kept_off = ws; ws = a256(ws + 4LL * n_sec_total);
+  const int64_t status_off = ws; ws = a256(ws + 4LL * n_sec_total);
+  const int64_t res_off = ws; ws = a256(ws + (int64_t)sizeof(SelectResult) * nreq);
+  const int64_t desc_off = ws;   // phase-1 descriptors start here; phase-2 reuses the same region
+
+  // count theta tasks to size descriptors
+  for (int u = 0; u < nreq; ++u) {
+    mps_s* h = reqs[u].h;
+    const int s = reqs[u].site, d = h->d;
+    const BondTable &Lb = h->bonds[s], &Mb = h->bonds[s + 1], &Rb = h->bonds[s + 2];
+    for (int li = 0; li < Lb.size(); ++li)
+      for (int ri = 0; ri < Rb.size(); ++ri) {
+        const int l = Lb.charge[li], r = Rb.charge[ri];
+        if (l - r < 0 || l - r > 2 * (d - 1)) continue;
+        bool any = false;
+        for (int mi = 0; mi < Mb.size(); ++mi) {
+          const int m = Mb.charge[mi];
+          if (l - m >= 0 && l - m <= d - 1 && m - r >= 0 && m - r <= d - 1) { any = true; break; }
+        }
+        if (!any) continue;
+        n_tasks++;
+        n_tiles += ((Lb.dim[li] + kTile - 1) / kTile) * ((Rb.dim[ri] + kTile - 1) / kTile);
+      }
+  }
+  const int64_t phase1_desc = a256((int64_t)sizeof(ThetaTask) * n_tasks) + a256(sizeof(TileRef) * (int64_t)n_tiles) +
+                              a256((int64_t)sizeof(SvdSector) * n_sec_total) +
+                              a256((int64_t)sizeof(SelectSector) * n_sec_total) +
+                              a256((int64_t)sizeof(SelectTask) * nreq) + a256(16LL * glen) * nreq;
+  const int64_t phase2_desc = a256((int64_t)sizeof(LambdaTask) * lam_bound) +
+                              a256((int64_t)sizeof(ScatterTask) * scatter_bound) +
+                              a256((int64_t)sizeof(GemmTask) * gemm_tasks_bound) +
+                              a256((int64_t)sizeof(TileRef) * gemm_tiles_bound);
+  const int64_t desc_bytes = std::max(phase1_desc, phase2_desc);
+  ws = desc_off + desc_bytes;
+
+  CUDA_OR_FAIL(owner, cudaEventSynchronize(owner->staged));   // pin_in free again
+  {
+    cudaError_t e = owner->work.reserve((size_t)ws);
+    if (e != cudaSuccess) return fail(owner, MPS_ENOMEM, std::string("workspace: ") + cudaGetErrorString(e));
+    e = owner->pin_in.reserve((size_t)std::max<int64_t>(desc_bytes, 1) + 4096);
+    if (e != cudaSuccess) return fail(owner, MPS_ENOMEM, "pinned staging");
+    e = owner->pin_out.reserve((size_t)(res_off - kept_off) + 4096);
+    if (e != cudaSuccess) return fail(owner, MPS_ENOMEM, "pinned staging");
+  }
+  char* base = (char*)owner->work.p;
+  auto dptr = [&](int64_t off) { return base + off; };
+  // gates go first into the staging area; tasks point at their device copies
+  Stager sg{(char*)owner->pin_in.p};
+  for (int u = 0; u < nreq; ++u) W[u].gate_off = desc_off + sg.put(reqs[u].gate, 2 * glen);
+
+  // ---- build phase-1 descriptors ------------------------------------------------------
+  std::vector<ThetaTask> tasks; tasks.reserve(n_tasks);
+  std::vector<TileRef> tiles; tiles.reserve(n_tiles);
+  std::vector<SvdSector> svd; svd.reserve(n_sec_total);
+  std::vector<SelectSector> selsec; selsec.reserve(n_sec_total);
+  std::vector<SelectTask> seltask; seltask.reserve(nreq);
+  int sec_global = 0;
+  for (int u = 0; u < nreq; ++u) {
+    mps_s* h = reqs[u].h;
+    const int s = reqs[u].site, d = h->d;
+    const BondTable &Lb = h->bonds[s], &Mb = h->bonds[s + 1], &Rb = h->bonds[s + 2];
+    const SiteTable &SL = h->sites[s], &SR = h->sites[s + 1];
+    const double2* slotL = h->slot_ptr(s, h->cur[s]);
+    const double2* slotR = h->slot_ptr(s + 1, h->cur[s + 1]);
+    const UpdatePlan& P = W[u].plan;
+    // sector index by charge
+    auto sector_of = [&](int c) -> int {
+      int lo = 0, hi = (int)P.sectors.size() - 1;
+      while (lo <= hi) {
+        int mid = (lo + hi) / 2;
+        if (P.sectors[mid].c == c) return mid;
+        if (P.sectors[mid].c < c) lo = mid + 1; else hi = mid - 1;
+      }
+      return -1;
+    };
+    for (int li = 0; li < Lb.size(); ++li)
+      for (int ri = 0; ri < Rb.size(); ++ri) {
+        const int l = Lb.charge[li], r = Rb.charge[ri];
+        const int n = l - r;
+        if (n < 0 || n > 2 * (d - 1)) continue;
+        ThetaTask T;
+        std::memset(&T, 0, sizeof(T));
+        const int base_n = std::max(0, n - d + 1);
+        T.nm = 0;
+        for (int mi = 0; mi < Mb.size(); ++mi) {
+          const int m = Mb.charge[mi];
+          if (l - m < 0 || l - m > d - 1 || m - r < 0 || m - r > d - 1) continue;
+          const int bl = SL.find(l, m), br = SR.find(m, r);
+          if (bl < 0 || br < 0) return fail(owner, MPS_EINVAL, "internal: missing block");
+          T.A[T.nm] = slotL + SL.blocks[bl].off;
+          T.B[T.nm] = slotR + SR.blocks[br].off;
+          T.Dm[T.nm] = Mb.dim[mi];
+          T.gi[T.nm] = (l - m) - base_n;
+          T.nm++;
+        }
+        if (T.nm == 0) continue;
+        T.nc = 0;
+        for (int c = std::max(r, l - d + 1); c <= std::min(l, r + d - 1); ++c) {
+          const int si = sector_of(c);
+          if (si < 0) return fail(owner, MPS_EINVAL, "internal: missing sector");
+          const SectorPlanEntry& E = P.sectors[si];
+          const int roff = Lb.off[li] - Lb.off[E.l0];
+          const int coff = Rb.off[ri] - Rb.off[E.r0];
+          T.out[T.nc] = reinterpret_cast<double2*>(dptr(W[u].theta_off[si])) + (int64_t)roff * E.cols + coff;
+          T.ldo[T.nc] = E.cols;
+          T.go[T.nc] = (l - c) - base_n;
+          T.nc++;
+        }
+        T.gate = reinterpret_cast<const double2*>(dptr(W[u].gate_off)) + gate_block_off(n, d);
+        T.sn = gate_sn(n, d);
+        T.Dl = Lb.dim[li];
+        T.Dr = Rb.dim[ri];
+        const int task_id = (int)tasks.size();
+        tasks.push_back(T);
+        for (int ti = 0; ti < (T.Dl + kTile - 1) / kTile; ++ti)
+          for (int tj = 0; tj < (T.Dr + kTile - 1) / kTile; ++tj) tiles.push_back(TileRef{task_id, ti, tj});
+      }
+    W[u].sel_first = (int)selsec.size();
+    for (size_t si = 0; si < P.sectors.size(); ++si, ++sec_global) {
+      const SectorPlanEntry& E = P.sectors[si];
+      SvdSector S;
+      S.theta = reinterpret_cast<const double2*>(dptr(W[u].theta_off[si]));
+      S.rowscale = h->lambda_ptr(s) + Lb.off[E.l0];
+      S.m = E.rows;
+      S.n = E.cols;
+      S.smem = jac_work[sec_global] < 0;
+      S.work = S.smem ? nullptr : reinterpret_cast<double2*>(dptr(jac_work[sec_global]));
+      S.norms = S.smem ? nullptr : reinterpret_cast<double*>(dptr(jac_norm[sec_global]));
+      S.order = S.smem ? nullptr : reinterpret_cast<int*>(dptr(jac_ord[sec_global]));
+      S.sigma = reinterpret_cast<double*>(dptr(W[u].sig_off[si]));
+      S.Y = reinterpret_cast<double2*>(dptr(W[u].y_off[si]));
+      S.status = reinterpret_cast<int*>(dptr(status_off)) + sec_global;
+      svd.push_back(S);
+      selsec.push_back(SelectSector{S.sigma, std::min(E.rows, E.cols)});
+    }
+    seltask.push_back(SelectTask{W[u].sel_first, (int)selsec.size(), reqs[u].chi, reqs[u].cutoff});
+  }
+  // largest sectors first so that the longest CTAs start earliest
+  std::vector<SvdSector> svd_sorted = svd;
+  std::stable_sort(svd_sorted.begin(), svd_sorted.end(), [](const SvdSector& a, const SvdSector& b) {
+    return (double)a.m * a.m * a.n > (double)b.m * b.m * b.n;
+  });
+
+  // ---- upload (one copy of all descriptors and gates) ---------------------------------
+  const int64_t o_tasks = sg.put(tasks.data(), (int64_t)tasks.size());
+  const int64_t o_tiles = sg.put(tiles.data(), (int64_t)tiles.size());
+  const int64_t o_svd = sg.put(svd_sorted.data(), (int64_t)svd_sorted.size());
+  const int64_t o_selsec = sg.put(selsec.data(), (int64_t)selsec.size());
+  const int64_t o_seltask = sg.put(seltask.data(), (int64_t)seltask.size());
+  if (sg.size > desc_bytes) return fail(owner, MPS_EINVAL, "internal: descriptor bound exceeded");
+  CUDA_OR_FAIL(owner, cudaMemcpyAsync(dptr(desc_off), owner->pin_in.p, sg.size, cudaMemcpyHostToDevice, st));
+  CUDA_OR_FAIL(owner, cudaEventRecord(owner->staged, st));
+
+  // ---- algorithmic work of the three kernels (flops: complex multiply-add = 8) -------
+  double th_flops = 0, th_bytes = (double)(theta_bytes_end - theta_bytes_begin);   // Theta' written
+  for (const ThetaTask& T : tasks) {
+    for (int i = 0; i < T.nm; ++i) th_flops += 8.0 * T.Dl * T.Dm[i] * T.Dr;
+    th_flops += 8.0 * T.nm * T.nc * T.Dl * T.Dr;
+  }
+  for (int u = 0; u < nreq; ++u) {
+    const int s = reqs[u].site;
+    th_bytes += 16.0 * (double)(reqs[u].h->sites[s].nnz + reqs[u].h->sites[s + 1].nnz);
+  }
+  double svd_flops = 0, svd_bytes = 0, sel_bytes = 0;
+  for (const SvdSector& S : svd) {
+    const double a = std::max(S.m, S.n), b = std::min(S.m, S.n);
+    svd_flops += 4.0 * (6.0 * a * b * b + 20.0 * b * b * b);
+    svd_bytes += 16.0 * S.m * S.n + 16.0 * S.n * b + 8.0 * b + 8.0 * S.m;
+    sel_bytes += 8.0 * b;
+  }
+  // ---- K1, K2, K3 ---------------------------------------------------------------------
+  CUDA_OR_FAIL(owner, cudaMemsetAsync(dptr(theta_bytes_begin), 0, theta_bytes_end - theta_bytes_begin, st));
+  CUDA_OR_FAIL(owner, timed(owner, MPS_K_THETA, !tiles.empty(), th_flops, th_bytes, [&] {
+    return launch_theta(reinterpret_cast<ThetaTask*>(dptr(desc_off + o_tasks)),
+                        reinterpret_cast<TileRef*>(dptr(desc_off + o_tiles)), (int)tiles.size(), st);
+  }));
+  CUDA_OR_FAIL(owner, timed(owner, MPS_K_SVD, !svd_sorted.empty(), svd_flops, svd_bytes, [&] {
+    return launch_svd(reinterpret_cast<SvdSector*>(dptr(desc_off + o_svd)), (int)svd_sorted.size(), svd_smem,
+                      kJacobiMaxSweeps, st);
+  }));
+  CUDA_OR_FAIL(owner, timed(owner, MPS_K_SELECT, nreq > 0, 0.0, sel_bytes, [&] {
+    return launch_select(reinterpret_cast<SelectSector*>(dptr(desc_off + o_selsec)),
+                         reinterpret_cast<SelectTask*>(dptr(desc_off + o_seltask)), nreq,
+                         reinterpret_cast<int*>(dptr(kept_off)), reinterpret_cast<SelectResult*>(dptr(res_off)), st);
+  }));
+  const int64_t out_bytes = res_off + (int64_t)sizeof(SelectResult) * nreq - kept_off;
+  CUDA_OR_FAIL(owner, cudaMemcpyAsync(owner->pin_out.p, dptr(kept_off), out_bytes, cudaMemcpyDeviceToHost, st));
+  CUDA_OR_FAIL(owner, cudaStreamSynchronize(st));
+  resolve_pending(owner);
+  const int* kept = (const int*)owner->pin_out.p;
+  const int* sstat = (const int*)((char*)owner->pin_out.p + (status_off - kept_off));
+  const SelectResult* res = (const SelectResult*)((char*)owner->pin_out.p + (res_off - kept_off));
+
+  // ---- host: new bond tables and block layouts; phase-2 descriptors -------------------
+  std::vector<LambdaTask> lam;
+  std::vector<ScatterTask> sc;
+  std::vector<GemmTask> gm;
+  std::vector<TileRef> gt;
+  int64_t sc_elems = 0;
+  std::vector<char> apply(nreq, 0);
+  std::vector<BondTable> newmid(nreq);
+  std::vector<SiteTable> newL(nreq), newR(nreq);
+  sec_global = 0;
+  for (int u = 0; u < nreq; ++u) {
+    mps_s* h = reqs[u].h;
+    const int s = reqs[u].site;
+    const UpdatePlan& P = W[u].plan;
+    const SelectResult R = res[u];
+    int max_sweeps = 0;
+    bool noconv = false;
+    for (size_t si = 0; si < P.sectors.size(); ++si) {
+      const int sw = sstat[W[u].sel_first + si];
+      if (sw < 0) noconv = true; else max_sweeps = std::max(max_sweeps, sw);
+    }
+    if (R.status != 0) {
+      reqs[u].status = MPS_EINVAL;
+      h->err = "all singular values vanish (the gate annihilated the state)";
+      continue;
+    }
+    reqs[u].status = noconv ? MPS_ENOCONV : MPS_OK;
+    if (noconv) h->err = "Jacobi SVD hit its sweep limit; state updated with the last iterate";
+    reqs[u].trunc = R.trunc_err;
+    const BondTable &Lb = h->bonds[s], &Rb = h->bonds[s + 2];
+    BondTable& M = newmid[u];
+    for (size_t si = 0; si < P.sectors.size(); ++si) {
+      const int k = kept[W[u].sel_first + si];
+      if (k > 0) { M.charge.push_back(P.sectors[si].c); M.dim.push_back(k); }
+    }
+    M.rebuild_offsets();
+    if (M.size() == 0) {
+      reqs[u].status = MPS_EINVAL;
+      h->err = "the cutoff discards every singular value";
+      continue;
+    }
+    if (M.total() > h->bond_cap[s + 1]) {
+      reqs[u].status = MPS_ENOMEM;
+      h->err = "new bond exceeds its capacity";
+      continue;
+    }
+    layout_site(Lb, M, h->d, newL[u]);
+    layout_site(M, Rb, h->d, newR[u]);
+    if (newL[u].nnz > h->site_cap[s] || newR[u].nnz > h->site_cap[s + 1]) {
+      reqs[u].status = MPS_ENOMEM;
+      h->err = "new site tensor exceeds its capacity";
+      continue;
+    }
+    apply[u] = 1;
+    const double scale = 1.0 / R.norm_kept;
+    double2* dstL = h->slot_ptr(s, h->cur[s] ^ 1);
+    double2* dstR = h->slot_ptr(s + 1, h->cur[s + 1] ^ 1);
+    int mi = 0;
+    for (size_t si = 0; si < P.sectors.size(); ++si) {
+      const int k = kept[W[u].sel_first + si];
+      if (k == 0) continue;
+      const SectorPlanEntry& E = P.sectors[si];
+      const double* sig = reinterpret_cast<const double*>(dptr(W[u].sig_off[si]));
+      const double2* Y = reinterpret_cast<const double2*>(dptr(W[u].y_off[si]));
+      const double2* th = reinterpret_cast<const double2*>(dptr(W[u].theta_off[si]));
+      lam.push_back(LambdaTask{sig, h->lambda_ptr(s + 1) + M.off[mi], k, scale});
+      for (int ri = E.r0; ri < E.r1; ++ri) {
+        const int b = newR[u].find(E.c, Rb.charge[ri]);
+        ScatterTask T;
+        T.Y = Y;
+        T.out = dstR + newR[u].blocks[b].off;
+        T.n = E.cols;
+        T.coff = Rb.off[ri] - Rb.off[E.r0];
+        T.k = k;
+        T.Dr = Rb.dim[ri];
+        T.first = sc_elems;
+        sc_elems += (int64_t)k * T.Dr;
+        sc.push_back(T);
+      }
+      for (int li = E.l0; li < E.l1; ++li) {
+        const int b = newL[u].find(Lb.charge[li], E.c);
+        GemmTask G;
+        G.A = th + (int64_t)(Lb.off[li] - Lb.off[E.l0]) * E.cols;
+        G.sar = E.cols; G.sac = 1;
+        G.B = Y; G.sbr = 1; G.sbc = E.cols;
+        G.C = dstL + newL[u].blocks[b].off;
+        G.ldc = k;
+        G.M = Lb.dim[li]; G.N = k; G.K = E.cols;
+        G.alpha = scale;
+        const int tid = (int)gm.size();
+        gm.push_back(G);
+        for (int ti = 0; ti < (G.M + kTile - 1) / kTile; ++ti)
+          for (int tj = 0; tj < (G.N + kTile - 1) / kTile; ++tj) gt.push_back(TileRef{tid, ti, tj});
+      }
+      ++mi;
+    }
+    Stats& S = h->stats;
+    S.n_sectors = (int)P.sectors.size();
+    S.n_triples = (int)P.triple_l.size();
+    S.max_sweeps = max_sweeps;
+    S.tie_band = R.band;
+    S.norm_all = R.norm_all;
+    S.norm_kept = R.norm_kept;
+  }
+  if (!lam.empty()) {
+    // phase-1 kernels are complete (stream synchronised), so the descriptor region is free
+    Stager s2{(char*)owner->pin_in.p};
+    const int64_t o_lam = s2.put(lam.data(), (int64_t)lam.size());
+    const int64_t o_sc = s2.put(sc.data(), (int64_t)sc.size());
+    const int64_t o_gm = s2.put(gm.data(), (int64_t)gm.size());
+    const int64_t o_gt = s2.put(gt.data(), (int64_t)gt.size());
+    if (s2.size > desc_bytes) return fail(owner, MPS_EINVAL, "internal: descriptor bound exceeded");
+    CUDA_OR_FAIL(owner, cudaMemcpyAsync(dptr(desc_off), owner->pin_in.p, s2.size, cudaMemcpyHostToDevice, st));
+    CUDA_OR_FAIL(owner, cudaEventRecord(owner->staged, st));
+    double lam_bytes = 0, gm_flops = 0, gm_bytes = 0;
+    for (const LambdaTask& T : lam) lam_bytes += 16.0 * T.k;
+    for (const GemmTask& T : gm) {
+      gm_flops += 8.0 * T.M * T.N * T.K;
+      gm_bytes += 16.0 * ((double)T.M * T.K + (double)T.K * T.N + (double)T.M * T.N);
+    }
+    CUDA_OR_FAIL(owner, timed(owner, MPS_K_LAMBDA, true, 0.0, lam_bytes, [&] {
+      return launch_lambda(reinterpret_cast<LambdaTask*>(dptr(desc_off + o_lam)), (int)lam.size(), st);
+    }));
+    CUDA_OR_FAIL(owner, timed(owner, MPS_K_SCATTER, sc_elems > 0, 0.0, 32.0 * (double)sc_elems, [&] {
+      return launch_scatter(reinterpret_cast<ScatterTask*>(dptr(desc_off + o_sc)), (int)sc.size(), sc_elems, st);
+    }));
+    CUDA_OR_FAIL(owner, timed(owner, MPS_K_GEMM, !gt.empty(), gm_flops, gm_bytes, [&] {
+      return launch_gemm(reinterpret_cast<GemmTask*>(dptr(desc_off + o_gm)),
+                         reinterpret_cast<TileRef*>(dptr(desc_off + o_gt)), (int)gt.size(), st);
+    }));
+  }
+  for (int u = 0; u < nreq; ++u) {
+    if (!apply[u]) continue;
+    mps_s* h = reqs[u].h;
+    const int s = reqs[u].site;
+    h->bonds[s + 1] = newmid[u];
+    h->sites[s] = newL[u];
+    h->sites[s + 1] = newR[u];
+    h->cur[s] ^= 1;
+    h->cur[s + 1] ^= 1;
+  }
+  return MPS_OK;
+}
+
+int check_handle(mps_s* h) { return h ? MPS_OK : MPS_EINVAL; }
+
+int check_site_ready(mps_s* h, int s) {
+  if (h->dirty[s]) return fail(h, MPS_EINVAL, "site " + std::to_string(s) + " needs mps_set_site");
+  return MPS_OK;
+}
+
+int check_gate_args(mps_s* h, int site, const double* gate, int chi, double cutoff) {
+  if (site < 0 || site >= h->L - 1) return fail(h, MPS_EINVAL, "site out of range");
+  if (!gate) return fail(h, MPS_EINVAL, "gate_blocks is NULL");
+  if (chi < 1 || chi > h->chi_max) return fail(h, MPS_EINVAL, "chi outside [1, chi_max]");
+  if (!(cutoff >= 0.0) || !std::isfinite(cutoff)) return fail(h, MPS_EINVAL, "cutoff must be finite and >= 0");
+  int rc = check_site_ready(h, site);
+  if (rc) return rc;
+  return check_site_ready(h, site + 1);
+}
+
+}  // namespace
+
+// ======================================================================================
+extern "C" {
+
+int mps_create(mps_t* out, int L, int d, const int32_t* site_charges, int precision, int chi_max,
+               void* cuda_stream) {
+  if (!out) return MPS_EINVAL;
+  *out = nullptr;
+  if (L < 2 || d < 2 || d > MPS_MAX_D || chi_max < 1 || !site_charges) return MPS_EINVAL;
+  if (precision != MPS_FP64) return MPS_EINVAL;   // reduced-precision sector GEMMs are not built
+  for (int s = 0; s < L; ++s)
+    if (site_charges[s] < 0 || site_charges[s] > d - 1) return MPS_ECHARGE;
+  mps_s* h = new mps_s();
+  h->L = L; h->d = d; h->chi_max = chi_max; h->precision = precision;
+  h->stream = (cudaStream_t)cuda_stream;
+  std::vector<int> c(L + 1, 0);
+  for (int b = L - 1; b >= 0; --b) c[b] = c[b + 1] + site_charges[b];
+  h->N = c[0];
+  const int N = h->N;
+  auto Wc = config_counts(L, d, N);
+  h->bonds.resize(L + 1);
+  h->bond_cap.resize(L + 1);
+  h->lam_base.resize(L + 1);
+  int64_t lam_total = 0;
+  for (int b = 0; b <= L; ++b) {
+    BondTable& t = h->bonds[b];
+    t.charge = {c[b]};
+    t.dim = {1};
+    t.rebuild_offsets();
+    double hb = 0.0;
+    const int lo = std::max(0, N - (d - 1) * b), hi = std::min(N, (d - 1) * (L - b));
+    for (int q = lo; q <= hi; ++q) hb += std::min(Wc[b][N - q], Wc[L - b][q]);
+    h->bond_cap[b] = (int64_t)std::max(1.0, std::min((double)chi_max, hb));
+    h->lam_base[b] = lam_total;
+    lam_total += (h->bond_cap[b] + 31) / 32 * 32;
+  }
+  h->sites.resize(L);
+  h->cur.assign(L, 0);
+  h->dirty.assign(L, 0);
+  h->site_cap.resize(L);
+  h->site_base.resize(L);
+  int64_t site_total = 0;
+  for (int s = 0; s < L; ++s) {
+    layout_site(h->bonds[s], h->bonds[s + 1], d, h->sites[s]);
+    h->site_cap[s] = std::max<int64_t>(1, h->bond_cap[s] * h->bond_cap[s + 1]);
+    h->site_base[s] = site_total;
+    site_total += 2 * ((h->site_cap[s] + 15) / 16 * 16);
+  }
+  cudaError_t e = cudaMalloc(&h->d_lambda, sizeof(double) * lam_total);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_sites, sizeof(double2) * site_total);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->staged, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    if (h->d_lambda) cudaFree(h->d_lambda);
+    if (h->d_sites) cudaFree(h->d_sites);
+    delete h;
+    return MPS_ENOMEM;
+  }
+  std::vector<double> lam(lam_total, 0.0);
+  for (int b = 0; b <= L; ++b) lam[h->lam_base[b]] = 1.0;
+  e = cudaMemcpyAsync(h->d_lambda, lam.data(), sizeof(double) * lam_total, cudaMemcpyHostToDevice, h->stream);
+  const double2 one = make_double2(1.0, 0.0);
+  for (int s = 0; s < L && e == cudaSuccess; ++s)
+    e = cudaMemcpyAsync(h->slot_ptr(s, 0), &one, sizeof(double2), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    mps_destroy(h);
+    return MPS_ECUDA;
+  }
+  *out = h;
+  return MPS_OK;
+}
+
+int mps_destroy(mps_t h) {
+  if (!h) return MPS_EINVAL;
+  cudaStreamSynchronize(h->stream);
+  if (h->d_lambda) cudaFree(h->d_lambda);
+  if (h->d_sites) cudaFree(h->d_sites);
+  if (h->staged) cudaEventDestroy(h->staged);
+  for (auto& p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  h->work.release();
+  h->pin_in.release();
+  h->pin_out.release();
+  delete h;
+  return MPS_OK;
+}
+
+const char* mps_last_error(mps_t h) { return h ? h->err.c_str() : "null handle"; }
+
+int mps_info(mps_t h, int* L, int* d, int* N, int* chi_max, int* precision) {
+  if (!h) return MPS_EINVAL;
+  if (L) *L = h->L;
+  if (d) *d = h->d;
+  if (N) *N = h->N;
+  if (chi_max) *chi_max = h->chi_max;
+  if (precision) *precision = h->precision;
+  return MPS_OK;
+}
+
+int mps_apply_gate2(mps_t h, int site, const double* gate_blocks, int chi, double cutoff,
+                    double* trunc_err_out) {
+  if (check_handle(h)) return MPS_EINVAL;
+  int rc = check_gate_args(h, site, gate_blocks, chi, cutoff);
+  if (rc) return rc;
+  std::vector<Req> r(1);
+  r[0].h = h; r[0].site = site; r[0].gate = gate_blocks; r[0].chi = chi; r[0].cutoff = cutoff;
+  rc = run_batch(r, h);
+  if (rc) return rc;
+  if (trunc_err_out) *trunc_err_out = r[0].trunc;
+  return r[0].status;
+}
+
+int mps_apply_layer(mps_t h, int n, const int* sites, const double* const* gate_blocks, int chi,
+                    double cutoff, double* trunc_err_out) {
+  if (check_handle(h)) return MPS_EINVAL;
+  if (n < 0 || (n > 0 && (!sites || !gate_blocks))) return fail(h, MPS_EINVAL, "bad layer arguments");
+  if (n == 0) return MPS_OK;
+  std::vector<int> sorted(sites, sites + n);
+  std::sort(sorted.begin(), sorted.end());
+  for (int k = 1; k < n; ++k)
+    if (sorted[k] - sorted[k - 1] < 2) return fail(h, MPS_EINVAL, "layer site pairs overlap");
+  std::vector<Req> r(n);
+  for (int k = 0; k < n; ++k) {
+    int rc = check_gate_args(h, sites[k], gate_blocks[k], chi, cutoff);
+    if (rc) return rc;
+    r[k].h = h; r[k].site = sites[k]; r[k].gate = gate_blocks[k]; r[k].chi = chi; r[k].cutoff = cutoff;
+  }
+  int rc = run_batch(r, h);
+  if (rc) return rc;
+  int first = MPS_OK;
+  for (int k = 0; k < n; ++k) {
+    if (trunc_err_out) trunc_err_out[k] = r[k].trunc;
+    if (first == MPS_OK && r[k].status != MPS_OK) first = r[k].status;
+  }
+  return first;
+}
+
+int mps_apply_gate2_batch(int n, mps_t* hs, const int* sites, const double* const* gates, const int* chis,
+                          const double* cutoffs, double* trunc_err_out, int* status_out) {
+  if (n < 0 || (n > 0 && (!hs || !sites || !gates || !chis || !cutoffs))) return MPS_EINVAL;
+  if (n == 0) return MPS_OK;
+  mps_s* owner = hs[0];
+  if (!owner) return MPS_EINVAL;
+  std::vector<Req> r(n);
+  std::vector<mps_s*> others;
+  for (int k = 0; k < n; ++k) {
+    mps_s* h = hs[k];
+    if (!h) return MPS_EINVAL;
+    int rc = check_gate_args(h, sites[k], gates[k], chis[k], cutoffs[k]);
+    if (rc) { if (status_out) status_out[k] = rc; return rc; }
+    for (int j = 0; j < k; ++j)
+      if (hs[j] == h && std::abs(sites[j] - sites[k]) < 2) return fail(owner, MPS_EINVAL, "overlapping pairs in batch");
+    r[k].h = h; r[k].site = sites[k]; r[k].gate = gates[k]; r[k].chi = chis[k]; r[k].cutoff = cutoffs[k];
+    if (h != owner && h->stream != owner->stream &&
+        std::find(others.begin(), others.end(), h) == others.end())
+      others.push_back(h);
+  }
+  // join the other handles' streams into the owner's stream, and back afterwards
+  cudaEvent_t ev;
+  CUDA_OR_FAIL(owner, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  for (mps_s* h : others) {
+    cudaEventRecord(ev, h->stream);
+    cudaStreamWaitEvent(owner->stream, ev, 0);
+  }
+  int rc = run_batch(r, owner);
+  cudaEventRecord(ev, owner->stream);
+  for (mps_s* h : others) cudaStreamWaitEvent(h->stream, ev, 0);
+  cudaEventDestroy(ev);
+  if (rc) return rc;
+  int first = MPS_OK;
+  for (int k = 0; k < n; ++k) {
+    if (trunc_err_out) trunc_err_out[k] = r[k].trunc;
+    if (status_out) status_out[k] = r[k].status;
+    if (first == MPS_OK && r[k].status != MPS_OK) first = r[k].status;
+  }
+  return first;
+}
+
+int mps_expect(mps_t h, int site, const double* diag_op, double* out) {
+  if (check_handle(h)) return MPS_EINVAL;
+  if (site < 0 || site >= h->L || !diag_op || !out) return fail(h, MPS_EINVAL, "bad expect arguments");
+  int rc = check_site_ready(h, site);
+  if (rc) return rc;
+  const SiteTable& S = h->sites[site];
+  const BondTable& Lb = h->bonds[site];
+  const double2* slot = h->slot_ptr(site, h->cur[site]);
+  std::vector<ExpectTask> t;
+  for (const SiteBlock& b : S.blocks)
+    t.push_back(ExpectTask{slot + b.off, h->lambda_ptr(site) + Lb.off[b.il], b.Dl, b.Dm, diag_op[b.l - b.m]});
+  const int nt = (int)t.size();
+  const int64_t bytes_t = a256(sizeof(ExpectTask) * (int64_t)nt);
+  CUDA_OR_FAIL(h, cudaEventSynchronize(h->staged));
+  if (h->work.reserve(bytes_t + 8 * (int64_t)nt + 512) != cudaSuccess) return fail(h, MPS_ENOMEM, "workspace");
+  if (h->pin_in.reserve(bytes_t + 512) != cudaSuccess || h->pin_out.reserve(8 * (size_t)nt + 512) != cudaSuccess)
+    return fail(h, MPS_ENOMEM, "pinned staging");
+  std::memcpy(h->pin_in.p, t.data(), sizeof(ExpectTask) * nt);
+  char* base = (char*)h->work.p;
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(base, h->pin_in.p, sizeof(ExpectTask) * nt, cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaEventRecord(h->staged, h->stream));
+  double ex_bytes = 0;
+  for (const ExpectTask& T : t) ex_bytes += 16.0 * T.Dl * T.Dm + 8.0 * T.Dl;
+  CUDA_OR_FAIL(h, timed(h, MPS_K_EXPECT, nt > 0, 0.0, ex_bytes,
+                        [&] { return launch_expect((ExpectTask*)base, nt, (double*)(base + bytes_t), h->stream); }));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->pin_out.p, base + bytes_t, 8 * (size_t)nt, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  double acc = 0.0;
+  for (int k = 0; k < nt; ++k) acc += ((double*)h->pin_out.p)[k];
+  *out = acc;
+  return MPS_OK;
+}
+
+int mps_amplitude_batch(mps_t h, int n, const int32_t* configs, double* out) {
+  if (check_handle(h)) return MPS_EINVAL;
+  if (n < 0 || (n > 0 && (!configs || !out))) return fail(h, MPS_EINVAL, "bad amplitude arguments");
+  if (n == 0) return MPS_OK;
+  for (int s = 0; s < h->L; ++s)
+    if (h->dirty[s]) return check_site_ready(h, s);
+  const int L = h->L;
+  std::vector<AmpStep> steps((size_t)n * L);
+  std::vector<int> c(L + 1);
+  int cap = 1;
+  for (int b = 0; b <= L; ++b) cap = std::max(cap, h->bonds[b].total());
+  for (int k = 0; k < n; ++k) {
+    const int32_t* cfg = configs + (size_t)k * L;
+    bool ok = true;
+    c[L] = 0;
+    for (int b = L - 1; b >= 0; --b) {
+      if (cfg[b] < 0 || cfg[b] > h->d - 1) ok = false;
+      c[b] = c[b + 1] + cfg[b];
+    }
+    if (c[0] != h->N) ok = false;
+    for (int s = 0; s < L; ++s) {
+      AmpStep a{nullptr, 0, 0};
+      if (ok) {
+        const int bi = h->sites[s].find(c[s], c[s + 1]);
+        if (bi >= 0) {
+          const SiteBlock& B = h->sites[s].blocks[bi];
+          a.blk = h->slot_ptr(s, h->cur[s]) + B.off;
+          a.Dl = B.Dl; a.Dm = B.Dm;
+        }
+      }
+      steps[(size_t)k * L + s] = a;
+    }
+  }
+  const int64_t bytes_s = a256(sizeof(AmpStep) * (int64_t)steps.size());
+  CUDA_OR_FAIL(h, cudaEventSynchronize(h->staged));
+  if (h->work.reserve(bytes_s + 16 * (int64_t)n + 512) != cudaSuccess) return fail(h, MPS_ENOMEM, "workspace");
+  if (h->pin_in.reserve(bytes_s + 512) != cudaSuccess || h->pin_out.reserve(16 * (size_t)n + 512) != cudaSuccess)
+    return fail(h, MPS_ENOMEM, "pinned staging");
+  std::memcpy(h->pin_in.p, steps.data(), sizeof(AmpStep) * steps.size());
+  char* base = (char*)h->work.p;
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(base, h->pin_in.p, sizeof(AmpStep) * steps.size(), cudaMemcpyHostToDevice,
+                                  h->stream));
+  CUDA_OR_FAIL(h, cudaEventRecord(h->staged, h->stream));
+  double amp_flops = 0;
+  for (const AmpStep& a : steps) amp_flops += 8.0 * a.Dl * a.Dm;
+  CUDA_OR_FAIL(h, timed(h, MPS_K_AMPLITUDE, n > 0, amp_flops, 16.0 * amp_flops / 8.0, [&] {
+    return launch_amplitude((AmpStep*)base, L, n, (double2*)(base + bytes_s), cap, h->stream);
+  }));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->pin_out.p, base + bytes_s, 16 * (size_t)n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  std::memcpy(out, h->pin_out.p, 16 * (size_t)n);
+  return MPS_OK;
+}
+
+int mps_amplitude(mps_t h, const int32_t* config, double out_complex[2]) {
+  return mps_amplitude_batch(h, 1, config, out_complex);
+}
+
+int mps_bond_spectrum(mps_t h, int bond, int32_t* charges, int32_t* dims, double* lambda, int cap, int* n_out) {
+  if (check_handle(h)) return MPS_EINVAL;
+  if (bond < 0 || bond > h->L || !n_out) return fail(h, MPS_EINVAL, "bad bond");
+  const BondTable& t = h->bonds[bond];
+  *n_out = t.size();
+  if (cap < t.size() || !charges || !dims || !lambda) return fail(h, MPS_EINVAL, "capacity too small");
+  for (int i = 0; i < t.size(); ++i) { charges[i] = t.charge[i]; dims[i] = t.dim[i]; }
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(lambda, h->lambda_ptr(bond), sizeof(double) * t.total(), cudaMemcpyDeviceToHost,
+                                  h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return MPS_OK;
+}
+
+int mps_get_site(mps_t h, int site, int32_t* lcharges, int32_t* mcharges, int cap_blocks, double* data,
+                 int64_t cap_values, int* n_blocks, int64_t* n_values) {
+  if (check_handle(h)) return MPS_EINVAL;
+  if (site < 0 || site >= h->L || !n_blocks || !n_values) return fail(h, MPS_EINVAL, "bad site");
+  const SiteTable& S = h->sites[site];
+  *n_blocks = (int)S.blocks.size();
+  *n_values = S.nnz;
+  if (cap_blocks < *n_blocks || cap_values < S.nnz || !lcharges || !mcharges || (!data && S.nnz))
+    return fail(h, MPS_EINVAL, "capacity too small");
+  for (size_t i = 0; i < S.blocks.size(); ++i) { lcharges[i] = S.blocks[i].l; mcharges[i] = S.blocks[i].m; }
+  if (S.nnz) {
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(data, h->slot_ptr(site, h->cur[site]), sizeof(double2) * S.nnz,
+                                    cudaMemcpyDeviceToHost, h->stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  }
+  return MPS_OK;
+}
+
+int mps_set_bond(mps_t h, int bond, int n_sectors, const int32_t* charges, const int32_t* dims,
+                 const double* lambda) {
+  if (check_handle(h)) return MPS_EINVAL;
+  if (bond < 1 || bond > h->L - 1) return fail(h, MPS_EINVAL, "only inner bonds 1..L-1 can be set");
+  if (n_sectors < 1 || !charges || !dims || !lambda) return fail(h, MPS_EINVAL, "bad bond table");
+  BondTable t;
+  t.charge.assign(charges, charges + n_sectors);
+  t.dim.assign(dims, dims + n_sectors);
+  const int d = h->d, L = h->L, N = h->N;
+  const int lo = std::max(0, N - (d - 1) * bond), hi = std::min(N, (d - 1) * (L - bond));
+  for (int i = 0; i < n_sectors; ++i) {
+    if (t.dim[i] < 1) return fail(h, MPS_EINVAL, "sector dimension < 1");
+    if (i && t.charge[i] <= t.charge[i - 1]) return fail(h, MPS_EINVAL, "charges not ascending");
+    if (t.charge[i] < lo || t.charge[i] > hi) return fail(h, MPS_ECHARGE, "charge outside the bond's range");
+  }
+  t.rebuild_offsets();
+  if (t.total() > h->bond_cap[bond]) return fail(h, MPS_ENOMEM, "bond dimension exceeds capacity");
+  CUDA_OR_FAIL(h, cudaEventSynchronize(h->staged));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpy(h->lambda_ptr(bond), lambda, sizeof(double) * t.total(), cudaMemcpyHostToDevice));
+  h->bonds[bond] = t;
+  h->dirty[bond - 1] = 1;
+  h->dirty[bond] = 1;
+  return MPS_OK;
+}
+
+int mps_set_site(mps_t h, int site, int n_blocks, const int32_t* lcharges, const int32_t* mcharges,
+                 const double* data) {
+  if (check_handle(h)) return MPS_EINVAL;
+  if (site < 0 || site >= h->L) return fail(h, MPS_EINVAL, "bad site");
+  SiteTable t;
+  layout_site(h->bonds[site], h->bonds[site + 1], h->d, t);
+  if (n_blocks != (int)t.blocks.size() || (n_blocks && (!lcharges || !mcharges)))
+    return fail(h, MPS_ECHARGE, "block list does not match the allowed (l, m) pairs");
+  for (int i = 0; i < n_blocks; ++i)
+    if (lcharges[i] != t.blocks[i].l || mcharges[i] != t.blocks[i].m)
+      return fail(h, MPS_ECHARGE, "block list does not match the allowed (l, m) pairs");
+  if (t.nnz > h->site_cap[site]) return fail(h, MPS_ENOMEM, "site exceeds capacity");
+  if (t.nnz && !data) return fail(h, MPS_EINVAL, "data is NULL");
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  if (t.nnz)
+    CUDA_OR_FAIL(h, cudaMemcpy(h->slot_ptr(site, h->cur[site]), data, sizeof(double2) * t.nnz,
+                               cudaMemcpyHostToDevice));
+  h->sites[site] = t;
+  h->dirty[site] = 0;
+  return MPS_OK;
+}
+
+int mps_set_profiling(mps_t h, int on) {
+  if (!h) return MPS_EINVAL;
+  h->profiling = on != 0;
+  return MPS_OK;
+}
+
+int mps_kernel_stats(mps_t h, int kind, int64_t* launches, double* ms, double* flops, double* bytes) {
+  if (!h || kind < 0 || kind >= MPS_K_COUNT) return MPS_EINVAL;
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  resolve_pending(h);
+  const KStat& k = h->kstat[kind];
+  if (launches) *launches = k.launches;
+  if (ms) *ms = k.ms;
+  if (flops) *flops = k.flops;
+  if (bytes) *bytes = k.bytes;
+  return MPS_OK;
+}
+
+int mps_reset_kernel_stats(mps_t h) {
+  if (!h) return MPS_EINVAL;
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  resolve_pending(h);
+  for (auto& k : h->kstat) k = KStat();
+  return MPS_OK;
+}
+
+int64_t mps_launch_count(void) { return g_launches.load(); }
+
+int mps_last_update_stats(mps_t h, int* n_sectors, int* n_triples, int* max_sweeps, int* tie_band,
+                          double* norm_all, double* norm_kept) {
+  if (!h) return MPS_EINVAL;
+  if (n_sectors) *n_sectors = h->stats.n_sectors;
+  if (n_triples) *n_triples = h->stats.n_triples;
+  if (max_sweeps) *max_sweeps = h->stats.max_sweeps;
+  if (tie_band) *tie_band = h->stats.tie_band;
+  if (norm_all) *norm_all = h->stats.norm_all;
+  if (norm_kept) *norm_kept = h->stats.norm_kept;
+  return MPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+// Internal declarations of the GB300 U(1) MPS library: handle state, host mirrors
+// of the charge tables, and the descriptors the host planner hands to kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "mps_gb300.h"
+
+namespace mps {
+
+// ---------------------------------------------------------------------------
+// Host mirror of the charge structure (Sec. II: right-charge labels per bond,
+// blocks (l, m) with 0 <= l - m <= d - 1 per site).
+// ---------------------------------------------------------------------------
+struct BondTable {
+  std::vector<int> charge;    // ascending
+  std::vector<int> dim;       // sector dimensions
+  std::vector<int> off;       // prefix sums of dim (size n+1): lambda offset of each sector
+  int total() const { return off.empty() ? 0 : off.back(); }
+  int size() const { return (int)charge.size(); }
+  int find(int c) const;      // sector index of charge c, or -1
+  void rebuild_offsets();
+};
+
+struct SiteBlock {
+  int l, m;        // bond-s charge, bond-(s+1) charge
+  int il, im;      // sector indices in the two bond tables
+  int Dl, Dm;
+  int64_t off;     // offset of the block in the site slot, complex numbers
+};
+
+struct SiteTable {
+  std::vector<SiteBlock> blocks;   // (l ascending, m ascending)
+  int64_t nnz = 0;
+  int find(int l, int m) const;    // block index or -1
+};
+
+// Enumerate the allowed blocks of a site between two bond tables, in (l, m) order.
+void layout_site(const BondTable& left, const BondTable& right, int d, SiteTable& out);
+
+// ---------------------------------------------------------------------------
+// Sector plan of one two-site update (the integer planner, K0).
+// ---------------------------------------------------------------------------
+struct SectorPlanEntry {
+  int c;             // candidate middle charge
+  int l0, l1;        // row sectors: indices [l0, l1) of the left bond table
+  int r0, r1;        // column sectors: indices [r0, r1) of the right bond table
+  int rows, cols;    // Theta(c) size
+};
+struct UpdatePlan {
+  std::vector<SectorPlanEntry> sectors;                 // c ascending
+  std::vector<int> triple_l, triple_m, triple_r;        // sector indices, lexicographic
+};
+void plan_update(const BondTable& left, const BondTable& mid, const BondTable& right, int d,
+                 UpdatePlan& plan);
+
+// ---------------------------------------------------------------------------
+// Kernel descriptors (plain structs, copied to device memory in one upload).
+// ---------------------------------------------------------------------------
+struct ThetaTask {            // one (l, r) block pair of one update: sum_m G * B[l,m] B[m,r]
+  const double2* A[MPS_MAX_D];   // B^[s][l, m] blocks, row-major Dl x Dm
+  const double2* B[MPS_MAX_D];   // B^[s+1][m, r] blocks, row-major Dm x Dr
+  int Dm[MPS_MAX_D];
+  int gi[MPS_MAX_D];             // gate column (input basis index) per m
+  double2* out[MPS_MAX_D];       // Theta'(c) at the (l, r) sub-block, per output charge c
+  int ldo[MPS_MAX_D];            // row stride of Theta'(c)
+  int go[MPS_MAX_D];             // gate row (output basis index) per c
+  const double2* gate;           // gate block n = l - r, sn x sn row-major
+  int sn;
+  int Dl, Dr, nm, nc;
+};
+struct TileRef { int task; int ti; int tj; };
+
+struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
+  const double2* theta;       // row-major m x n
+  const double* rowscale;     // m values (lambda of the left bond), or nullptr
+  double2* work;              // n x m column-major scratch (the Jacobi matrix A = M^dag)
+  double* norms;              // m doubles scratch
+  int* order;                 // m ints scratch
+  double* sigma;              // out: min(m, n) values, descending
+  double2* Y;                 // out: n x min(m, n) column-major right singular vectors
+  int* status;                // out: sweeps used, or -1 when not converged
+  int m, n;
+  int smem;                   // 1 when the CTA stages A in shared memory
+};
+
+struct SelectSector {         // one sector's spectrum as seen by the truncation
+  const double* sigma;        // descending
+  int k;                      // number of values (min(m, n))
+};
+struct SelectTask {           // one update: its sectors are [s0, s1) of the sector array
+  int s0, s1;
+  int chi;
+  double cutoff;
+};
+struct SelectResult {         // per update
+  double norm_all, norm_kept, trunc_err;
+  int band, n_candidates, status, pad;
+};
+
+struct GemmTask {             // C = alpha * A * B, A(i,k) = A[i*sar + k*sac], B(k,j) = B[k*sbr + j*sbc]
+  const double2* A; const double2* B; double2* C;
+  int M, N, K;
+  int sar, sac, sbr, sbc, ldc;
+  double alpha;
+};
+struct ScatterTask {          // B^[s+1][c, r] block: out[j*Dr + b] = conj(Y[(coff + b) + j*n])
+  const double2* Y; double2* out;
+  int n, coff, k, Dr;
+  int64_t first;              // first flat element index of this task
+};
+struct LambdaTask {           // lambda[j] = sigma[j] * scale, j < k
+  const double* sigma; double* lambda; int k; double scale;
+};
+
+// ---------------------------------------------------------------------------
+// Device memory helpers.
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr; size_t bytes = 0;
+  cudaError_t reserve(size_t want);
+  void release();
+};
+struct PinnedBuf {
+  void* p = nullptr; size_t bytes = 0;
+  cudaError_t reserve(size_t want);
+  void release();
+};
+
+struct Stats {
+  int n_sectors = 0, n_triples = 0, max_sweeps = 0, tie_band = 0;
+  double norm_all = 0, norm_kept = 0;
+};
+
+struct KStat { int64_t launches = 0; double ms = 0, flops = 0, bytes = 0; };
+struct PendingTiming { int kind; cudaEvent_t a, b; };
+
+// Kernel launches made by the library in this process (all handles).
+void count_launch();
+
+}  // namespace mps
+
+struct mps_s {
+  int L = 0, d = 0, N = 0, chi_max = 0, precision = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<mps::BondTable> bonds;      // L + 1
+  std::vector<mps::SiteTable> sites;      // L
+  std::vector<int> cur;                   // current slot (0/1) per site
+  std::vector<char> dirty;                // site needs mps_set_site
+  std::vector<int64_t> bond_cap;          // lambda capacity per bond
+  std::vector<int64_t> lam_base;          // offset of each bond's lambda slot (doubles)
+  std::vector<int64_t> site_cap;          // complex capacity of one site slot
+  std::vector<int64_t> site_base;         // offset of slot 0 of each site (complex); slot 1 follows
+  double* d_lambda = nullptr;
+  double2* d_sites = nullptr;
+  mps::DevBuf work;                       // per-update workspace
+  mps::PinnedBuf pin_in, pin_out;         // staging of descriptors and results
+  cudaEvent_t staged = nullptr;           // last upload out of pin_in has completed
+  std::string err;
+  mps::Stats stats;
+  bool profiling = false;
+  mps::KStat kstat[MPS_K_COUNT];
+  std::vector<mps::PendingTiming> pending;   // event pairs not yet read back
+  std::vector<cudaEvent_t> event_pool;
+
+  double2* slot_ptr(int s, int slot) { return d_sites + site_base[s] + (slot ? site_cap[s] : 0); }
+  double* lambda_ptr(int b) { return d_lambda + lam_base[b]; }
+};
+
+namespace mps {
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_theta(const ThetaTask* d_tasks, const TileRef* d_tiles, int n_tiles, cudaStream_t st);
+cudaError_t launch_svd(const SvdSector* d_secs, int n_secs, int smem_bytes, int max_sweeps, cudaStream_t st);
+cudaError_t launch_select(const SelectSector* d_secs, const SelectTask* d_tasks, int n_tasks,
+                          int* d_kept, SelectResult* d_res, cudaStream_t st);
+cudaError_t launch_gemm(const GemmTask* d_tasks, const TileRef* d_tiles, int n_tiles, cudaStream_t st);
+cudaError_t launch_scatter(const ScatterTask* d_tasks, int n_tasks, int64_t n_elems, cudaStream_t st);
+cudaError_t launch_lambda(const LambdaTask* d_tasks, int n_tasks, cudaStream_t st);
+
+struct ExpectTask { const double2* blk; const double* lam; int Dl, Dm; double w; };
+cudaError_t launch_expect(const ExpectTask* d_tasks, int n_tasks, double* d_partial, cudaStream_t st);
+struct AmpStep { const double2* blk; int Dl, Dm; };
+cudaError_t launch_amplitude(const AmpStep* d_steps, int L, int n_cfg, double2* d_out, int chi_max,
+                             cudaStream_t st);
+
+// Shared-memory budget of the Jacobi kernel and its staging rule.
+constexpr int kSvdThreads = 256;
+constexpr int kSvdSmemMax = 200 * 1024;
+inline int64_t svd_smem_need(int m, int n) { return 16LL * m * n + 8LL * m + 4LL * m + 64; }
+constexpr int kJacobiMaxSweeps = 40;
+constexpr double kTieRel = 1e-11;
+
+// GEMM tiling shared by the Theta build and the reassembly GEMM.
+constexpr int kTile = 64;
+
+}  // namespace mps

@@ -1,0 +1,136 @@
+// Integer sector planner of the two-site update (host side, bit-exact).
+//
+// arXiv:2303.11409, Sec. II: the Kronecker deltas of the U(1) amplitude formula
+// allow a block (l, m) of a site only when c^[k-1] - c^[k] = i_k lies in
+// [0, d-1]; a two-site update therefore couples the charges (l, m, r) of three
+// consecutive bonds with 0 <= l-m <= d-1 and 0 <= m-r <= d-1, and its result
+// splits by the new middle charge c into blocks Theta(c) whose rows are the left
+// charges c <= l <= c+d-1 and whose columns are the right charges
+// c-d+1 <= r <= c.  Because bond tables are sorted by charge, the rows and the
+// columns of every Theta(c) are contiguous ranges of the left and right tables
+// (the "charge-sorted memory alignment" of Sec. II).
+#include <algorithm>
+#include <cstring>
+
+#include "mps_internal.h"
+
+namespace mps {
+
+int BondTable::find(int c) const {
+  auto it = std::lower_bound(charge.begin(), charge.end(), c);
+  if (it == charge.end() || *it != c) return -1;
+  return (int)(it - charge.begin());
+}
+
+void BondTable::rebuild_offsets() {
+  off.assign(charge.size() + 1, 0);
+  for (size_t i = 0; i < charge.size(); ++i) off[i + 1] = off[i] + dim[i];
+}
+
+int SiteTable::find(int l, int m) const {
+  // blocks are sorted by (l, m)
+  int lo = 0, hi = (int)blocks.size();
+  while (lo < hi) {
+    int mid = (lo + hi) / 2;
+    const SiteBlock& b = blocks[mid];
+    if (b.l < l || (b.l == l && b.m < m)) lo = mid + 1; else hi = mid;
+  }
+  if (lo < (int)blocks.size() && blocks[lo].l == l && blocks[lo].m == m) return lo;
+  return -1;
+}
+
+void layout_site(const BondTable& left, const BondTable& right, int d, SiteTable& out) {
+  out.blocks.clear();
+  int64_t off = 0;
+  for (int i = 0; i < left.size(); ++i) {
+    for (int j = 0; j < right.size(); ++j) {
+      int diff = left.charge[i] - right.charge[j];
+      if (diff < 0 || diff > d - 1) continue;
+      SiteBlock b;
+      b.l = left.charge[i]; b.m = right.charge[j];
+      b.il = i; b.im = j;
+      b.Dl = left.dim[i]; b.Dm = right.dim[j];
+      b.off = off;
+      off += (int64_t)b.Dl * b.Dm;
+      out.blocks.push_back(b);
+    }
+  }
+  out.nnz = off;
+}
+
+void plan_update(const BondTable& left, const BondTable& mid, const BondTable& right, int d,
+                 UpdatePlan& plan) {
+  plan.sectors.clear();
+  plan.triple_l.clear(); plan.triple_m.clear(); plan.triple_r.clear();
+  for (int i = 0; i < left.size(); ++i)
+    for (int j = 0; j < mid.size(); ++j) {
+      int a = left.charge[i] - mid.charge[j];
+      if (a < 0 || a > d - 1) continue;
+      for (int k = 0; k < right.size(); ++k) {
+        int b = mid.charge[j] - right.charge[k];
+        if (b < 0 || b > d - 1) continue;
+        plan.triple_l.push_back(i); plan.triple_m.push_back(j); plan.triple_r.push_back(k);
+      }
+    }
+  if (left.size() == 0 || right.size() == 0) return;
+  // Candidate middle charges: c with some left l in [c, c+d-1] and right r in [c-d+1, c].
+  int cmin = std::max(right.charge.front(), left.charge.front() - (d - 1));
+  int cmax = std::min(left.charge.back(), right.charge.back() + (d - 1));
+  for (int c = cmin; c <= cmax; ++c) {
+    // rows: left sectors with c <= l <= c + d - 1 (contiguous in the sorted table)
+    int l0 = (int)(std::lower_bound(left.charge.begin(), left.charge.end(), c) - left.charge.begin());
+    int l1 = (int)(std::upper_bound(left.charge.begin(), left.charge.end(), c + d - 1) - left.charge.begin());
+    int r0 = (int)(std::lower_bound(right.charge.begin(), right.charge.end(), c - (d - 1)) - right.charge.begin());
+    int r1 = (int)(std::upper_bound(right.charge.begin(), right.charge.end(), c) - right.charge.begin());
+    if (l0 >= l1 || r0 >= r1) continue;
+    SectorPlanEntry e;
+    e.c = c; e.l0 = l0; e.l1 = l1; e.r0 = r0; e.r1 = r1;
+    e.rows = left.off[l1] - left.off[l0];
+    e.cols = right.off[r1] - right.off[r0];
+    plan.sectors.push_back(e);
+  }
+}
+
+}  // namespace mps
+
+using namespace mps;
+
+static bool make_table(int n, const int32_t* c, const int32_t* dims, BondTable& t) {
+  if (n < 0 || (n > 0 && (!c || !dims))) return false;
+  t.charge.assign(c, c + n);
+  t.dim.assign(dims, dims + n);
+  for (int i = 0; i < n; ++i) {
+    if (t.dim[i] < 1) return false;
+    if (i && t.charge[i] <= t.charge[i - 1]) return false;
+  }
+  t.rebuild_offsets();
+  return true;
+}
+
+extern "C" int mps_plan_sectors(int d, int nl, const int32_t* lc, const int32_t* ld,
+                                int nm, const int32_t* mc, const int32_t* md,
+                                int nr, const int32_t* rc, const int32_t* rd,
+                                int32_t* triples, int cap_triples, int* n_triples,
+                                int32_t* sectors, int cap_sectors, int* n_sectors) {
+  if (d < 2 || d > MPS_MAX_D || !n_triples || !n_sectors) return MPS_EINVAL;
+  BondTable L, M, R;
+  if (!make_table(nl, lc, ld, L) || !make_table(nm, mc, md, M) || !make_table(nr, rc, rd, R))
+    return MPS_EINVAL;
+  UpdatePlan p;
+  plan_update(L, M, R, d, p);
+  *n_triples = (int)p.triple_l.size();
+  *n_sectors = (int)p.sectors.size();
+  if (*n_triples > cap_triples || *n_sectors > cap_sectors) return MPS_EINVAL;
+  if ((*n_triples && !triples) || (*n_sectors && !sectors)) return MPS_EINVAL;
+  for (int t = 0; t < *n_triples; ++t) {
+    triples[3 * t + 0] = L.charge[p.triple_l[t]];
+    triples[3 * t + 1] = M.charge[p.triple_m[t]];
+    triples[3 * t + 2] = R.charge[p.triple_r[t]];
+  }
+  for (int s = 0; s < *n_sectors; ++s) {
+    sectors[3 * s + 0] = p.sectors[s].c;
+    sectors[3 * s + 1] = p.sectors[s].rows;
+    sectors[3 * s + 2] = p.sectors[s].cols;
+  }
+  return MPS_OK;
+}

@@ -34,3 +34,42 @@ def evolve_bh_both(L, d, J, U, dt, steps, chi, cutoff, occ):
 
 def rel_close(a, b, scale, tol):
     return abs(a - b) <= tol * max(abs(b), scale)
+
+
+# ---------------------------------------------------------------------------
+# Random U(1) states (oracle-side) and loading them into the CUDA library
+# ---------------------------------------------------------------------------
+from oracle.synth import random_state, saturated_dims  # noqa: E402,F401
+
+
+def load_state(gpu, st):
+    for b in range(1, st.L):
+        gpu.set_bond(b, st.lam[b])
+    for s in range(st.L):
+        gpu.set_site(s, st.B[s])
+
+
+def two_site_product(Bl, Br):
+    """Gauge-invariant contraction over the middle bond: {(l, r): sum_m Bl[l,m] Br[m,r]}."""
+    out = {}
+    for (l, m), a in Bl.items():
+        for (m2, r), b in Br.items():
+            if m2 == m:
+                out[(l, r)] = out.get((l, r), 0) + a @ b
+    return out
+
+
+def compare_update(gpu, st, s, tol_lam=1e-12, tol_prod=1e-9):
+    """Exact sector structure of bond s+1, lambdas, and the two-site product of sites s, s+1."""
+    gb = gpu.bond(s + 1)
+    assert sorted(gb) == sorted(st.bond[s + 1]), (sorted(gb), sorted(st.bond[s + 1]))
+    for c in gb:
+        assert len(gb[c]) == st.bond[s + 1][c], (c, len(gb[c]), st.bond[s + 1][c])
+        assert np.max(np.abs(gb[c] - st.lam[s + 1][c])) <= tol_lam
+    pg = two_site_product(gpu.site(s), gpu.site(s + 1))
+    po = two_site_product(st.B[s], st.B[s + 1])
+    assert pg.keys() == po.keys()
+    scale = max(np.max(np.abs(v)) for v in po.values())
+    err = max(np.max(np.abs(pg[k] - po[k])) for k in po)
+    assert err <= tol_prod * scale, err / scale
+    return err / scale

@@ -1,0 +1,67 @@
+"""Kernel-level GPU tests: the batched Jacobi SVD (through mps_svd_sectors) against LAPACK."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(M, sig, Y, sweeps, tol=1e-12):
+    ref = np.linalg.svd(M, compute_uv=False)
+    k = min(M.shape)
+    assert sig.shape == (k,)
+    smax = max(ref[0], 1e-300)
+    assert np.all(np.diff(sig) <= 0)
+    assert np.max(np.abs(sig - ref[:k])) <= tol * smax * max(1.0, np.sqrt(max(M.shape)) / 4)
+    assert sweeps >= 0
+    good = sig > 1e-8 * smax
+    Yg = Y[:, good]
+    assert np.max(np.abs(Yg.conj().T @ Yg - np.eye(Yg.shape[1]))) < 1e-10
+    # M y_j has norm sigma_j and the y_j span the row space of M for the kept part
+    assert np.max(np.abs(np.linalg.norm(M @ Yg, axis=0) - sig[good])) <= 1e-12 * smax * np.sqrt(M.shape[1])
+
+
+SHAPES = [(1, 1), (1, 7), (7, 1), (2, 2), (5, 5), (30, 20), (20, 30), (64, 64), (100, 110),
+          (150, 170), (200, 90), (33, 257)]
+
+
+def test_svd_random_shapes(gpu_lib):
+    rng = np.random.default_rng(0)
+    mats = [W.random_complex(s, rng) for s in SHAPES]
+    for M, (sig, Y, sw) in zip(mats, gpu_lib.svd_sectors(mats)):
+        _check(M, sig, Y, sw)
+
+
+def test_svd_rowscale_graded_and_rank_deficient(gpu_lib):
+    rng = np.random.default_rng(1)
+    mats, scales = [], []
+    # graded rows spanning 12 decades (the lambda weighting of a Schmidt spectrum)
+    A = W.random_complex((60, 50), rng)
+    mats.append(A)
+    scales.append(np.logspace(0, -12, 60))
+    # exact rank 3
+    B = W.random_complex((40, 3), rng) @ W.random_complex((3, 45), rng)
+    mats.append(B)
+    scales.append(np.ones(40))
+    # zero matrix block with a single nonzero row
+    C = np.zeros((8, 9), complex)
+    C[3] = W.random_complex(9, rng)
+    mats.append(C)
+    scales.append(np.ones(8))
+    out = gpu_lib.svd_sectors(mats, rowscales=scales)
+    for M, r, (sig, Y, sw) in zip(mats, scales, out):
+        Ms = r[:, None] * M
+        ref = np.linalg.svd(Ms, compute_uv=False)
+        k = min(Ms.shape)
+        assert np.max(np.abs(sig - ref[:k])) <= 1e-13 * ref[0]
+    # rank 3: everything past the third value is at rounding level
+    assert np.all(out[1][0][3:] < 1e-13 * out[1][0][0])
+
+
+def test_svd_many_sectors_one_launch(gpu_lib):
+    rng = np.random.default_rng(2)
+    shapes = [(int(rng.integers(1, 90)), int(rng.integers(1, 90))) for _ in range(200)]
+    mats = [W.random_complex(s, rng) for s in shapes]
+    for M, (sig, Y, sw) in zip(mats, gpu_lib.svd_sectors(mats)):
+        _check(M, sig, Y, sw)

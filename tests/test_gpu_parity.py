@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the float64 oracle.
+
+Bar (FP64 mode): kept sector labels and per-sector dimensions identical to the
+oracle; Schmidt values within 1e-12 absolute (they are normalised); local
+observables within 1e-9 * max(|ref|, |O|), |O| = 1/2 for Sz, n_max for n and
+ln(chi) for bond entropies; gauge-invariant two-site products within 1e-9
+relative.  Amplitudes are gauge invariant (the SVD gauge of every bond cancels in the
+chain of blocks) and are compared directly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import U1MPS, gates, permanent, tebd
+from tests.helpers import compare_update, load_state, random_state
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu(m, d, occ, chi_max):
+    return m.MPS(d, occ, chi_max)
+
+
+def _bond_tables_equal(g, st):
+    for b in range(st.L + 1):
+        assert g.bond_dims(b) == st.bond[b], (b, g.bond_dims(b), st.bond[b])
+
+
+# ---------------------------------------------------------------------------
+# single updates on random states: several tiles, ragged tails, truncation on/off
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("d,L,N,chi_state,chi,cutoff", [
+    (2, 8, 4, 40, 64, 1e-10),
+    (3, 7, 7, 60, 25, 1e-10),
+    (5, 6, 6, 150, 90, 1e-10),
+    (5, 6, 6, 150, 400, 0.0),
+])
+def test_single_update_random_state(gpu_lib, d, L, N, chi_state, chi, cutoff):
+    st = random_state(L, d, N, chi_state, seed=d * 100 + chi)
+    # the initial occupations only fix N; every inner bond and site is then loaded
+    g = _gpu(gpu_lib, d, W.random_occupations(L, d, N, np.random.default_rng(0)), max(chi_state, chi))
+    load_state(g, st)
+    G = gates.bh_gate(L, 2, d, 1.0, 2.0, 0.3) if d > 2 else gates.xxz_gate(0.5, 0.4)
+    for s in range(L - 1):
+        # reload so both sides share the gauge of the left bond (the two-site product is
+        # invariant only under the gauge of the middle bond the update rewrites)
+        load_state(g, st)
+        te_g = g.apply_gate2(s, G, chi, cutoff)
+        info = st.apply_gate2(s, G, chi, cutoff)
+        compare_update(g, st, s)
+        assert abs(te_g - info["trunc_err"]) <= 1e-12 + 1e-9 * info["trunc_err"]
+
+
+def test_layer_equals_sequential_updates(gpu_lib):
+    L, d, N, chi = 10, 3, 10, 50
+    st = random_state(L, d, N, chi, seed=7)
+    a = _gpu(gpu_lib, d, [1] * L, chi)
+    b = _gpu(gpu_lib, d, [1] * L, chi)
+    load_state(a, st)
+    load_state(b, st)
+    G = gates.bh_gate(L, 3, d, 1.0, 3.0, 0.2)
+    sites = [0, 2, 4, 6, 8]
+    a.apply_layer(sites, [G] * len(sites), 30, 1e-10)
+    for s in sites:
+        b.apply_gate2(s, G, 30, 1e-10)
+    for s in range(L):
+        sa, sb = a.site(s), b.site(s)
+        assert sa.keys() == sb.keys()
+        for k in sa:
+            assert np.array_equal(sa[k], sb[k])
+
+
+# ---------------------------------------------------------------------------
+# whole TEBD runs
+# ---------------------------------------------------------------------------
+def _run_both(m, L, d, occ, gate_of, steps, chi, cutoff, check_every_layer=True):
+    g = _gpu(m, d, occ, chi)
+    st = U1MPS.product(d, occ)
+    for _ in range(steps):
+        for sites, f in tebd.strang_layers(L):
+            g.apply_layer(sites, [gate_of(s, f) for s in sites], chi, cutoff)
+            for s in sites:
+                st.apply_gate2(s, gate_of(s, f), chi, cutoff)
+            if check_every_layer:
+                _bond_tables_equal(g, st)
+    return g, st
+
+
+def test_xxz_cfg1_parity(gpu_lib):
+    """XXZ L=16, Delta=0.5, Neel, dt=0.05 x 20, chi<=64, cutoff 1e-10."""
+    L = 16
+    gate_of = tebd.xxz_gates(L, 0.5, 0.05)
+    g, st = _run_both(gpu_lib, L, 2, W.neel_occupations(L), gate_of, 20, 64, 1e-10)
+    for s in range(L):
+        ref = st.expect_local(s, [-0.5, 0.5])
+        assert abs(g.expect(s, [-0.5, 0.5]) - ref) <= 1e-9 * max(abs(ref), 0.5)
+    for b in range(1, L):
+        ref = st.entropy(b)
+        assert abs(g.entropy(b) - ref) <= 1e-9 * max(abs(ref), math.log(64))
+    rng = np.random.default_rng(3)
+    cfgs = [W.random_occupations(L, 2, 8, rng) for _ in range(64)] + [W.neel_occupations(L)]
+    ag = g.amplitudes(cfgs)
+    ao = np.array([st.amplitude(c) for c in cfgs])
+    assert np.max(np.abs(ag - ao)) < 1e-10
+
+
+def test_bose_hubbard_truncated_parity(gpu_lib):
+    """BH d=5 with the chi cap active in most updates."""
+    L, d = 12, 5
+    gate_of = tebd.bh_gates(L, d, 1.0, 2.0, 0.05)
+    g, st = _run_both(gpu_lib, L, d, W.mott_occupations(L), gate_of, 8, 24, 1e-10)
+    n_op = np.arange(d)
+    for s in range(L):
+        ref = st.expect_local(s, n_op)
+        assert abs(g.expect(s, n_op) - ref) <= 1e-9 * max(abs(ref), d - 1)
+    assert max(st.bond_dim(b) for b in range(L + 1)) == 24
+
+
+def test_boson_sampling_amplitudes(gpu_lib):
+    M, n = 8, 4
+    d = n + 1
+    occ = W.single_photon_occupations(M, n)
+    layers = W.brickwork_pairs(M, 8)
+    ang = W.haar_beam_splitter_angles(sum(map(len, layers)), seed=0)
+    g = _gpu(gpu_lib, d, occ, 512)
+    st = U1MPS.product(d, occ)
+    k = 0
+    for sites in layers:
+        gs = []
+        for s in sites:
+            gs.append(gates.beam_splitter_gate(*ang[k], d))
+            k += 1
+        g.apply_layer(sites, gs, 512, 0.0)
+        for s, G in zip(sites, gs):
+            st.apply_gate2(s, G, 512, 0.0)
+    U = tebd.interferometer(M, layers, ang)
+    rng = np.random.default_rng(4)
+    cfgs = [W.random_occupations(M, d, n, rng) for _ in range(40)]
+    ag = g.amplitudes(cfgs)
+    for c, a in zip(cfgs, ag):
+        rows = [j for j in range(M) for _ in range(c[j])]
+        p = abs(permanent.permanent_bruteforce(U[np.ix_(rows, list(range(n)))])) ** 2
+        p /= np.prod([math.factorial(x) for x in c])
+        assert abs(abs(a) ** 2 - p) < 1e-12
+    # an amplitude is gauge invariant (bond gauges cancel in the chain), so compare it directly
+    ao = np.array([st.amplitude(c) for c in cfgs])
+    assert np.max(np.abs(ag - ao)) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_two_sites_and_chi_one(gpu_lib):
+    g = _gpu(gpu_lib, 2, [1, 0], 4)
+    st = U1MPS.product(2, [1, 0])
+    G = gates.xxz_gate(0.3, 0.7)
+    g.apply_gate2(0, G, 1, 1e-10)
+    st.apply_gate2(0, G, 1, 1e-10)
+    compare_update(g, st, 0)
+    assert g.bond_dims(1) == st.bond[1]
+
+
+def test_product_state_amplitudes_and_bad_configs(gpu_lib):
+    occ = [2, 0, 1, 3, 0]
+    g = _gpu(gpu_lib, 4, occ, 8)
+    assert g.amplitude(occ) == 1.0
+    assert g.amplitude([2, 0, 1, 2, 1]) == 0.0        # same N, absent block
+    assert g.amplitude([2, 0, 1, 3, 1]) == 0.0        # wrong N
+    assert g.amplitude([5, 0, 1, 0, 0]) == 0.0        # occupation out of range
+    assert abs(g.expect(3, [0, 1, 2, 3]) - 3.0) < 1e-15
+
+
+def test_invalid_arguments(gpu_lib):
+    m = gpu_lib
+    g = _gpu(m, 2, [1, 0, 1, 0], 8)
+    G = gates.xxz_gate(0.5, 0.1)
+    with pytest.raises(m.MPSError):
+        g.apply_gate2(3, G, 4, 1e-10)          # site + 1 out of range
+    with pytest.raises(m.MPSError):
+        g.apply_gate2(0, G, 9, 1e-10)          # chi > chi_max
+    with pytest.raises(m.MPSError):
+        g.apply_gate2(0, G, 4, -1.0)           # negative cutoff
+    with pytest.raises(m.MPSError):
+        g.apply_layer([0, 1], [G, G], 4, 1e-10)  # overlapping pairs
+    with pytest.raises(m.MPSError):
+        m.MPS(2, [1, 2], 4)                    # occupation outside [0, d-1]
+    with pytest.raises(m.MPSError):
+        m.MPS(2, [1, 0], 4, precision=m.MPS_TF32)
+
+
+def test_annihilating_gate_leaves_state_unchanged(gpu_lib):
+    m = gpu_lib
+    g = _gpu(m, 2, [1, 0, 1, 0], 8)
+    zero = [np.zeros_like(b) for b in gates.xxz_gate(0.5, 0.1)]
+    before = g.site(1)
+    with pytest.raises(m.MPSError):
+        g.apply_gate2(1, zero, 4, 1e-10)
+    after = g.site(1)
+    assert before.keys() == after.keys()
+
+
+# ---------------------------------------------------------------------------
+# full size: the Bose-Hubbard L=64, chi=512 chain at saturation, one odd layer
+# launched like the benchmark; sampled updates recomputed by the oracle
+# ---------------------------------------------------------------------------
+def test_full_size_bose_hubbard_layer_sampled(gpu_lib):
+    L, d, N, chi = 64, 5, 64, 512
+    st = random_state(L, d, N, chi, seed=11, occ=W.mott_occupations(L))
+    g = _gpu(gpu_lib, d, W.mott_occupations(L), chi)
+    load_state(g, st)
+    gate_of = tebd.bh_gates(L, d, 1.0, 2.0, 0.02)
+    sites = list(range(0, L - 1, 2))
+    g.apply_layer(sites, [gate_of(s, 0.5) for s in sites], chi, 1e-10)
+    for s in (0, 30, 32, 62):
+        ref = st.copy()
+        ref.apply_gate2(s, gate_of(s, 0.5), chi, 1e-10)
+        compare_update(g, ref, s, tol_lam=1e-12, tol_prod=1e-8)
