@@ -224,6 +224,12 @@ MPS_API int mps_reset_kernel_stats(mps_t h);
 MPS_API int64_t mps_launch_count(void);
 
 /*
+ * mps_last_batch_sweeps - Jacobi sweeps of the last update call on h over all of its
+ * sectors: sector count, summed sweeps and the largest sweep count (any may be NULL).
+ */
+MPS_API int mps_last_batch_sweeps(mps_t h, int* n_sectors, int64_t* sweeps_sum, int* sweeps_max);
+
+/*
  * mps_plan_sectors - the integer sector planner alone (host code, no GPU needed).
  * Given the charge tables of bonds s, s+1, s+2 (ascending charges), it lists every
  * compatible (l, m, r) with 0 <= l-m <= d-1 and 0 <= m-r <= d-1, and every

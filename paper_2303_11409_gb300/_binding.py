@@ -73,6 +73,7 @@ _SIGS = {
     "mps_plan_sectors": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.c_int, _i32p, _i32p,
                                         ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_int, _intp, _i32p,
                                         ctypes.c_int, _intp]),
+    "mps_last_batch_sweeps": (ctypes.c_int, [_h, _intp, _i64p, _intp]),
     "mps_set_profiling": (ctypes.c_int, [_h, ctypes.c_int]),
     "mps_kernel_stats": (ctypes.c_int, [_h, ctypes.c_int, _i64p, _dblp, _dblp, _dblp]),
     "mps_reset_kernel_stats": (ctypes.c_int, [_h]),
@@ -272,6 +273,12 @@ class MPS:
             data = np.zeros(1, np.complex128)
         self._check(lib.mps_set_site(self._h, s, len(keys), _ptr(lc, _i32p), _ptr(mc, _i32p),
                                      data.ctypes.data_as(_dblp)), "mps_set_site")
+
+    def batch_sweeps(self) -> dict:
+        """Jacobi sweeps of the last update call: sectors, mean and max."""
+        n, tot, mx = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+        lib.mps_last_batch_sweeps(self._h, ctypes.byref(n), ctypes.byref(tot), ctypes.byref(mx))
+        return dict(sectors=n.value, mean=tot.value / max(n.value, 1), max=mx.value)
 
     def set_profiling(self, on: bool = True):
         self._check(lib.mps_set_profiling(self._h, int(bool(on))), "mps_set_profiling")

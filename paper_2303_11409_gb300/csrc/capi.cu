@@ -197,19 +197,17 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
         gemm_tiles_bound += (int64_t)((Dl + kTile - 1) / kTile) * ((k + kTile - 1) / kTile);
       }
     }
-  std::vector<int64_t> jac_work, jac_norm, jac_ord;
-  int svd_smem = 0;
-  for (int u = 0; u < nreq; ++u)
-    for (auto& e : W[u].plan.sectors) {
-      if (svd_smem_need(e.rows, e.cols) > kSvdSmemMax) {
-        jac_work.push_back(ws); ws = a256(ws + 16LL * e.rows * e.cols);
-        jac_norm.push_back(ws); ws = a256(ws + 8LL * e.rows);
-        jac_ord.push_back(ws); ws = a256(ws + 4LL * e.rows);
-      } else {
-        jac_work.push_back(-1); jac_norm.push_back(-1); jac_ord.push_back(-1);
-        svd_smem = std::max<int>(svd_smem, (int)svd_smem_need(e.rows, e.cols));
-      }
-    }
+  // Jacobi scratch: one-CTA sectors live in shared memory, cluster sectors in L2
+  SvdScratchLayout JL;
+  {
+    std::vector<int> sm, sn;
+    for (int u = 0; u < nreq; ++u)
+      for (auto& e : W[u].plan.sectors) { sm.push_back(e.rows); sn.push_back(e.cols); }
+    svd_layout((int)sm.size(), sm.data(), sn.data(), JL);
+  }
+  const int64_t jac_base = ws;
+  ws = a256(ws + JL.total);
+  const int svd_smem = JL.smem;
   const int64_t glen = gate_len(owner->d);
   for (int u = 0; u < nreq; ++u)
     if (reqs[u].h->d != owner->d) return fail(owner, MPS_EINVAL, "batched handles must share d");
@@ -333,15 +331,12 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     W[u].sel_first = (int)selsec.size();
     for (size_t si = 0; si < P.sectors.size(); ++si, ++sec_global) {
       const SectorPlanEntry& E = P.sectors[si];
-      SvdSector S;
+      SvdSector S = {};
       S.theta = reinterpret_cast<const double2*>(dptr(W[u].theta_off[si]));
       S.rowscale = h->lambda_ptr(s) + Lb.off[E.l0];
       S.m = E.rows;
       S.n = E.cols;
-      S.smem = jac_work[sec_global] < 0;
-      S.work = S.smem ? nullptr : reinterpret_cast<double2*>(dptr(jac_work[sec_global]));
-      S.norms = S.smem ? nullptr : reinterpret_cast<double*>(dptr(jac_norm[sec_global]));
-      S.order = S.smem ? nullptr : reinterpret_cast<int*>(dptr(jac_ord[sec_global]));
+      svd_fill_scratch(S, JL, sec_global, dptr(jac_base));
       S.sigma = reinterpret_cast<double*>(dptr(W[u].sig_off[si]));
       S.Y = reinterpret_cast<double2*>(dptr(W[u].y_off[si]));
       S.status = reinterpret_cast<int*>(dptr(status_off)) + sec_global;
@@ -351,10 +346,20 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     seltask.push_back(SelectTask{W[u].sel_first, (int)selsec.size(), reqs[u].chi, reqs[u].cutoff});
   }
   // largest sectors first so that the longest CTAs start earliest
-  std::vector<SvdSector> svd_sorted = svd;
-  std::stable_sort(svd_sorted.begin(), svd_sorted.end(), [](const SvdSector& a, const SvdSector& b) {
-    return (double)a.m * a.m * a.n > (double)b.m * b.m * b.n;
-  });
+  // one list per kernel, most expensive sectors first so the longest CTAs start earliest
+  std::vector<SvdSector> svd_sorted;
+  int n_svd_cta = 0;
+  for (int mode : {kSvdSmem, kSvdCluster}) {
+    const size_t first = svd_sorted.size();
+    for (const SvdSector& S : svd)
+      if (S.mode == mode) svd_sorted.push_back(S);
+    std::stable_sort(svd_sorted.begin() + first, svd_sorted.end(), [](const SvdSector& a, const SvdSector& b) {
+      const double ca = (double)std::max(a.m, a.n) * std::min(a.m, a.n) * std::min(a.m, a.n);
+      const double cb = (double)std::max(b.m, b.n) * std::min(b.m, b.n) * std::min(b.m, b.n);
+      return ca > cb;
+    });
+    if (mode == kSvdSmem) n_svd_cta = (int)svd_sorted.size();
+  }
 
   // ---- upload (one copy of all descriptors and gates) ---------------------------------
   const int64_t o_tasks = sg.put(tasks.data(), (int64_t)tasks.size());
@@ -390,8 +395,9 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
                         reinterpret_cast<TileRef*>(dptr(desc_off + o_tiles)), (int)tiles.size(), st);
   }));
   CUDA_OR_FAIL(owner, timed(owner, MPS_K_SVD, !svd_sorted.empty(), svd_flops, svd_bytes, [&] {
-    return launch_svd(reinterpret_cast<SvdSector*>(dptr(desc_off + o_svd)), (int)svd_sorted.size(), svd_smem,
-                      kJacobiMaxSweeps, st);
+    const SvdSector* d_svd = reinterpret_cast<SvdSector*>(dptr(desc_off + o_svd));
+    return launch_svd_all(d_svd, n_svd_cta, d_svd + n_svd_cta, (int)svd_sorted.size() - n_svd_cta, svd_smem, st,
+                          owner->side, owner->fork, owner->join);
   }));
   CUDA_OR_FAIL(owner, timed(owner, MPS_K_SELECT, nreq > 0, 0.0, sel_bytes, [&] {
     return launch_select(reinterpret_cast<SelectSector*>(dptr(desc_off + o_selsec)),
@@ -413,6 +419,17 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   std::vector<TileRef> gt;
   int64_t sc_elems = 0;
   std::vector<char> apply(nreq, 0);
+  {
+    int bmax = 0;
+    int64_t bsum = 0;
+    for (int k = 0; k < n_sec_total; ++k) {
+      bmax = std::max(bmax, sstat[k]);
+      bsum += std::max(sstat[k], 0);
+    }
+    owner->stats.batch_sectors = n_sec_total;
+    owner->stats.batch_sweeps_sum = bsum;
+    owner->stats.batch_sweeps_max = bmax;
+  }
   std::vector<BondTable> newmid(nreq);
   std::vector<SiteTable> newL(nreq), newR(nreq);
   sec_global = 0;
@@ -619,6 +636,9 @@ int mps_create(mps_t* out, int L, int d, const int32_t* site_charges, int precis
   cudaError_t e = cudaMalloc(&h->d_lambda, sizeof(double) * lam_total);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_sites, sizeof(double2) * site_total);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->staged, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     if (h->d_lambda) cudaFree(h->d_lambda);
     if (h->d_sites) cudaFree(h->d_sites);
@@ -646,6 +666,9 @@ int mps_destroy(mps_t h) {
   if (h->d_lambda) cudaFree(h->d_lambda);
   if (h->d_sites) cudaFree(h->d_sites);
   if (h->staged) cudaEventDestroy(h->staged);
+  if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->join) cudaEventDestroy(h->join);
   for (auto& p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   h->work.release();
@@ -943,6 +966,14 @@ int mps_reset_kernel_stats(mps_t h) {
 }
 
 int64_t mps_launch_count(void) { return g_launches.load(); }
+
+int mps_last_batch_sweeps(mps_t h, int* n_sectors, int64_t* sweeps_sum, int* sweeps_max) {
+  if (!h) return MPS_EINVAL;
+  if (n_sectors) *n_sectors = h->stats.batch_sectors;
+  if (sweeps_sum) *sweeps_sum = h->stats.batch_sweeps_sum;
+  if (sweeps_max) *sweeps_max = h->stats.batch_sweeps_max;
+  return MPS_OK;
+}
 
 int mps_last_update_stats(mps_t h, int* n_sectors, int* n_triples, int* max_sweeps, int* tie_band,
                           double* norm_all, double* norm_kept) {

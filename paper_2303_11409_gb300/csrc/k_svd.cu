@@ -1,22 +1,38 @@
-// Batched per-sector SVD of the two-site update (K2), FP64 one-sided Jacobi.
+// Batched per-sector SVD of the two-site update (K2), FP64, QR-preconditioned
+// one-sided Jacobi.
 //
 // arXiv:2303.11409, Sec. II: after the U(1) split a local update needs only
-// block-sparse SVDs of the submatrices Theta(c), each at most chi x chi.  One CTA
-// decomposes one sector M = diag(lambda) Theta'(c) (m x n).  It works on the
-// columns of A = M^dag (n x m): Hestenes rotations orthogonalise the m columns of
-// A; at convergence A V = [sigma_1 y_1, ..., sigma_m y_m], so the column norms are
-// the singular values and the normalised columns are the right singular vectors Y
-// of M = X S Y^dag that the right-canonical reassembly needs (X is never formed).
+// block-sparse SVDs of the submatrices Theta(c), each at most chi x chi.  Each
+// sector M = diag(lambda) Theta'(c) (m x n, K = min(m, n)) is decomposed as
+//   1. Householder QR with column pivoting  M P = Q R  (R: K x n, upper trapezoidal);
+//   2. one-sided (Hestenes) Jacobi on the columns of R^dag (n x K):
+//      R^dag U = [s_1 v_1, ..., s_K v_K], so the column norms are the singular
+//      values and the normalised columns are the right singular vectors of R;
+//   3. Y = P [v_1 ... v_K], the right singular vectors of M = X S Y^dag.
+// Neither Q nor the rotations are accumulated: the right-canonical reassembly
+// needs only S and Y.  Pivoted QR is the Drmac-Veselic preconditioner: the
+// lambda-graded sectors of an MPS (singular values over 10-15 decades) need
+// 20-35 plain Jacobi sweeps but 6-8 after it.
 //
-// Pairs follow the round-robin (circle) ordering, so each round's pairs are
-// disjoint and are spread over the CTA's warps; every dot product and rotation is
-// one warp with a shuffle reduction.  A sector whose working set fits in shared
-// memory is staged there; larger ones work in global memory (L2 resident).
-// Convergence: a whole sweep without a rotation, where a pair is rotated when
-// |a_p^dag a_q| > tol |a_p| |a_q|, tol = eps * max(n, 32), and both columns are
-// above the noise floor 32 eps |A|_F.  Singular values at or below that floor are
-// reported as exactly 0 (their vectors are not determined by the data).  A sector that is not
-// converged after the sweep limit reports -1 (MPS_ENOCONV at the API).
+// Storage: M is kept row-major with an odd leading dimension ld >= n, so the QR
+// rank-1 updates are coalesced (32 consecutive columns per warp) and, once R's
+// rows are conjugated in place, they are the contiguous columns of R^dag.
+// GB300 runs FP64 at 2 FMA/clk/SM, so one SM per large sector would leave a
+// layer waiting on its largest sectors.  Two kernels share the work:
+//   jacobi_cta_kernel:     one CTA per sector, all of it in shared memory;
+//   jacobi_cluster_kernel: a thread-block cluster of 8 or 16 CTAs per large
+//                          sector, data in L2 (ld.global.cg / st.global.cg, no
+//                          stale L1 lines across SMs), steps separated by the
+//                          hardware cluster barrier.
+// Jacobi pairs follow the round-robin ordering (disjoint pairs per round, one
+// warp per pair).  A pair is rotated when |a_p^dag a_q|^2 > tol^2 |a_p|^2 |a_q|^2,
+// tol = eps * max(n, 32), and both columns are above the noise floor 32 eps
+// |M|_F; singular values at or below the floor are reported as exactly 0.
+// Convergence is a sweep without a rotation; a sector that does not converge
+// within the sweep limit reports -1.  FP64 costs a warp 64 cycles per
+// instruction here, so per-pair scalar work is kept small (no square root in the
+// test; two rsqrt, one sqrt and one division per rotation; column norms tracked
+// through the exact 2x2 relations within a sweep).
 #include <algorithm>
 #include <vector>
 
@@ -25,13 +41,16 @@
 namespace mps {
 namespace {
 
+constexpr double kEps = 2.220446049250313e-16;
+constexpr int kMaxCached = 16;          // rows cached in registers per lane (n <= 512)
+constexpr int kMaxCluster = 16;
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Round-robin pairing of mp (even) slots, round r in [0, mp-1), pair k in [0, mp/2).
 __device__ __forceinline__ void rr_pair(int k, int r, int mp, int& p, int& q) {
   const int ring = mp - 1;
   if (k == 0) {
@@ -43,197 +62,601 @@ __device__ __forceinline__ void rr_pair(int k, int r, int mp, int& p, int& q) {
   }
 }
 
-__global__ void __launch_bounds__(kSvdThreads) jacobi_svd_kernel(const SvdSector* __restrict__ secs,
-                                                                 int max_sweeps) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_rot;
-  __shared__ double s_fro2;
-  const SvdSector S = secs[blockIdx.x];
-  const int m = S.m, n = S.n;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  double2* A;
-  double* nrm;
-  int* ord;
-  if (S.smem) {
-    A = reinterpret_cast<double2*>(smem_raw);
-    nrm = reinterpret_cast<double*>(A + (int64_t)m * n);
-    ord = reinterpret_cast<int*>(nrm + m);
-  } else {
-    A = S.work;
-    nrm = S.norms;
-    ord = S.order;
-  }
-  // A[:, j] = conj(rowscale_j * Theta'[j, :])  (column j of A is row j of M, conjugated)
-  const int64_t mn = (int64_t)m * n;
-  for (int64_t e = tid; e < mn; e += blockDim.x) {
-    const int j = (int)(e / n);
-    const double s = S.rowscale ? S.rowscale[j] : 1.0;
-    const double2 v = S.theta[e];
-    A[e] = make_double2(s * v.x, -s * v.y);
-  }
-  __syncthreads();
-  for (int j = warp; j < m; j += nwarps) {
-    const double2* a = A + (int64_t)j * n;
-    double acc = 0.0;
-    for (int i = lane; i < n; i += 32) acc = fma(a[i].x, a[i].x, fma(a[i].y, a[i].y, acc));
-    acc = warp_sum(acc);
-    if (lane == 0) nrm[j] = acc;
-  }
-  __syncthreads();
-  if (warp == 0) {   // |A|_F^2 is invariant under the rotations
-    double f = 0.0;
-    for (int j = lane; j < m; j += 32) f += nrm[j];
-    f = warp_sum(f);
-    if (lane == 0) s_fro2 = f;
-  }
-  __syncthreads();
-  const double tol = 2.220446049250313e-16 * (double)max(n, 32);
-  // a column whose norm is below 32 eps |A|_F is rounding noise: rotating it against
-  // another column cannot make the pair more orthogonal (two noise columns of a
-  // rank-deficient sector stay parallel), so such pairs are left alone
-  const double floor2 = (32.0 * 2.220446049250313e-16) * (32.0 * 2.220446049250313e-16) * s_fro2;
-  const int mp = m + (m & 1);
-  int sweep = 0;
-  bool converged = (m < 2);
-  for (; !converged && sweep < max_sweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
-    __syncthreads();
-    for (int r = 0; r < mp - 1; ++r) {
-      for (int k = warp; k < mp / 2; k += nwarps) {
-        int p, q;
-        rr_pair(k, r, mp, p, q);
-        if (p >= m || q >= m) continue;
-        if (p > q) { int t = p; p = q; q = t; }
-        double2* ap = A + (int64_t)p * n;
-        double2* aq = A + (int64_t)q * n;
-        double gr = 0.0, gi = 0.0;
-        for (int i = lane; i < n; i += 32) {
-          const double2 x = ap[i], y = aq[i];
-          gr = fma(x.x, y.x, fma(x.y, y.y, gr));      // Re conj(x) y
-          gi = fma(x.x, y.y, fma(-x.y, y.x, gi));     // Im conj(x) y
-        }
-        gr = warp_sum(gr);
-        gi = warp_sum(gi);
-        const double alpha = nrm[p], beta = nrm[q];
-        const double g = hypot(gr, gi);
-        if (!(g > 0.0) || !(g > tol * sqrt(alpha) * sqrt(beta)) || fmin(alpha, beta) <= floor2) continue;
-        // 2x2 Hermitian Gram [[alpha, gamma], [conj(gamma), beta]] -> diagonal
-        const double zeta = (beta - alpha) / (2.0 * g);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t);
-        const double s = c * t;
-        const double er = gr / g, ei = gi / g;          // gamma / |gamma|
-        double np = 0.0, nq = 0.0;
-        for (int i = lane; i < n; i += 32) {
-          const double2 x = ap[i], y = aq[i];
-          double2 xn, yn;
-          // x' = c x - s conj(e) y ;  y' = s e x + c y
-          xn.x = c * x.x - s * (er * y.x + ei * y.y);
-          xn.y = c * x.y - s * (er * y.y - ei * y.x);
-          yn.x = c * y.x + s * (er * x.x - ei * x.y);
-          yn.y = c * y.y + s * (er * x.y + ei * x.x);
-          ap[i] = xn;
-          aq[i] = yn;
-          np = fma(xn.x, xn.x, fma(xn.y, xn.y, np));
-          nq = fma(yn.x, yn.x, fma(yn.y, yn.y, nq));
-        }
-        np = warp_sum(np);
-        nq = warp_sum(nq);
-        if (lane == 0) {
-          nrm[p] = np;
-          nrm[q] = nq;
-          s_rot = 1;
-        }
-      }
-      __syncthreads();
-    }
-    converged = (s_rot == 0);
-    __syncthreads();
-  }
-  // singular values: fresh column norms, sorted descending (ties by column index)
-  for (int j = warp; j < m; j += nwarps) {
-    const double2* a = A + (int64_t)j * n;
-    double acc = 0.0;
-    for (int i = lane; i < n; i += 32) acc = fma(a[i].x, a[i].x, fma(a[i].y, a[i].y, acc));
-    acc = warp_sum(acc);
-    // at or below the noise floor a column is rounding noise: its singular value is 0
-    if (lane == 0) nrm[j] = acc <= floor2 ? 0.0 : sqrt(acc);
-  }
-  __syncthreads();
-  // NaN (from non-finite input) ranks last, so the ranks always form a permutation
-  for (int j = tid; j < m; j += blockDim.x) {
-    const double v = isnan(nrm[j]) ? -1.0 : nrm[j];
-    int rank = 0;
-    for (int k = 0; k < m; ++k) {
-      const double w = isnan(nrm[k]) ? -1.0 : nrm[k];
-      rank += (w > v) || (w == v && k < j);
-    }
-    ord[rank] = j;
-  }
-  __syncthreads();
-  const int kmin = min(m, n);
-  for (int r = tid; r < kmin; r += blockDim.x) S.sigma[r] = nrm[ord[r]];
-  const int64_t ny = (int64_t)n * kmin;
-  for (int64_t e = tid; e < ny; e += blockDim.x) {
-    const int r = (int)(e / n), i = (int)(e % n);
-    const int j = ord[r];
-    const double sv = nrm[j];
-    double2 y = make_double2(0.0, 0.0);
-    if (sv > 0.0) {
-      const double2 a = A[(int64_t)j * n + i];
-      y = make_double2(a.x / sv, a.y / sv);
-    }
-    S.Y[e] = y;
-  }
-  if (tid == 0) *S.status = converged ? sweep : -1;
+// Memory access policy: plain (shared memory) or L2-only (cluster, global memory).
+struct PlainMem {
+  static constexpr bool kCache = false;
+  template <typename T> static __device__ __forceinline__ T ld(const T* p) { return *p; }
+  template <typename T> static __device__ __forceinline__ void st(T* p, T v) { *p = v; }
+};
+struct L2Mem {
+  static constexpr bool kCache = true;    // load each column pair once per round
+  static __device__ __forceinline__ double2 ld(const double2* p) { return __ldcg(p); }
+  static __device__ __forceinline__ double ld(const double* p) { return __ldcg(p); }
+  static __device__ __forceinline__ int ld(const int* p) { return __ldcg(p); }
+  static __device__ __forceinline__ void st(double2* p, double2 v) { __stcg(p, v); }
+  static __device__ __forceinline__ void st(double* p, double v) { __stcg(p, v); }
+  static __device__ __forceinline__ void st(int* p, int v) { __stcg(p, v); }
+};
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
 }
 
-bool g_svd_attr_set = false;
+struct Rot { double c, u, v; };   // c = cos, (u + i v) = sin * gamma / |gamma|
+
+__device__ __forceinline__ void rotate_pair(double2& x, double2& y, const Rot& R) {
+  // x' = c x - s conj(e) y ;  y' = s e x + c y   with s e = u + i v
+  const double2 xo = x, yo = y;
+  x.x = fma(R.c, xo.x, -fma(R.u, yo.x, R.v * yo.y));
+  x.y = fma(R.c, xo.y, -fma(R.u, yo.y, -R.v * yo.x));
+  y.x = fma(R.c, yo.x, fma(R.u, xo.x, -R.v * xo.y));
+  y.y = fma(R.c, yo.y, fma(R.u, xo.y, R.v * xo.x));
+}
+
+// One warp: orthogonalise columns p, q (length R, stride ld) of the Jacobi matrix.
+// nrm holds squared column norms, updated by alpha' = alpha - t|g|, beta' = beta + t|g|.
+template <class Mem>
+__device__ bool jacobi_pair(double2* A, int R, int ld, double* nrm, int p, int q, double tol2, double floor2) {
+  const int lane = threadIdx.x & 31;
+  const double alpha = Mem::ld(nrm + p), beta = Mem::ld(nrm + q);
+  if (fmin(alpha, beta) <= floor2) return false;      // a noise column: nothing to orthogonalise
+  double2* ap = A + (int64_t)p * ld;
+  double2* aq = A + (int64_t)q * ld;
+  const bool cached = Mem::kCache && R <= 32 * kMaxCached;
+  double2 xs[kMaxCached], ys[kMaxCached];
+  double gr = 0.0, gi = 0.0;
+  if (cached) {
+#pragma unroll
+    for (int t = 0; t < kMaxCached; ++t) {
+      const int i = lane + 32 * t;
+      xs[t] = make_double2(0.0, 0.0);
+      ys[t] = make_double2(0.0, 0.0);
+      if (i < R) {
+        xs[t] = Mem::ld(ap + i);
+        ys[t] = Mem::ld(aq + i);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kMaxCached; ++t) {
+      if (32 * t < R) {
+        gr = fma(xs[t].x, ys[t].x, fma(xs[t].y, ys[t].y, gr));
+        gi = fma(xs[t].x, ys[t].y, fma(-xs[t].y, ys[t].x, gi));
+      }
+    }
+  } else {
+    for (int i = lane; i < R; i += 32) {
+      const double2 x = Mem::ld(ap + i), y = Mem::ld(aq + i);
+      gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+      gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+    }
+  }
+  gr = warp_sum(gr);
+  gi = warp_sum(gi);
+  const double g2 = fma(gr, gr, gi * gi);
+  if (!(g2 > tol2 * alpha * beta)) return false;       // orthogonal to tolerance
+  // 2x2 Hermitian Gram [[alpha, gamma], [conj(gamma), beta]] -> diagonal
+  const double inv_g = rsqrt(g2);
+  const double g = g2 * inv_g;
+  const double zeta = (beta - alpha) * (0.5 * inv_g);
+  const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+  Rot Rt;
+  Rt.c = rsqrt(fma(t, t, 1.0));
+  const double s_over_g = Rt.c * t * inv_g;
+  Rt.u = s_over_g * gr;
+  Rt.v = s_over_g * gi;
+  if (cached) {
+#pragma unroll
+    for (int k = 0; k < kMaxCached; ++k) {
+      const int i = lane + 32 * k;
+      if (32 * k < R) {
+        rotate_pair(xs[k], ys[k], Rt);
+        if (i < R) {
+          Mem::st(ap + i, xs[k]);
+          Mem::st(aq + i, ys[k]);
+        }
+      }
+    }
+  } else {
+    for (int i = lane; i < R; i += 32) {
+      double2 x = Mem::ld(ap + i), y = Mem::ld(aq + i);
+      rotate_pair(x, y, Rt);
+      Mem::st(ap + i, x);
+      Mem::st(aq + i, y);
+    }
+  }
+  if (lane == 0) {
+    const double tg = t * g;
+    Mem::st(nrm + p, fmax(alpha - tg, 0.0));
+    Mem::st(nrm + q, beta + tg);
+  }
+  return true;
+}
+
+// Per-sector working set (shared memory or global scratch).
+struct Work {
+  double2* W;     // m x ld, row-major: M, then R (rows 0..K-1), then R^dag's columns
+  double2* u;     // m: Householder vector of the current step
+  double* nu;     // n: partial squared column norms for pivoting
+  double* nu0;    // n: their reference values (recompute when cancellation sets in)
+  int* perm;      // n: column permutation P
+  double* nrm;    // K: Jacobi column norms / singular values
+  int* ord;       // K: descending order of the singular values
+  int* flags;     // max_sweeps + 1: rotation seen in sweep s
+  double* pv;     // per-CTA pivot candidates (value)
+  int* pi;        // per-CTA pivot candidates (index)
+  double* scal;   // [0] = 2 / u^dag u, [1] = |M|_F^2
+};
+
+__host__ __device__ inline int odd_ld(int n) { return n | 1; }
+
+template <class Mem, class Sync>
+__device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int nctas, Sync sync, int max_sweeps) {
+  __shared__ double red_d[8][33];
+  __shared__ double red_v[8];
+  __shared__ int red_i[8];
+  const int m = S.m, n = S.n, K = min(m, n), ld = odd_ld(n);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int tid_all = rank * blockDim.x + tid, threads_all = nctas * blockDim.x;
+  const int worker = rank * nwarps + warp, workers = nctas * nwarps;
+  double2* W = w.W;
+
+  // ---- load M = diag(lambda) Theta' (row-major), column norms, identity permutation ----
+  const int64_t mn = (int64_t)m * n;
+  for (int64_t e = tid_all; e < mn; e += threads_all) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const double s = S.rowscale ? S.rowscale[i] : 1.0;
+    const double2 t = S.theta[e];
+    Mem::st(W + (int64_t)i * ld + j, make_double2(s * t.x, s * t.y));
+  }
+  for (int s = tid_all; s <= max_sweeps; s += threads_all) Mem::st(w.flags + s, 0);
+  sync();
+  for (int j = tid_all; j < n; j += threads_all) {
+    double acc = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double2 x = Mem::ld(W + (int64_t)i * ld + j);
+      acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+    }
+    Mem::st(w.nu + j, acc);
+    Mem::st(w.nu0 + j, acc);
+    Mem::st(w.perm + j, j);
+  }
+  sync();
+  if (tid_all == 0) {
+    double f = 0.0;
+    for (int j = 0; j < n; ++j) f += Mem::ld(w.nu + j);
+    Mem::st(w.scal + 1, f);
+  }
+  sync();
+  const double fro2 = Mem::ld(w.scal + 1);
+
+  // ---- Householder QR with column pivoting: M P = Q R ---------------------------------
+  for (int k = 0; k < K; ++k) {
+    // pivot: largest remaining partial norm, ties to the smaller index
+    double bv = -1.0;
+    int bi = n;
+    for (int j = k + tid_all; j < n; j += threads_all) {
+      const double v = Mem::ld(w.nu + j);
+      if (v > bv || (v == bv && j < bi)) { bv = v; bi = j; }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = bv; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int x = 1; x < nwarps; ++x)
+        if (red_v[x] > bv || (red_v[x] == bv && red_i[x] < bi)) { bv = red_v[x]; bi = red_i[x]; }
+      Mem::st(w.pv + rank, bv);
+      Mem::st(w.pi + rank, bi);
+    }
+    sync();
+    bv = Mem::ld(w.pv);
+    bi = Mem::ld(w.pi);
+    for (int x = 1; x < nctas; ++x) {
+      const double v = Mem::ld(w.pv + x);
+      const int ix = Mem::ld(w.pi + x);
+      if (v > bv || (v == bv && ix < bi)) { bv = v; bi = ix; }
+    }
+    const int p = (bi < n) ? bi : k;
+    if (p != k) {
+      for (int i = tid_all; i < m; i += threads_all) {
+        double2* rowp = W + (int64_t)i * ld;
+        const double2 a = Mem::ld(rowp + k), b = Mem::ld(rowp + p);
+        Mem::st(rowp + k, b);
+        Mem::st(rowp + p, a);
+      }
+      if (tid_all == 0) {
+        double a = Mem::ld(w.nu + k), b = Mem::ld(w.nu + p);
+        Mem::st(w.nu + k, b); Mem::st(w.nu + p, a);
+        a = Mem::ld(w.nu0 + k); b = Mem::ld(w.nu0 + p);
+        Mem::st(w.nu0 + k, b); Mem::st(w.nu0 + p, a);
+        const int ia = Mem::ld(w.perm + k), ib = Mem::ld(w.perm + p);
+        Mem::st(w.perm + k, ib); Mem::st(w.perm + p, ia);
+      }
+    }
+    sync();
+    // reflector H = I - (2 / u^dag u) u u^dag with H x = beta e_k, |beta| = |x|
+    if (worker == 0) {
+      double x2 = 0.0;
+      for (int i = k + lane; i < m; i += 32) {
+        const double2 x = Mem::ld(W + (int64_t)i * ld + k);
+        x2 = fma(x.x, x.x, fma(x.y, x.y, x2));
+      }
+      x2 = warp_sum(x2);
+      const double xn = sqrt(x2);
+      const double2 x0 = Mem::ld(W + (int64_t)k * ld + k);
+      const double a0 = hypot(x0.x, x0.y);
+      double2 beta;
+      if (a0 > 0.0) beta = make_double2(-x0.x / a0 * xn, -x0.y / a0 * xn);
+      else beta = make_double2(-xn, 0.0);
+      const double uu = 2.0 * x2 + 2.0 * xn * a0;
+      for (int i = k + lane; i < m; i += 32) {
+        double2 x = Mem::ld(W + (int64_t)i * ld + k);
+        if (i == k) x = make_double2(x.x - beta.x, x.y - beta.y);
+        Mem::st(w.u + i, x);
+        Mem::st(W + (int64_t)i * ld + k, i == k ? beta : make_double2(0.0, 0.0));
+      }
+      if (lane == 0) Mem::st(w.scal, uu > 0.0 ? 2.0 / uu : 0.0);
+    }
+    sync();
+    // trailing update W[k:, j] -= (2/u^dag u) u (u^dag W[k:, j]) for j > k, 32 columns x 8 row chunks per CTA
+    const double sc = Mem::ld(w.scal);
+    const int ncols = n - k - 1;
+    const int ntiles = (ncols + 31) / 32;
+    if (sc != 0.0) {
+      for (int tile = rank; tile < ntiles; tile += nctas) {
+        const int j = k + 1 + tile * 32 + lane;
+        double pr = 0.0, pim = 0.0;
+        if (j < n) {
+          for (int i = k + warp; i < m; i += nwarps) {
+            const double2 ui = Mem::ld(w.u + i);
+            const double2 x = Mem::ld(W + (int64_t)i * ld + j);
+            pr = fma(ui.x, x.x, fma(ui.y, x.y, pr));      // conj(u_i) x
+            pim = fma(ui.x, x.y, fma(-ui.y, x.x, pim));
+          }
+        }
+        red_d[warp][lane] = pr;
+        __syncthreads();
+        double wr = 0.0;
+        for (int x = 0; x < nwarps; ++x) wr += red_d[x][lane];
+        __syncthreads();
+        red_d[warp][lane] = pim;
+        __syncthreads();
+        double wi = 0.0;
+        for (int x = 0; x < nwarps; ++x) wi += red_d[x][lane];
+        __syncthreads();
+        wr *= sc;
+        wi *= sc;
+        if (j < n) {
+          for (int i = k + warp; i < m; i += nwarps) {
+            const double2 ui = Mem::ld(w.u + i);
+            double2 x = Mem::ld(W + (int64_t)i * ld + j);
+            x.x -= ui.x * wr - ui.y * wi;
+            x.y -= ui.x * wi + ui.y * wr;
+            Mem::st(W + (int64_t)i * ld + j, x);
+          }
+        }
+        __syncthreads();
+        if (warp == 0 && j < n) {       // downdate the partial norm, recompute on cancellation
+          const double2 r = Mem::ld(W + (int64_t)k * ld + j);
+          double v = Mem::ld(w.nu + j) - (r.x * r.x + r.y * r.y);
+          if (v <= 1.4901161193847656e-8 * Mem::ld(w.nu0 + j)) {
+            v = 0.0;
+            for (int i = k + 1; i < m; ++i) {
+              const double2 x = Mem::ld(W + (int64_t)i * ld + j);
+              v = fma(x.x, x.x, fma(x.y, x.y, v));
+            }
+            Mem::st(w.nu0 + j, v);
+          }
+          Mem::st(w.nu + j, v);
+        }
+      }
+    } else {
+      for (int tile = rank; tile < ntiles; tile += nctas) {
+        const int j = k + 1 + tile * 32 + lane;
+        if (warp == 0 && j < n) {
+          const double2 r = Mem::ld(W + (int64_t)k * ld + j);
+          Mem::st(w.nu + j, fmax(Mem::ld(w.nu + j) - (r.x * r.x + r.y * r.y), 0.0));
+        }
+      }
+    }
+    sync();
+  }
+
+  // ---- R^dag: conjugate rows 0..K-1 in place; they are the Jacobi columns ------------
+  const int64_t kn = (int64_t)K * n;
+  for (int64_t e = tid_all; e < kn; e += threads_all) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    double2* a = W + (int64_t)i * ld + j;
+    const double2 x = Mem::ld(a);
+    Mem::st(a, make_double2(x.x, -x.y));
+  }
+  sync();
+  for (int j = worker; j < K; j += workers) {
+    const double2* a = W + (int64_t)j * ld;
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double2 x = Mem::ld(a + i);
+      acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) Mem::st(w.nrm + j, acc);
+  }
+  sync();
+
+  // ---- one-sided Jacobi on the K columns (length n) of R^dag -----------------------------
+  const double tol = kEps * (double)max(n, 32);
+  const double tol2 = tol * tol;
+  const double floor2 = (32.0 * kEps) * (32.0 * kEps) * fro2;
+  const int mp = K + (K & 1);
+  int sweep = 0;
+  bool converged = K < 2;
+  for (; !converged && sweep < max_sweeps; ++sweep) {
+    if (sweep > 0) {          // fresh squared norms at the start of every sweep
+      for (int j = worker; j < K; j += workers) {
+        const double2* a = W + (int64_t)j * ld;
+        double acc = 0.0;
+        for (int i = lane; i < n; i += 32) {
+          const double2 x = Mem::ld(a + i);
+          acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) Mem::st(w.nrm + j, acc);
+      }
+      sync();
+    }
+    for (int r = 0; r < mp - 1; ++r) {
+      bool rot = false;
+      for (int kk = worker; kk < mp / 2; kk += workers) {
+        int p, q;
+        rr_pair(kk, r, mp, p, q);
+        if (p >= K || q >= K) continue;
+        if (p > q) { const int t = p; p = q; q = t; }
+        rot |= jacobi_pair<Mem>(W, n, ld, w.nrm, p, q, tol2, floor2);
+      }
+      if (rot && lane == 0) Mem::st(w.flags + sweep, 1);
+      sync();
+    }
+    converged = Mem::ld(w.flags + sweep) == 0;
+  }
+
+  // ---- singular values (noise floor -> 0), descending, ties by column index -----------
+  for (int j = worker; j < K; j += workers) {
+    const double2* a = W + (int64_t)j * ld;
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      const double2 x = Mem::ld(a + i);
+      acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) Mem::st(w.nrm + j, acc <= floor2 ? 0.0 : sqrt(acc));
+  }
+  sync();
+  for (int j = tid_all; j < K; j += threads_all) {
+    const double vj = Mem::ld(w.nrm + j);
+    const double v = isnan(vj) ? -1.0 : vj;       // NaN ranks last: ranks stay a permutation
+    int rk = 0;
+    for (int q = 0; q < K; ++q) {
+      const double wq = Mem::ld(w.nrm + q);
+      const double x = isnan(wq) ? -1.0 : wq;
+      rk += (x > v) || (x == v && q < j);
+    }
+    Mem::st(w.ord + rk, j);
+  }
+  sync();
+  for (int r = tid_all; r < K; r += threads_all) S.sigma[r] = Mem::ld(w.nrm + Mem::ld(w.ord + r));
+  // Y[perm[j], r] = column ord[r] of R^dag, row j, divided by its norm
+  for (int64_t e = tid_all; e < kn; e += threads_all) {
+    const int r = (int)(e / n), j = (int)(e % n);
+    const int c = Mem::ld(w.ord + r);
+    const double sv = Mem::ld(w.nrm + c);
+    double2 y = make_double2(0.0, 0.0);
+    if (sv > 0.0) {
+      const double2 a = Mem::ld(W + (int64_t)c * ld + j);
+      y = make_double2(a.x / sv, a.y / sv);
+    }
+    S.Y[(int64_t)r * n + Mem::ld(w.perm + j)] = y;
+  }
+  if (tid_all == 0) *S.status = converged ? sweep : -1;
+}
+
+struct CtaSync {
+  __device__ void operator()() const { __syncthreads(); }
+};
+struct ClusterSync {
+  __device__ void operator()() const { cluster_sync_all(); }
+};
+
+// shared-memory layout of the one-CTA kernel (offsets in bytes)
+struct SmemLayout {
+  int64_t W, u, nu, nu0, perm, nrm, ord, flags, pv, pi, scal, total;
+};
+__host__ __device__ inline SmemLayout smem_layout(int m, int n) {
+  auto al = [](int64_t x) { return (x + 15) & ~int64_t(15); };
+  const int K = m < n ? m : n;
+  SmemLayout L;
+  int64_t o = 0;
+  L.W = o; o = al(o + 16LL * m * odd_ld(n));
+  L.u = o; o = al(o + 16LL * m);
+  L.nu = o; o = al(o + 8LL * n);
+  L.nu0 = o; o = al(o + 8LL * n);
+  L.perm = o; o = al(o + 4LL * n);
+  L.nrm = o; o = al(o + 8LL * K);
+  L.ord = o; o = al(o + 4LL * K);
+  L.flags = o; o = al(o + 4LL * (kJacobiMaxSweeps + 1));
+  L.pv = o; o = al(o + 8);
+  L.pi = o; o = al(o + 4);
+  L.scal = o; o = al(o + 16);
+  L.total = o;
+  return L;
+}
+
+__global__ void __launch_bounds__(kSvdThreads, 1) jacobi_cta_kernel(const SvdSector* __restrict__ secs,
+                                                                 int max_sweeps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SvdSector S = secs[blockIdx.x];
+  const SmemLayout L = smem_layout(S.m, S.n);
+  Work w;
+  w.W = reinterpret_cast<double2*>(smem_raw + L.W);
+  w.u = reinterpret_cast<double2*>(smem_raw + L.u);
+  w.nu = reinterpret_cast<double*>(smem_raw + L.nu);
+  w.nu0 = reinterpret_cast<double*>(smem_raw + L.nu0);
+  w.perm = reinterpret_cast<int*>(smem_raw + L.perm);
+  w.nrm = reinterpret_cast<double*>(smem_raw + L.nrm);
+  w.ord = reinterpret_cast<int*>(smem_raw + L.ord);
+  w.flags = reinterpret_cast<int*>(smem_raw + L.flags);
+  w.pv = reinterpret_cast<double*>(smem_raw + L.pv);
+  w.pi = reinterpret_cast<int*>(smem_raw + L.pi);
+  w.scal = reinterpret_cast<double*>(smem_raw + L.scal);
+  svd_sector<PlainMem>(S, w, 0, 1, CtaSync{}, max_sweeps);
+}
+
+__global__ void __launch_bounds__(kSvdThreads) jacobi_cluster_kernel(const SvdSector* __restrict__ secs,
+                                                                     int cluster, int max_sweeps) {
+  const int rank = (int)cluster_rank();
+  const SvdSector S = secs[blockIdx.x / cluster];
+  Work w;
+  w.W = S.work;
+  w.u = S.uwork;
+  w.nu = S.norms;
+  w.nu0 = S.norms + S.n;
+  w.perm = S.order;
+  w.nrm = S.norms + 2 * S.n;
+  w.ord = S.order + S.n;
+  w.flags = S.flags;
+  w.pv = S.pivv;
+  w.pi = S.flags + kJacobiMaxSweeps + 1;
+  w.scal = S.pivv + kMaxCluster;
+  svd_sector<L2Mem>(S, w, rank, cluster, ClusterSync{}, max_sweeps);
+}
+
+bool g_cta_attr = false;
+int g_cluster = 0;
 
 }  // namespace
 
-cudaError_t launch_svd(const SvdSector* d_secs, int n_secs, int smem_bytes, int max_sweeps, cudaStream_t st) {
+int64_t svd_smem_need(int m, int n) { return smem_layout(m, n).total; }
+
+int svd_cluster_size() {
+  if (g_cluster) return g_cluster;
+  int c = 8;
+  if (cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+      cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(kSvdThreads);
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = 16;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, jacobi_cluster_kernel, &cfg) == cudaSuccess && n >= 4) c = 16;
+  }
+  cudaGetLastError();
+  g_cluster = c;
+  return c;
+}
+
+cudaError_t launch_svd_cta(const SvdSector* d_secs, int n_secs, int smem_bytes, int max_sweeps, cudaStream_t st) {
   if (n_secs <= 0) return cudaSuccess;
-  if (!g_svd_attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (!g_cta_attr) {
+    cudaError_t e = cudaFuncSetAttribute(jacobi_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSvdSmemMax);
     if (e != cudaSuccess) return e;
-    g_svd_attr_set = true;
+    g_cta_attr = true;
   }
   count_launch();
-  jacobi_svd_kernel<<<n_secs, kSvdThreads, smem_bytes, st>>>(d_secs, max_sweeps);
+  jacobi_cta_kernel<<<n_secs, kSvdThreads, smem_bytes, st>>>(d_secs, max_sweeps);
   return cudaGetLastError();
 }
 
-// Layout of the scratch of the standalone entry point: descriptors, then per
-// sector the Jacobi matrix (when not staged), norms and order.
-struct SvdScratchLayout {
-  int64_t desc_bytes = 0;
-  std::vector<int64_t> work_off, norm_off, ord_off;
-  int64_t total = 0;
-};
+cudaError_t launch_svd_cluster(const SvdSector* d_secs, int n_secs, int max_sweeps, cudaStream_t st) {
+  if (n_secs <= 0) return cudaSuccess;
+  const int cl = svd_cluster_size();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_secs * cl);
+  cfg.blockDim = dim3(kSvdThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = cl;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, d_secs, cl, max_sweeps);
+}
 
-static int64_t align256(int64_t x) { return (x + 255) & ~int64_t(255); }
-
-static bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L) {
+bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L) {
+  L.mode.assign(ns, kSvdSmem);
   L.work_off.assign(ns, -1);
-  L.norm_off.assign(ns, 0);
-  L.ord_off.assign(ns, 0);
-  int64_t off = align256((int64_t)sizeof(SvdSector) * ns);
-  L.desc_bytes = off;
+  L.v_off.assign(ns, -1);
+  L.norm_off.assign(ns, -1);
+  L.ord_off.assign(ns, -1);
+  L.flag_off.assign(ns, -1);
+  L.piv_off.assign(ns, -1);
+  L.smem = 0;
+  int64_t off = 0;
+  auto a256 = [](int64_t x) { return (x + 255) & ~int64_t(255); };
   for (int k = 0; k < ns; ++k) {
     if (m[k] < 1 || n[k] < 1) return false;
-    if (svd_smem_need(m[k], n[k]) > kSvdSmemMax) {
-      L.work_off[k] = off;
-      off = align256(off + 16LL * m[k] * n[k]);
-      L.norm_off[k] = off;
-      off = align256(off + 8LL * m[k]);
-      L.ord_off[k] = off;
-      off = align256(off + 4LL * m[k]);
+    const int64_t need = svd_smem_need(m[k], n[k]);
+    if (need <= kSvdSmemMax) {
+      L.smem = std::max<int>(L.smem, (int)need);
+      continue;
     }
+    const int64_t M = m[k], N = n[k], Kk = std::min(m[k], n[k]);
+    L.mode[k] = kSvdCluster;
+    L.work_off[k] = off; off = a256(off + 16 * M * odd_ld(n[k]));
+    L.v_off[k] = off;    off = a256(off + 16 * M);                      // Householder vector
+    L.norm_off[k] = off; off = a256(off + 8 * (2 * N + Kk));            // nu, nu0, nrm
+    L.ord_off[k] = off;  off = a256(off + 4 * (N + Kk));                // perm, ord
+    L.flag_off[k] = off; off = a256(off + 4 * (kJacobiMaxSweeps + 1 + kMaxCluster));   // flags, pivot index
+    L.piv_off[k] = off;  off = a256(off + 8 * (kMaxCluster + 2));       // pivot value, scalars
   }
   L.total = off;
   return true;
+}
+
+void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base) {
+  S.mode = L.mode[k];
+  if (S.mode != kSvdCluster) return;
+  S.work = reinterpret_cast<double2*>(base + L.work_off[k]);
+  S.uwork = reinterpret_cast<double2*>(base + L.v_off[k]);
+  S.norms = reinterpret_cast<double*>(base + L.norm_off[k]);
+  S.order = reinterpret_cast<int*>(base + L.ord_off[k]);
+  S.flags = reinterpret_cast<int*>(base + L.flag_off[k]);
+  S.pivv = reinterpret_cast<double*>(base + L.piv_off[k]);
+}
+
+cudaError_t launch_svd_all(const SvdSector* d_cta, int n_cta, const SvdSector* d_cl, int n_cl, int smem,
+                           cudaStream_t st, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+  // small sectors on the side stream, large ones on the main stream, joined afterwards
+  cudaError_t e = cudaSuccess;
+  if (n_cta > 0 && n_cl > 0 && side) {
+    if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_svd_cta(d_cta, n_cta, smem, kJacobiMaxSweeps, side)) != cudaSuccess) return e;
+    if ((e = launch_svd_cluster(d_cl, n_cl, kJacobiMaxSweeps, st)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(st, join, 0);
+  }
+  if ((e = launch_svd_cluster(d_cl, n_cl, kJacobiMaxSweeps, st)) != cudaSuccess) return e;
+  return launch_svd_cta(d_cta, n_cta, smem, kJacobiMaxSweeps, st);
 }
 
 }  // namespace mps
@@ -244,7 +667,7 @@ extern "C" int64_t mps_svd_work_bytes(int n_sectors, const int* m, const int* n)
   if (n_sectors < 0 || (n_sectors > 0 && (!m || !n))) return -1;
   SvdScratchLayout L;
   if (!svd_layout(n_sectors, m, n, L)) return -1;
-  return L.total;
+  return ((int64_t)sizeof(SvdSector) * n_sectors + 255) / 256 * 256 + L.total;
 }
 
 extern "C" int mps_svd_sectors(int n_sectors, const int* m, const int* n,
@@ -259,33 +682,34 @@ extern "C" int mps_svd_sectors(int n_sectors, const int* m, const int* n,
     return MPS_EINVAL;
   if (d_rowscale && !row_off) return MPS_EINVAL;
   SvdScratchLayout L;
-  if (!svd_layout(n_sectors, m, n, L) || work_bytes < L.total) return MPS_EINVAL;
+  if (!svd_layout(n_sectors, m, n, L)) return MPS_EINVAL;
+  const int64_t desc = ((int64_t)sizeof(SvdSector) * n_sectors + 255) / 256 * 256;
+  if (work_bytes < desc + L.total) return MPS_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  std::vector<SvdSector> secs(n_sectors);
-  char* base = (char*)d_work;
-  int smem = 0;
+  std::vector<SvdSector> cta, cl;
+  char* base = (char*)d_work + desc;
   for (int k = 0; k < n_sectors; ++k) {
-    SvdSector& S = secs[k];
+    SvdSector S = {};
     S.theta = reinterpret_cast<const double2*>(d_mats) + mat_off[k];
     S.rowscale = d_rowscale ? d_rowscale + row_off[k] : nullptr;
     S.m = m[k];
     S.n = n[k];
-    S.smem = L.work_off[k] < 0;
-    S.work = S.smem ? nullptr : reinterpret_cast<double2*>(base + L.work_off[k]);
-    S.norms = S.smem ? nullptr : reinterpret_cast<double*>(base + L.norm_off[k]);
-    S.order = S.smem ? nullptr : reinterpret_cast<int*>(base + L.ord_off[k]);
+    svd_fill_scratch(S, L, k, base);
     S.sigma = d_sigma + sig_off[k];
     S.Y = reinterpret_cast<double2*>(d_y) + y_off[k];
     S.status = d_status + k;
-    if (S.smem) smem = std::max<int>(smem, (int)svd_smem_need(m[k], n[k]));
+    (S.mode == kSvdCluster ? cl : cta).push_back(S);
   }
-  if (cudaMemcpyAsync(d_work, secs.data(), sizeof(SvdSector) * n_sectors, cudaMemcpyHostToDevice, st) !=
+  std::vector<SvdSector> all(cta);
+  all.insert(all.end(), cl.begin(), cl.end());
+  if (cudaMemcpyAsync(d_work, all.data(), sizeof(SvdSector) * all.size(), cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return MPS_ECUDA;
-  if (launch_svd(reinterpret_cast<const SvdSector*>(d_work), n_sectors, smem, kJacobiMaxSweeps, st) !=
-      cudaSuccess)
+  const SvdSector* d_all = reinterpret_cast<const SvdSector*>(d_work);
+  if (launch_svd_all(d_all, (int)cta.size(), d_all + cta.size(), (int)cl.size(), L.smem, st, nullptr, nullptr,
+                     nullptr) != cudaSuccess)
     return MPS_ECUDA;
-  // the descriptors live in pageable host memory: finish the copy before returning
+  // the descriptors came from pageable host memory: finish before returning
   if (cudaStreamSynchronize(st) != cudaSuccess) return MPS_ECUDA;
   return MPS_OK;
 }

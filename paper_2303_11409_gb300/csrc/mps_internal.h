@@ -74,18 +74,35 @@ struct ThetaTask {            // one (l, r) block pair of one update: sum_m G * 
 };
 struct TileRef { int task; int ti; int tj; };
 
+constexpr int kSvdSmem = 0;      // one CTA, Jacobi matrix staged in shared memory
+constexpr int kSvdCluster = 1;   // a thread-block cluster, Jacobi matrix in L2
+
 struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   const double2* theta;       // row-major m x n
   const double* rowscale;     // m values (lambda of the left bond), or nullptr
-  double2* work;              // n x m column-major scratch (the Jacobi matrix A = M^dag)
-  double* norms;              // m doubles scratch
-  int* order;                 // m ints scratch
+  double2* work;              // cluster mode: M / R / R^dag, m x ld row-major (ld = n | 1)
+  double2* uwork;             // cluster mode: Householder vector, m
+  double* norms;              // cluster mode: 2n + K doubles (pivot norms, reference norms, Jacobi norms)
+  int* order;                 // cluster mode: n + K ints (column permutation, singular value order)
+  int* flags;                 // cluster mode: per-sweep rotation flags, then per-CTA pivot indices
+  double* pivv;               // cluster mode: per-CTA pivot values, then two scalars
   double* sigma;              // out: min(m, n) values, descending
   double2* Y;                 // out: n x min(m, n) column-major right singular vectors
-  int* status;                // out: sweeps used, or -1 when not converged
+  int* status;                // out: Jacobi sweeps used, or -1 when not converged
   int m, n;
-  int smem;                   // 1 when the CTA stages A in shared memory
+  int mode;                   // kSvdSmem or kSvdCluster
 };
+
+// Scratch layout of a batch of sector SVDs (cluster-mode sectors only need global scratch).
+struct SvdScratchLayout {
+  std::vector<int> mode;
+  std::vector<int64_t> work_off, v_off, norm_off, ord_off, flag_off, piv_off;
+  int smem = 0;               // dynamic shared memory of the one-CTA kernel
+  int64_t total = 0;
+};
+bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L);
+// Points the cluster-mode scratch of sector k at base + the layout's offsets; sets S.mode.
+void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base);
 
 struct SelectSector {         // one sector's spectrum as seen by the truncation
   const double* sigma;        // descending
@@ -133,6 +150,8 @@ struct PinnedBuf {
 struct Stats {
   int n_sectors = 0, n_triples = 0, max_sweeps = 0, tie_band = 0;
   double norm_all = 0, norm_kept = 0;
+  int batch_sectors = 0, batch_sweeps_max = 0;   // over every update of the last call
+  int64_t batch_sweeps_sum = 0;
 };
 
 struct KStat { int64_t launches = 0; double ms = 0, flops = 0, bytes = 0; };
@@ -159,6 +178,8 @@ struct mps_s {
   mps::DevBuf work;                       // per-update workspace
   mps::PinnedBuf pin_in, pin_out;         // staging of descriptors and results
   cudaEvent_t staged = nullptr;           // last upload out of pin_in has completed
+  cudaStream_t side = nullptr;            // second stream for the one-CTA SVD kernel
+  cudaEvent_t fork = nullptr, join = nullptr;
   std::string err;
   mps::Stats stats;
   bool profiling = false;
@@ -174,7 +195,10 @@ namespace mps {
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_theta(const ThetaTask* d_tasks, const TileRef* d_tiles, int n_tiles, cudaStream_t st);
-cudaError_t launch_svd(const SvdSector* d_secs, int n_secs, int smem_bytes, int max_sweeps, cudaStream_t st);
+// Small sectors on `side` (if given), large ones as clusters on `st`; `st` waits for both.
+cudaError_t launch_svd_all(const SvdSector* d_cta, int n_cta, const SvdSector* d_cl, int n_cl, int smem,
+                           cudaStream_t st, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+int svd_cluster_size();
 cudaError_t launch_select(const SelectSector* d_secs, const SelectTask* d_tasks, int n_tasks,
                           int* d_kept, SelectResult* d_res, cudaStream_t st);
 cudaError_t launch_gemm(const GemmTask* d_tasks, const TileRef* d_tiles, int n_tiles, cudaStream_t st);
@@ -190,7 +214,7 @@ cudaError_t launch_amplitude(const AmpStep* d_steps, int L, int n_cfg, double2* 
 // Shared-memory budget of the Jacobi kernel and its staging rule.
 constexpr int kSvdThreads = 256;
 constexpr int kSvdSmemMax = 200 * 1024;
-inline int64_t svd_smem_need(int m, int n) { return 16LL * m * n + 8LL * m + 4LL * m + 64; }
+int64_t svd_smem_need(int m, int n);
 constexpr int kJacobiMaxSweeps = 40;
 constexpr double kTieRel = 1e-11;
 

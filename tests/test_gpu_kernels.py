@@ -22,8 +22,10 @@ def _check(M, sig, Y, sweeps, tol=1e-12):
     assert np.max(np.abs(np.linalg.norm(M @ Yg, axis=0) - sig[good])) <= 1e-12 * smax * np.sqrt(M.shape[1])
 
 
+# one-CTA shared-memory sectors (wide and tall), cluster sectors (wide, tall with V, and
+# more than 512 rows, the register-cache limit)
 SHAPES = [(1, 1), (1, 7), (7, 1), (2, 2), (5, 5), (30, 20), (20, 30), (64, 64), (100, 110),
-          (150, 170), (200, 90), (33, 257)]
+          (150, 170), (200, 90), (33, 257), (600, 300), (300, 600), (420, 410)]
 
 
 def test_svd_random_shapes(gpu_lib):
