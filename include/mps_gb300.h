@@ -267,6 +267,37 @@ MPS_API int mps_svd_sectors(int n_sectors, const int* m, const int* n,
                     double* d_y, const int64_t* y_off,
                     int* d_status, void* d_work, int64_t work_bytes, void* cuda_stream);
 
+/*
+ * mps_svd_sectors_noalloc - the batched sector SVD of mps_svd_sectors for callers
+ * that must not allocate device memory.  The paper has no counterpart to this
+ * entry point; it exists for callers whose device memory is owned by someone
+ * else: code running under a framework's memory manager that reserves the whole
+ * budget, hot loops where the implicit device synchronisation of cudaMalloc and
+ * cudaFree is not acceptable, and callers that are not allowed to hand the
+ * library a scratch buffer at all.
+ *   Arguments, layouts and outputs are those of mps_svd_sectors, without d_work
+ *   and work_bytes.  Instead of caller scratch it uses one file-scope device
+ *   array of MPS_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the
+ *   library holds until the process exits.
+ *   Limit: mps_svd_work_bytes() of the batch must not exceed
+ *   MPS_NOALLOC_SCRATCH_BYTES; larger batches are rejected with MPS_ENOMEM before
+ *   anything runs (split the batch, or use mps_svd_sectors).
+ *   The first call on a device looks up the array's device address with that
+ *   device current; make that first call before any stream capture.
+ *   It calls no cudaMalloc, cudaFree or other allocating routine.  All calls
+ *   share the one array, and each call overwrites every part of it that it reads,
+ *   so nothing needs clearing between calls; calls that overlap on the GPU (other
+ *   streams, other host threads) race on it and must be serialised by the caller.
+ *   Like mps_svd_sectors it synchronises cuda_stream before returning.
+ */
+#define MPS_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+MPS_API int mps_svd_sectors_noalloc(int n_sectors, const int* m, const int* n,
+                                    const double* d_mats, const int64_t* mat_off,
+                                    const double* d_rowscale, const int64_t* row_off,
+                                    double* d_sigma, const int64_t* sig_off,
+                                    double* d_y, const int64_t* y_off,
+                                    int* d_status, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,4 +9,5 @@ from ._binding import (EXPORTED, LIB_PATH, MPS, MPS_BF16X3, MPS_EINVAL, MPS_ECHA
                        JacobiNotConverged, KERNEL_KINDS, MPSError, apply_gate2_batch, gate_length, launch_count, lib,
                        plan_sectors,
                        svd_sectors, svd_work_bytes)
+from ._binding import MPS_NOALLOC_SCRATCH_BYTES, svd_sectors_noalloc  # noqa: F401
 from . import models, tebd  # noqa: F401

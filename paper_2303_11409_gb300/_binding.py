@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmps_gb300.so")
 MPS_OK, MPS_EINVAL, MPS_ECHARGE, MPS_ENOMEM, MPS_ENOCONV, MPS_ECUDA, MPS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 MPS_FP64, MPS_TF32, MPS_BF16X3 = 0, 1, 2
 MPS_MAX_D = 8
+MPS_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 KERNEL_KINDS = ("theta", "svd", "select", "lambda", "scatter", "gemm", "expect", "amplitude")
 STATUS_NAMES = {0: "MPS_OK", -1: "MPS_EINVAL", -2: "MPS_ECHARGE", -3: "MPS_ENOMEM", -4: "MPS_ENOCONV",
                 -5: "MPS_ECUDA", -6: "MPS_ETIMEOUT"}
@@ -79,6 +80,8 @@ _SIGS = {
     "mps_reset_kernel_stats": (ctypes.c_int, [_h]),
     "mps_launch_count": (ctypes.c_int64, []),
     "mps_svd_work_bytes": (ctypes.c_int64, [ctypes.c_int, _intp, _intp]),
+    "mps_svd_sectors_noalloc": (ctypes.c_int, [ctypes.c_int, _intp, _intp, _vp, _i64p, _vp, _i64p, _vp, _i64p,
+                                               _vp, _i64p, _vp, _vp]),
     "mps_svd_sectors": (ctypes.c_int, [ctypes.c_int, _intp, _intp, _vp, _i64p, _vp, _i64p, _vp, _i64p, _vp,
                                        _i64p, _vp, _vp, ctypes.c_int64, _vp]),
 }
@@ -396,5 +399,51 @@ def svd_sectors(mats, rowscales=None, stream=None):
     out = []
     for k in range(len(mats)):
         Y = y[y_off[k]:y_off[k] + ns[k] * ks[k]].reshape(ks[k], ns[k]).T   # column-major n x k
+        out.append((sig[s_off[k]:s_off[k] + ks[k]].copy(), Y.copy(), int(sts[k])))
+    return out
+
+
+def svd_sectors_noalloc(mats, rowscales=None, stream=None):
+    """The same batched sector SVD through mps_svd_sectors_noalloc.
+
+    For callers that must not allocate device memory: no scratch buffer is passed
+    and the library allocates nothing (its scratch is a fixed device array of
+    MPS_NOALLOC_SCRATCH_BYTES).  torch holds only the inputs and outputs here.
+    Returns [(sigma, Y, sweeps)] like svd_sectors.
+    """
+    import torch
+    dev = torch.device("cuda")
+    ms = [a.shape[0] for a in mats]
+    ns = [a.shape[1] for a in mats]
+    ks = [min(a, b) for a, b in zip(ms, ns)]
+    mat_off = np.cumsum([0] + [a * b for a, b in zip(ms, ns)])[:-1].astype(np.int64)
+    y_off = np.cumsum([0] + [n * k for n, k in zip(ns, ks)])[:-1].astype(np.int64)
+    s_off = np.cumsum([0] + ks)[:-1].astype(np.int64)
+    r_off = np.cumsum([0] + ms)[:-1].astype(np.int64)
+    flat = np.concatenate([np.ascontiguousarray(a, np.complex128).reshape(-1) for a in mats])
+    d_mats = torch.from_numpy(flat.view(np.float64).copy()).to(dev)
+    d_sig = torch.zeros(sum(ks), dtype=torch.float64, device=dev)
+    d_y = torch.zeros(2 * sum(n * k for n, k in zip(ns, ks)), dtype=torch.float64, device=dev)
+    d_st = torch.zeros(len(mats), dtype=torch.int32, device=dev)
+    d_rs = None
+    if rowscales is not None:
+        d_rs = torch.from_numpy(np.concatenate([np.asarray(r, np.float64) for r in rowscales])).to(dev)
+    st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    m_a = np.asarray(ms, np.intc)
+    n_a = np.asarray(ns, np.intc)
+    rc = lib.mps_svd_sectors_noalloc(len(mats), _ptr(m_a, _intp), _ptr(n_a, _intp), d_mats.data_ptr(),
+                                     _ptr(mat_off, _i64p), d_rs.data_ptr() if d_rs is not None else None,
+                                     _ptr(r_off, _i64p) if d_rs is not None else None,
+                                     d_sig.data_ptr(), _ptr(s_off, _i64p), d_y.data_ptr(), _ptr(y_off, _i64p),
+                                     d_st.data_ptr(), st)
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_svd_sectors_noalloc")
+    torch.cuda.synchronize()
+    sig = d_sig.cpu().numpy()
+    y = d_y.cpu().numpy().view(np.complex128)
+    sts = d_st.cpu().numpy()
+    out = []
+    for k in range(len(mats)):
+        Y = y[y_off[k]:y_off[k] + ns[k] * ks[k]].reshape(ks[k], ns[k]).T
         out.append((sig[s_off[k]:s_off[k] + ks[k]].copy(), Y.copy(), int(sts[k])))
     return out

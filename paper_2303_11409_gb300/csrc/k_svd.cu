@@ -34,6 +34,7 @@
 // test; two rsqrt, one sqrt and one division per rotation; column norms tracked
 // through the exact 2x2 relations within a sweep).
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "mps_internal.h"
@@ -710,6 +711,74 @@ extern "C" int mps_svd_sectors(int n_sectors, const int* m, const int* n,
                      nullptr) != cudaSuccess)
     return MPS_ECUDA;
   // the descriptors came from pageable host memory: finish before returning
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MPS_ECUDA;
+  return MPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant: the scratch is a file-scope device array.  In host
+// code the array's name is only a host-side stand-in, so its device address is
+// looked up once per device (with that device current) and passed to the
+// kernels; device code never names it.
+// ---------------------------------------------------------------------------
+namespace {
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MPS_NOALLOC_SCRATCH_BYTES];
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+extern "C" int mps_svd_sectors_noalloc(int n_sectors, const int* m, const int* n,
+                                       const double* d_mats, const int64_t* mat_off,
+                                       const double* d_rowscale, const int64_t* row_off,
+                                       double* d_sigma, const int64_t* sig_off,
+                                       double* d_y, const int64_t* y_off,
+                                       int* d_status, void* cuda_stream) {
+  if (n_sectors == 0) return MPS_OK;
+  if (n_sectors < 0 || !m || !n || !d_mats || !mat_off || !d_sigma || !sig_off || !d_y || !y_off || !d_status)
+    return MPS_EINVAL;
+  if (d_rowscale && !row_off) return MPS_EINVAL;
+  SvdScratchLayout L;
+  if (!svd_layout(n_sectors, m, n, L)) return MPS_EINVAL;
+  const int64_t desc = ((int64_t)sizeof(SvdSector) * n_sectors + 255) / 256 * 256;
+  if (desc + L.total > (int64_t)MPS_NOALLOC_SCRATCH_BYTES) return MPS_ENOMEM;   // over the fixed scratch
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MPS_ECUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return MPS_EINVAL;
+  void* d_work = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return MPS_ECUDA;
+      g_noalloc_addr[dev] = p;
+    }
+    d_work = g_noalloc_addr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::vector<SvdSector> cta, cl;
+  char* base = (char*)d_work + desc;
+  for (int k = 0; k < n_sectors; ++k) {
+    SvdSector S = {};
+    S.theta = reinterpret_cast<const double2*>(d_mats) + mat_off[k];
+    S.rowscale = d_rowscale ? d_rowscale + row_off[k] : nullptr;
+    S.m = m[k];
+    S.n = n[k];
+    svd_fill_scratch(S, L, k, base);
+    S.sigma = d_sigma + sig_off[k];
+    S.Y = reinterpret_cast<double2*>(d_y) + y_off[k];
+    S.status = d_status + k;
+    (S.mode == kSvdCluster ? cl : cta).push_back(S);
+  }
+  std::vector<SvdSector> all(cta);
+  all.insert(all.end(), cl.begin(), cl.end());
+  if (cudaMemcpyAsync(d_work, all.data(), sizeof(SvdSector) * all.size(), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return MPS_ECUDA;
+  const SvdSector* d_all = reinterpret_cast<const SvdSector*>(d_work);
+  if (launch_svd_all(d_all, (int)cta.size(), d_all + cta.size(), (int)cl.size(), L.smem, st, nullptr, nullptr,
+                     nullptr) != cudaSuccess)
+    return MPS_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return MPS_ECUDA;
   return MPS_OK;
 }
