@@ -33,6 +33,8 @@ L, D, N_PART, J, U, DT, CHI, CUTOFF = 64, 5, 64, 1.0, 2.0, 0.02, 512, 1e-10
 UPDATES_PER_STEP = 32 + 31 + 32
 METRIC = "two-site updates/s"
 WORKLOAD = "bose_hubbard_L64_nmax4_N64_J1_U2_dt0.02_chi512_cutoff1e-10_fp64"
+# --case small: the same model on L=32, chi=256, for profiler captures of every kernel on a small case
+SMALL = dict(L=32, N=32, CHI=256, WORKLOAD="bose_hubbard_L32_nmax4_N32_J1_U2_dt0.02_chi256_cutoff1e-10_fp64")
 # FP64 peak of the GB300 CUDA cores: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz.
 # (An FMA-chain probe measured 1.195 TFLOP/s, i.e. 2 FMA/clk/SM at the clock it ran.)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
@@ -49,7 +51,15 @@ def parse():
     p.add_argument("--max-prep", type=int, default=120)
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    p.add_argument("--case", default="full", choices=["full", "small"],
+                   help="small: L=32, chi=256 (for profiler captures); full: the benchmark workload")
+    a = p.parse_args()
+    if a.case == "small":
+        global L, N_PART, CHI, WORKLOAD, UPDATES_PER_STEP
+        L, N_PART, CHI, WORKLOAD = SMALL["L"], SMALL["N"], SMALL["CHI"], SMALL["WORKLOAD"]
+        UPDATES_PER_STEP = (L // 2) + (L - 1) // 2 + (L // 2)
+        a.no_cpu_baseline = True
+    return a
 
 
 def config(extra=None):
@@ -160,8 +170,8 @@ def oracle_sample(seconds: float, max_updates: int | None = None):
     import workloads as W
     st = synth.random_state(L, D, N_PART, CHI, seed=0, occ=W.mott_occupations(L))
     gate_of = otebd.bh_gates(L, D, J, U, DT)
-    order = [30, 32, 28, 34, 26, 36, 24, 38, 22, 40, 20, 42, 18, 44, 16, 46, 14, 48, 12, 50, 10, 52, 8, 54,
-             6, 56, 4, 58, 2, 60, 0, 62]
+    odd = list(range(0, L - 1, 2))
+    order = sorted(odd, key=lambda s: (abs(s - (L // 2 - 1)), s))     # middle bonds first
     n, t0 = 0, time.perf_counter()
     for s in order * 4:
         st.apply_gate2(s, gate_of(s, 0.5), CHI, CUTOFF)

@@ -207,7 +207,6 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   }
   const int64_t jac_base = ws;
   ws = a256(ws + JL.total);
-  const int svd_smem = JL.smem;
   const int64_t glen = gate_len(owner->d);
   for (int u = 0; u < nreq; ++u)
     if (reqs[u].h->d != owner->d) return fail(owner, MPS_EINVAL, "batched handles must share d");
@@ -346,20 +345,10 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     seltask.push_back(SelectTask{W[u].sel_first, (int)selsec.size(), reqs[u].chi, reqs[u].cutoff});
   }
   // largest sectors first so that the longest CTAs start earliest
-  // one list per kernel, most expensive sectors first so the longest CTAs start earliest
-  std::vector<SvdSector> svd_sorted;
-  int n_svd_cta = 0;
-  for (int mode : {kSvdSmem, kSvdCluster}) {
-    const size_t first = svd_sorted.size();
-    for (const SvdSector& S : svd)
-      if (S.mode == mode) svd_sorted.push_back(S);
-    std::stable_sort(svd_sorted.begin() + first, svd_sorted.end(), [](const SvdSector& a, const SvdSector& b) {
-      const double ca = (double)std::max(a.m, a.n) * std::min(a.m, a.n) * std::min(a.m, a.n);
-      const double cb = (double)std::max(b.m, b.n) * std::min(b.m, b.n) * std::min(b.m, b.n);
-      return ca > cb;
-    });
-    if (mode == kSvdSmem) n_svd_cta = (int)svd_sorted.size();
-  }
+  // group the sectors by SVD kernel and cluster size, most expensive first inside a group
+  std::vector<SvdSector> svd_sorted = svd;
+  std::vector<SvdGroup> svd_groups;
+  CUDA_OR_FAIL(owner, svd_group(svd_sorted, svd_groups));
 
   // ---- upload (one copy of all descriptors and gates) ---------------------------------
   const int64_t o_tasks = sg.put(tasks.data(), (int64_t)tasks.size());
@@ -394,10 +383,9 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     return launch_theta(reinterpret_cast<ThetaTask*>(dptr(desc_off + o_tasks)),
                         reinterpret_cast<TileRef*>(dptr(desc_off + o_tiles)), (int)tiles.size(), st);
   }));
-  CUDA_OR_FAIL(owner, timed(owner, MPS_K_SVD, !svd_sorted.empty(), svd_flops, svd_bytes, [&] {
+  CUDA_OR_FAIL(owner, timed(owner, MPS_K_SVD, !svd_sorted.empty(), svd_flops, svd_bytes, [&] {   // one or more kernels
     const SvdSector* d_svd = reinterpret_cast<SvdSector*>(dptr(desc_off + o_svd));
-    return launch_svd_all(d_svd, n_svd_cta, d_svd + n_svd_cta, (int)svd_sorted.size() - n_svd_cta, svd_smem, st,
-                          owner->side, owner->fork, owner->join);
+    return launch_svd_groups(d_svd, svd_groups, st, owner->side, kSvdSideStreams, owner->fork, owner->join);
   }));
   CUDA_OR_FAIL(owner, timed(owner, MPS_K_SELECT, nreq > 0, 0.0, sel_bytes, [&] {
     return launch_select(reinterpret_cast<SelectSector*>(dptr(desc_off + o_selsec)),
@@ -636,9 +624,11 @@ int mps_create(mps_t* out, int L, int d, const int32_t* site_charges, int precis
   cudaError_t e = cudaMalloc(&h->d_lambda, sizeof(double) * lam_total);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_sites, sizeof(double2) * site_total);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->staged, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  for (int i = 0; i < kSvdSideStreams && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join[i], cudaEventDisableTiming);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     if (h->d_lambda) cudaFree(h->d_lambda);
     if (h->d_sites) cudaFree(h->d_sites);
@@ -666,9 +656,11 @@ int mps_destroy(mps_t h) {
   if (h->d_lambda) cudaFree(h->d_lambda);
   if (h->d_sites) cudaFree(h->d_sites);
   if (h->staged) cudaEventDestroy(h->staged);
-  if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
+  for (int i = 0; i < kSvdSideStreams; ++i) {
+    if (h->side[i]) { cudaStreamSynchronize(h->side[i]); cudaStreamDestroy(h->side[i]); }
+    if (h->join[i]) cudaEventDestroy(h->join[i]);
+  }
   if (h->fork) cudaEventDestroy(h->fork);
-  if (h->join) cudaEventDestroy(h->join);
   for (auto& p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   h->work.release();

@@ -45,6 +45,8 @@ namespace {
 constexpr double kEps = 2.220446049250313e-16;
 constexpr int kMaxCached = 16;          // rows cached in registers per lane (n <= 512)
 constexpr int kMaxCluster = 16;
+constexpr int kMaxWarps = 16;
+constexpr int kBlockThreads = 384;      // block-Jacobi cluster kernel: 12 warps per CTA
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -196,11 +198,158 @@ struct Work {
 
 __host__ __device__ inline int odd_ld(int n) { return n | 1; }
 
-template <class Mem, class Sync>
-__device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int nctas, Sync sync, int max_sweeps) {
-  __shared__ double red_d[8][33];
-  __shared__ double red_v[8];
-  __shared__ int red_i[8];
+// Round-robin Jacobi sweeps: every round's disjoint pairs spread over all warps that
+// share the sector, one barrier per round.
+template <class Mem>
+struct JacobiRoundRobin {
+  template <class Sync>
+  __device__ int operator()(double2* W, int n, int ld, int K, const Work& w, int rank, int nctas, Sync sync,
+                            double tol2, double floor2, int max_sweeps, bool& converged) const {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int worker = rank * nwarps + warp, workers = nctas * nwarps;
+    const int mp = K + (K & 1);
+    int sweep = 0;
+    converged = K < 2;
+    for (; !converged && sweep < max_sweeps; ++sweep) {
+      if (sweep > 0) {          // fresh squared norms at the start of every sweep
+        for (int j = worker; j < K; j += workers) {
+          const double2* a = W + (int64_t)j * ld;
+          double acc = 0.0;
+          for (int i = lane; i < n; i += 32) {
+            const double2 x = Mem::ld(a + i);
+            acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+          }
+          acc = warp_sum(acc);
+          if (lane == 0) Mem::st(w.nrm + j, acc);
+        }
+        sync();
+      }
+      for (int r = 0; r < mp - 1; ++r) {
+        bool rot = false;
+        for (int kk = worker; kk < mp / 2; kk += workers) {
+          int p, q;
+          rr_pair(kk, r, mp, p, q);
+          if (p >= K || q >= K) continue;
+          if (p > q) { const int t = p; p = q; q = t; }
+          rot |= jacobi_pair<Mem>(W, n, ld, w.nrm, p, q, tol2, floor2);
+        }
+        if (rot && lane == 0) Mem::st(w.flags + sweep, 1);
+        sync();
+      }
+      converged = Mem::ld(w.flags + sweep) == 0;
+    }
+    return sweep;
+  }
+};
+
+// Block-Jacobi sweeps for a cluster sector (data in L2).  The K columns form
+// nb = 2 * nctas * g contiguous blocks; in block round r the blocks are paired by the
+// round-robin ordering and CTA `rank` takes the pairs rank, rank + nctas, ...: for each
+// it stages both blocks and their norms in shared memory, orthogonalises every cross
+// pair (cyclic shifts of the larger block against the smaller, so each inner round is
+// disjoint) and, in round 0, every pair inside each block, with CTA-local barriers
+// only, then writes the blocks back; one cluster barrier ends the round.  Every pair
+// is visited once per sweep.  g > 1 keeps two blocks within shared memory when the
+// sector is large for its cluster.
+struct JacobiBlocks {
+  double2* sm;   // 2 * bsmax columns of n complex (shared memory)
+  double* smn;   // 2 * bsmax norms (shared memory)
+  int bsmax;
+  int g;
+  template <class Sync>
+  __device__ int operator()(double2* W, int n, int ld, int K, const Work& w, int rank, int nctas, Sync sync,
+                            double tol2, double floor2, int max_sweeps, bool& converged) const {
+    __shared__ int s_rot;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int worker = rank * nwarps + warp, workers = nctas * nwarps;
+    const int nb = 2 * nctas * g;
+    int sweep = 0;
+    converged = K < 2;
+    for (; !converged && sweep < max_sweeps; ++sweep) {
+      if (sweep > 0) {
+        for (int j = worker; j < K; j += workers) {
+          const double2* a = W + (int64_t)j * ld;
+          double acc = 0.0;
+          for (int i = lane; i < n; i += 32) {
+            const double2 x = __ldcg(a + i);
+            acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+          }
+          acc = warp_sum(acc);
+          if (lane == 0) __stcg(w.nrm + j, acc);
+        }
+        sync();
+      }
+      if (tid == 0) s_rot = 0;
+      for (int r = 0; r < nb - 1; ++r) {
+       for (int pair = rank; pair < nb / 2; pair += nctas) {
+        int bp, bq;
+        rr_pair(pair, r, nb, bp, bq);
+        const int p0 = (int)((int64_t)K * bp / nb), sp = (int)((int64_t)K * (bp + 1) / nb) - p0;
+        const int q0 = (int)((int64_t)K * bq / nb), sq = (int)((int64_t)K * (bq + 1) / nb) - q0;
+        for (int64_t e = tid; e < (int64_t)sp * n; e += blockDim.x) {
+          const int c = (int)(e / n), i = (int)(e % n);
+          sm[e] = __ldcg(W + (int64_t)(p0 + c) * ld + i);
+        }
+        for (int64_t e = tid; e < (int64_t)sq * n; e += blockDim.x) {
+          const int c = (int)(e / n), i = (int)(e % n);
+          sm[(int64_t)bsmax * n + e] = __ldcg(W + (int64_t)(q0 + c) * ld + i);
+        }
+        for (int c = tid; c < sp; c += blockDim.x) smn[c] = __ldcg(w.nrm + p0 + c);
+        for (int c = tid; c < sq; c += blockDim.x) smn[bsmax + c] = __ldcg(w.nrm + q0 + c);
+        __syncthreads();
+        bool rot = false;
+        if (r == 0) {
+          for (int which = 0; which < 2; ++which) {
+            const int b = which ? sq : sp, base = which ? bsmax : 0;
+            const int mp = b + (b & 1);
+            for (int rr = 0; rr < mp - 1; ++rr) {
+              for (int k = warp; k < mp / 2; k += nwarps) {
+                int i, j;
+                rr_pair(k, rr, mp, i, j);
+                if (i < b && j < b)
+                  rot |= jacobi_pair<PlainMem>(sm, n, n, smn, base + min(i, j), base + max(i, j), tol2, floor2);
+              }
+              __syncthreads();
+            }
+          }
+        }
+        const bool swap = sp > sq;
+        const int sa = swap ? sq : sp, sb = swap ? sp : sq;
+        const int ba = swap ? bsmax : 0, bb = swap ? 0 : bsmax;
+        for (int t = 0; t < sb; ++t) {
+          for (int i = warp; i < sa; i += nwarps)
+            rot |= jacobi_pair<PlainMem>(sm, n, n, smn, ba + i, bb + (i + t) % sb, tol2, floor2);
+          __syncthreads();
+        }
+        if (rot && lane == 0) s_rot = 1;
+        for (int64_t e = tid; e < (int64_t)sp * n; e += blockDim.x) {
+          const int c = (int)(e / n), i = (int)(e % n);
+          __stcg(W + (int64_t)(p0 + c) * ld + i, sm[e]);
+        }
+        for (int64_t e = tid; e < (int64_t)sq * n; e += blockDim.x) {
+          const int c = (int)(e / n), i = (int)(e % n);
+          __stcg(W + (int64_t)(q0 + c) * ld + i, sm[(int64_t)bsmax * n + e]);
+        }
+        for (int c = tid; c < sp; c += blockDim.x) __stcg(w.nrm + p0 + c, smn[c]);
+        for (int c = tid; c < sq; c += blockDim.x) __stcg(w.nrm + q0 + c, smn[bsmax + c]);
+        __syncthreads();     // the next pair of this round reuses the staging buffers
+       }
+        sync();
+      }
+      if (tid == 0 && s_rot) __stcg(w.flags + sweep, 1);
+      sync();
+      converged = __ldcg(w.flags + sweep) == 0;
+    }
+    return sweep;
+  }
+};
+
+template <class Mem, class Sync, class Jacobi>
+__device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int nctas, Sync sync, int max_sweeps,
+                           Jacobi jacobi) {
+  __shared__ double red_d[kMaxWarps][33];
+  __shared__ double red_v[kMaxWarps];
+  __shared__ int red_i[kMaxWarps];
   const int m = S.m, n = S.n, K = min(m, n), ld = odd_ld(n);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int tid_all = rank * blockDim.x + tid, threads_all = nctas * blockDim.x;
@@ -398,37 +547,8 @@ __device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int ncta
   const double tol = kEps * (double)max(n, 32);
   const double tol2 = tol * tol;
   const double floor2 = (32.0 * kEps) * (32.0 * kEps) * fro2;
-  const int mp = K + (K & 1);
-  int sweep = 0;
-  bool converged = K < 2;
-  for (; !converged && sweep < max_sweeps; ++sweep) {
-    if (sweep > 0) {          // fresh squared norms at the start of every sweep
-      for (int j = worker; j < K; j += workers) {
-        const double2* a = W + (int64_t)j * ld;
-        double acc = 0.0;
-        for (int i = lane; i < n; i += 32) {
-          const double2 x = Mem::ld(a + i);
-          acc = fma(x.x, x.x, fma(x.y, x.y, acc));
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) Mem::st(w.nrm + j, acc);
-      }
-      sync();
-    }
-    for (int r = 0; r < mp - 1; ++r) {
-      bool rot = false;
-      for (int kk = worker; kk < mp / 2; kk += workers) {
-        int p, q;
-        rr_pair(kk, r, mp, p, q);
-        if (p >= K || q >= K) continue;
-        if (p > q) { const int t = p; p = q; q = t; }
-        rot |= jacobi_pair<Mem>(W, n, ld, w.nrm, p, q, tol2, floor2);
-      }
-      if (rot && lane == 0) Mem::st(w.flags + sweep, 1);
-      sync();
-    }
-    converged = Mem::ld(w.flags + sweep) == 0;
-  }
+  bool converged = false;
+  const int sweep = jacobi(W, n, ld, K, w, rank, nctas, sync, tol2, floor2, max_sweeps, converged);
 
   // ---- singular values (noise floor -> 0), descending, ties by column index -----------
   for (int j = worker; j < K; j += workers) {
@@ -502,7 +622,7 @@ __host__ __device__ inline SmemLayout smem_layout(int m, int n) {
 }
 
 __global__ void __launch_bounds__(kSvdThreads, 1) jacobi_cta_kernel(const SvdSector* __restrict__ secs,
-                                                                 int max_sweeps) {
+                                                                    int max_sweeps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SvdSector S = secs[blockIdx.x];
   const SmemLayout L = smem_layout(S.m, S.n);
@@ -518,13 +638,10 @@ __global__ void __launch_bounds__(kSvdThreads, 1) jacobi_cta_kernel(const SvdSec
   w.pv = reinterpret_cast<double*>(smem_raw + L.pv);
   w.pi = reinterpret_cast<int*>(smem_raw + L.pi);
   w.scal = reinterpret_cast<double*>(smem_raw + L.scal);
-  svd_sector<PlainMem>(S, w, 0, 1, CtaSync{}, max_sweeps);
+  svd_sector<PlainMem>(S, w, 0, 1, CtaSync{}, max_sweeps, JacobiRoundRobin<PlainMem>{});
 }
 
-__global__ void __launch_bounds__(kSvdThreads) jacobi_cluster_kernel(const SvdSector* __restrict__ secs,
-                                                                     int cluster, int max_sweeps) {
-  const int rank = (int)cluster_rank();
-  const SvdSector S = secs[blockIdx.x / cluster];
+__device__ __forceinline__ Work cluster_work(const SvdSector& S) {
   Work w;
   w.W = S.work;
   w.u = S.uwork;
@@ -537,24 +654,66 @@ __global__ void __launch_bounds__(kSvdThreads) jacobi_cluster_kernel(const SvdSe
   w.pv = S.pivv;
   w.pi = S.flags + kJacobiMaxSweeps + 1;
   w.scal = S.pivv + kMaxCluster;
-  svd_sector<L2Mem>(S, w, rank, cluster, ClusterSync{}, max_sweeps);
+  return w;
 }
 
-bool g_cta_attr = false;
-int g_cluster = 0;
+__global__ void __launch_bounds__(kSvdThreads) jacobi_cluster_kernel(const SvdSector* __restrict__ secs,
+                                                                     int cluster, int max_sweeps) {
+  const int rank = (int)cluster_rank();
+  const SvdSector S = secs[blockIdx.x / cluster];
+  svd_sector<L2Mem>(S, cluster_work(S), rank, cluster, ClusterSync{}, max_sweeps, JacobiRoundRobin<L2Mem>{});
+}
+
+__global__ void __launch_bounds__(kBlockThreads, 1) jacobi_cluster_block_kernel(const SvdSector* __restrict__ secs,
+                                                                                int cluster, int max_sweeps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int rank = (int)cluster_rank();
+  const SvdSector S = secs[blockIdx.x / cluster];
+  const int K = min(S.m, S.n);
+  JacobiBlocks jb;
+  jb.g = S.groups;
+  jb.bsmax = (K + 2 * cluster * jb.g - 1) / (2 * cluster * jb.g);
+  jb.sm = reinterpret_cast<double2*>(smem_raw);
+  jb.smn = reinterpret_cast<double*>(smem_raw + 16LL * 2 * jb.bsmax * S.n);
+  svd_sector<L2Mem>(S, cluster_work(S), rank, cluster, ClusterSync{}, max_sweeps, jb);
+}
+
 
 }  // namespace
 
 int64_t svd_smem_need(int m, int n) { return smem_layout(m, n).total; }
 
-int svd_cluster_size() {
-  if (g_cluster) return g_cluster;
-  int c = 8;
+namespace {
+
+constexpr int kBlockSmemMax = 200 * 1024;
+// 8 CTAs per large sector: the GPU places about twice as many 8-CTA clusters as
+// 16-CTA ones, which keeps more SMs busy when a layer has hundreds of large sectors
+constexpr int kBigCluster = 8;
+bool g_attr_done = false;
+int g_big_cluster = 0;
+
+int64_t block_smem_need(int m, int n, int cl, int g) {
+  const int64_t K = std::min(m, n), bs = (K + 2 * cl * g - 1) / (2 * cl * g);
+  return 16 * 2 * bs * n + 8 * 2 * bs + 64;
+}
+
+cudaError_t set_attrs() {
+  if (g_attr_done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(jacobi_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSvdSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(jacobi_cluster_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kBlockSmemMax);
+  if (e != cudaSuccess) return e;
+  // clusters of 16 CTAs are non-portable: use them only where the device can place them
+  int big = 8;
   if (cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-      cudaSuccess) {
+          cudaSuccess &&
+      cudaFuncSetAttribute(jacobi_cluster_block_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+          cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16);
-    cfg.blockDim = dim3(kSvdThreads);
+    cfg.blockDim = dim3(kBlockThreads);
+    cfg.dynamicSmemBytes = kBlockSmemMax;
     cudaLaunchAttribute at;
     at.id = cudaLaunchAttributeClusterDimension;
     at.val.clusterDim.x = 16;
@@ -563,43 +722,123 @@ int svd_cluster_size() {
     cfg.attrs = &at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, jacobi_cluster_kernel, &cfg) == cudaSuccess && n >= 4) c = 16;
+    if (cudaOccupancyMaxActiveClusters(&n, jacobi_cluster_block_kernel, &cfg) == cudaSuccess && n >= 4) big = 16;
   }
   cudaGetLastError();
-  g_cluster = c;
-  return c;
+  g_big_cluster = big;
+  g_attr_done = true;
+  return cudaSuccess;
 }
 
-cudaError_t launch_svd_cta(const SvdSector* d_secs, int n_secs, int smem_bytes, int max_sweeps, cudaStream_t st) {
-  if (n_secs <= 0) return cudaSuccess;
-  if (!g_cta_attr) {
-    cudaError_t e = cudaFuncSetAttribute(jacobi_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSvdSmemMax);
-    if (e != cudaSuccess) return e;
-    g_cta_attr = true;
-  }
+cudaError_t launch_group(const SvdSector* d_secs, const SvdGroup& g, int max_sweeps, cudaStream_t st) {
+  if (g.count <= 0) return cudaSuccess;
+  const SvdSector* d = d_secs + g.first;
   count_launch();
-  jacobi_cta_kernel<<<n_secs, kSvdThreads, smem_bytes, st>>>(d_secs, max_sweeps);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_svd_cluster(const SvdSector* d_secs, int n_secs, int max_sweeps, cudaStream_t st) {
-  if (n_secs <= 0) return cudaSuccess;
-  const int cl = svd_cluster_size();
+  if (g.kind == kSvdSmem) {
+    jacobi_cta_kernel<<<g.count, kSvdThreads, g.smem, st>>>(d, max_sweeps);
+    return cudaGetLastError();
+  }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(n_secs * cl);
-  cfg.blockDim = dim3(kSvdThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.gridDim = dim3(g.count * g.cl);
+  cfg.blockDim = dim3(g.kind == kSvdClusterBlock ? kBlockThreads : kSvdThreads);
+  cfg.dynamicSmemBytes = g.smem;
   cfg.stream = st;
   cudaLaunchAttribute at;
   at.id = cudaLaunchAttributeClusterDimension;
-  at.val.clusterDim.x = cl;
+  at.val.clusterDim.x = g.cl;
   at.val.clusterDim.y = 1;
   at.val.clusterDim.z = 1;
   cfg.attrs = &at;
   cfg.numAttrs = 1;
-  count_launch();
-  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, d_secs, cl, max_sweeps);
+  if (g.kind == kSvdClusterBlock) return cudaLaunchKernelEx(&cfg, jacobi_cluster_block_kernel, d, g.cl, max_sweeps);
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, d, g.cl, max_sweeps);
+}
+
+}  // namespace
+
+cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& groups) {
+  cudaError_t e = set_attrs();
+  if (e != cudaSuccess) return e;
+  // every sector gets a kernel and a cluster size
+  std::vector<std::pair<int, int>> key(secs.size());
+  std::vector<int64_t> smem(secs.size(), 0);
+  for (size_t k = 0; k < secs.size(); ++k) {
+    const SvdSector S = secs[k];
+    if (S.mode == kSvdSmem) {
+      key[k] = {kSvdSmem, 1};
+      smem[k] = svd_smem_need(S.m, S.n);
+      continue;
+    }
+    const int K = std::min(S.m, S.n);
+    const int cl = K >= 96 ? kBigCluster : 4;
+    // fewest block groups per CTA whose two staged blocks fit in shared memory
+    int g = 1;
+    while (g < 8 && block_smem_need(S.m, S.n, cl, g) > kBlockSmemMax) ++g;
+    const int64_t need = block_smem_need(S.m, S.n, cl, g);
+    if (need <= kBlockSmemMax) {
+      key[k] = {kSvdClusterBlock, cl};
+      smem[k] = need;
+      secs[k].groups = g;
+    } else {
+      key[k] = {kSvdCluster, g_big_cluster};
+    }
+  }
+  // group by (kind, cluster size); the most expensive sectors first inside a group
+  std::vector<size_t> idx(secs.size());
+  for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+  auto cost = [&](size_t k) {
+    const double C = std::min(secs[k].m, secs[k].n);
+    return (double)secs[k].n * C * C + (double)secs[k].m * secs[k].n * C;
+  };
+  std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+    if (key[a] != key[b]) return key[a] > key[b];
+    return cost(a) > cost(b);
+  });
+  std::vector<SvdSector> out;
+  out.reserve(secs.size());
+  groups.clear();
+  for (size_t t = 0; t < idx.size(); ++t) {
+    const size_t k = idx[t];
+    if (groups.empty() || groups.back().kind != key[k].first || groups.back().cl != key[k].second) {
+      SvdGroup g;
+      g.kind = key[k].first;
+      g.cl = key[k].second;
+      g.smem = 0;
+      g.first = (int)out.size();
+      g.count = 0;
+      groups.push_back(g);
+    }
+    groups.back().count++;
+    groups.back().smem = std::max<int>(groups.back().smem, (int)smem[k]);
+    out.push_back(secs[k]);
+  }
+  secs.swap(out);
+  return cudaSuccess;
+}
+
+cudaError_t launch_svd_groups(const SvdSector* d_secs, const std::vector<SvdGroup>& groups, cudaStream_t st,
+                              const cudaStream_t* side, int n_side, cudaEvent_t fork, const cudaEvent_t* join) {
+  // group 0 on st, the others on side streams when given, all joined back into st
+  cudaError_t e = cudaSuccess;
+  const int ng = (int)groups.size();
+  if (ng == 0) return cudaSuccess;
+  const bool fan = side && n_side >= ng - 1 && ng > 1;
+  if (fan) {
+    if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
+    for (int g = 1; g < ng; ++g)
+      if ((e = cudaStreamWaitEvent(side[g - 1], fork, 0)) != cudaSuccess) return e;
+  }
+  for (int g = 0; g < ng; ++g) {
+    cudaStream_t s = (fan && g > 0) ? side[g - 1] : st;
+    if ((e = launch_group(d_secs, groups[g], kJacobiMaxSweeps, s)) != cudaSuccess) return e;
+  }
+  if (fan) {
+    for (int g = 1; g < ng; ++g) {
+      if ((e = cudaEventRecord(join[g - 1], side[g - 1])) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(st, join[g - 1], 0)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L) {
@@ -642,22 +881,6 @@ void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base
   S.order = reinterpret_cast<int*>(base + L.ord_off[k]);
   S.flags = reinterpret_cast<int*>(base + L.flag_off[k]);
   S.pivv = reinterpret_cast<double*>(base + L.piv_off[k]);
-}
-
-cudaError_t launch_svd_all(const SvdSector* d_cta, int n_cta, const SvdSector* d_cl, int n_cl, int smem,
-                           cudaStream_t st, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
-  // small sectors on the side stream, large ones on the main stream, joined afterwards
-  cudaError_t e = cudaSuccess;
-  if (n_cta > 0 && n_cl > 0 && side) {
-    if ((e = cudaEventRecord(fork, st)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) return e;
-    if ((e = launch_svd_cta(d_cta, n_cta, smem, kJacobiMaxSweeps, side)) != cudaSuccess) return e;
-    if ((e = launch_svd_cluster(d_cl, n_cl, kJacobiMaxSweeps, st)) != cudaSuccess) return e;
-    if ((e = cudaEventRecord(join, side)) != cudaSuccess) return e;
-    return cudaStreamWaitEvent(st, join, 0);
-  }
-  if ((e = launch_svd_cluster(d_cl, n_cl, kJacobiMaxSweeps, st)) != cudaSuccess) return e;
-  return launch_svd_cta(d_cta, n_cta, smem, kJacobiMaxSweeps, st);
 }
 
 }  // namespace mps
@@ -703,13 +926,13 @@ extern "C" int mps_svd_sectors(int n_sectors, const int* m, const int* n,
   }
   std::vector<SvdSector> all(cta);
   all.insert(all.end(), cl.begin(), cl.end());
+  std::vector<SvdGroup> groups;
+  if (svd_group(all, groups) != cudaSuccess) return MPS_ECUDA;
   if (cudaMemcpyAsync(d_work, all.data(), sizeof(SvdSector) * all.size(), cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return MPS_ECUDA;
   const SvdSector* d_all = reinterpret_cast<const SvdSector*>(d_work);
-  if (launch_svd_all(d_all, (int)cta.size(), d_all + cta.size(), (int)cl.size(), L.smem, st, nullptr, nullptr,
-                     nullptr) != cudaSuccess)
-    return MPS_ECUDA;
+  if (launch_svd_groups(d_all, groups, st, nullptr, 0, nullptr, nullptr) != cudaSuccess) return MPS_ECUDA;
   // the descriptors came from pageable host memory: finish before returning
   if (cudaStreamSynchronize(st) != cudaSuccess) return MPS_ECUDA;
   return MPS_OK;
@@ -772,13 +995,13 @@ extern "C" int mps_svd_sectors_noalloc(int n_sectors, const int* m, const int* n
   }
   std::vector<SvdSector> all(cta);
   all.insert(all.end(), cl.begin(), cl.end());
+  std::vector<SvdGroup> groups;
+  if (svd_group(all, groups) != cudaSuccess) return MPS_ECUDA;
   if (cudaMemcpyAsync(d_work, all.data(), sizeof(SvdSector) * all.size(), cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return MPS_ECUDA;
   const SvdSector* d_all = reinterpret_cast<const SvdSector*>(d_work);
-  if (launch_svd_all(d_all, (int)cta.size(), d_all + cta.size(), (int)cl.size(), L.smem, st, nullptr, nullptr,
-                     nullptr) != cudaSuccess)
-    return MPS_ECUDA;
+  if (launch_svd_groups(d_all, groups, st, nullptr, 0, nullptr, nullptr) != cudaSuccess) return MPS_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return MPS_ECUDA;
   return MPS_OK;
 }

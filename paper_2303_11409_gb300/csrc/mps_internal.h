@@ -11,6 +11,8 @@
 
 namespace mps {
 
+constexpr int kSvdSideStreams = 3;      // side streams for concurrent SVD kernel groups
+
 // ---------------------------------------------------------------------------
 // Host mirror of the charge structure (Sec. II: right-charge labels per bond,
 // blocks (l, m) with 0 <= l - m <= d - 1 per site).
@@ -74,8 +76,9 @@ struct ThetaTask {            // one (l, r) block pair of one update: sum_m G * 
 };
 struct TileRef { int task; int ti; int tj; };
 
-constexpr int kSvdSmem = 0;      // one CTA, Jacobi matrix staged in shared memory
-constexpr int kSvdCluster = 1;   // a thread-block cluster, Jacobi matrix in L2
+constexpr int kSvdSmem = 0;          // one CTA, the whole sector in shared memory
+constexpr int kSvdCluster = 1;       // a thread-block cluster, data in L2, round-robin Jacobi
+constexpr int kSvdClusterBlock = 2;  // a thread-block cluster, data in L2, block Jacobi staged in shared memory
 
 struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   const double2* theta;       // row-major m x n
@@ -90,7 +93,8 @@ struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   double2* Y;                 // out: n x min(m, n) column-major right singular vectors
   int* status;                // out: Jacobi sweeps used, or -1 when not converged
   int m, n;
-  int mode;                   // kSvdSmem or kSvdCluster
+  int mode;                   // kSvdSmem, kSvdCluster or kSvdClusterBlock
+  int groups;                 // block Jacobi: block pairs per CTA and round
 };
 
 // Scratch layout of a batch of sector SVDs (cluster-mode sectors only need global scratch).
@@ -178,8 +182,8 @@ struct mps_s {
   mps::DevBuf work;                       // per-update workspace
   mps::PinnedBuf pin_in, pin_out;         // staging of descriptors and results
   cudaEvent_t staged = nullptr;           // last upload out of pin_in has completed
-  cudaStream_t side = nullptr;            // second stream for the one-CTA SVD kernel
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side[mps::kSvdSideStreams] = {};     // side streams for concurrent SVD kernel groups
+  cudaEvent_t fork = nullptr, join[mps::kSvdSideStreams] = {};
   std::string err;
   mps::Stats stats;
   bool profiling = false;
@@ -195,10 +199,14 @@ namespace mps {
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_theta(const ThetaTask* d_tasks, const TileRef* d_tiles, int n_tiles, cudaStream_t st);
-// Small sectors on `side` (if given), large ones as clusters on `st`; `st` waits for both.
-cudaError_t launch_svd_all(const SvdSector* d_cta, int n_cta, const SvdSector* d_cl, int n_cl, int smem,
-                           cudaStream_t st, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
-int svd_cluster_size();
+// Sectors grouped by kernel and cluster size (a group is a contiguous run of the array).
+struct SvdGroup { int kind, cl, smem, first, count; };
+// Orders `secs` into groups (costliest first inside each) and fills `groups`.
+cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& groups);
+// Group 0 on st, group g > 0 on side[g-1] when n_side >= groups - 1; st then waits for all.
+cudaError_t launch_svd_groups(const SvdSector* d_secs, const std::vector<SvdGroup>& groups, cudaStream_t st,
+                              const cudaStream_t* side, int n_side, cudaEvent_t fork, const cudaEvent_t* join);
+
 cudaError_t launch_select(const SelectSector* d_secs, const SelectTask* d_tasks, int n_tasks,
                           int* d_kept, SelectResult* d_res, cudaStream_t st);
 cudaError_t launch_gemm(const GemmTask* d_tasks, const TileRef* d_tiles, int n_tiles, cudaStream_t st);
