@@ -33,8 +33,8 @@ L, D, N_PART, J, U, DT, CHI, CUTOFF = 64, 5, 64, 1.0, 2.0, 0.02, 512, 1e-10
 UPDATES_PER_STEP = 32 + 31 + 32
 METRIC = "two-site updates/s"
 WORKLOAD = "bose_hubbard_L64_nmax4_N64_J1_U2_dt0.02_chi512_cutoff1e-10_fp64"
-# --case small: the same model on L=32, chi=256, for profiler captures of every kernel on a small case
-SMALL = dict(L=32, N=32, CHI=256, WORKLOAD="bose_hubbard_L32_nmax4_N32_J1_U2_dt0.02_chi256_cutoff1e-10_fp64")
+# --case small: the same model on L=32, chi=512 (half the chain, same sector sizes), for profiler captures
+SMALL = dict(L=32, N=32, CHI=512, WORKLOAD="bose_hubbard_L32_nmax4_N32_J1_U2_dt0.02_chi512_cutoff1e-10_fp64")
 # FP64 peak of the GB300 CUDA cores: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz.
 # (An FMA-chain probe measured 1.195 TFLOP/s, i.e. 2 FMA/clk/SM at the clock it ran.)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
@@ -51,8 +51,11 @@ def parse():
     p.add_argument("--max-prep", type=int, default=120)
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--serve", action="store_true",
+                   help="serving workload instead: continuous batching vs the plain one-request-at-a-time form")
+    p.add_argument("--serve-requests", type=int, default=48)
     p.add_argument("--case", default="full", choices=["full", "small"],
-                   help="small: L=32, chi=256 (for profiler captures); full: the benchmark workload")
+                   help="small: L=32, chi=512 (for profiler captures); full: the benchmark workload")
     a = p.parse_args()
     if a.case == "small":
         global L, N_PART, CHI, WORKLOAD, UPDATES_PER_STEP
@@ -306,10 +309,83 @@ def run_ours(args, world, rank, local):
     psi.close()
 
 
+def run_serving(args, world, rank, local):
+    """Serving: Poisson arrivals of mixed XXZ / Bose-Hubbard quenches through the
+    continuous-batching server, next to the plain form (each request alone, in turn).
+
+    Reported: the served capacity (all requests queued at once) against the plain
+    form's, and p50/p99 latency under Poisson arrivals at 0.8 x the served capacity.
+    The request mix is the serving configuration scaled down so that the whole run
+    takes minutes: L in {16, 32}, chi in {32, 64, 128}, 5..40 Trotter steps (the full
+    mix has L up to 128, chi up to 1024 and up to 500 steps per request).
+    """
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2303_11409_gb300 as m
+    import workloads as W
+    mix = dict(L_choices=(16, 32), chi_choices=(32, 64, 128), steps_range=(5, 40))
+    raw = W.serving_requests(args.serve_requests, seed=rank, rate_hz=1.0, **mix)
+    reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=0.0)
+            for r in raw]
+    budget = 64 << 30
+    # plain form: one request at a time, no merging
+    t0 = time.perf_counter()
+    plain_updates = 0
+    for q in reqs:
+        srv = m.serve.Server(budget_bytes=budget, max_slots=1)
+        res = srv.run([q])
+        srv.close()
+        plain_updates += res[0].updates
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_rate = plain_updates / plain_s                    # updates/s
+    # served capacity: every request queued at t = 0, merged launches across requests
+    srv = m.serve.Server(budget_bytes=budget, max_slots=64)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    torch.cuda.synchronize()
+    cap_s = time.perf_counter() - t0
+    srv.close()
+    served_cap = sum(r.updates for r in res) / cap_s
+    # latency under load: Poisson arrivals at 0.8 x the served capacity (in requests/s)
+    req_rate = 0.8 * len(reqs) / cap_s
+    raw = W.serving_requests(args.serve_requests, seed=rank, rate_hz=req_rate, **mix)
+    reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=r["arrival"])
+            for r in raw]
+    srv = m.serve.Server(budget_bytes=budget, max_slots=64)
+    launches0 = m.launch_count()
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    srv.close()
+    summ = m.serve.summarize(res, wall)
+    if rank == 0:
+        line = {"metric": "serving two-site updates/s (p50/p99 request latency)", "value": served_cap,
+                "unit": "updates/s", "n_gpus": world, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "p50_latency_s": summ["p50_latency_s"], "p99_latency_s": summ["p99_latency_s"],
+                "requests": len(res), "updates": summ["updates"], "loaded_wall_s": wall,
+                "loaded_updates_per_s": summ["updates_per_s"],
+                "plain_updates_per_s": plain_rate, "served_over_plain": served_cap / plain_rate,
+                "arrival_rate_hz": req_rate, "max_active_under_load": srv.max_active_seen,
+                "gpu_launches": m.launch_count() - launches0,
+                "config": {"workload": "serving_mix_scaled", "requests": len(reqs), **{k: list(v) for k, v in mix.items()},
+                           "models": "xxz Delta~U[0,2] (Neel) / bh U~U[1,10] J=1 (Mott), 50/50",
+                           "value": "served capacity (all requests queued at t=0, merged launches)",
+                           "latency": "Poisson arrivals at 0.8 x the served capacity",
+                           "plain": "each request alone, one after another", "budget_bytes": budget,
+                           "max_slots": 64}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.serve:
+        run_serving(args, world, rank, local)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)

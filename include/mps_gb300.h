@@ -126,6 +126,31 @@ MPS_API int mps_apply_gate2_batch(int n, mps_t* hs, const int* sites, const doub
                           int* status_out);
 
 /*
+ * mps_exec_t - an executor for merged updates across handles (serving): it owns the
+ * workspace, staging buffers and stream that mps_exec_apply uses, so that handles can
+ * come and go (requests admitted and completed) without the workspace moving.
+ * mps_exec_create: cuda_stream as for mps_create.  mps_exec_destroy: after its stream drains.
+ * mps_exec_apply: as mps_apply_gate2_batch, on the executor's stream and workspace;
+ *   the handles may differ in L, d, chi_max (independent problems, Sec. II: "independent
+ *   two-site updates ... processed in parallel").
+ */
+typedef struct mps_s* mps_exec_t;
+MPS_API int mps_exec_create(mps_exec_t* out, void* cuda_stream);
+MPS_API int mps_exec_destroy(mps_exec_t ex);
+MPS_API int mps_exec_apply(mps_exec_t ex, int n, mps_t* hs, const int* sites, const double* const* gates,
+                           const int* chis, const double* cutoffs, double* trunc_err_out, int* status_out);
+
+/*
+ * mps_footprint_bytes - device memory a handle of (L, d, N, chi_max) holds (the arena
+ * mps_create allocates: per bond min(chi_max, Hilbert bound) lambdas, two slots per
+ * site of bond_cap(s) * bond_cap(s+1) complex numbers) and an upper bound of the
+ * update workspace one of its Trotter layers needs (about 64 d chi^2 bytes per
+ * update).  Host-only; used for admission by HBM footprint.
+ */
+MPS_API int mps_footprint_bytes(int L, int d, int N, int chi_max, int64_t* arena_bytes,
+                                int64_t* layer_workspace_bytes);
+
+/*
  * mps_expect - <O_site> of a diagonal one-site operator (U(1)-conserving one-site
  * operators are diagonal in the occupation basis).
  *   diag_op  host array of d real values O(i)

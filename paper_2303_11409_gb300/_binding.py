@@ -62,6 +62,11 @@ _SIGS = {
                                        ctypes.c_double, _dblp]),
     "mps_apply_gate2_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_h), _intp, ctypes.POINTER(_dblp),
                                              _intp, _dblp, _dblp, _intp]),
+    "mps_exec_create": (ctypes.c_int, [ctypes.POINTER(_h), _vp]),
+    "mps_exec_destroy": (ctypes.c_int, [_h]),
+    "mps_exec_apply": (ctypes.c_int, [_h, ctypes.c_int, ctypes.POINTER(_h), _intp, ctypes.POINTER(_dblp), _intp,
+                                      _dblp, _dblp, _intp]),
+    "mps_footprint_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, _i64p]),
     "mps_expect": (ctypes.c_int, [_h, ctypes.c_int, _dblp, _dblp]),
     "mps_amplitude": (ctypes.c_int, [_h, _i32p, _dblp]),
     "mps_amplitude_batch": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _dblp]),
@@ -307,6 +312,57 @@ class MPS:
                                   ctypes.byref(na), ctypes.byref(nk))
         return dict(n_sectors=a.value, n_triples=b.value, max_sweeps=c.value, tie_band=t.value,
                     norm_all=na.value, norm_kept=nk.value)
+
+
+class Executor:
+    """Merged updates across handles on one workspace and stream (mps_exec_*)."""
+
+    def __init__(self, stream=None):
+        self.stream = _default_stream() if stream is None else stream
+        h = _h()
+        rc = lib.mps_exec_create(ctypes.byref(h), self.stream)
+        if rc != MPS_OK:
+            raise MPSError(rc, "mps_exec_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mps_exec_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, items):
+        """items = [(mps, site, flat_gate, chi, cutoff), ...]; returns (trunc_err, status) arrays."""
+        n = len(items)
+        if n == 0:
+            return np.zeros(0), np.zeros(0, dtype=np.intc)
+        hs = (_h * n)(*[it[0].handle for it in items])
+        sites = np.array([it[1] for it in items], dtype=np.intc)
+        gs = [_c128_flat(it[2]) for it in items]
+        garr = (_dblp * n)(*[g.ctypes.data_as(_dblp) for g in gs])
+        chis = np.array([it[3] for it in items], dtype=np.intc)
+        cuts = np.array([it[4] for it in items], dtype=np.float64)
+        te = np.zeros(n)
+        st = np.zeros(n, dtype=np.intc)
+        rc = lib.mps_exec_apply(self._h, n, hs, _ptr(sites, _intp), garr, _ptr(chis, _intp), _ptr(cuts, _dblp),
+                                _ptr(te, _dblp), _ptr(st, _intp))
+        if rc not in (MPS_OK, MPS_ENOCONV):
+            raise MPSError(rc, "mps_exec_apply: " + lib.mps_last_error(self._h).decode())
+        return te, st
+
+
+def footprint_bytes(L: int, d: int, N: int, chi_max: int) -> tuple[int, int]:
+    """(arena bytes of a handle, upper bound of one layer's update workspace)."""
+    a, w = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib.mps_footprint_bytes(L, d, N, chi_max, ctypes.byref(a), ctypes.byref(w))
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_footprint_bytes")
+    return a.value, w.value
 
 
 def launch_count() -> int:

@@ -207,9 +207,8 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   }
   const int64_t jac_base = ws;
   ws = a256(ws + JL.total);
-  const int64_t glen = gate_len(owner->d);
-  for (int u = 0; u < nreq; ++u)
-    if (reqs[u].h->d != owner->d) return fail(owner, MPS_EINVAL, "batched handles must share d");
+  int64_t gates_bytes = 0;                      // gate blocks of every update (d may differ)
+  for (int u = 0; u < nreq; ++u) gates_bytes += a256(16LL * gate_len(reqs[u].h->d));
   const int64_t kept_off = ws; ws = a256(ws + 4LL * n_sec_total);
   const int64_t status_off = ws; ws = a256(ws + 4LL * n_sec_total);
   const int64_t res_off = ws; ws = a256(ws + (int64_t)sizeof(SelectResult) * nreq);
@@ -237,7 +236,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   const int64_t phase1_desc = a256((int64_t)sizeof(ThetaTask) * n_tasks) + a256(sizeof(TileRef) * (int64_t)n_tiles) +
                               a256((int64_t)sizeof(SvdSector) * n_sec_total) +
                               a256((int64_t)sizeof(SelectSector) * n_sec_total) +
-                              a256((int64_t)sizeof(SelectTask) * nreq) + a256(16LL * glen) * nreq;
+                              a256((int64_t)sizeof(SelectTask) * nreq) + gates_bytes;
   const int64_t phase2_desc = a256((int64_t)sizeof(LambdaTask) * lam_bound) +
                               a256((int64_t)sizeof(ScatterTask) * scatter_bound) +
                               a256((int64_t)sizeof(GemmTask) * gemm_tasks_bound) +
@@ -258,7 +257,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   auto dptr = [&](int64_t off) { return base + off; };
   // gates go first into the staging area; tasks point at their device copies
   Stager sg{(char*)owner->pin_in.p};
-  for (int u = 0; u < nreq; ++u) W[u].gate_off = desc_off + sg.put(reqs[u].gate, 2 * glen);
+  for (int u = 0; u < nreq; ++u) W[u].gate_off = desc_off + sg.put(reqs[u].gate, 2 * gate_len(reqs[u].h->d));
 
   // ---- build phase-1 descriptors ------------------------------------------------------
   std::vector<ThetaTask> tasks; tasks.reserve(n_tasks);
@@ -720,12 +719,70 @@ int mps_apply_layer(mps_t h, int n, const int* sites, const double* const* gate_
   return first;
 }
 
+static int batch_on(mps_s* owner, int n, mps_t* hs, const int* sites, const double* const* gates,
+                    const int* chis, const double* cutoffs, double* trunc_err_out, int* status_out);
+
 int mps_apply_gate2_batch(int n, mps_t* hs, const int* sites, const double* const* gates, const int* chis,
                           const double* cutoffs, double* trunc_err_out, int* status_out) {
   if (n < 0 || (n > 0 && (!hs || !sites || !gates || !chis || !cutoffs))) return MPS_EINVAL;
   if (n == 0) return MPS_OK;
-  mps_s* owner = hs[0];
-  if (!owner) return MPS_EINVAL;
+  if (!hs[0]) return MPS_EINVAL;
+  return batch_on(hs[0], n, hs, sites, gates, chis, cutoffs, trunc_err_out, status_out);
+}
+
+int mps_exec_create(mps_exec_t* out, void* cuda_stream) {
+  if (!out) return MPS_EINVAL;
+  *out = nullptr;
+  mps_s* h = new mps_s();
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaEventCreateWithFlags(&h->staged, cudaEventDisableTiming);
+  for (int i = 0; i < kSvdSideStreams && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    mps_destroy(h);
+    return MPS_ECUDA;
+  }
+  *out = h;
+  return MPS_OK;
+}
+
+int mps_exec_destroy(mps_exec_t ex) { return mps_destroy(ex); }
+
+int mps_exec_apply(mps_exec_t ex, int n, mps_t* hs, const int* sites, const double* const* gates, const int* chis,
+                   const double* cutoffs, double* trunc_err_out, int* status_out) {
+  if (!ex || n < 0 || (n > 0 && (!hs || !sites || !gates || !chis || !cutoffs))) return MPS_EINVAL;
+  if (n == 0) return MPS_OK;
+  return batch_on(ex, n, hs, sites, gates, chis, cutoffs, trunc_err_out, status_out);
+}
+
+int mps_footprint_bytes(int L, int d, int N, int chi_max, int64_t* arena_bytes, int64_t* layer_workspace_bytes) {
+  if (L < 2 || d < 2 || d > MPS_MAX_D || N < 0 || N > L * (d - 1) || chi_max < 1) return MPS_EINVAL;
+  auto Wc = config_counts(L, d, N);
+  std::vector<int64_t> cap(L + 1);
+  int64_t lam = 0, sites = 0;
+  for (int b = 0; b <= L; ++b) {
+    double hb = 0.0;
+    const int lo = std::max(0, N - (d - 1) * b), hi = std::min(N, (d - 1) * (L - b));
+    for (int q = lo; q <= hi; ++q) hb += std::min(Wc[b][N - q], Wc[L - b][q]);
+    cap[b] = (int64_t)std::max(1.0, std::min((double)chi_max, hb));
+    lam += (cap[b] + 31) / 32 * 32;
+  }
+  int64_t ws = 0;
+  for (int s = 0; s < L; ++s) {
+    const int64_t c = std::max<int64_t>(1, cap[s] * cap[s + 1]);
+    sites += 2 * ((c + 15) / 16 * 16);
+    if (s + 1 < L) ws = std::max<int64_t>(ws, 64LL * d * std::max(cap[s], cap[s + 2]) * std::max(cap[s], cap[s + 2]));
+  }
+  if (arena_bytes) *arena_bytes = 8 * lam + 16 * sites;
+  if (layer_workspace_bytes) *layer_workspace_bytes = ws * (L / 2);
+  return MPS_OK;
+}
+
+static int batch_on(mps_s* owner, int n, mps_t* hs, const int* sites, const double* const* gates,
+                    const int* chis, const double* cutoffs, double* trunc_err_out, int* status_out) {
   std::vector<Req> r(n);
   std::vector<mps_s*> others;
   for (int k = 0; k < n; ++k) {

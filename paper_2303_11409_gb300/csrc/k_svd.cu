@@ -770,10 +770,12 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
       continue;
     }
     const int K = std::min(S.m, S.n);
-    const int cl = K >= 96 ? kBigCluster : 4;
-    // fewest block groups per CTA whose two staged blocks fit in shared memory
-    int g = 1;
-    while (g < 8 && block_smem_need(S.m, S.n, cl, g) > kBlockSmemMax) ++g;
+    // blocks of about 12 columns keep the 12 warps of a CTA busy in every inner round:
+    // 2, 4 or 8 CTAs per sector, then more block groups per CTA for larger sectors
+    int cl = 2;
+    while (cl < kBigCluster && K >= 24 * 2 * cl) cl *= 2;
+    int g = std::max(1, (K + 12 * cl) / (24 * cl));
+    while (g < 16 && block_smem_need(S.m, S.n, cl, g) > kBlockSmemMax) ++g;
     const int64_t need = block_smem_need(S.m, S.n, cl, g);
     if (need <= kBlockSmemMax) {
       key[k] = {kSvdClusterBlock, cl};

@@ -11,7 +11,7 @@
 
 namespace mps {
 
-constexpr int kSvdSideStreams = 3;      // side streams for concurrent SVD kernel groups
+constexpr int kSvdSideStreams = 4;      // side streams for concurrent SVD kernel groups
 
 // ---------------------------------------------------------------------------
 // Host mirror of the charge structure (Sec. II: right-charge labels per bond,

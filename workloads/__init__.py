@@ -93,12 +93,14 @@ def random_occupations(L: int, d: int, N: int, rng: np.random.Generator) -> list
     return occ
 
 
-def serving_requests(n: int, seed: int = 0, rate_hz: float = 1.0):
+def serving_requests(n: int, seed: int = 0, rate_hz: float = 1.0, L_choices=(32, 64, 128),
+                     chi_choices=(64, 256, 1024), steps_range=(50, 500)):
     """Seeded request mix for the serving workload.
 
     Each request is a dict: arrival time (Poisson process of `rate_hz`), model
-    ('xxz' with Delta ~ U[0,2], or 'bh' with U/J ~ U[1,10]), chain length L in
-    {32, 64, 128}, chi in {64, 256, 1024} and a Trotter step count in 50..500.
+    ('xxz' with Delta ~ U[0,2], or 'bh' with U/J ~ U[1,10]), chain length L from
+    L_choices, chi from chi_choices and a Trotter step count in steps_range
+    (inclusive).  The defaults are the full serving configuration.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate_hz, size=n)
@@ -106,9 +108,9 @@ def serving_requests(n: int, seed: int = 0, rate_hz: float = 1.0):
     out = []
     for k in range(n):
         model = "xxz" if rng.random() < 0.5 else "bh"
-        L = int(rng.choice([32, 64, 128]))
-        chi = int(rng.choice([64, 256, 1024]))
-        steps = int(rng.integers(50, 501))
+        L = int(rng.choice(list(L_choices)))
+        chi = int(rng.choice(list(chi_choices)))
+        steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
         param = float(rng.uniform(0.0, 2.0)) if model == "xxz" else float(rng.uniform(1.0, 10.0))
         out.append(dict(id=k, arrival=float(t[k]), model=model, L=L, chi=chi, steps=steps, param=param))
     return out
