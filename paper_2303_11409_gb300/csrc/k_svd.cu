@@ -46,7 +46,7 @@ constexpr double kEps = 2.220446049250313e-16;
 constexpr int kMaxCached = 16;          // rows cached in registers per lane (n <= 512)
 constexpr int kMaxCluster = 16;
 constexpr int kMaxWarps = 16;
-constexpr int kBlockThreads = 384;      // block-Jacobi cluster kernel: 12 warps per CTA
+constexpr int kBlockThreads = 192;      // block-Jacobi cluster kernel: 6 warps per CTA, 2 CTAs per SM
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(kSvdThreads) jacobi_cluster_kernel(const SvdSe
   svd_sector<L2Mem>(S, cluster_work(S), rank, cluster, ClusterSync{}, max_sweeps, JacobiRoundRobin<L2Mem>{});
 }
 
-__global__ void __launch_bounds__(kBlockThreads, 1) jacobi_cluster_block_kernel(const SvdSector* __restrict__ secs,
+__global__ void __launch_bounds__(kBlockThreads, 2) jacobi_cluster_block_kernel(const SvdSector* __restrict__ secs,
                                                                                 int cluster, int max_sweeps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int rank = (int)cluster_rank();
@@ -685,7 +685,7 @@ int64_t svd_smem_need(int m, int n) { return smem_layout(m, n).total; }
 
 namespace {
 
-constexpr int kBlockSmemMax = 200 * 1024;
+constexpr int kBlockSmemMax = 110 * 1024;   // two block-Jacobi CTAs per SM
 // 8 CTAs per large sector: the GPU places about twice as many 8-CTA clusters as
 // 16-CTA ones, which keeps more SMs busy when a layer has hundreds of large sectors
 constexpr int kBigCluster = 8;
@@ -770,12 +770,12 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
       continue;
     }
     const int K = std::min(S.m, S.n);
-    // blocks of about 12 columns keep the 12 warps of a CTA busy in every inner round:
-    // 2, 4 or 8 CTAs per sector, then more block groups per CTA for larger sectors
+    // blocks of about 6 columns give each of the 6 warps of a CTA one pair per inner
+    // round; 2, 4 or 8 CTAs per sector, then more block groups per CTA when larger
     int cl = 2;
-    while (cl < kBigCluster && K >= 24 * 2 * cl) cl *= 2;
-    int g = std::max(1, (K + 12 * cl) / (24 * cl));
-    while (g < 16 && block_smem_need(S.m, S.n, cl, g) > kBlockSmemMax) ++g;
+    while (cl < kBigCluster && K >= 12 * 2 * cl) cl *= 2;
+    int g = std::max(1, (K + 6 * cl) / (12 * cl));
+    while (g < 32 && block_smem_need(S.m, S.n, cl, g) > kBlockSmemMax) ++g;
     const int64_t need = block_smem_need(S.m, S.n, cl, g);
     if (need <= kBlockSmemMax) {
       key[k] = {kSvdClusterBlock, cl};
