@@ -38,6 +38,10 @@ SMALL = dict(L=32, N=32, CHI=512, WORKLOAD="bose_hubbard_L32_nmax4_N32_J1_U2_dt0
 # FP64 peak of the GB300 CUDA cores: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz.
 # (An FMA-chain probe measured 1.195 TFLOP/s, i.e. 2 FMA/clk/SM at the clock it ran.)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# DRAM bytes per launch of the SVD phase of a saturated layer of this workload (the block-Jacobi
+# cluster kernel 1342 MB read + 7337 MB written, the one-CTA kernel 5 MB read), from an ncu
+# capture of dram__bytes_read.sum + dram__bytes_write.sum; set to None when those kernels change.
+NCU_TRAFFIC = {"svd": (1342.1 + 7336.8 + 5.3) * 1e6}
 KERNEL_BOUND = {"theta": "alu", "svd": "alu", "gemm": "alu", "select": "hbm", "lambda": "hbm",
                 "scatter": "hbm", "expect": "hbm", "amplitude": "alu"}
 
@@ -225,6 +229,7 @@ def run_ours(args, world, rank, local):
     gates = m.tebd.GateTable("bh", L, D, DT, J=J, U=U)
     step = lambda: m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
 
+    fp64_measured = m.fp64_peak_probe(stream.cuda_stream)
     prep = 0
     while prep < args.max_prep and sum(psi.bond_dims(L // 2).values()) < CHI:
         step()
@@ -265,13 +270,17 @@ def run_ours(args, world, rank, local):
         achieved = kd["flops"] / (kd["ms"] / 1000.0) / 1e9
         peak, unit = FP64_PEAK_GFLOPS, "GFLOP/s"
     roofline = {"kernel": dom, "bound": KERNEL_BOUND[dom], "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get(dom) if args.case == "full" else None,
+                "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the phase",
                 "per_launch": {"flops" if unit == "GFLOP/s" else "bytes":
                                (kd["flops"] if unit == "GFLOP/s" else kd["bytes"]) / max(kd["launches"], 1),
                                "ms": kd["ms"] / max(kd["launches"], 1)},
                 "peak_source": ("FP64 CUDA-core peak from unit counts and the 2070 MHz max clock "
-                                "(152 SMs x 2 FMA/clk x 2 flop); an FMA-chain probe measured 1195 GFLOP/s")
+                                "(152 SMs x 2 FMA/clk x 2 flop)")
                 if unit == "GFLOP/s" else "MEASURED_PEAKS.json hbm_gbs (measured copy)",
+                "fp64_peak_measured_gflops": fp64_measured,
+                "frac_of_measured_fp64": achieved / fp64_measured if unit == "GFLOP/s" else None,
                 "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                                 "share": v["ms"] / max(sum(x["ms"] for x in ks.values()), 1e-12)}
                             for k, v in ks.items() if v["launches"]}}

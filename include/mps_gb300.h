@@ -255,6 +255,14 @@ MPS_API int64_t mps_launch_count(void);
 MPS_API int mps_last_batch_sweeps(mps_t h, int* n_sectors, int64_t* sweeps_sum, int* sweeps_max);
 
 /*
+ * mps_fp64_peak_probe - measured FP64 FMA throughput of the current device in GFLOP/s
+ * (independent FMA chains on every SM, about 70 ms).  The paper has no counterpart; the
+ * SVD and GEMM kernels here are bound by this rate, so it is the denominator to read
+ * their roofline against.  Allocates a small buffer on cuda_stream; synchronises it.
+ */
+MPS_API int mps_fp64_peak_probe(double* gflops, void* cuda_stream);
+
+/*
  * mps_plan_sectors - the integer sector planner alone (host code, no GPU needed).
  * Given the charge tables of bonds s, s+1, s+2 (ascending charges), it lists every
  * compatible (l, m, r) with 0 <= l-m <= d-1 and 0 <= m-r <= d-1, and every

@@ -85,6 +85,7 @@ _SIGS = {
     "mps_reset_kernel_stats": (ctypes.c_int, [_h]),
     "mps_launch_count": (ctypes.c_int64, []),
     "mps_svd_work_bytes": (ctypes.c_int64, [ctypes.c_int, _intp, _intp]),
+    "mps_fp64_peak_probe": (ctypes.c_int, [_dblp, _vp]),
     "mps_svd_sectors_noalloc": (ctypes.c_int, [ctypes.c_int, _intp, _intp, _vp, _i64p, _vp, _i64p, _vp, _i64p,
                                                _vp, _i64p, _vp, _vp]),
     "mps_svd_sectors": (ctypes.c_int, [ctypes.c_int, _intp, _intp, _vp, _i64p, _vp, _i64p, _vp, _i64p, _vp,
@@ -363,6 +364,15 @@ def footprint_bytes(L: int, d: int, N: int, chi_max: int) -> tuple[int, int]:
     if rc != MPS_OK:
         raise MPSError(rc, "mps_footprint_bytes")
     return a.value, w.value
+
+
+def fp64_peak_probe(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current GPU, GFLOP/s."""
+    g = ctypes.c_double()
+    rc = lib.mps_fp64_peak_probe(ctypes.byref(g), _default_stream() if stream is None else stream)
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_fp64_peak_probe")
+    return g.value
 
 
 def launch_count() -> int:
