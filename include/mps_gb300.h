@@ -255,6 +255,20 @@ MPS_API int64_t mps_launch_count(void);
 MPS_API int mps_last_batch_sweeps(mps_t h, int* n_sectors, int64_t* sweeps_sum, int* sweeps_max);
 
 /*
+ * mps_zgemm_tc - the tensor-core complex GEMM kernel alone, on device memory:
+ * C = A B with A (M x K), B (K x N), C (M x N) complex128 row-major (leading
+ * dimensions lda >= K, ldb >= N, ldc >= N, in complex numbers).  precision must be
+ * MPS_TF32: the complex product is lowered to one real GEMM
+ * [Cr Ci] = [Ar Ai] [[Br, Bi], [-Bi, Br]] and run by tcgen05.mma kind::tf32 with
+ * FP32 accumulation in tensor memory (the reduced-precision sector GEMM of the
+ * precision mode, Sec. II: "efficient use of tensor cores").  d_work is device
+ * scratch of at least 256 + 64 * ceil(M/128) * ceil(N/64) bytes.  Returns
+ * MPS_ETIMEOUT if a bounded wait inside the kernel expired.  Synchronises cuda_stream.
+ */
+MPS_API int mps_zgemm_tc(int precision, int M, int N, int K, const double* d_A, int lda, const double* d_B,
+                         int ldb, double* d_C, int ldc, void* d_work, int64_t work_bytes, void* cuda_stream);
+
+/*
  * mps_fp64_peak_probe - measured FP64 FMA throughput of the current device in GFLOP/s
  * (independent FMA chains on every SM, about 70 ms).  The paper has no counterpart; the
  * SVD and GEMM kernels here are bound by this rate, so it is the denominator to read

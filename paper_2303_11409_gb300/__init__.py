@@ -10,5 +10,5 @@ from ._binding import (EXPORTED, LIB_PATH, MPS, MPS_BF16X3, MPS_EINVAL, MPS_ECHA
                        plan_sectors,
                        svd_sectors, svd_work_bytes)
 from ._binding import MPS_NOALLOC_SCRATCH_BYTES, svd_sectors_noalloc  # noqa: F401
-from ._binding import Executor, footprint_bytes, fp64_peak_probe  # noqa: F401
+from ._binding import Executor, footprint_bytes, fp64_peak_probe, zgemm_tc  # noqa: F401
 from . import models, tebd, serve  # noqa: F401

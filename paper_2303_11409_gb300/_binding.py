@@ -86,6 +86,8 @@ _SIGS = {
     "mps_launch_count": (ctypes.c_int64, []),
     "mps_svd_work_bytes": (ctypes.c_int64, [ctypes.c_int, _intp, _intp]),
     "mps_fp64_peak_probe": (ctypes.c_int, [_dblp, _vp]),
+    "mps_zgemm_tc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                    ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_int64, _vp]),
     "mps_svd_sectors_noalloc": (ctypes.c_int, [ctypes.c_int, _intp, _intp, _vp, _i64p, _vp, _i64p, _vp, _i64p,
                                                _vp, _i64p, _vp, _vp]),
     "mps_svd_sectors": (ctypes.c_int, [ctypes.c_int, _intp, _intp, _vp, _i64p, _vp, _i64p, _vp, _i64p, _vp,
@@ -364,6 +366,29 @@ def footprint_bytes(L: int, d: int, N: int, chi_max: int) -> tuple[int, int]:
     if rc != MPS_OK:
         raise MPSError(rc, "mps_footprint_bytes")
     return a.value, w.value
+
+
+def zgemm_tc(A: np.ndarray, B: np.ndarray, precision: int = MPS_TF32, stream=None) -> np.ndarray:
+    """C = A B (complex) on the tensor cores through mps_zgemm_tc; torch holds the device buffers."""
+    import torch
+    A = np.ascontiguousarray(A, np.complex128)
+    B = np.ascontiguousarray(B, np.complex128)
+    M, K = A.shape
+    K2, N = B.shape
+    if K2 != K:
+        raise ValueError("inner dimensions differ")
+    dev = torch.device("cuda")
+    dA = torch.from_numpy(A.view(np.float64).copy()).to(dev)
+    dB = torch.from_numpy(B.view(np.float64).copy()).to(dev)
+    dC = torch.zeros(2 * M * N, dtype=torch.float64, device=dev)
+    wb = 256 + 64 * ((M + 127) // 128) * ((N + 63) // 64)
+    dW = torch.zeros(wb, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    rc = lib.mps_zgemm_tc(precision, M, N, K, dA.data_ptr(), K, dB.data_ptr(), N, dC.data_ptr(), N, dW.data_ptr(),
+                          wb, st)
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_zgemm_tc")
+    return dC.cpu().numpy().view(np.complex128).reshape(M, N)
 
 
 def fp64_peak_probe(stream=None) -> float:

@@ -67,3 +67,24 @@ def test_svd_many_sectors_one_launch(gpu_lib):
     mats = [W.random_complex(s, rng) for s in shapes]
     for M, (sig, Y, sw) in zip(mats, gpu_lib.svd_sectors(mats)):
         _check(M, sig, Y, sw)
+
+
+# ---------------------------------------------------------------------------
+# tensor-core (tcgen05, TF32) complex GEMM
+# ---------------------------------------------------------------------------
+TC_SHAPES = [(1, 1, 1), (8, 16, 4), (100, 70, 90), (129, 65, 33), (128, 64, 32), (300, 200, 150), (37, 300, 257)]
+
+
+@pytest.mark.parametrize("M,N,K", TC_SHAPES)
+def test_zgemm_tc_tf32(gpu_lib, M, N, K):
+    """TF32 keeps 10 mantissa bits (unit roundoff 2^-11); with FP32 accumulation the error of
+    each output is bounded by about sqrt(K) * 2^-11 * sum |a||b|; checked against that."""
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = W.random_complex((M, K), rng)
+    B = W.random_complex((K, N), rng)
+    C = gpu_lib.zgemm_tc(A, B)
+    ref = A @ B
+    bound = (np.abs(A) @ np.abs(B)) * (4 * 2.0 ** -11) * np.sqrt(K) + 1e-12
+    assert np.all(np.abs(C - ref) <= bound), np.max(np.abs(C - ref) / bound)
+    # and it is really a product, not noise: relative error well below 1
+    assert np.linalg.norm(C - ref) <= 5e-3 * np.linalg.norm(ref)
