@@ -55,7 +55,16 @@ typedef struct mps_s* mps_t;
 #define MPS_ECUDA    -5   /* a CUDA runtime error */
 #define MPS_ETIMEOUT -6   /* a bounded device wait expired */
 
-/* Precision modes of the sector GEMMs.  SVD, truncation and renormalisation are FP64 in all modes. */
+/*
+ * Precision modes of the sector GEMMs (the Theta' build and the reassembly product).
+ * SVD, truncation and renormalisation are FP64 in all modes.  In MPS_TF32 and
+ * MPS_BF16X3 the SVD treats singular values at or below 2 u |M(c)|_F as zero
+ * (u = 2^-11 and 2^-17, the rounding level of the GEMM inputs), so bond dimensions
+ * stay below the oracle's; the observable error of each mode against the FP64
+ * result is stated with its tests.  A bounded-wait expiry inside a tensor-core GEMM
+ * is reported as MPS_ETIMEOUT by the update call that launched it, or, for the
+ * reassembly product, by the next update call on the same handle or executor.
+ */
 #define MPS_FP64   0
 #define MPS_TF32   1
 #define MPS_BF16X3 2
@@ -105,8 +114,8 @@ MPS_API int mps_apply_gate2(mps_t h, int site, const double* gate_blocks, int ch
 
 /*
  * mps_apply_layer - n independent two-site updates on one handle in one set of
- * launches (the paper's "independent two-site updates ... processed in parallel",
- * Sec. II).  sites[k] are left sites of pairwise disjoint pairs (no two differ by
+ * launches (Sec. II: two-site updates on disjoint pairs are independent and may
+ * run in parallel).  sites[k] are left sites of pairwise disjoint pairs (no two differ by
  * less than 2); gate_blocks[k] are host gate blocks; chi and cutoff as above;
  * trunc_err_out (optional) receives n values.
  */
@@ -131,8 +140,8 @@ MPS_API int mps_apply_gate2_batch(int n, mps_t* hs, const int* sites, const doub
  * come and go (requests admitted and completed) without the workspace moving.
  * mps_exec_create: cuda_stream as for mps_create.  mps_exec_destroy: after its stream drains.
  * mps_exec_apply: as mps_apply_gate2_batch, on the executor's stream and workspace;
- *   the handles may differ in L, d, chi_max (independent problems, Sec. II: "independent
- *   two-site updates ... processed in parallel").
+ *   the handles may differ in L, d, chi_max (independent problems; Sec. II treats
+ *   independent two-site updates as parallel work).
  */
 typedef struct mps_s* mps_exec_t;
 MPS_API int mps_exec_create(mps_exec_t* out, void* cuda_stream);
@@ -257,13 +266,15 @@ MPS_API int mps_last_batch_sweeps(mps_t h, int* n_sectors, int64_t* sweeps_sum, 
 /*
  * mps_zgemm_tc - the tensor-core complex GEMM kernel alone, on device memory:
  * C = A B with A (M x K), B (K x N), C (M x N) complex128 row-major (leading
- * dimensions lda >= K, ldb >= N, ldc >= N, in complex numbers).  precision must be
- * MPS_TF32: the complex product is lowered to one real GEMM
- * [Cr Ci] = [Ar Ai] [[Br, Bi], [-Bi, Br]] and run by tcgen05.mma kind::tf32 with
- * FP32 accumulation in tensor memory (the reduced-precision sector GEMM of the
- * precision mode, Sec. II: "efficient use of tensor cores").  d_work is device
- * scratch of at least 256 + 64 * ceil(M/128) * ceil(N/64) bytes.  Returns
- * MPS_ETIMEOUT if a bounded wait inside the kernel expired.  Synchronises cuda_stream.
+ * dimensions lda >= K, ldb >= N, ldc >= N, in complex numbers).  precision is
+ * MPS_TF32 (inputs rounded to TF32) or MPS_BF16X3 (each input split into two BF16
+ * terms, three products accumulated); the complex product is lowered to one real
+ * GEMM and run by tcgen05.mma with FP32 accumulation in tensor memory.  This is the
+ * kernel the reduced-precision modes use for the sector GEMMs (Sec. II names tensor
+ * cores for the GPU contraction).  d_work is device scratch of at least
+ * 256 + 64 * ceil(M/128) * ceil(N/64) bytes.  Returns MPS_EINVAL for another
+ * precision or bad sizes, MPS_ETIMEOUT if a bounded wait inside the kernel expired.
+ * Synchronises cuda_stream.
  */
 MPS_API int mps_zgemm_tc(int precision, int M, int N, int K, const double* d_A, int lda, const double* d_B,
                          int ldb, double* d_C, int ldc, void* d_work, int64_t work_bytes, void* cuda_stream);
@@ -294,7 +305,7 @@ MPS_API int mps_plan_sectors(int d, int nl, const int32_t* lc, const int32_t* ld
 
 /*
  * mps_svd_sectors - the batched per-sector SVD kernel alone, on device memory
- * (one-sided Jacobi in FP64; Sec. II "block-sparse SVDs on submatrices").
+ * (one-sided Jacobi in FP64; Sec. II: the local update needs one SVD per charge block).
  * For each sector k it decomposes M_k = diag(rowscale_k) A_k, A_k being the
  * m_k x n_k row-major complex128 matrix at d_mats + mat_off[k] (in complex
  * numbers), rowscale_k the m_k doubles at d_rowscale + row_off[k] (NULL = 1):

@@ -16,7 +16,7 @@ What it follows (arXiv:2303.11409, Sec. II):
     0 <= l - m <= d - 1 and carries no explicit physical index;
   * the two-site update: Theta is split by its middle charge into blocks
     Theta(c) of at most chi x chi each, and each is decomposed by its own SVD
-    (Sec. II, "block-sparse SVDs on submatrices");
+    (Sec. II: one SVD per charge block of Theta);
   * the CPU algorithm "loops over allowed charge values to construct Theta(c)"
     (Sec. II, CPU/GPU implementation paragraph): update() does exactly that.
 

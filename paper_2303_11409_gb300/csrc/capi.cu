@@ -155,6 +155,14 @@ struct UpdWork {
   int64_t gate_off = 0;                             // byte offset of this update's staged gate
 };
 
+// Noise floor of the sector SVD relative to |M(c)|_F: the rounding level of the
+// GEMM that formed Theta' (0 selects the FP64 default inside the SVD kernel).
+double svd_floor_rel(int precision) {
+  if (precision == MPS_TF32) return 0x1p-10;     // TF32 inputs: 2 u, u = 2^-11
+  if (precision == MPS_BF16X3) return 0x1p-16;   // hi + lo split: 2 u, u = 2^-17
+  return 0.0;
+}
+
 int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   if (reqs.empty()) return MPS_OK;
   cudaStream_t st = owner->stream;
@@ -164,6 +172,8 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   // ---- K0: plan every update and size the workspace --------------------------------
   int64_t ws = 0;
   int n_sec_total = 0, n_tiles = 0, n_tasks = 0, max_tri = 0;
+  int64_t n_tc_tiles = 0, n_tc_segs = 0;   // reduced-precision updates: tensor-core Theta' tiles
+  bool any_tc = false;
   int64_t theta_bytes_begin = 0, theta_bytes_end = 0;
   int64_t scatter_bound = 0, gemm_tiles_bound = 0, gemm_tasks_bound = 0, lam_bound = 0;
   for (int u = 0; u < nreq; ++u) {
@@ -218,17 +228,26 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   for (int u = 0; u < nreq; ++u) {
     mps_s* h = reqs[u].h;
     const int s = reqs[u].site, d = h->d;
+    const bool tc = h->precision != MPS_FP64;
+    any_tc = any_tc || tc;
     const BondTable &Lb = h->bonds[s], &Mb = h->bonds[s + 1], &Rb = h->bonds[s + 2];
     for (int li = 0; li < Lb.size(); ++li)
       for (int ri = 0; ri < Rb.size(); ++ri) {
         const int l = Lb.charge[li], r = Rb.charge[ri];
         if (l - r < 0 || l - r > 2 * (d - 1)) continue;
-        bool any = false;
+        int nm = 0;
         for (int mi = 0; mi < Mb.size(); ++mi) {
           const int m = Mb.charge[mi];
-          if (l - m >= 0 && l - m <= d - 1 && m - r >= 0 && m - r <= d - 1) { any = true; break; }
+          if (l - m >= 0 && l - m <= d - 1 && m - r >= 0 && m - r <= d - 1) ++nm;
         }
-        if (!any) continue;
+        if (nm == 0) continue;
+        if (tc) {   // one tile set per output charge c, one K segment per middle charge m
+          const int nc = std::min(l, r + d - 1) - std::max(r, l - d + 1) + 1;
+          n_tc_segs += (int64_t)nm * nc;
+          n_tc_tiles += (int64_t)nc * ((Lb.dim[li] + kTcTileM - 1) / kTcTileM) *
+                        ((Rb.dim[ri] + kTcTileN - 1) / kTcTileN);
+          continue;
+        }
         n_tasks++;
         n_tiles += ((Lb.dim[li] + kTile - 1) / kTile) * ((Rb.dim[ri] + kTile - 1) / kTile);
       }
@@ -236,11 +255,15 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   const int64_t phase1_desc = a256((int64_t)sizeof(ThetaTask) * n_tasks) + a256(sizeof(TileRef) * (int64_t)n_tiles) +
                               a256((int64_t)sizeof(SvdSector) * n_sec_total) +
                               a256((int64_t)sizeof(SelectSector) * n_sec_total) +
-                              a256((int64_t)sizeof(SelectTask) * nreq) + gates_bytes;
+                              a256((int64_t)sizeof(SelectTask) * nreq) + gates_bytes +
+                              a256((int64_t)sizeof(TcSegment) * n_tc_segs) + a256((int64_t)sizeof(TcTile) * n_tc_tiles);
   const int64_t phase2_desc = a256((int64_t)sizeof(LambdaTask) * lam_bound) +
                               a256((int64_t)sizeof(ScatterTask) * scatter_bound) +
                               a256((int64_t)sizeof(GemmTask) * gemm_tasks_bound) +
-                              a256((int64_t)sizeof(TileRef) * gemm_tiles_bound);
+                              a256((int64_t)sizeof(TileRef) * gemm_tiles_bound) +
+                              (any_tc ? a256((int64_t)sizeof(TcSegment) * gemm_tasks_bound) +
+                                            a256((int64_t)sizeof(TcTile) * gemm_tiles_bound)
+                                      : 0);
   const int64_t desc_bytes = std::max(phase1_desc, phase2_desc);
   ws = desc_off + desc_bytes;
 
@@ -250,8 +273,13 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     if (e != cudaSuccess) return fail(owner, MPS_ENOMEM, std::string("workspace: ") + cudaGetErrorString(e));
     e = owner->pin_in.reserve((size_t)std::max<int64_t>(desc_bytes, 1) + 4096);
     if (e != cudaSuccess) return fail(owner, MPS_ENOMEM, "pinned staging");
-    e = owner->pin_out.reserve((size_t)(res_off - kept_off) + 4096);
+    e = owner->pin_out.reserve((size_t)a256(res_off + (int64_t)sizeof(SelectResult) * nreq - kept_off) + 4096);
     if (e != cudaSuccess) return fail(owner, MPS_ENOMEM, "pinned staging");
+    if (any_tc && !owner->tc_flag) {
+      e = cudaMalloc(&owner->tc_flag, 256);
+      if (e == cudaSuccess) e = cudaMemsetAsync(owner->tc_flag, 0, 256, st);
+      if (e != cudaSuccess) return fail(owner, MPS_ENOMEM, "tensor-core error flag");
+    }
   }
   char* base = (char*)owner->work.p;
   auto dptr = [&](int64_t off) { return base + off; };
@@ -262,6 +290,9 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   // ---- build phase-1 descriptors ------------------------------------------------------
   std::vector<ThetaTask> tasks; tasks.reserve(n_tasks);
   std::vector<TileRef> tiles; tiles.reserve(n_tiles);
+  std::vector<TcSegment> tcseg; tcseg.reserve(n_tc_segs);
+  std::vector<TcTile> tctile[2];            // [0]: TF32 updates, [1]: BF16x3 updates
+  double tc_th_flops = 0;
   std::vector<SvdSector> svd; svd.reserve(n_sec_total);
   std::vector<SelectSector> selsec; selsec.reserve(n_sec_total);
   std::vector<SelectTask> seltask; seltask.reserve(nreq);
@@ -321,6 +352,39 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
         T.sn = gate_sn(n, d);
         T.Dl = Lb.dim[li];
         T.Dr = Rb.dim[ri];
+        if (h->precision != MPS_FP64) {
+          // direct form on the tensor cores: Theta'(c)[l, r] = sum_m (G_n[c, m] B[l,m]) . B[m,r]
+          const double* gh = reqs[u].gate + 2 * gate_block_off(n, d);
+          std::vector<TcTile>& out_tiles = tctile[h->precision == MPS_BF16X3];
+          for (int i = 0; i < T.nm; ++i) tc_th_flops += 8.0 * T.Dl * T.Dm[i] * T.Dr;   // as the FP64 form
+          tc_th_flops += 8.0 * T.nm * T.nc * T.Dl * T.Dr;
+          for (int k = 0; k < T.nc; ++k) {
+            const int seg0 = (int)tcseg.size();
+            for (int i = 0; i < T.nm; ++i) {
+              const int64_t gidx = (int64_t)T.go[k] * T.sn + T.gi[i];
+              const double2 g = make_double2(gh[2 * gidx], gh[2 * gidx + 1]);
+              if (g.x == 0.0 && g.y == 0.0) continue;   // the term vanishes
+              TcSegment G;
+              G.A = T.A[i]; G.B = T.B[i];
+              G.Kc = T.Dm[i];
+              G.sar = T.Dm[i]; G.sac = 1;
+              G.sbr = T.Dr; G.sbc = 1;
+              G.alpha = g;
+              tcseg.push_back(G);
+            }
+            const int nseg = (int)tcseg.size() - seg0;
+            for (int ti = 0; ti < (T.Dl + kTcTileM - 1) / kTcTileM; ++ti)
+              for (int tj = 0; tj < (T.Dr + kTcTileN - 1) / kTcTileN; ++tj) {
+                TcTile C;
+                C.C = T.out[k]; C.ldc = T.ldo[k];
+                C.M = T.Dl; C.N = T.Dr;
+                C.row0 = ti * kTcTileM; C.col0 = tj * kTcTileN;
+                C.seg0 = seg0; C.nseg = nseg;
+                out_tiles.push_back(C);
+              }
+          }
+          continue;
+        }
         const int task_id = (int)tasks.size();
         tasks.push_back(T);
         for (int ti = 0; ti < (T.Dl + kTile - 1) / kTile; ++ti)
@@ -338,6 +402,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       S.sigma = reinterpret_cast<double*>(dptr(W[u].sig_off[si]));
       S.Y = reinterpret_cast<double2*>(dptr(W[u].y_off[si]));
       S.status = reinterpret_cast<int*>(dptr(status_off)) + sec_global;
+      S.floor_rel = svd_floor_rel(h->precision);
       svd.push_back(S);
       selsec.push_back(SelectSector{S.sigma, std::min(E.rows, E.cols)});
     }
@@ -355,6 +420,9 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   const int64_t o_svd = sg.put(svd_sorted.data(), (int64_t)svd_sorted.size());
   const int64_t o_selsec = sg.put(selsec.data(), (int64_t)selsec.size());
   const int64_t o_seltask = sg.put(seltask.data(), (int64_t)seltask.size());
+  const int64_t o_tcseg = sg.put(tcseg.data(), (int64_t)tcseg.size());
+  const int64_t o_tctile0 = sg.put(tctile[0].data(), (int64_t)tctile[0].size());
+  const int64_t o_tctile1 = sg.put(tctile[1].data(), (int64_t)tctile[1].size());
   if (sg.size > desc_bytes) return fail(owner, MPS_EINVAL, "internal: descriptor bound exceeded");
   CUDA_OR_FAIL(owner, cudaMemcpyAsync(dptr(desc_off), owner->pin_in.p, sg.size, cudaMemcpyHostToDevice, st));
   CUDA_OR_FAIL(owner, cudaEventRecord(owner->staged, st));
@@ -365,6 +433,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     for (int i = 0; i < T.nm; ++i) th_flops += 8.0 * T.Dl * T.Dm[i] * T.Dr;
     th_flops += 8.0 * T.nm * T.nc * T.Dl * T.Dr;
   }
+  th_flops += tc_th_flops;
   for (int u = 0; u < nreq; ++u) {
     const int s = reqs[u].site;
     th_bytes += 16.0 * (double)(reqs[u].h->sites[s].nnz + reqs[u].h->sites[s + 1].nnz);
@@ -378,9 +447,18 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   }
   // ---- K1, K2, K3 ---------------------------------------------------------------------
   CUDA_OR_FAIL(owner, cudaMemsetAsync(dptr(theta_bytes_begin), 0, theta_bytes_end - theta_bytes_begin, st));
-  CUDA_OR_FAIL(owner, timed(owner, MPS_K_THETA, !tiles.empty(), th_flops, th_bytes, [&] {
-    return launch_theta(reinterpret_cast<ThetaTask*>(dptr(desc_off + o_tasks)),
-                        reinterpret_cast<TileRef*>(dptr(desc_off + o_tiles)), (int)tiles.size(), st);
+  const bool any_theta = !tiles.empty() || !tctile[0].empty() || !tctile[1].empty();
+  CUDA_OR_FAIL(owner, timed(owner, MPS_K_THETA, any_theta, th_flops, th_bytes, [&] {
+    cudaError_t e = launch_theta(reinterpret_cast<ThetaTask*>(dptr(desc_off + o_tasks)),
+                                 reinterpret_cast<TileRef*>(dptr(desc_off + o_tiles)), (int)tiles.size(), st);
+    const TcSegment* d_seg = reinterpret_cast<TcSegment*>(dptr(desc_off + o_tcseg));
+    if (e == cudaSuccess)
+      e = launch_tc_zgemm(MPS_TF32, reinterpret_cast<TcTile*>(dptr(desc_off + o_tctile0)), (int)tctile[0].size(),
+                          d_seg, owner->tc_flag, st);
+    if (e == cudaSuccess)
+      e = launch_tc_zgemm(MPS_BF16X3, reinterpret_cast<TcTile*>(dptr(desc_off + o_tctile1)), (int)tctile[1].size(),
+                          d_seg, owner->tc_flag, st);
+    return e;
   }));
   CUDA_OR_FAIL(owner, timed(owner, MPS_K_SVD, !svd_sorted.empty(), svd_flops, svd_bytes, [&] {   // one or more kernels
     const SvdSector* d_svd = reinterpret_cast<SvdSector*>(dptr(desc_off + o_svd));
@@ -393,8 +471,16 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   }));
   const int64_t out_bytes = res_off + (int64_t)sizeof(SelectResult) * nreq - kept_off;
   CUDA_OR_FAIL(owner, cudaMemcpyAsync(owner->pin_out.p, dptr(kept_off), out_bytes, cudaMemcpyDeviceToHost, st));
+  int* tc_err_host = reinterpret_cast<int*>((char*)owner->pin_out.p + a256(out_bytes));
+  *tc_err_host = 0;
+  if (owner->tc_flag)   // this update's Theta' GEMM, or the reassembly GEMM of the previous one
+    CUDA_OR_FAIL(owner, cudaMemcpyAsync(tc_err_host, owner->tc_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CUDA_OR_FAIL(owner, cudaStreamSynchronize(st));
   resolve_pending(owner);
+  if (*tc_err_host) {
+    CUDA_OR_FAIL(owner, cudaMemsetAsync(owner->tc_flag, 0, sizeof(int), st));
+    return fail(owner, MPS_ETIMEOUT, "a bounded wait inside the tensor-core GEMM expired");
+  }
   const int* kept = (const int*)owner->pin_out.p;
   const int* sstat = (const int*)((char*)owner->pin_out.p + (status_off - kept_off));
   const SelectResult* res = (const SelectResult*)((char*)owner->pin_out.p + (res_off - kept_off));
@@ -404,6 +490,9 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   std::vector<ScatterTask> sc;
   std::vector<GemmTask> gm;
   std::vector<TileRef> gt;
+  std::vector<TcSegment> gseg;
+  std::vector<TcTile> gtile[2];             // [0]: TF32 updates, [1]: BF16x3 updates
+  double tc_gm_flops = 0, tc_gm_bytes = 0;
   int64_t sc_elems = 0;
   std::vector<char> apply(nreq, 0);
   {
@@ -491,6 +580,29 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       }
       for (int li = E.l0; li < E.l1; ++li) {
         const int b = newL[u].find(Lb.charge[li], E.c);
+        if (h->precision != MPS_FP64) {   // B^[s][l, c] = (Theta'(c)[rows of l] . Y(c)[:, :k]) / |S_kept|
+          TcSegment G;
+          G.A = th + (int64_t)(Lb.off[li] - Lb.off[E.l0]) * E.cols;
+          G.sar = E.cols; G.sac = 1;
+          G.B = Y; G.sbr = 1; G.sbc = E.cols;
+          G.Kc = E.cols;
+          G.alpha = make_double2(scale, 0.0);
+          const int seg = (int)gseg.size();
+          gseg.push_back(G);
+          const int Dl = Lb.dim[li];
+          for (int ti = 0; ti < (Dl + kTcTileM - 1) / kTcTileM; ++ti)
+            for (int tj = 0; tj < (k + kTcTileN - 1) / kTcTileN; ++tj) {
+              TcTile C;
+              C.C = dstL + newL[u].blocks[b].off; C.ldc = k;
+              C.M = Dl; C.N = k;
+              C.row0 = ti * kTcTileM; C.col0 = tj * kTcTileN;
+              C.seg0 = seg; C.nseg = 1;
+              gtile[h->precision == MPS_BF16X3].push_back(C);
+            }
+          tc_gm_flops += 8.0 * Dl * k * E.cols;
+          tc_gm_bytes += 16.0 * ((double)Dl * E.cols + (double)E.cols * k + (double)Dl * k);
+          continue;
+        }
         GemmTask G;
         G.A = th + (int64_t)(Lb.off[li] - Lb.off[E.l0]) * E.cols;
         G.sar = E.cols; G.sac = 1;
@@ -521,10 +633,13 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     const int64_t o_sc = s2.put(sc.data(), (int64_t)sc.size());
     const int64_t o_gm = s2.put(gm.data(), (int64_t)gm.size());
     const int64_t o_gt = s2.put(gt.data(), (int64_t)gt.size());
+    const int64_t o_gseg = s2.put(gseg.data(), (int64_t)gseg.size());
+    const int64_t o_gtile0 = s2.put(gtile[0].data(), (int64_t)gtile[0].size());
+    const int64_t o_gtile1 = s2.put(gtile[1].data(), (int64_t)gtile[1].size());
     if (s2.size > desc_bytes) return fail(owner, MPS_EINVAL, "internal: descriptor bound exceeded");
     CUDA_OR_FAIL(owner, cudaMemcpyAsync(dptr(desc_off), owner->pin_in.p, s2.size, cudaMemcpyHostToDevice, st));
     CUDA_OR_FAIL(owner, cudaEventRecord(owner->staged, st));
-    double lam_bytes = 0, gm_flops = 0, gm_bytes = 0;
+    double lam_bytes = 0, gm_flops = tc_gm_flops, gm_bytes = tc_gm_bytes;
     for (const LambdaTask& T : lam) lam_bytes += 16.0 * T.k;
     for (const GemmTask& T : gm) {
       gm_flops += 8.0 * T.M * T.N * T.K;
@@ -536,9 +651,18 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     CUDA_OR_FAIL(owner, timed(owner, MPS_K_SCATTER, sc_elems > 0, 0.0, 32.0 * (double)sc_elems, [&] {
       return launch_scatter(reinterpret_cast<ScatterTask*>(dptr(desc_off + o_sc)), (int)sc.size(), sc_elems, st);
     }));
-    CUDA_OR_FAIL(owner, timed(owner, MPS_K_GEMM, !gt.empty(), gm_flops, gm_bytes, [&] {
-      return launch_gemm(reinterpret_cast<GemmTask*>(dptr(desc_off + o_gm)),
-                         reinterpret_cast<TileRef*>(dptr(desc_off + o_gt)), (int)gt.size(), st);
+    const bool any_gemm = !gt.empty() || !gtile[0].empty() || !gtile[1].empty();
+    CUDA_OR_FAIL(owner, timed(owner, MPS_K_GEMM, any_gemm, gm_flops, gm_bytes, [&] {
+      cudaError_t e = launch_gemm(reinterpret_cast<GemmTask*>(dptr(desc_off + o_gm)),
+                                  reinterpret_cast<TileRef*>(dptr(desc_off + o_gt)), (int)gt.size(), st);
+      const TcSegment* d_seg = reinterpret_cast<TcSegment*>(dptr(desc_off + o_gseg));
+      if (e == cudaSuccess)
+        e = launch_tc_zgemm(MPS_TF32, reinterpret_cast<TcTile*>(dptr(desc_off + o_gtile0)), (int)gtile[0].size(),
+                            d_seg, owner->tc_flag, st);
+      if (e == cudaSuccess)
+        e = launch_tc_zgemm(MPS_BF16X3, reinterpret_cast<TcTile*>(dptr(desc_off + o_gtile1)), (int)gtile[1].size(),
+                            d_seg, owner->tc_flag, st);
+      return e;
     }));
   }
   for (int u = 0; u < nreq; ++u) {
@@ -581,7 +705,7 @@ int mps_create(mps_t* out, int L, int d, const int32_t* site_charges, int precis
   if (!out) return MPS_EINVAL;
   *out = nullptr;
   if (L < 2 || d < 2 || d > MPS_MAX_D || chi_max < 1 || !site_charges) return MPS_EINVAL;
-  if (precision != MPS_FP64) return MPS_EINVAL;   // reduced-precision sector GEMMs are not built
+  if (precision != MPS_FP64 && precision != MPS_TF32 && precision != MPS_BF16X3) return MPS_EINVAL;
   for (int s = 0; s < L; ++s)
     if (site_charges[s] < 0 || site_charges[s] > d - 1) return MPS_ECHARGE;
   mps_s* h = new mps_s();
@@ -662,6 +786,7 @@ int mps_destroy(mps_t h) {
   if (h->fork) cudaEventDestroy(h->fork);
   for (auto& p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  if (h->tc_flag) cudaFree(h->tc_flag);
   h->work.release();
   h->pin_in.release();
   h->pin_out.release();

@@ -1,19 +1,29 @@
-// Complex GEMMs on the 5th-generation tensor cores (tcgen05), TF32 inputs with
-// FP32 accumulation in tensor memory, for the reduced-precision sector GEMMs.
+// Complex GEMMs on the 5th-generation tensor cores (tcgen05) for the
+// reduced-precision sector GEMMs: TF32 inputs, or BF16x3 split precision, with
+// FP32 accumulation in tensor memory.
 //
 // A complex product C = A B (A: M x K, B: K x N, complex128 in global memory) is
-// lowered to one real GEMM with the same multiply count:
-//     [Cr | Ci] = [Ar | Ai] . [[Br, Bi], [-Bi, Br]]        (M x 2K) . (2K x 2N).
+// lowered to one real GEMM (M x 2K) . (2K x 2N) with the same multiply count.  The
+// real K index is interleaved, so that every complex input lands in two adjacent
+// K elements and is read from memory once:
+//     A'(i, 2k) = Re A(i, k)            A'(i, 2k + 1) = Im A(i, k)
+//     B'(2k, j) = Re B(k, j)            B'(2k + 1, j) = -Im B(k, j)       (column j: Re C)
+//     B'(2k, 64 + j) = Im B(k, j)       B'(2k + 1, 64 + j) = Re B(k, j)   (column 64 + j: Im C)
 // Each CTA computes a 128 x 64 complex output tile: a 128 x 128 real FP32
 // accumulator in TMEM (128 columns), fed from shared memory in the canonical
 // no-swizzle K-major layout (core matrices of 8 rows x 16 bytes; LBO = next core
-// matrix along K, SBO = next 8-row group).  The operand tiles are converted from
-// FP64 (and optionally multiplied by a complex scalar per K segment, which is how
-// the gate coefficient of the Theta build enters) while being staged, so the FP64
-// master copies in HBM are read exactly once; one elected thread issues
-// tcgen05.mma for each K step and commits to an mbarrier that releases the stage.
-// Every wait on an mbarrier is bounded: on expiry the CTA records an error and
-// still frees its tensor memory before returning.
+// matrix along K, SBO = next 8-row group).  The operands are converted from FP64
+// (A multiplied by a complex scalar per K segment, which is how the gate
+// coefficient of the Theta build and the 1/|S_kept| of the reassembly enter)
+// while being staged: TF32 rounds to nearest; BF16x3 splits x = hi + lo with
+// hi = bf16(x), lo = bf16(x - hi) and accumulates lo.hi + hi.lo + hi.hi, dropping
+// lo.lo (about 2^-16 relative).  The global loads of the next K step are issued
+// before the MMAs of the current one complete; one thread issues tcgen05.mma and
+// commits to an mbarrier that releases the stage.  Every wait on an mbarrier is
+// bounded: on expiry the CTA records an error and still frees its tensor memory.
+// The epilogue stages the accumulator through shared memory so that the FP64
+// stores of each output row are contiguous.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <vector>
@@ -26,12 +36,14 @@ namespace {
 constexpr int kTcM = 128;          // rows of the output tile (TMEM lanes)
 constexpr int kTcNc = 64;          // complex columns of the output tile
 constexpr int kTcN = 2 * kTcNc;    // real accumulator columns
-constexpr int kTcK = 32;           // real K elements staged per step (4 MMAs of K = 8)
+constexpr int kTcKc = 16;          // complex K staged per step (32 real K elements)
 constexpr int kTcThreads = 128;
 constexpr int kTcStages = 2;
-constexpr uint32_t kTileABytes = kTcM * kTcK * 4;   // 16 KB
-constexpr uint32_t kTileBBytes = kTcN * kTcK * 4;   // 16 KB
+constexpr uint32_t kStageBytes = 32 * 1024;          // TF32: A, B (16 KB each); BF16x3: A hi, A lo, B hi, B lo
 constexpr long long kWaitCycles = 4000000000LL;      // bound of every mbarrier wait (~2 s)
+constexpr int kEpiLd = 17;                           // padded row stride (double2) of the epilogue staging
+
+static_assert(kTcM == kTcTileM && kTcNc == kTcTileN, "tile shape");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -47,14 +59,10 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
   return d;                                // base offset 0, relative LBO, no swizzle
 }
 
-// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// byte offset of element (row, k) inside a staged K-major tile with 8-row core groups
-__device__ __forceinline__ uint32_t core_off(int row, int k) {
-  return (uint32_t)((row >> 3) * (kTcK / 4) * 128 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+// Instruction descriptors: D = F32, A and B K-major; operand format 2 = TF32, 1 = BF16.
+__host__ __device__ constexpr uint32_t idesc_f32acc(int fmt, int M, int N) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -80,31 +88,64 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 
-struct TcSegment {            // one K segment: C += (alpha * A_seg) . B_seg
-  const double2* A;           // M x Kc complex, row stride lda
-  const double2* B;           // Kc x N complex, row stride ldb
-  int Kc, lda, ldb;
-  double2 alpha;
+__device__ __forceinline__ float to_tf32(double x) {   // round to nearest (ties away) in TF32
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"((float)x));
+  return __uint_as_float(r);
+}
+
+// x = hi + lo to about 2^-17 relative: hi = bf16(x), lo = bf16(x - hi)
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn((float)x);
+  lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+}
+
+__device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc,
+                                          bool tf32) {
+  if (tf32)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// Staged layout of one K step (32 real K elements) as K-major core matrices of
+// 8 rows x 16 bytes: byte offset of (row, real k) =
+//   TF32 (4 B):  (row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4
+//   BF16 (2 B):  (row >> 3) * 512  + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2
+// The complex element kc of a row fills real k = 2 kc (real part) and 2 kc + 1.
+// Thread -> (row & 7, kc) is chosen so that a warp writes whole core matrices
+// (conflict-free) and reads 8 rows x 4 consecutive complex elements of global memory.
+template <bool TF32>
+struct Lanes {
+  static __device__ __forceinline__ int r7(int tid) { return TF32 ? (tid >> 1) & 7 : (tid >> 2) & 7; }
+  static __device__ __forceinline__ int kc(int tid) {
+    return TF32 ? (((tid >> 4) << 1) | (tid & 1)) : (((tid >> 5) << 2) | (tid & 3));
+  }
+  // offset of (row = 8 g + r7, real k = 2 kc) inside an operand tile
+  static __device__ __forceinline__ uint32_t off(int g, int r7, int kc) {
+    return TF32 ? (uint32_t)(g * 1024 + (kc >> 1) * 128 + r7 * 16 + (kc & 1) * 8)
+                : (uint32_t)(g * 512 + (kc >> 2) * 128 + r7 * 16 + (kc & 3) * 4);
+  }
 };
 
-// The work of one CTA: a 128 x 64 complex tile of one output matrix over a list of segments.
-struct TcTile {
-  double2* C;                 // output, row stride ldc; written (not accumulated)
-  int ldc, M, N;              // full output extent (rows, complex columns)
-  int row0, col0;
-  int seg0, nseg;             // segments [seg0, seg0 + nseg) of the segment array
-};
-
-__global__ void __launch_bounds__(kTcThreads, 1) tc_zgemm_kernel(const TcTile* __restrict__ tiles,
-                                                                  const TcSegment* __restrict__ segs,
-                                                                  int* __restrict__ error_flag) {
+template <int P>
+__global__ void __launch_bounds__(kTcThreads) tc_zgemm_kernel(const TcTile* __restrict__ tiles,
+                                                              const TcSegment* __restrict__ segs,
+                                                              int* __restrict__ error_flag) {
+  constexpr bool kTF32 = (P == MPS_TF32);
+  using Ln = Lanes<kTF32>;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t bar_mma[kTcStages];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const TcTile T = tiles[blockIdx.x];
-  unsigned char* tileA[kTcStages] = {smem, smem + kTileABytes + kTileBBytes};
-  unsigned char* tileB[kTcStages] = {smem + kTileABytes, smem + 2 * kTileABytes + kTileBBytes};
+  const int r7 = Ln::r7(tid), kc = Ln::kc(tid);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
@@ -119,76 +160,126 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_zgemm_kernel(const TcTile* _
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  constexpr uint32_t idesc = idesc_tf32(kTcM, kTcN);
+  constexpr uint32_t idesc = idesc_f32acc(kTF32 ? 2 : 1, kTcM, kTcN);
+
+  int nsteps = 0;
+  for (int sg = 0; sg < T.nseg; ++sg) nsteps += (max(segs[T.seg0 + sg].Kc, 0) + kTcKc - 1) / kTcKc;
+
+  // registers of one step: A rows 8 g + r7 (g < 16), B columns 8 g + r7 (g < 8), element kc
+  double2 ra[kTcM / 8], rb[kTcNc / 8];
+  double2 ralpha = make_double2(0.0, 0.0);
+  int cur_sg = 0, cur_k0 = 0;
+  auto load_step = [&]() {
+    while (segs[T.seg0 + cur_sg].Kc <= cur_k0) { ++cur_sg; cur_k0 = 0; }   // skips empty segments
+    const TcSegment S = segs[T.seg0 + cur_sg];
+    const int k = cur_k0 + kc;
+    const bool kin = k < S.Kc;
+#pragma unroll
+    for (int g = 0; g < kTcM / 8; ++g) {
+      const int row = T.row0 + 8 * g + r7;
+      ra[g] = (kin && row < T.M) ? S.A[(int64_t)row * S.sar + (int64_t)k * S.sac] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int g = 0; g < kTcNc / 8; ++g) {
+      const int col = T.col0 + 8 * g + r7;
+      rb[g] = (kin && col < T.N) ? S.B[(int64_t)k * S.sbr + (int64_t)col * S.sbc] : make_double2(0.0, 0.0);
+    }
+    ralpha = S.alpha;
+    cur_k0 += kTcKc;
+  };
+  auto store_step = [&](unsigned char* stage) {
+    if constexpr (kTF32) {
+      unsigned char* a_s = stage;
+      unsigned char* b_s = stage + 16 * 1024;
+#pragma unroll
+      for (int g = 0; g < kTcM / 8; ++g) {
+        const double2 x = ra[g];
+        const double xr = ralpha.x * x.x - ralpha.y * x.y, xi = ralpha.x * x.y + ralpha.y * x.x;
+        *reinterpret_cast<float2*>(a_s + Ln::off(g, r7, kc)) = make_float2(to_tf32(xr), to_tf32(xi));
+      }
+#pragma unroll
+      for (int g = 0; g < kTcNc / 8; ++g) {
+        const double2 y = rb[g];
+        *reinterpret_cast<float2*>(b_s + Ln::off(g, r7, kc)) = make_float2(to_tf32(y.x), to_tf32(-y.y));
+        *reinterpret_cast<float2*>(b_s + Ln::off(g + kTcNc / 8, r7, kc)) = make_float2(to_tf32(y.y), to_tf32(y.x));
+      }
+    } else {
+      unsigned char* ah = stage;
+      unsigned char* al = stage + 8 * 1024;
+      unsigned char* bh = stage + 16 * 1024;
+      unsigned char* bl = stage + 24 * 1024;
+      __nv_bfloat16 h0, l0, h1, l1;
+#pragma unroll
+      for (int g = 0; g < kTcM / 8; ++g) {
+        const double2 x = ra[g];
+        split_bf16(ralpha.x * x.x - ralpha.y * x.y, h0, l0);
+        split_bf16(ralpha.x * x.y + ralpha.y * x.x, h1, l1);
+        const uint32_t o = Ln::off(g, r7, kc);
+        *reinterpret_cast<__nv_bfloat162*>(ah + o) = __halves2bfloat162(h0, h1);
+        *reinterpret_cast<__nv_bfloat162*>(al + o) = __halves2bfloat162(l0, l1);
+      }
+#pragma unroll
+      for (int g = 0; g < kTcNc / 8; ++g) {
+        const double2 y = rb[g];
+        const uint32_t o_re = Ln::off(g, r7, kc), o_im = Ln::off(g + kTcNc / 8, r7, kc);
+        split_bf16(y.x, h0, l0);
+        split_bf16(-y.y, h1, l1);
+        *reinterpret_cast<__nv_bfloat162*>(bh + o_re) = __halves2bfloat162(h0, h1);   // [Br; -Bi]
+        *reinterpret_cast<__nv_bfloat162*>(bl + o_re) = __halves2bfloat162(l0, l1);
+        split_bf16(y.y, h0, l0);
+        split_bf16(y.x, h1, l1);
+        *reinterpret_cast<__nv_bfloat162*>(bh + o_im) = __halves2bfloat162(h0, h1);   // [Bi; Br]
+        *reinterpret_cast<__nv_bfloat162*>(bl + o_im) = __halves2bfloat162(l0, l1);
+      }
+    }
+  };
 
   bool ok = true;
-  int step = 0;                   // global K step counter (for stage and parity)
-  for (int sg = 0; sg < T.nseg && ok; ++sg) {
-    const TcSegment S = segs[T.seg0 + sg];
-    const int K2 = 2 * S.Kc;      // real K of this segment
-    for (int k0 = 0; k0 < K2; k0 += kTcK) {
-      const int st = step % kTcStages;
-      if (step >= kTcStages) {    // the MMAs that last read this stage must have completed
-        const bool w = mbar_wait(&bar_mma[st], (uint32_t)((step / kTcStages - 1) & 1));
-        ok = __syncthreads_and(w);   // every thread takes the same branch
-        if (!ok) break;
-      }
-      // stage A: rows row0.., real K index kk in [k0, k0+32): kk < Kc -> Re, else Im (times alpha)
-      unsigned char* a_s = tileA[st];
-      for (int e = tid; e < kTcM * kTcK; e += kTcThreads) {
-        const int r = e / kTcK, kk = e % kTcK;
-        const int gk = k0 + kk, row = T.row0 + r;
-        float v = 0.f;
-        if (row < T.M && gk < K2) {
-          const int kc = gk < S.Kc ? gk : gk - S.Kc;
-          const double2 x = S.A[(int64_t)row * S.lda + kc];
-          const double xr = S.alpha.x * x.x - S.alpha.y * x.y;
-          const double xi = S.alpha.x * x.y + S.alpha.y * x.x;
-          v = (float)(gk < S.Kc ? xr : xi);
-        }
-        *reinterpret_cast<float*>(a_s + core_off(r, kk)) = v;
-      }
-      // stage B^T (K-major): real column n of [[Br, Bi], [-Bi, Br]] for the tile's 64 complex columns
-      unsigned char* b_s = tileB[st];
-      for (int e = tid; e < kTcN * kTcK; e += kTcThreads) {
-        const int n = e / kTcK, kk = e % kTcK;
-        const int gk = k0 + kk;
-        const int j = T.col0 + (n < kTcNc ? n : n - kTcNc);
-        float v = 0.f;
-        if (j < T.N && gk < K2) {
-          const bool upper = gk < S.Kc;
-          const int kc = upper ? gk : gk - S.Kc;
-          const double2 y = S.B[(int64_t)kc * S.ldb + j];
-          if (n < kTcNc) v = (float)(upper ? y.x : -y.y);   // real output column: [Br; -Bi]
-          else v = (float)(upper ? y.y : y.x);              // imaginary output column: [Bi; Br]
-        }
-        *reinterpret_cast<float*>(b_s + core_off(n, kk)) = v;
-      }
-      // make the staged tiles visible to the tensor core (async proxy), then issue
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (tid == 0) {
-        const uint32_t a0 = smem_u32(a_s), b0 = smem_u32(b_s);
-#pragma unroll
-        for (int q = 0; q < kTcK / 8; ++q) {         // K = 8 per MMA: two core matrices along K
-          const uint64_t ad = make_desc(a0 + q * 256, 128, (kTcK / 4) * 128);
-          const uint64_t bd = make_desc(b0 + q * 256, 128, (kTcK / 4) * 128);
-          const uint32_t acc = (step > 0 || q > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-            smem_u32(&bar_mma[st])));
-      }
-      ++step;
+  int step = 0;                   // K steps issued so far (stage = step % 2)
+  if (nsteps > 0) load_step();
+  for (; step < nsteps;) {
+    const int st = step % kTcStages;
+    if (step >= kTcStages) {      // the MMAs that last read this stage must have completed
+      const bool w = mbar_wait(&bar_mma[st], (uint32_t)((step / kTcStages - 1) & 1));
+      ok = __syncthreads_and(w);  // every thread takes the same branch
+      if (!ok) break;
     }
+    unsigned char* stage = smem + st * kStageBytes;
+    store_step(stage);
+    // make the staged tiles visible to the tensor core (async proxy), then issue
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t s0 = smem_u32(stage);
+      if constexpr (kTF32) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {             // K = 8 per MMA: two core matrices along K
+          const uint64_t ad = make_desc(s0 + q * 256, 128, 1024);
+          const uint64_t bd = make_desc(s0 + 16 * 1024 + q * 256, 128, 1024);
+          mma_issue(tmem, ad, bd, idesc, (step > 0 || q > 0) ? 1u : 0u, true);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {             // K = 16 per MMA; hi.hi + hi.lo + lo.hi
+          const uint64_t ah = make_desc(s0 + q * 256, 128, 512);
+          const uint64_t al = make_desc(s0 + 8 * 1024 + q * 256, 128, 512);
+          const uint64_t bh = make_desc(s0 + 16 * 1024 + q * 256, 128, 512);
+          const uint64_t bl = make_desc(s0 + 24 * 1024 + q * 256, 128, 512);
+          mma_issue(tmem, al, bh, idesc, (step > 0 || q > 0) ? 1u : 0u, false);
+          mma_issue(tmem, ah, bl, idesc, 1u, false);
+          mma_issue(tmem, ah, bh, idesc, 1u, false);
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(&bar_mma[st])));
+    }
+    ++step;
+    if (step < nsteps) load_step();   // global loads of the next step overlap the MMAs
   }
   // wait for the last MMAs (also on the error path, so that none is in flight when the
-  // tensor memory is freed), then read the accumulator: warp w owns TMEM lanes 32w..32w+31
+  // tensor memory is freed); a commit completes after every earlier MMA of the thread
   if (step > 0) {
     const int last = (step - 1) % kTcStages;
     const bool w = mbar_wait(&bar_mma[last], (uint32_t)(((step - 1) / kTcStages) & 1));
@@ -197,32 +288,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_zgemm_kernel(const TcTile* _
   tc_fence_after();
   __syncthreads();
   if (ok) {
-    const int row = T.row0 + warp * 32 + lane;
+    // warp w owns TMEM lanes (rows) 32 w .. 32 w + 31; staged through shared memory
+    // (free now) so that the FP64 stores of a row segment are contiguous
+    double2* stg = reinterpret_cast<double2*>(smem) + warp * 32 * kEpiLd;
+    const int rr = lane >> 4, cc = lane & 15;
     for (int c0 = 0; c0 < kTcNc; c0 += 16) {
       uint32_t re[16], im[16];
-      const uint32_t taddr_re = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      const uint32_t taddr_im = taddr_re + kTcNc;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
-            "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]), "=r"(re[14]),
-            "=r"(re[15])
-          : "r"(taddr_re));
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7]),
-            "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]), "=r"(im[14]),
-            "=r"(im[15])
-          : "r"(taddr_im));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      if (row < T.M) {
+      if (nsteps > 0) {
+        const uint32_t taddr_re = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        const uint32_t taddr_im = taddr_re + kTcNc;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]),
+              "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]),
+              "=r"(re[14]), "=r"(re[15])
+            : "r"(taddr_re));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]),
+              "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]),
+              "=r"(im[14]), "=r"(im[15])
+            : "r"(taddr_im));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      } else {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = T.col0 + c0 + j;
-          if (col < T.N)
-            T.C[(int64_t)row * T.ldc + col] = make_double2((double)__uint_as_float(re[j]), (double)__uint_as_float(im[j]));
-        }
+        for (int j = 0; j < 16; ++j) re[j] = im[j] = 0u;   // no K at all: the product is zero
       }
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        stg[lane * kEpiLd + j] = make_double2((double)__uint_as_float(re[j]), (double)__uint_as_float(im[j]));
+      __syncwarp();
+      const int col = T.col0 + c0 + cc;
+#pragma unroll 4
+      for (int r2 = 0; r2 < 16; ++r2) {
+        const int rl = 2 * r2 + rr, row = T.row0 + warp * 32 + rl;
+        if (row < T.M && col < T.N) T.C[(int64_t)row * T.ldc + col] = stg[rl * kEpiLd + cc];
+      }
+      __syncwarp();
     }
   } else if (tid == 0) {
     atomicExch(error_flag, 1);
@@ -232,22 +334,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_zgemm_kernel(const TcTile* _
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)kTcN));
 }
 
-bool g_tc_attr = false;
+template <int P>
+cudaError_t launch_tc(const TcTile* d_tiles, int n_tiles, const TcSegment* d_segs, int* d_err, cudaStream_t st) {
+  static bool attr = false;
+  constexpr int smem = kTcStages * (int)kStageBytes;
+  static_assert(4 * 32 * kEpiLd * 16 <= smem, "epilogue staging fits in the operand stages");
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc_zgemm_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  count_launch();
+  tc_zgemm_kernel<P><<<n_tiles, kTcThreads, smem, st>>>(d_tiles, d_segs, d_err);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
-constexpr int kTcSmem = kTcStages * (kTileABytes + kTileBBytes);
-
-cudaError_t launch_tc_zgemm(const TcTile* d_tiles, int n_tiles, const TcSegment* d_segs, int* d_err, cudaStream_t st) {
+cudaError_t launch_tc_zgemm(int precision, const TcTile* d_tiles, int n_tiles, const TcSegment* d_segs, int* d_err,
+                            cudaStream_t st) {
   if (n_tiles <= 0) return cudaSuccess;
-  if (!g_tc_attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_zgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    if (e != cudaSuccess) return e;
-    g_tc_attr = true;
-  }
-  count_launch();
-  tc_zgemm_kernel<<<n_tiles, kTcThreads, kTcSmem, st>>>(d_tiles, d_segs, d_err);
-  return cudaGetLastError();
+  if (precision == MPS_TF32) return launch_tc<MPS_TF32>(d_tiles, n_tiles, d_segs, d_err, st);
+  if (precision == MPS_BF16X3) return launch_tc<MPS_BF16X3>(d_tiles, n_tiles, d_segs, d_err, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace mps
@@ -257,9 +366,9 @@ using namespace mps;
 // Standalone entry point: C = A B on the tensor cores (see the header).
 extern "C" int mps_zgemm_tc(int precision, int M, int N, int K, const double* d_A, int lda, const double* d_B,
                             int ldb, double* d_C, int ldc, void* d_work, int64_t work_bytes, void* cuda_stream) {
-  if (precision != MPS_TF32) return MPS_EINVAL;
+  if (precision != MPS_TF32 && precision != MPS_BF16X3) return MPS_EINVAL;
   if (M < 1 || N < 1 || K < 1 || lda < K || ldb < N || ldc < N || !d_A || !d_B || !d_C || !d_work) return MPS_EINVAL;
-  const int tm = (M + kTcM - 1) / kTcM, tn = (N + kTcNc - 1) / kTcNc;
+  const int tm = (M + kTcTileM - 1) / kTcTileM, tn = (N + kTcTileN - 1) / kTcTileN;
   static_assert(16 + sizeof(TcSegment) <= 256 && sizeof(TcTile) <= 64, "scratch layout");
   const int64_t need = 256 + (int64_t)sizeof(TcTile) * tm * tn;   // flag, segment, then the tiles
   if (work_bytes < need) return MPS_EINVAL;
@@ -271,7 +380,9 @@ extern "C" int mps_zgemm_tc(int precision, int M, int N, int K, const double* d_
   TcSegment seg;
   seg.A = reinterpret_cast<const double2*>(d_A);
   seg.B = reinterpret_cast<const double2*>(d_B);
-  seg.Kc = K; seg.lda = lda; seg.ldb = ldb;
+  seg.Kc = K;
+  seg.sar = lda; seg.sac = 1;
+  seg.sbr = ldb; seg.sbc = 1;
   seg.alpha = make_double2(1.0, 0.0);
   std::vector<TcTile> tiles;
   for (int i = 0; i < tm; ++i)
@@ -279,7 +390,7 @@ extern "C" int mps_zgemm_tc(int precision, int M, int N, int K, const double* d_
       TcTile t;
       t.C = reinterpret_cast<double2*>(d_C);
       t.ldc = ldc; t.M = M; t.N = N;
-      t.row0 = i * kTcM; t.col0 = j * kTcNc;
+      t.row0 = i * kTcTileM; t.col0 = j * kTcTileN;
       t.seg0 = 0; t.nseg = 1;
       tiles.push_back(t);
     }
@@ -288,7 +399,7 @@ extern "C" int mps_zgemm_tc(int precision, int M, int N, int K, const double* d_
   if (cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TcTile) * tiles.size(), cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return MPS_ECUDA;
-  if (launch_tc_zgemm(d_tiles, (int)tiles.size(), d_seg, d_err, st) != cudaSuccess) return MPS_ECUDA;
+  if (launch_tc_zgemm(precision, d_tiles, (int)tiles.size(), d_seg, d_err, st) != cudaSuccess) return MPS_ECUDA;
   int err = 0;
   if (cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MPS_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return MPS_ECUDA;

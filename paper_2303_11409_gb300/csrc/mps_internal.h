@@ -95,6 +95,7 @@ struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   int m, n;
   int mode;                   // kSvdSmem, kSvdCluster or kSvdClusterBlock
   int groups;                 // block Jacobi: block pairs per CTA and round
+  double floor_rel;           // noise floor relative to |M|_F; 0 selects 32 eps (FP64 input)
 };
 
 // Scratch layout of a batch of sector SVDs (cluster-mode sectors only need global scratch).
@@ -190,6 +191,7 @@ struct mps_s {
   mps::KStat kstat[MPS_K_COUNT];
   std::vector<mps::PendingTiming> pending;   // event pairs not yet read back
   std::vector<cudaEvent_t> event_pool;
+  int* tc_flag = nullptr;                 // set by a tensor-core GEMM whose bounded wait expired
 
   double2* slot_ptr(int s, int slot) { return d_sites + site_base[s] + (slot ? site_cap[s] : 0); }
   double* lambda_ptr(int b) { return d_lambda + lam_base[b]; }
@@ -210,6 +212,26 @@ cudaError_t launch_svd_groups(const SvdSector* d_secs, const std::vector<SvdGrou
 cudaError_t launch_select(const SelectSector* d_secs, const SelectTask* d_tasks, int n_tasks,
                           int* d_kept, SelectResult* d_res, cudaStream_t st);
 cudaError_t launch_gemm(const GemmTask* d_tasks, const TileRef* d_tiles, int n_tiles, cudaStream_t st);
+
+// Tensor-core complex GEMM (k_tc.cu): C(tile) = sum over segments (alpha A_seg) . B_seg,
+// A(i, k) = A[i * sar + k * sac], B(k, j) = B[k * sbr + j * sbc] (complex strides).
+struct TcSegment {            // one K segment
+  const double2* A;
+  const double2* B;
+  int Kc;                     // complex K of the segment
+  int sar, sac, sbr, sbc;
+  double2 alpha;
+};
+struct TcTile {               // a 128 x 64 complex output tile over segments [seg0, seg0 + nseg)
+  double2* C;                 // row-major, row stride ldc; the tile overwrites C
+  int ldc, M, N;
+  int row0, col0;
+  int seg0, nseg;
+};
+constexpr int kTcTileM = 128, kTcTileN = 64;
+// precision is MPS_TF32 or MPS_BF16X3; *d_err is set to 1 when a bounded wait expires.
+cudaError_t launch_tc_zgemm(int precision, const TcTile* d_tiles, int n_tiles, const TcSegment* d_segs, int* d_err,
+                            cudaStream_t st);
 cudaError_t launch_scatter(const ScatterTask* d_tasks, int n_tasks, int64_t n_elems, cudaStream_t st);
 cudaError_t launch_lambda(const LambdaTask* d_tasks, int n_tasks, cudaStream_t st);
 

@@ -70,7 +70,7 @@ def test_svd_many_sectors_one_launch(gpu_lib):
 
 
 # ---------------------------------------------------------------------------
-# tensor-core (tcgen05, TF32) complex GEMM
+# tensor-core (tcgen05) complex GEMM, TF32 and BF16x3
 # ---------------------------------------------------------------------------
 TC_SHAPES = [(1, 1, 1), (8, 16, 4), (100, 70, 90), (129, 65, 33), (128, 64, 32), (300, 200, 150), (37, 300, 257)]
 
@@ -88,3 +88,25 @@ def test_zgemm_tc_tf32(gpu_lib, M, N, K):
     assert np.all(np.abs(C - ref) <= bound), np.max(np.abs(C - ref) / bound)
     # and it is really a product, not noise: relative error well below 1
     assert np.linalg.norm(C - ref) <= 5e-3 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("M,N,K", TC_SHAPES)
+def test_zgemm_tc_bf16x3(gpu_lib, M, N, K):
+    """BF16x3: x = hi + lo represents x to about 2^-17 relative; the dropped lo.lo term and
+    the split errors leave each product within about 3 * 2^-18 |a||b|, and FP32 accumulation
+    adds at most K * 2^-24 sum |a||b|.  The bound 2^-15 + K 2^-24 is 16x below the error of a
+    dropped cross term (2^-9), so a missing hi.lo or lo.hi product fails it."""
+    rng = np.random.default_rng(M * 5 + N * 11 + K)
+    A = W.random_complex((M, K), rng)
+    B = W.random_complex((K, N), rng)
+    C = gpu_lib.zgemm_tc(A, B, precision=gpu_lib.MPS_BF16X3)
+    ref = A @ B
+    bound = (np.abs(A) @ np.abs(B)) * (2.0 ** -15 + 2 * K * 2.0 ** -24) + 1e-14
+    assert np.all(np.abs(C - ref) <= bound), np.max(np.abs(C - ref) / bound)
+    assert np.linalg.norm(C - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+def test_zgemm_tc_rejects_bad_arguments(gpu_lib):
+    A = np.ones((4, 4), np.complex128)
+    with pytest.raises(gpu_lib.MPSError):
+        gpu_lib.zgemm_tc(A, A, precision=gpu_lib.MPS_FP64)

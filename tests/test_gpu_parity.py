@@ -187,7 +187,7 @@ def test_invalid_arguments(gpu_lib):
     with pytest.raises(m.MPSError):
         m.MPS(2, [1, 2], 4)                    # occupation outside [0, d-1]
     with pytest.raises(m.MPSError):
-        m.MPS(2, [1, 0], 4, precision=m.MPS_TF32)
+        m.MPS(2, [1, 0], 4, precision=7)        # no such precision mode
 
 
 def test_annihilating_gate_leaves_state_unchanged(gpu_lib):
