@@ -42,6 +42,10 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # cluster kernel 1342 MB read + 7337 MB written, the one-CTA kernel 5 MB read), from an ncu
 # capture of dram__bytes_read.sum + dram__bytes_write.sum; set to None when those kernels change.
 NCU_TRAFFIC = {"svd": (1342.1 + 7336.8 + 5.3) * 1e6}
+# Tensor peaks of the reduced-precision GEMMs, from the measured dense BF16 rate times the nominal
+# ratio of the format (TF32 1.1 / BF16 2.25 PFLOP/s dense); BF16x3 issues three BF16 MMAs per product.
+BF16_MEASURED_TFLOPS = 1913.8
+TENSOR_PEAK_TFLOPS = {"tf32": BF16_MEASURED_TFLOPS * 1.1 / 2.25, "bf16x3": BF16_MEASURED_TFLOPS / 3.0}
 KERNEL_BOUND = {"theta": "alu", "svd": "alu", "gemm": "alu", "select": "hbm", "lambda": "hbm",
                 "scatter": "hbm", "expect": "hbm", "amplitude": "alu"}
 
@@ -60,12 +64,16 @@ def parse():
     p.add_argument("--serve-requests", type=int, default=48)
     p.add_argument("--case", default="full", choices=["full", "small"],
                    help="small: L=32, chi=512 (for profiler captures); full: the benchmark workload")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16x3"],
+                   help="sector GEMMs in FP64 (default) or on the tensor cores; SVD and truncation stay FP64")
     a = p.parse_args()
+    global L, N_PART, CHI, WORKLOAD, UPDATES_PER_STEP
     if a.case == "small":
-        global L, N_PART, CHI, WORKLOAD, UPDATES_PER_STEP
         L, N_PART, CHI, WORKLOAD = SMALL["L"], SMALL["N"], SMALL["CHI"], SMALL["WORKLOAD"]
         UPDATES_PER_STEP = (L // 2) + (L - 1) // 2 + (L // 2)
         a.no_cpu_baseline = True
+    if a.precision != "fp64":
+        WORKLOAD = WORKLOAD.replace("_fp64", f"_{a.precision}")
     return a
 
 
@@ -227,13 +235,23 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
     psi = m.MPS(D, W.mott_occupations(L), CHI, stream=stream.cuda_stream)
     gates = m.tebd.GateTable("bh", L, D, DT, J=J, U=U)
-    step = lambda: m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
 
     fp64_measured = m.fp64_peak_probe(stream.cuda_stream)
     prep = 0
     while prep < args.max_prep and sum(psi.bond_dims(L // 2).values()) < CHI:
-        step()
+        m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
         prep += 1
+    if args.precision != "fp64":
+        # the same saturated state, continued with the sector GEMMs on the tensor cores
+        prec = {"tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[args.precision]
+        low = m.MPS(D, W.mott_occupations(L), CHI, precision=prec, stream=stream.cuda_stream)
+        for b in range(1, L):
+            low.set_bond(b, psi.bond(b))
+        for s_ in range(L):
+            low.set_site(s_, psi.site(s_))
+        psi.close()
+        psi = low
+    step = lambda: m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
     for _ in range(args.warmup):
         step()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -271,7 +289,7 @@ def run_ours(args, world, rank, local):
         peak, unit = FP64_PEAK_GFLOPS, "GFLOP/s"
     roofline = {"kernel": dom, "bound": KERNEL_BOUND[dom], "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get(dom) if args.case == "full" else None,
+                "traffic": NCU_TRAFFIC.get(dom) if args.case == "full" and args.precision == "fp64" else None,
                 "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the phase",
                 "per_launch": {"flops" if unit == "GFLOP/s" else "bytes":
                                (kd["flops"] if unit == "GFLOP/s" else kd["bytes"]) / max(kd["launches"], 1),
@@ -280,10 +298,25 @@ def run_ours(args, world, rank, local):
                                 "(152 SMs x 2 FMA/clk x 2 flop)")
                 if unit == "GFLOP/s" else "MEASURED_PEAKS.json hbm_gbs (measured copy)",
                 "fp64_peak_measured_gflops": fp64_measured,
+                "precision": args.precision,
                 "frac_of_measured_fp64": achieved / fp64_measured if unit == "GFLOP/s" else None,
                 "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                                 "share": v["ms"] / max(sum(x["ms"] for x in ks.values()), 1e-12)}
                             for k, v in ks.items() if v["launches"]}}
+    if args.precision != "fp64":
+        # the tensor-core sector GEMMs (Theta' build and reassembly) against the format's peak
+        tc = {}
+        for k in ("theta", "gemm"):
+            v = ks[k]
+            if v["launches"] and v["ms"] > 0:
+                tf = v["flops"] / (v["ms"] / 1000.0) / 1e12
+                tc[k] = {"achieved": tf, "unit": "TFLOP/s", "peak": TENSOR_PEAK_TFLOPS[args.precision],
+                         "frac": tf / TENSOR_PEAK_TFLOPS[args.precision],
+                         "bytes_per_s_gb": v["bytes"] / (v["ms"] / 1000.0) / 1e9}
+        roofline["tensor_gemms"] = tc
+        roofline["tensor_peak_source"] = ("MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 ratio (1.1/2.25)"
+                                          if args.precision == "tf32" else
+                                          "MEASURED_PEAKS.json bf16_tflops / 3 (three BF16 MMAs per product)")
 
     # e2e: the public API with host buffers, host wall clock, one observable read back per step
     glen = m.gate_length(D)
@@ -309,9 +342,11 @@ def run_ours(args, world, rank, local):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else f"{args.precision}+f64", "data": "synthetic",
                 "config": config({"prep_steps": prep, "middle_bond_dim": mid_dims,
-                                  "parallelism": "replicas" if world > 1 else "single"}),
+                                  "parallelism": "replicas" if world > 1 else "single",
+                                  "precision": args.precision}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "step_ms": [round(x, 3) for x in step_ms]}
         print(json.dumps(line), flush=True)

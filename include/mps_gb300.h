@@ -57,11 +57,10 @@ typedef struct mps_s* mps_t;
 
 /*
  * Precision modes of the sector GEMMs (the Theta' build and the reassembly product).
- * SVD, truncation and renormalisation are FP64 in all modes.  In MPS_TF32 and
- * MPS_BF16X3 the SVD treats singular values at or below 2 u |M(c)|_F as zero
- * (u = 2^-11 and 2^-17, the rounding level of the GEMM inputs), so bond dimensions
- * stay below the oracle's; the observable error of each mode against the FP64
- * result is stated with its tests.  A bounded-wait expiry inside a tensor-core GEMM
+ * SVD, truncation and renormalisation are FP64 in all modes and follow the same
+ * rules (the reduced modes only round the GEMM inputs); the observable error of
+ * each mode against the FP64 result is stated with its tests.  A bounded-wait
+ * expiry inside a tensor-core GEMM
  * is reported as MPS_ETIMEOUT by the update call that launched it, or, for the
  * reassembly product, by the next update call on the same handle or executor.
  */

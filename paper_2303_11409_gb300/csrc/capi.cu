@@ -155,14 +155,6 @@ struct UpdWork {
   int64_t gate_off = 0;                             // byte offset of this update's staged gate
 };
 
-// Noise floor of the sector SVD relative to |M(c)|_F: the rounding level of the
-// GEMM that formed Theta' (0 selects the FP64 default inside the SVD kernel).
-double svd_floor_rel(int precision) {
-  if (precision == MPS_TF32) return 0x1p-10;     // TF32 inputs: 2 u, u = 2^-11
-  if (precision == MPS_BF16X3) return 0x1p-16;   // hi + lo split: 2 u, u = 2^-17
-  return 0.0;
-}
-
 int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   if (reqs.empty()) return MPS_OK;
   cudaStream_t st = owner->stream;
@@ -402,7 +394,6 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       S.sigma = reinterpret_cast<double*>(dptr(W[u].sig_off[si]));
       S.Y = reinterpret_cast<double2*>(dptr(W[u].y_off[si]));
       S.status = reinterpret_cast<int*>(dptr(status_off)) + sec_global;
-      S.floor_rel = svd_floor_rel(h->precision);
       svd.push_back(S);
       selsec.push_back(SelectSector{S.sigma, std::min(E.rows, E.cols)});
     }

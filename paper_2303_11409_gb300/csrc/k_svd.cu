@@ -26,9 +26,8 @@
 //                          hardware cluster barrier.
 // Jacobi pairs follow the round-robin ordering (disjoint pairs per round, one
 // warp per pair).  A pair is rotated when |a_p^dag a_q|^2 > tol^2 |a_p|^2 |a_q|^2,
-// tol = eps * max(n, 32), and both columns are above the noise floor f |M|_F
-// (f = 32 eps for an FP64 Theta, larger when Theta came from a reduced-precision
-// GEMM); singular values at or below the floor are reported as exactly 0.
+// tol = eps * max(n, 32), and both columns are above the noise floor 32 eps
+// |M|_F; singular values at or below the floor are reported as exactly 0.
 // Convergence is a sweep without a rotation; a sector that does not converge
 // within the sweep limit reports -1.  FP64 costs a warp 64 cycles per
 // instruction here, so per-pair scalar work is kept small (no square root in the
@@ -547,8 +546,7 @@ __device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int ncta
   // ---- one-sided Jacobi on the K columns (length n) of R^dag -----------------------------
   const double tol = kEps * (double)max(n, 32);
   const double tol2 = tol * tol;
-  const double floor_rel = S.floor_rel > 0.0 ? S.floor_rel : 32.0 * kEps;   // GEMM input precision
-  const double floor2 = floor_rel * floor_rel * fro2;
+  const double floor2 = (32.0 * kEps) * (32.0 * kEps) * fro2;
   bool converged = false;
   const int sweep = jacobi(W, n, ld, K, w, rank, nctas, sync, tol2, floor2, max_sweeps, converged);
 

@@ -95,7 +95,6 @@ struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   int m, n;
   int mode;                   // kSvdSmem, kSvdCluster or kSvdClusterBlock
   int groups;                 // block Jacobi: block pairs per CTA and round
-  double floor_rel;           // noise floor relative to |M|_F; 0 selects 32 eps (FP64 input)
 };
 
 // Scratch layout of a batch of sector SVDs (cluster-mode sectors only need global scratch).

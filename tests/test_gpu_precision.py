@@ -2,24 +2,25 @@
 
 In these modes only the two contractions of an update run on the tensor cores: the
 Theta' build and the reassembly product Theta' Y / |S_kept|.  The SVD, the global
-truncation and the renormalisation stay FP64, and the SVD treats singular values at
-or below 2 u |M(c)|_F as zero (u = 2^-11 for TF32, 2^-17 for BF16x3): below that
-level they cannot be told apart from the rounding of Theta'.
+truncation and the renormalisation stay FP64 and follow the FP64 rules unchanged, so
+the rounding of Theta' shows up as small singular values that the cutoff keeps and the
+chi cap trims like any others.
 
 Stated error against the FP64 oracle, after the whole run (max over sites/bonds);
 measured on GB300 in brackets:
     XXZ L=16, Neel, dt=0.05 x 20 steps, chi<=64, cutoff 1e-10 (600 updates)
-        TF32:   <Sz_i> 6e-3 [2.7e-3]   bond entropy 1e-2 [4.0e-3]   amplitude 8e-3 [3.5e-3]
-        BF16x3: <Sz_i> 8e-5 [2.8e-5]   bond entropy 1.5e-4 [4.9e-5] amplitude 1e-4 [4.3e-5]
+        TF32:   <Sz_i> 5e-3 [1.5e-3]   bond entropy 5e-3 [1.6e-3]   amplitude 1.5e-3 [3.1e-4]
+        BF16x3: <Sz_i> 8e-5 [2.1e-5]   bond entropy 1e-4 [2.7e-5]   amplitude 2e-5 [3.9e-6]
     Bose-Hubbard L=12, d=5, Mott, dt=0.05 x 8 steps, chi<=24 (176 updates)
-        TF32:   <n_i> 6e-3 [1.5e-3]    bond entropy 1e-2 [1.3e-3]
-        BF16x3: <n_i> 8e-5 [1.6e-5]    bond entropy 1.5e-4 [1.4e-5]
+        TF32:   <n_i> 5e-3 [1.6e-3]    bond entropy 5e-3 [1.1e-3]
+        BF16x3: <n_i> 8e-5 [2.2e-5]    bond entropy 1e-4 [2.1e-5]
+    one update on a random state, two-site product relative to its largest entry
+        TF32: 2e-3 [5.6e-4]            BF16x3: 5e-5 [1.3e-5]
 Each update perturbs the state by about u times a small factor (the number of terms
-summed per element enters as sqrt, the rounding is unbiased) plus the weight of the
-singular values under the floor, so the deviation grows like u sqrt(updates) to
-u * updates.  The kept bond dimensions are smaller than the oracle's (the floor
-removes the tail the rounding hides), so sector dimensions are not compared; the
-sector charges are.
+summed per element enters as sqrt, the rounding is unbiased), u = 2^-11 for TF32 and
+about 2^-17 for BF16x3, so the deviation grows like u sqrt(updates) to u * updates.
+On the XXZ run every update keeps the oracle's sector labels and dimensions (checked
+after every layer); that is a property of this run, not a guarantee of the mode.
 """
 import numpy as np
 import pytest
@@ -31,8 +32,8 @@ from tests.helpers import load_state, random_state, two_site_product
 pytestmark = pytest.mark.gpu
 
 TOL = {
-    "tf32": dict(obs=6e-3, ent=1e-2, amp=8e-3, prod=2e-3),
-    "bf16x3": dict(obs=8e-5, ent=1.5e-4, amp=1e-4, prod=5e-5),
+    "tf32": dict(obs=5e-3, ent=5e-3, amp=1.5e-3, prod=2e-3),
+    "bf16x3": dict(obs=8e-5, ent=1e-4, amp=2e-5, prod=5e-5),
 }
 
 
@@ -41,21 +42,28 @@ def _prec(m, name):
 
 
 def _run(m, L, d, occ, gate_of, steps, chi, cutoff, prec):
+    """Both evolutions; returns them and the fraction of layers after which every bond
+    table (sector labels and dimensions) equals the oracle's."""
     g = m.MPS(d, occ, chi, precision=prec)
     st = U1MPS.product(d, occ)
+    same = layers = 0
     for _ in range(steps):
         for sites, f in tebd.strang_layers(L):
             g.apply_layer(sites, [gate_of(s, f) for s in sites], chi, cutoff)
             for s in sites:
                 st.apply_gate2(s, gate_of(s, f), chi, cutoff)
-    return g, st
+            layers += 1
+            same += all(g.bond_dims(b) == st.bond[b] for b in range(L + 1))
+    return g, st, same / layers
 
 
 @pytest.mark.parametrize("name", ["tf32", "bf16x3"])
 def test_xxz_mixed_precision_observables(gpu_lib, name):
     L = 16
-    g, st = _run(gpu_lib, L, 2, W.neel_occupations(L), tebd.xxz_gates(L, 0.5, 0.05), 20, 64, 1e-10,
-                 _prec(gpu_lib, name))
+    g, st, same = _run(gpu_lib, L, 2, W.neel_occupations(L), tebd.xxz_gates(L, 0.5, 0.05), 20, 64, 1e-10,
+                       _prec(gpu_lib, name))
+    print(f"XXZ {name}: fraction of layers with the oracle's bond tables {same:.3f}")
+    assert same == 1.0
     t = TOL[name]
     dz = max(abs(g.expect(s, [-0.5, 0.5]) - st.expect_local(s, [-0.5, 0.5])) for s in range(L))
     dS = max(abs(g.entropy(b) - st.entropy(b)) for b in range(1, L))
@@ -73,8 +81,9 @@ def test_xxz_mixed_precision_observables(gpu_lib, name):
 @pytest.mark.parametrize("name", ["tf32", "bf16x3"])
 def test_bose_hubbard_mixed_precision_observables(gpu_lib, name):
     L, d = 12, 5
-    g, st = _run(gpu_lib, L, d, W.mott_occupations(L), tebd.bh_gates(L, d, 1.0, 2.0, 0.05), 8, 24, 1e-10,
-                 _prec(gpu_lib, name))
+    g, st, same = _run(gpu_lib, L, d, W.mott_occupations(L), tebd.bh_gates(L, d, 1.0, 2.0, 0.05), 8, 24, 1e-10,
+                       _prec(gpu_lib, name))
+    print(f"Bose-Hubbard {name}: fraction of layers with the oracle's bond tables {same:.3f}")
     t = TOL[name]
     n_op = np.arange(d)
     dn = max(abs(g.expect(s, n_op) - st.expect_local(s, n_op)) for s in range(L))
