@@ -38,10 +38,10 @@ SMALL = dict(L=32, N=32, CHI=512, WORKLOAD="bose_hubbard_L32_nmax4_N32_J1_U2_dt0
 # FP64 peak of the GB300 CUDA cores: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz.
 # (An FMA-chain probe measured 1.195 TFLOP/s, i.e. 2 FMA/clk/SM at the clock it ran.)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
-# DRAM bytes per launch of the SVD phase of a saturated layer of this workload (the block-Jacobi
-# cluster kernel 1342 MB read + 7337 MB written, the one-CTA kernel 5 MB read), from an ncu
-# capture of dram__bytes_read.sum + dram__bytes_write.sum; set to None when those kernels change.
-NCU_TRAFFIC = {"svd": (1342.1 + 7336.8 + 5.3) * 1e6}
+# DRAM bytes per launch of the SVD phase of a saturated layer of this workload, from an ncu
+# capture of dram__bytes_read.sum + dram__bytes_write.sum; emptied whenever those kernels change
+# (the grouped-pair block-Jacobi kernel has not been captured yet).
+NCU_TRAFFIC = {}
 # Tensor peaks of the reduced-precision GEMMs, from the measured dense BF16 rate times the nominal
 # ratio of the format (TF32 1.1 / BF16 2.25 PFLOP/s dense); BF16x3 issues three BF16 MMAs per product.
 BF16_MEASURED_TFLOPS = 1913.8

@@ -263,6 +263,24 @@ MPS_API int64_t mps_launch_count(void);
 MPS_API int mps_last_batch_sweeps(mps_t h, int* n_sectors, int64_t* sweeps_sum, int* sweeps_max);
 
 /*
+ * mps_save - writes the current state of h (bond charge tables and Schmidt values,
+ * site blocks) to the file `path` (created or truncated).  The file holds the
+ * right-canonical B = Gamma lambda form the updates keep (Sec. II), so a handle
+ * loaded from it continues the evolution bit for bit.  Synchronises h's stream.
+ * Errors: MPS_EINVAL (NULL arguments, a site awaiting mps_set_site, I/O failure;
+ * mps_last_error says which), MPS_ECUDA.
+ *
+ * mps_load - a new handle with the state stored by mps_save, on cuda_stream (as in
+ * mps_create).  The stored L, d, N, chi_max and precision are reused.  The library
+ * owns the handle; free it with mps_destroy.  Errors: MPS_EINVAL (unreadable,
+ * truncated or foreign file), MPS_ECHARGE (charge tables or blocks that violate the
+ * U(1) structure), MPS_ENOMEM, MPS_ECUDA; *out is NULL on error.
+ * The paper describes no checkpoint; this pair exists for long runs and serving.
+ */
+MPS_API int mps_save(mps_t h, const char* path);
+MPS_API int mps_load(mps_t* out, const char* path, void* cuda_stream);
+
+/*
  * mps_zgemm_tc - the tensor-core complex GEMM kernel alone, on device memory:
  * C = A B with A (M x K), B (K x N), C (M x N) complex128 row-major (leading
  * dimensions lda >= K, ldb >= N, ldc >= N, in complex numbers).  precision is

@@ -71,6 +71,8 @@ _SIGS = {
     "mps_amplitude": (ctypes.c_int, [_h, _i32p, _dblp]),
     "mps_amplitude_batch": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _dblp]),
     "mps_bond_spectrum": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _i32p, _dblp, ctypes.c_int, _intp]),
+    "mps_save": (ctypes.c_int, [_h, ctypes.c_char_p]),
+    "mps_load": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_char_p, _vp]),
     "mps_get_site": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _i32p, ctypes.c_int, _dblp, ctypes.c_int64,
                                     _intp, _i64p]),
     "mps_set_bond": (ctypes.c_int, [_h, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _dblp]),
@@ -150,6 +152,26 @@ class MPS:
             raise MPSError(rc, "mps_create failed")
         self._h = h
         self.N = int(occ.sum())
+
+    # -- checkpoint -------------------------------------------------------------
+    def save(self, path) -> None:
+        """Write the state to `path` (mps_save)."""
+        self._check(lib.mps_save(self._h, os.fsencode(path)), "mps_save")
+
+    @classmethod
+    def load(cls, path, stream=None) -> "MPS":
+        """A new handle holding the state saved at `path` (mps_load)."""
+        obj = cls.__new__(cls)
+        obj.stream = _default_stream() if stream is None else stream
+        h = _h()
+        rc = lib.mps_load(ctypes.byref(h), os.fsencode(path), obj.stream)
+        if rc != MPS_OK:
+            raise MPSError(rc, f"mps_load failed for {path}")
+        obj._h = h
+        L, d, N, chi, prec = (ctypes.c_int() for _ in range(5))
+        lib.mps_info(h, ctypes.byref(L), ctypes.byref(d), ctypes.byref(N), ctypes.byref(chi), ctypes.byref(prec))
+        obj.L, obj.d, obj.N, obj.chi_max = L.value, d.value, N.value, chi.value
+        return obj
 
     # -- lifetime ---------------------------------------------------------------
     def close(self):

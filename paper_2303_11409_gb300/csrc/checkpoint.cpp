@@ -1,0 +1,167 @@
+// Checkpoint of a U(1) MPS handle: mps_save writes the charge tables, the Schmidt
+// values and the site blocks of the current state to a file, mps_load rebuilds a
+// handle from it.  The state is the right-canonical form the update keeps
+// (B = Gamma lambda per site, lambda per bond; Sec. II), so a loaded handle
+// continues an evolution exactly where the saved one stopped.
+//
+// File layout (little-endian, all integers int32 unless noted):
+//   "U1MPSCK1"                                   8-byte magic
+//   version (1), L, d, N, chi_max, precision
+//   per bond b = 0..L:  n, charge[n], dim[n], lambda[sum dim] (float64)
+//   per site s = 0..L-1: n_blocks (int32), nnz (int64), block (l, m) pairs
+//                        [2 n_blocks], data[2 nnz] (float64, interleaved complex)
+//   "U1MPSEND"                                   8-byte trailer
+// The block order is the library's (l ascending, then m ascending), which the
+// loader checks against the order the bond tables imply.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "mps_internal.h"
+
+namespace {
+
+const char kMagic[8] = {'U', '1', 'M', 'P', 'S', 'C', 'K', '1'};
+const char kTrailer[8] = {'U', '1', 'M', 'P', 'S', 'E', 'N', 'D'};
+
+struct File {
+  FILE* f = nullptr;
+  ~File() { if (f) std::fclose(f); }
+};
+
+template <class T>
+bool put(FILE* f, const T* p, size_t n) { return n == 0 || std::fwrite(p, sizeof(T), n, f) == n; }
+template <class T>
+bool get(FILE* f, T* p, size_t n) { return n == 0 || std::fread(p, sizeof(T), n, f) == n; }
+
+int save_fail(mps_t h, const std::string& msg) {
+  h->err = msg;
+  return MPS_EINVAL;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mps_save(mps_t h, const char* path) {
+  if (!h) return MPS_EINVAL;
+  if (!path) return save_fail(h, "path is NULL");
+  for (int s = 0; s < h->L; ++s)
+    if (h->dirty[s]) return save_fail(h, "site " + std::to_string(s) + " needs mps_set_site before saving");
+  File out;
+  out.f = std::fopen(path, "wb");
+  if (!out.f) return save_fail(h, std::string("cannot open ") + path + " for writing");
+  const int32_t hdr[6] = {1, h->L, h->d, h->N, h->chi_max, h->precision};
+  bool ok = put(out.f, kMagic, 8) && put(out.f, hdr, 6);
+  std::vector<int32_t> ch, dm;
+  std::vector<double> lam;
+  for (int b = 0; ok && b <= h->L; ++b) {
+    const mps::BondTable& t = h->bonds[b];
+    const int n = t.size();
+    ch.assign(t.charge.begin(), t.charge.end());
+    dm.assign(t.dim.begin(), t.dim.end());
+    lam.assign(t.total(), 0.0);
+    int n_out = 0;
+    int rc = mps_bond_spectrum(h, b, ch.data(), dm.data(), lam.data(), n, &n_out);
+    if (rc != MPS_OK) return rc;
+    ok = put(out.f, &n, 1) && put(out.f, ch.data(), n) && put(out.f, dm.data(), n) &&
+         put(out.f, lam.data(), lam.size());
+  }
+  std::vector<int32_t> lc, mc, pairs;
+  std::vector<double> data;
+  for (int s = 0; ok && s < h->L; ++s) {
+    const mps::SiteTable& S = h->sites[s];
+    const int nb = (int)S.blocks.size();
+    lc.resize(nb);
+    mc.resize(nb);
+    data.resize(2 * (size_t)S.nnz);
+    int n_blocks = 0;
+    int64_t n_values = 0;
+    int rc = mps_get_site(h, s, lc.data(), mc.data(), nb, data.data(), S.nnz, &n_blocks, &n_values);
+    if (rc != MPS_OK) return rc;
+    pairs.resize(2 * (size_t)nb);
+    for (int i = 0; i < nb; ++i) { pairs[2 * i] = lc[i]; pairs[2 * i + 1] = mc[i]; }
+    const int64_t nnz = S.nnz;
+    ok = put(out.f, &nb, 1) && put(out.f, &nnz, 1) && put(out.f, pairs.data(), pairs.size()) &&
+         put(out.f, data.data(), data.size());
+  }
+  ok = ok && put(out.f, kTrailer, 8);
+  if (!ok) return save_fail(h, std::string("write to ") + path + " failed");
+  if (std::fclose(out.f) != 0) {
+    out.f = nullptr;
+    return save_fail(h, std::string("closing ") + path + " failed");
+  }
+  out.f = nullptr;
+  return MPS_OK;
+}
+
+int mps_load(mps_t* out, const char* path, void* cuda_stream) {
+  if (!out || !path) return MPS_EINVAL;
+  *out = nullptr;
+  File in;
+  in.f = std::fopen(path, "rb");
+  if (!in.f) return MPS_EINVAL;
+  char magic[8];
+  int32_t hdr[6];
+  if (!get(in.f, magic, 8) || std::memcmp(magic, kMagic, 8) != 0 || !get(in.f, hdr, 6) || hdr[0] != 1)
+    return MPS_EINVAL;
+  const int L = hdr[1], d = hdr[2], N = hdr[3], chi_max = hdr[4], precision = hdr[5];
+  if (L < 2 || d < 2 || d > MPS_MAX_D || N < 0 || N > L * (d - 1) || chi_max < 1) return MPS_EINVAL;
+  // a product state with the same total charge; every bond and site is then overwritten
+  std::vector<int32_t> occ(L, 0);
+  for (int s = 0, left = N; s < L; ++s) { occ[s] = left < d - 1 ? left : d - 1; left -= occ[s]; }
+  mps_t h = nullptr;
+  int rc = mps_create(&h, L, d, occ.data(), precision, chi_max, cuda_stream);
+  if (rc != MPS_OK) return rc;
+  std::unique_ptr<mps_s, int (*)(mps_t)> guard(h, mps_destroy);
+  std::vector<int32_t> ch, dm;
+  std::vector<double> lam;
+  for (int b = 0; b <= L; ++b) {
+    int32_t n = 0;
+    if (!get(in.f, &n, 1) || n < 1 || n > N + 1) return MPS_EINVAL;
+    ch.resize(n);
+    dm.resize(n);
+    if (!get(in.f, ch.data(), n) || !get(in.f, dm.data(), n)) return MPS_EINVAL;
+    int64_t tot = 0;
+    for (int i = 0; i < n; ++i) {
+      if (dm[i] < 1 || dm[i] > chi_max) return MPS_EINVAL;
+      tot += dm[i];
+    }
+    lam.resize(tot);
+    if (!get(in.f, lam.data(), tot)) return MPS_EINVAL;
+    if (b == 0 || b == L) {   // boundary bonds: one sector (N at the left end, 0 at the right), lambda = 1
+      if (n != 1 || dm[0] != 1 || ch[0] != (b == 0 ? N : 0) || lam[0] != 1.0) return MPS_ECHARGE;
+      continue;
+    }
+    rc = mps_set_bond(h, b, n, ch.data(), dm.data(), lam.data());
+    if (rc != MPS_OK) return rc;
+  }
+  std::vector<int32_t> pairs, lc, mc;
+  std::vector<double> data;
+  for (int s = 0; s < L; ++s) {
+    int32_t nb = 0;
+    int64_t nnz = 0;
+    if (!get(in.f, &nb, 1) || !get(in.f, &nnz, 1) || nb < 0 || nnz < 0) return MPS_EINVAL;
+    if (nnz > h->site_cap[s] || nb > (int64_t)h->site_cap[s]) return MPS_ENOMEM;
+    pairs.resize(2 * (size_t)nb);
+    data.resize(2 * (size_t)nnz);
+    if (!get(in.f, pairs.data(), pairs.size()) || !get(in.f, data.data(), data.size())) return MPS_EINVAL;
+    lc.resize(nb);
+    mc.resize(nb);
+    for (int i = 0; i < nb; ++i) { lc[i] = pairs[2 * i]; mc[i] = pairs[2 * i + 1]; }
+    mps::SiteTable t;
+    mps::layout_site(h->bonds[s], h->bonds[s + 1], d, t);
+    if (t.nnz != nnz) return MPS_ECHARGE;   // the blocks do not fit the bond tables
+    rc = mps_set_site(h, s, nb, lc.data(), mc.data(), data.data());
+    if (rc != MPS_OK) return rc;
+  }
+  char trailer[8];
+  if (!get(in.f, trailer, 8) || std::memcmp(trailer, kTrailer, 8) != 0) return MPS_EINVAL;
+  *out = guard.release();
+  return MPS_OK;
+}
+
+}  // extern "C"

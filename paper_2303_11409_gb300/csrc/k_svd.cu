@@ -47,6 +47,7 @@ constexpr int kMaxCached = 16;          // rows cached in registers per lane (n 
 constexpr int kMaxCluster = 16;
 constexpr int kMaxWarps = 16;
 constexpr int kBlockThreads = 192;      // block-Jacobi cluster kernel: 6 warps per CTA, 2 CTAs per SM
+constexpr int kMaxStaged = 16;          // block pairs staged at once by one block-Jacobi CTA
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -181,6 +182,78 @@ __device__ bool jacobi_pair(double2* A, int R, int ld, double* nrm, int p, int q
   return true;
 }
 
+// G lanes (G = 8, 16 or 32; groups aligned within the warp) orthogonalise columns p, q
+// (length R, column c at A + c * ld) of a shared-memory matrix, so that one warp works
+// on 32 / G pairs at once.  On this part every FP64 warp instruction costs the same
+// whatever its lane count, so the group-wide reduction and the scalar rotation
+// parameters, which all lanes of a group compute redundantly, are shared by the
+// 32 / G pairs of a warp instead of being paid per pair.  Lanes of an invalid slot only
+// take part in the shuffles.  The rotation follows from the 2x2 Gram matrix
+// [[alpha, g], [conj g, beta]] with tau = tan(theta) / |g| = 2 sign(D) / (|D| + sqrt(D^2 + 4|g|^2)),
+// D = beta - alpha, which avoids a separate 1 / |g|; norms update by -/+ tau |g|^2.
+__device__ bool jacobi_pair_grp(double2* A, int R, int ld, double* nrm, int p, int q, bool valid, int G,
+                                double tol2, double floor2) {
+  const int gl = threadIdx.x & (G - 1);
+  double alpha = 0.0, beta = 0.0;
+  if (valid) {
+    alpha = nrm[p];
+    beta = nrm[q];
+  }
+  bool act = valid && fmin(alpha, beta) > floor2;   // noise columns are left alone
+  double2* ap = A + (int64_t)(act ? p : 0) * ld;
+  double2* aq = A + (int64_t)(act ? q : 0) * ld;
+  double gr = 0.0, gi = 0.0;
+  if (act) {
+    for (int i = gl; i < R; i += G) {
+      const double2 x = ap[i], y = aq[i];
+      gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+      gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+    }
+  }
+  for (int o = G >> 1; o; o >>= 1) {
+    gr += __shfl_xor_sync(0xffffffffu, gr, o);
+    gi += __shfl_xor_sync(0xffffffffu, gi, o);
+  }
+  const double g2 = fma(gr, gr, gi * gi);
+  act = act && (g2 > tol2 * alpha * beta);           // orthogonal to tolerance otherwise
+  if (act) {
+    const double delta = beta - alpha;
+    const double tau = copysign(2.0, delta) / (fabs(delta) + sqrt(fma(delta, delta, 4.0 * g2)));
+    Rot Rt;
+    Rt.c = rsqrt(fma(tau * tau, g2, 1.0));
+    const double ct = Rt.c * tau;
+    Rt.u = ct * gr;
+    Rt.v = ct * gi;
+    for (int i = gl; i < R; i += G) {
+      double2 x = ap[i], y = aq[i];
+      rotate_pair(x, y, Rt);
+      ap[i] = x;
+      aq[i] = y;
+    }
+    if (gl == 0) {
+      const double tg = tau * g2;
+      nrm[p] = fmax(alpha - tg, 0.0);
+      nrm[q] = beta + tg;
+    }
+  }
+  return act;
+}
+
+// Group width for P disjoint pairs of columns of length R spread over nwarps warps:
+// the width with the fewest FP64 warp instructions per warp, counting the passes
+// needed (ceil(P / slots)) times the instructions of one pass (about 16 per column
+// element a lane holds, plus about 50 for the reduction and the rotation parameters).
+__device__ __forceinline__ int group_width(int P, int R, int nwarps) {
+  int best = 32;
+  long long best_cost = -1;
+  for (int G = 32; G >= 8; G >>= 1) {
+    const int slots = nwarps * (32 / G);
+    const long long cost = (long long)((P + slots - 1) / slots) * (16 * ((R + G - 1) / G) + 50);
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = G; }
+  }
+  return best;
+}
+
 // Per-sector working set (shared memory or global scratch).
 struct Work {
   double2* W;     // m x ld, row-major: M, then R (rows 0..K-1), then R^dag's columns
@@ -226,14 +299,26 @@ struct JacobiRoundRobin {
       }
       for (int r = 0; r < mp - 1; ++r) {
         bool rot = false;
-        for (int kk = worker; kk < mp / 2; kk += workers) {
-          int p, q;
-          rr_pair(kk, r, mp, p, q);
-          if (p >= K || q >= K) continue;
-          if (p > q) { const int t = p; p = q; q = t; }
-          rot |= jacobi_pair<Mem>(W, n, ld, w.nrm, p, q, tol2, floor2);
+        if constexpr (!Mem::kCache) {   // shared memory: several pairs per warp
+          const int G = group_width(mp / 2, n, workers), per = 32 / G, slot = worker * per + lane / G;
+          for (int base = 0; base < mp / 2; base += workers * per) {
+            const int kk = base + slot;
+            int p = 0, q = 0;
+            if (kk < mp / 2) rr_pair(kk, r, mp, p, q);
+            const bool valid = kk < mp / 2 && p < K && q < K;
+            rot |= jacobi_pair_grp(W, n, ld, w.nrm, min(p, q), max(p, q), valid, G, tol2, floor2);
+          }
+          if (rot) Mem::st(w.flags + sweep, 1);
+        } else {
+          for (int kk = worker; kk < mp / 2; kk += workers) {
+            int p, q;
+            rr_pair(kk, r, mp, p, q);
+            if (p >= K || q >= K) continue;
+            if (p > q) { const int t = p; p = q; q = t; }
+            rot |= jacobi_pair<Mem>(W, n, ld, w.nrm, p, q, tol2, floor2);
+          }
+          if (rot && lane == 0) Mem::st(w.flags + sweep, 1);
         }
-        if (rot && lane == 0) Mem::st(w.flags + sweep, 1);
         sync();
       }
       converged = Mem::ld(w.flags + sweep) == 0;
@@ -244,22 +329,26 @@ struct JacobiRoundRobin {
 
 // Block-Jacobi sweeps for a cluster sector (data in L2).  The K columns form
 // nb = 2 * nctas * g contiguous blocks; in block round r the blocks are paired by the
-// round-robin ordering and CTA `rank` takes the pairs rank, rank + nctas, ...: for each
-// it stages both blocks and their norms in shared memory, orthogonalises every cross
-// pair (cyclic shifts of the larger block against the smaller, so each inner round is
-// disjoint) and, in round 0, every pair inside each block, with CTA-local barriers
-// only, then writes the blocks back; one cluster barrier ends the round.  Every pair
-// is visited once per sweep.  g > 1 keeps two blocks within shared memory when the
-// sector is large for its cluster.
+// round-robin ordering and CTA `rank` takes the pairs rank, rank + nctas, ... (g of
+// them), staging gs of them at a time (both blocks and their norms) in shared memory.
+// For the staged pairs it orthogonalises, in round 0, every pair inside each block
+// (round-robin inside the block) and then every cross pair (cyclic shifts of the
+// larger block against the smaller), all staged block pairs advancing together so
+// that each step has about gs * K / nb disjoint pairs for the warp groups; steps are
+// separated by CTA barriers, the round by one cluster barrier.  Every pair is visited
+// once per sweep.
 struct JacobiBlocks {
-  double2* sm;   // 2 * bsmax columns of n complex (shared memory)
-  double* smn;   // 2 * bsmax norms (shared memory)
+  double2* sm;   // 2 * gs * bsmax columns of n complex (shared memory)
+  double* smn;   // 2 * gs * bsmax norms (shared memory)
   int bsmax;
-  int g;
+  int g;         // block pairs per CTA and round
+  int gs;        // block pairs staged at once
   template <class Sync>
   __device__ int operator()(double2* W, int n, int ld, int K, const Work& w, int rank, int nctas, Sync sync,
                             double tol2, double floor2, int max_sweeps, bool& converged) const {
     __shared__ int s_rot;
+    __shared__ int s_col[2 * kMaxStaged];   // first column of each staged block
+    __shared__ int s_len[2 * kMaxStaged];   // its width (0: slot unused)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int worker = rank * nwarps + warp, workers = nctas * nwarps;
     const int nb = 2 * nctas * g;
@@ -280,62 +369,94 @@ struct JacobiBlocks {
         sync();
       }
       if (tid == 0) s_rot = 0;
+      bool rot = false;
       for (int r = 0; r < nb - 1; ++r) {
-       for (int pair = rank; pair < nb / 2; pair += nctas) {
-        int bp, bq;
-        rr_pair(pair, r, nb, bp, bq);
-        const int p0 = (int)((int64_t)K * bp / nb), sp = (int)((int64_t)K * (bp + 1) / nb) - p0;
-        const int q0 = (int)((int64_t)K * bq / nb), sq = (int)((int64_t)K * (bq + 1) / nb) - q0;
-        for (int64_t e = tid; e < (int64_t)sp * n; e += blockDim.x) {
-          const int c = (int)(e / n), i = (int)(e % n);
-          sm[e] = __ldcg(W + (int64_t)(p0 + c) * ld + i);
-        }
-        for (int64_t e = tid; e < (int64_t)sq * n; e += blockDim.x) {
-          const int c = (int)(e / n), i = (int)(e % n);
-          sm[(int64_t)bsmax * n + e] = __ldcg(W + (int64_t)(q0 + c) * ld + i);
-        }
-        for (int c = tid; c < sp; c += blockDim.x) smn[c] = __ldcg(w.nrm + p0 + c);
-        for (int c = tid; c < sq; c += blockDim.x) smn[bsmax + c] = __ldcg(w.nrm + q0 + c);
-        __syncthreads();
-        bool rot = false;
-        if (r == 0) {
-          for (int which = 0; which < 2; ++which) {
-            const int b = which ? sq : sp, base = which ? bsmax : 0;
-            const int mp = b + (b & 1);
-            for (int rr = 0; rr < mp - 1; ++rr) {
-              for (int k = warp; k < mp / 2; k += nwarps) {
-                int i, j;
-                rr_pair(k, rr, mp, i, j);
-                if (i < b && j < b)
-                  rot |= jacobi_pair<PlainMem>(sm, n, n, smn, base + min(i, j), base + max(i, j), tol2, floor2);
+        for (int c0 = 0; c0 < g; c0 += gs) {        // chunks of gs block pairs of this CTA
+          const int ns = min(gs, g - c0);
+          if (tid < 2 * gs) {
+            const int j = tid >> 1;
+            int col = 0, len = 0;
+            if (j < ns) {
+              int bp, bq;
+              rr_pair(rank + (c0 + j) * nctas, r, nb, bp, bq);
+              const int b = (tid & 1) ? bq : bp;
+              col = (int)((int64_t)K * b / nb);
+              len = (int)((int64_t)K * (b + 1) / nb) - col;
+            }
+            s_col[tid] = col;
+            s_len[tid] = len;
+          }
+          __syncthreads();
+          // stage: block slot j occupies columns [j * bsmax, j * bsmax + len) of sm
+          for (int j = 0; j < 2 * ns; ++j) {
+            const int col = s_col[j], len = s_len[j];
+            double2* dst = sm + (int64_t)j * bsmax * n;
+            for (int64_t e = tid; e < (int64_t)len * n; e += blockDim.x) {
+              const int c = (int)(e / n), i = (int)(e % n);
+              dst[e] = __ldcg(W + (int64_t)(col + c) * ld + i);
+            }
+            for (int c = tid; c < len; c += blockDim.x) smn[j * bsmax + c] = __ldcg(w.nrm + col + c);
+          }
+          __syncthreads();
+          if (r == 0) {   // pairs inside each staged block, round-robin within the block
+            const int mpb = bsmax + (bsmax & 1);
+            const int P = 2 * ns * (mpb / 2);
+            const int G = group_width(P, n, nwarps), per = 32 / G, slot = warp * per + lane / G;
+            for (int rr = 0; rr < mpb - 1; ++rr) {
+              for (int base = 0; base < P; base += nwarps * per) {
+                const int k = base + slot, j = k / (mpb / 2);
+                int a = 0, b = 0;
+                bool valid = k < P;
+                if (valid) {
+                  rr_pair(k % (mpb / 2), rr, mpb, a, b);
+                  valid = a < s_len[j] && b < s_len[j];
+                }
+                rot |= jacobi_pair_grp(sm, n, n, smn, j * bsmax + min(a, b), j * bsmax + max(a, b), valid, G,
+                                       tol2, floor2);
               }
               __syncthreads();
             }
           }
+          {   // cross pairs: block slots 2j and 2j + 1, the smaller block shifted against the larger
+            const int P = ns * bsmax;
+            const int G = group_width(P, n, nwarps), per = 32 / G, slot = warp * per + lane / G;
+            for (int t = 0; t < bsmax; ++t) {
+              for (int base = 0; base < P; base += nwarps * per) {
+                const int k = base + slot, j = k / bsmax, i = k % bsmax;
+                int p = 0, q = 0;
+                bool valid = false;
+                if (k < P) {
+                  const int la = s_len[2 * j], lb = s_len[2 * j + 1];
+                  const bool swap = la > lb;
+                  const int sa = swap ? lb : la, sb = swap ? la : lb;
+                  valid = i < sa && t < sb;
+                  if (valid) {
+                    const int pa = (2 * j + (swap ? 1 : 0)) * bsmax + i;
+                    const int pb = (2 * j + (swap ? 0 : 1)) * bsmax + (i + t) % sb;
+                    p = min(pa, pb);
+                    q = max(pa, pb);
+                  }
+                }
+                rot |= jacobi_pair_grp(sm, n, n, smn, p, q, valid, G, tol2, floor2);
+              }
+              __syncthreads();
+            }
+          }
+          for (int j = 0; j < 2 * ns; ++j) {
+            const int col = s_col[j], len = s_len[j];
+            const double2* src = sm + (int64_t)j * bsmax * n;
+            for (int64_t e = tid; e < (int64_t)len * n; e += blockDim.x) {
+              const int c = (int)(e / n), i = (int)(e % n);
+              __stcg(W + (int64_t)(col + c) * ld + i, src[e]);
+            }
+            for (int c = tid; c < len; c += blockDim.x) __stcg(w.nrm + col + c, smn[j * bsmax + c]);
+          }
+          __syncthreads();   // the next chunk reuses the staging buffers and block tables
         }
-        const bool swap = sp > sq;
-        const int sa = swap ? sq : sp, sb = swap ? sp : sq;
-        const int ba = swap ? bsmax : 0, bb = swap ? 0 : bsmax;
-        for (int t = 0; t < sb; ++t) {
-          for (int i = warp; i < sa; i += nwarps)
-            rot |= jacobi_pair<PlainMem>(sm, n, n, smn, ba + i, bb + (i + t) % sb, tol2, floor2);
-          __syncthreads();
-        }
-        if (rot && lane == 0) s_rot = 1;
-        for (int64_t e = tid; e < (int64_t)sp * n; e += blockDim.x) {
-          const int c = (int)(e / n), i = (int)(e % n);
-          __stcg(W + (int64_t)(p0 + c) * ld + i, sm[e]);
-        }
-        for (int64_t e = tid; e < (int64_t)sq * n; e += blockDim.x) {
-          const int c = (int)(e / n), i = (int)(e % n);
-          __stcg(W + (int64_t)(q0 + c) * ld + i, sm[(int64_t)bsmax * n + e]);
-        }
-        for (int c = tid; c < sp; c += blockDim.x) __stcg(w.nrm + p0 + c, smn[c]);
-        for (int c = tid; c < sq; c += blockDim.x) __stcg(w.nrm + q0 + c, smn[bsmax + c]);
-        __syncthreads();     // the next pair of this round reuses the staging buffers
-       }
         sync();
       }
+      if (rot) s_rot = 1;
+      __syncthreads();
       if (tid == 0 && s_rot) __stcg(w.flags + sweep, 1);
       sync();
       converged = __ldcg(w.flags + sweep) == 0;
@@ -672,9 +793,10 @@ __global__ void __launch_bounds__(kBlockThreads, 2) jacobi_cluster_block_kernel(
   const int K = min(S.m, S.n);
   JacobiBlocks jb;
   jb.g = S.groups;
+  jb.gs = S.staged;
   jb.bsmax = (K + 2 * cluster * jb.g - 1) / (2 * cluster * jb.g);
   jb.sm = reinterpret_cast<double2*>(smem_raw);
-  jb.smn = reinterpret_cast<double*>(smem_raw + 16LL * 2 * jb.bsmax * S.n);
+  jb.smn = reinterpret_cast<double*>(smem_raw + 16LL * 2 * jb.gs * jb.bsmax * S.n);
   svd_sector<L2Mem>(S, cluster_work(S), rank, cluster, ClusterSync{}, max_sweeps, jb);
 }
 
@@ -692,9 +814,9 @@ constexpr int kBigCluster = 8;
 bool g_attr_done = false;
 int g_big_cluster = 0;
 
-int64_t block_smem_need(int m, int n, int cl, int g) {
+int64_t block_smem_need(int m, int n, int cl, int g, int gs) {
   const int64_t K = std::min(m, n), bs = (K + 2 * cl * g - 1) / (2 * cl * g);
-  return 16 * 2 * bs * n + 8 * 2 * bs + 64;
+  return 16 * 2 * gs * bs * n + 8 * 2 * gs * bs + 64;
 }
 
 cudaError_t set_attrs() {
@@ -769,18 +891,32 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
       smem[k] = svd_smem_need(S.m, S.n);
       continue;
     }
-    const int K = std::min(S.m, S.n);
-    // blocks of about 6 columns give each of the 6 warps of a CTA one pair per inner
-    // round; 2, 4 or 8 CTAs per sector, then more block groups per CTA when larger
-    int cl = 2;
-    while (cl < kBigCluster && K >= 12 * 2 * cl) cl *= 2;
-    int g = std::max(1, (K + 6 * cl) / (12 * cl));
-    while (g < 32 && block_smem_need(S.m, S.n, cl, g) > kBlockSmemMax) ++g;
-    const int64_t need = block_smem_need(S.m, S.n, cl, g);
-    if (need <= kBlockSmemMax) {
-      key[k] = {kSvdClusterBlock, cl};
-      smem[k] = need;
-      secs[k].groups = g;
+    // blocks of about 6 columns; the smallest cluster (2, 4 or 8 CTAs) whose CTAs can
+    // stage all of their block pairs of a round at once, so that a step offers the warp
+    // groups about 3 K / (2 cl) disjoint pairs; failing that, 8 CTAs staging as many
+    // pairs as fit, with more pairs per CTA when a single one does not fit
+    int pick_cl = 0, pick_g = 0, pick_gs = 0;
+    for (int cl = 2; cl <= kBigCluster && !pick_cl; cl *= 2) {
+      const int g = std::max(1, (std::min(S.m, S.n) + 6 * cl) / (12 * cl));
+      if (g <= kMaxStaged && block_smem_need(S.m, S.n, cl, g, g) <= kBlockSmemMax) {
+        pick_cl = cl; pick_g = g; pick_gs = g;
+      }
+    }
+    if (!pick_cl) {
+      const int cl = kBigCluster;
+      int g = std::max(1, (std::min(S.m, S.n) + 6 * cl) / (12 * cl));
+      while (g < 64 && block_smem_need(S.m, S.n, cl, g, 1) > kBlockSmemMax) ++g;
+      int gs = 1;
+      while (gs < std::min(g, kMaxStaged) && block_smem_need(S.m, S.n, cl, g, gs + 1) <= kBlockSmemMax) ++gs;
+      if (block_smem_need(S.m, S.n, cl, g, gs) <= kBlockSmemMax) {
+        pick_cl = cl; pick_g = g; pick_gs = gs;
+      }
+    }
+    if (pick_cl) {
+      key[k] = {kSvdClusterBlock, pick_cl};
+      smem[k] = block_smem_need(S.m, S.n, pick_cl, pick_g, pick_gs);
+      secs[k].groups = pick_g;
+      secs[k].staged = pick_gs;
     } else {
       key[k] = {kSvdCluster, g_big_cluster};
     }

@@ -95,6 +95,7 @@ struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   int m, n;
   int mode;                   // kSvdSmem, kSvdCluster or kSvdClusterBlock
   int groups;                 // block Jacobi: block pairs per CTA and round
+  int staged;                 // block Jacobi: block pairs staged in shared memory at once
 };
 
 // Scratch layout of a batch of sector SVDs (cluster-mode sectors only need global scratch).

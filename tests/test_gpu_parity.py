@@ -217,3 +217,64 @@ def test_full_size_bose_hubbard_layer_sampled(gpu_lib):
         ref = st.copy()
         ref.apply_gate2(s, gate_of(s, 0.5), chi, 1e-10)
         compare_update(g, ref, s, tol_lam=1e-12, tol_prod=1e-8)
+
+
+# ---------------------------------------------------------------------------
+# checkpoint: mps_save / mps_load
+# ---------------------------------------------------------------------------
+def test_save_load_round_trip_continues_bit_for_bit(gpu_lib, tmp_path):
+    m = gpu_lib
+    L, d = 10, 3
+    gate_of = tebd.bh_gates(L, d, 1.0, 2.0, 0.05)
+    a = _gpu(m, d, W.mott_occupations(L), 40)
+    layers = tebd.strang_layers(L)
+    for sites, f in layers * 3:
+        a.apply_layer(sites, [gate_of(s, f) for s in sites], 40, 1e-10)
+    path = tmp_path / "state.u1mps"
+    a.save(path)
+    b = m.MPS.load(path)
+    assert (b.L, b.d, b.N, b.chi_max) == (a.L, a.d, a.N, a.chi_max)
+    for bond in range(L + 1):
+        ba, bb = a.bond(bond), b.bond(bond)
+        assert ba.keys() == bb.keys() and all(np.array_equal(ba[c], bb[c]) for c in ba)
+    for sites, f in layers * 2:   # both continue identically
+        a.apply_layer(sites, [gate_of(s, f) for s in sites], 40, 1e-10)
+        b.apply_layer(sites, [gate_of(s, f) for s in sites], 40, 1e-10)
+    for s in range(L):
+        sa, sb = a.site(s), b.site(s)
+        assert sa.keys() == sb.keys() and all(np.array_equal(sa[k], sb[k]) for k in sa)
+
+
+def test_load_rejects_missing_and_damaged_files(gpu_lib, tmp_path):
+    m = gpu_lib
+    with pytest.raises(m.MPSError):
+        m.MPS.load(tmp_path / "missing.u1mps")
+    a = _gpu(m, 2, W.neel_occupations(8), 16)
+    G = gates.xxz_gate(0.5, 0.1)
+    a.apply_layer([0, 2, 4, 6], [G] * 4, 16, 1e-10)
+    good = tmp_path / "good.u1mps"
+    a.save(good)
+    raw = good.read_bytes()
+    for name, blob in [("truncated", raw[: len(raw) // 2]), ("no_trailer", raw[:-8]),
+                       ("bad_magic", b"X" + raw[1:])]:
+        p = tmp_path / f"{name}.u1mps"
+        p.write_bytes(blob)
+        with pytest.raises(m.MPSError):
+            m.MPS.load(p)
+    # a charge table with a charge outside the bond's range is refused
+    import struct
+    hdr = struct.calcsize("<8s6i")
+    L = 8
+    off = hdr
+    for b in range(L + 1):   # walk to bond 1's first charge
+        n = struct.unpack_from("<i", raw, off)[0]
+        if b == 1:
+            bad = bytearray(raw)
+            struct.pack_into("<i", bad, off + 4, 99)
+            p = tmp_path / "bad_charge.u1mps"
+            p.write_bytes(bytes(bad))
+            with pytest.raises(m.MPSError):
+                m.MPS.load(p)
+            break
+        dims = struct.unpack_from(f"<{n}i", raw, off + 4 + 4 * n)
+        off += 4 + 8 * n + 8 * sum(dims)
