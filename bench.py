@@ -35,13 +35,21 @@ METRIC = "two-site updates/s"
 WORKLOAD = "bose_hubbard_L64_nmax4_N64_J1_U2_dt0.02_chi512_cutoff1e-10_fp64"
 # --case small: the same model on L=32, chi=512 (half the chain, same sector sizes), for profiler captures
 SMALL = dict(L=32, N=32, CHI=512, WORKLOAD="bose_hubbard_L32_nmax4_N32_J1_U2_dt0.02_chi512_cutoff1e-10_fp64")
+# --case bh128: Bose-Hubbard L=128, N=128, chi<=2048 (the mixed-precision configuration); the chain
+# is brought to saturation by untimed layers of seeded Haar-random U(1) two-site gates, then timed
+# on Bose-Hubbard Trotter steps
+BH128 = dict(L=128, N=128, CHI=2048, WORKLOAD="bose_hubbard_L128_nmax4_N128_J1_U2_dt0.02_chi2048_cutoff1e-10_fp64")
+# --case boson: boson sampling, M=100 modes, single photons in modes 0..49, per-mode cutoff 4
+# (d=5), brickwork of seeded Haar beam splitters, chi<=1024; a step is one brickwork layer
+BOSON = dict(L=100, N=50, CHI=1024, DEPTH=100,
+             WORKLOAD="boson_sampling_M100_photons50_d5_brickwork100_chi1024_cutoff1e-10_fp64")
 # FP64 peak of the GB300 CUDA cores: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz.
 # (An FMA-chain probe measured 1.195 TFLOP/s, i.e. 2 FMA/clk/SM at the clock it ran.)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
-# DRAM bytes per launch of the SVD phase of a saturated layer of this workload, from an ncu
-# capture of dram__bytes_read.sum + dram__bytes_write.sum; emptied whenever those kernels change
-# (the grouped-pair block-Jacobi kernel has not been captured yet).
-NCU_TRAFFIC = {}
+# DRAM bytes per launch of the SVD phase of a saturated layer of this workload (all SVD kernels
+# of one layer), from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum with the
+# default tile shape; emptied whenever those kernels change.
+NCU_TRAFFIC = {"svd": 29.16e9}
 # Tensor peaks of the reduced-precision GEMMs, from the measured dense BF16 rate times the nominal
 # ratio of the format (TF32 1.1 / BF16 2.25 PFLOP/s dense); BF16x3 issues three BF16 MMAs per product.
 BF16_MEASURED_TFLOPS = 1913.8
@@ -62,14 +70,19 @@ def parse():
     p.add_argument("--serve", action="store_true",
                    help="serving workload instead: continuous batching vs the plain one-request-at-a-time form")
     p.add_argument("--serve-requests", type=int, default=48)
-    p.add_argument("--case", default="full", choices=["full", "small"],
-                   help="small: L=32, chi=512 (for profiler captures); full: the benchmark workload")
+    p.add_argument("--case", default="full", choices=["full", "small", "bh128", "boson"],
+                   help="full: the benchmark workload; small: L=32, chi=512 (for profiler captures); "
+                        "bh128: L=128, chi=2048; boson: boson sampling M=100, chi=1024")
     p.add_argument("--precision", default="fp64", choices=["fp64", "tf32", "bf16x3"],
                    help="sector GEMMs in FP64 (default) or on the tensor cores; SVD and truncation stay FP64")
+    p.add_argument("--graphs", type=int, default=1, help="capture each update call's launch phases in CUDA graphs")
+    p.add_argument("--autotune", type=int, default=0,
+                   help="SVD tile shape chosen per sector-size histogram (tuning runs happen before the timed steps)")
     a = p.parse_args()
     global L, N_PART, CHI, WORKLOAD, UPDATES_PER_STEP
-    if a.case == "small":
-        L, N_PART, CHI, WORKLOAD = SMALL["L"], SMALL["N"], SMALL["CHI"], SMALL["WORKLOAD"]
+    if a.case != "full":
+        c = {"small": SMALL, "bh128": BH128, "boson": BOSON}[a.case]
+        L, N_PART, CHI, WORKLOAD = c["L"], c["N"], c["CHI"], c["WORKLOAD"]
         UPDATES_PER_STEP = (L // 2) + (L - 1) // 2 + (L // 2)
         a.no_cpu_baseline = True
     if a.precision != "fp64":
@@ -77,11 +90,20 @@ def parse():
     return a
 
 
-def config(extra=None):
-    c = {"workload": WORKLOAD, "model": "bose_hubbard", "L": L, "d": D, "N": N_PART, "J": J, "U": U,
-         "dt": DT, "chi": CHI, "cutoff": CUTOFF, "updates_per_step": UPDATES_PER_STEP,
-         "regime": "saturated (timed steps follow untimed Trotter steps from the Mott state until the middle bond reaches chi)",
-         "l2": "flushed between timed steps (256 MiB device write outside the timed events)"}
+def config(extra=None, case="full"):
+    if case == "boson":
+        c = {"workload": WORKLOAD, "model": "boson_sampling", "M": L, "d": D, "photons": N_PART,
+             "depth": BOSON["DEPTH"], "chi": CHI, "cutoff": CUTOFF,
+             "step": "one brickwork layer of Haar beam splitters (49 or 50 two-site updates)",
+             "regime": "the brickwork from the input state; timed layers follow the layers that bring the largest bond to chi"}
+    else:
+        c = {"workload": WORKLOAD, "model": "bose_hubbard", "L": L, "d": D, "N": N_PART, "J": J, "U": U,
+             "dt": DT, "chi": CHI, "cutoff": CUTOFF, "updates_per_step": UPDATES_PER_STEP,
+             "regime": ("saturated (timed steps follow untimed layers of seeded Haar-random U(1) two-site gates "
+                        "that bring the middle bond to chi)" if case == "bh128" else
+                        "saturated (timed steps follow untimed Trotter steps from the Mott state until the middle "
+                        "bond reaches chi)")}
+    c["l2"] = "flushed between timed steps (256 MiB device write outside the timed events)"
     if extra:
         c.update(extra)
     return c
@@ -232,51 +254,96 @@ def run_ours(args, world, rank, local):
     import paper_2303_11409_gb300 as m
     import workloads as W
 
-    stream = torch.cuda.current_stream()
-    psi = m.MPS(D, W.mott_occupations(L), CHI, stream=stream.cuda_stream)
-    gates = m.tebd.GateTable("bh", L, D, DT, J=J, U=U)
-
+    # a stream of its own: the legacy default stream cannot be captured into CUDA graphs
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     fp64_measured = m.fp64_peak_probe(stream.cuda_stream)
+    prec = {"fp64": m.MPS_FP64, "tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[args.precision]
+
+    def new_psi(occ, precision):
+        p = m.MPS(D, occ, CHI, precision=precision, stream=stream.cuda_stream)
+        p.set_graphs(bool(args.graphs))
+        p.set_autotune(bool(args.autotune))
+        return p
+
     prep = 0
-    while prep < args.max_prep and sum(psi.bond_dims(L // 2).values()) < CHI:
-        m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
-        prep += 1
-    if args.precision != "fp64":
-        # the same saturated state, continued with the sector GEMMs on the tensor cores
-        prec = {"tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[args.precision]
-        low = m.MPS(D, W.mott_occupations(L), CHI, precision=prec, stream=stream.cuda_stream)
-        for b in range(1, L):
-            low.set_bond(b, psi.bond(b))
-        for s_ in range(L):
-            low.set_site(s_, psi.site(s_))
-        psi.close()
-        psi = low
-    step = lambda: m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
+    if args.case == "boson":
+        layers = W.brickwork_pairs(L, BOSON["DEPTH"])
+        ang = W.haar_beam_splitter_angles(sum(map(len, layers)), seed=0)
+        first = np.cumsum([0] + [len(x) for x in layers])
+        psi = new_psi(W.single_photon_occupations(L, N_PART), prec)
+        pos = [0]
+
+        def step():                      # the next brickwork layer (wrapping round after the last)
+            li = pos[0] % len(layers)
+            sites = layers[li]
+            gs = [m.models.flatten(m.models.beam_splitter_gate(*ang[first[li] + k], D)) for k in range(len(sites))]
+            psi.apply_layer(sites, gs, CHI, CUTOFF)
+            pos[0] += 1
+            return len(sites)
+
+        while prep < args.max_prep and max(sum(psi.bond_dims(b).values()) for b in range(L + 1)) < CHI:
+            step()
+            prep += 1
+    else:
+        gates = m.tebd.GateTable("bh", L, D, DT, J=J, U=U)
+        if args.case == "bh128":
+            # saturation by layers of Haar-random charge-conserving gates, at the run's precision
+            psi = new_psi(W.mott_occupations(L), prec)
+            rng = np.random.default_rng(0)
+            while prep < min(args.max_prep, 30) and sum(psi.bond_dims(L // 2).values()) < CHI:
+                sites = list(range(prep % 2, L - 1, 2))
+                psi.apply_layer(sites, [m.models.flatten(W.random_u1_gate(D, rng)) for _ in sites], CHI, CUTOFF)
+                prep += 1
+        else:
+            psi = new_psi(W.mott_occupations(L), m.MPS_FP64)
+            while prep < args.max_prep and sum(psi.bond_dims(L // 2).values()) < CHI:
+                m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
+                prep += 1
+            if args.precision != "fp64":
+                # the same saturated state, continued with the sector GEMMs on the tensor cores
+                low = new_psi(W.mott_occupations(L), prec)
+                for b in range(1, L):
+                    low.set_bond(b, psi.bond(b))
+                for s_ in range(L):
+                    low.set_site(s_, psi.site(s_))
+                psi.close()
+                psi = low
+
+        def step():
+            m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
+            return UPDATES_PER_STEP
+
     for _ in range(args.warmup):
         step()
+    # tile shapes are tuned during the evolution to saturation and the warm-up steps; a
+    # sector-size histogram first seen inside the timed steps keeps the default shape
+    m.autotune_freeze(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     psi.reset_kernel_stats()
     psi.set_profiling(True)
     launches0 = m.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n_upd = 0
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             flush.random_(0, 255)
             ev[k][0].record(stream)
-            step()
+            n_upd += step()
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     barrier(world)
     launches = m.launch_count() - launches0
+    graph_stats = psi.graph_stats()
     psi.set_profiling(False)
     ks = psi.kernel_stats()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), world)
-    value = world * UPDATES_PER_STEP * args.steps / (total_ms / 1000.0)
-    mid_dims = sum(psi.bond_dims(L // 2).values())
+    value = world * n_upd / (total_ms / 1000.0)
+    mid_dims = max(sum(psi.bond_dims(b).values()) for b in range(L + 1))
 
     # roofline of the dominant kernel (largest device time in the timed region)
     dom = max(ks, key=lambda k: ks[k]["ms"])
@@ -289,7 +356,8 @@ def run_ours(args, world, rank, local):
         peak, unit = FP64_PEAK_GFLOPS, "GFLOP/s"
     roofline = {"kernel": dom, "bound": KERNEL_BOUND[dom], "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get(dom) if args.case == "full" and args.precision == "fp64" else None,
+                "traffic": (NCU_TRAFFIC.get(dom) if args.case == "full" and args.precision == "fp64"
+                            and not args.autotune else None),
                 "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the phase",
                 "per_launch": {"flops" if unit == "GFLOP/s" else "bytes":
                                (kd["flops"] if unit == "GFLOP/s" else kd["bytes"]) / max(kd["launches"], 1),
@@ -323,15 +391,17 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
+    e2e_upd = 0
     for _ in range(args.steps):
-        step()
+        e2e_upd += step()
         psi.expect(L // 2, np.arange(D, dtype=np.float64))
     t1 = time.perf_counter()
     e2e_s = max_over_ranks(t1 - t0, world)
-    e2e = {"value": world * UPDATES_PER_STEP * args.steps / e2e_s, "unit": "updates/s",
-           "h2d_bytes_per_step": UPDATES_PER_STEP * glen * 16,
-           "d2h_bytes_per_step": UPDATES_PER_STEP * 8 + 8,
-           "what": "trotter steps through MPS.apply_layer with host gate buffers, plus <n_L/2> read back"}
+    per_step = e2e_upd / args.steps
+    e2e = {"value": world * e2e_upd / e2e_s, "unit": "updates/s",
+           "h2d_bytes_per_step": int(per_step * glen * 16),
+           "d2h_bytes_per_step": int(per_step * 8 + 8),
+           "what": "steps through MPS.apply_layer with host gate buffers, plus one <n_i> read back per step"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -344,9 +414,11 @@ def run_ours(args, world, rank, local):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else f"{args.precision}+f64", "data": "synthetic",
-                "config": config({"prep_steps": prep, "middle_bond_dim": mid_dims,
+                "config": config({"prep_steps": prep, "largest_bond_dim": mid_dims, "updates_timed": n_upd,
                                   "parallelism": "replicas" if world > 1 else "single",
-                                  "precision": args.precision}),
+                                  "precision": args.precision, "cuda_graphs": bool(args.graphs),
+                                  "autotune": bool(args.autotune)}, case=args.case),
+                "graphs": graph_stats, "autotune": {**m.autotune_stats(), "table": m.autotune_table()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "step_ms": [round(x, 3) for x in step_ms]}
         print(json.dumps(line), flush=True)

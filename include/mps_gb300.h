@@ -257,6 +257,48 @@ MPS_API int mps_reset_kernel_stats(mps_t h);
 MPS_API int64_t mps_launch_count(void);
 
 /*
+ * mps_set_graphs - when on, each update call on h (mps_apply_gate2/_layer, and the
+ * merged calls whose owner or executor is h) captures its two launch phases (upload,
+ * Theta' build, SVD, top-chi selection and read-back; upload and reassembly) into CUDA
+ * graphs and launches those: one executable graph per phase and handle, updated in
+ * place (cudaGraphExecUpdate) when only launch parameters changed and instantiated
+ * again when the topology changed.  Results are bit-identical to direct launches.
+ * A handle on the legacy default stream (NULL) cannot be captured and keeps launching
+ * directly.  Sec. II describes no graph mechanism; this is a launch-overhead measure.
+ * mps_graph_stats - graph launches, in-place updates and instantiations on h so far.
+ */
+MPS_API int mps_set_graphs(mps_t h, int on);
+MPS_API int mps_graph_stats(mps_t h, int64_t* launches, int64_t* updates, int64_t* instantiations);
+
+/*
+ * mps_set_autotune - when on, update calls on h choose the tile shape of the cluster
+ * SVD kernel (target column-block width 4, 6, 8 or 12 and smallest cluster 2 or 4 CTAs)
+ * from a process-wide table keyed on the histogram of the batch's large sectors
+ * (octaves of min(m, n) holding at least 5% of the nominal SVD work, counts rounded to
+ * powers of two).  The first batch with a new key whose nominal SVD work is at least
+ * the tuning threshold (2e10 flops unless set) runs all eight shapes on its own inputs,
+ * timed with CUDA events, and stores the fastest (the default shape, width 6 from
+ * 2 CTAs, unless another beats it by more than 3%); its outputs come from the stored
+ * shape.  Shapes differ only in rounding (the Jacobi pair order changes), so a tuned run
+ * agrees with an untuned one to rounding, not bit for bit.
+ * mps_autotune_stats - keys in the table, tuning runs made, and batches that reused a
+ * stored shape (any pointer may be NULL).
+ * mps_autotune_table - the table as text, one line per key; *len receives the length
+ * without the terminator; buf may be NULL to query it (MPS_EINVAL if cap is too small).
+ * mps_autotune_clear - empties the table.
+ * mps_autotune_freeze - when frozen, batches with a key not in the table use the
+ *   default shape and are not tuned (stored keys are still used).
+ * mps_autotune_min_flops - the nominal SVD work (flops, >= 0) below which a batch is
+ *   not tuned and uses the default shape.
+ */
+MPS_API int mps_set_autotune(mps_t h, int on);
+MPS_API int mps_autotune_stats(int64_t* keys, int64_t* tuning_runs, int64_t* hits);
+MPS_API int mps_autotune_table(char* buf, int cap, int* len);
+MPS_API int mps_autotune_clear(void);
+MPS_API int mps_autotune_freeze(int frozen);
+MPS_API int mps_autotune_min_flops(double flops);
+
+/*
  * mps_last_batch_sweeps - Jacobi sweeps of the last update call on h over all of its
  * sectors: sector count, summed sweeps and the largest sweep count (any may be NULL).
  */

@@ -94,6 +94,14 @@ _SIGS = {
                                                _vp, _i64p, _vp, _vp]),
     "mps_svd_sectors": (ctypes.c_int, [ctypes.c_int, _intp, _intp, _vp, _i64p, _vp, _i64p, _vp, _i64p, _vp,
                                        _i64p, _vp, _vp, ctypes.c_int64, _vp]),
+    "mps_set_graphs": (ctypes.c_int, [_h, ctypes.c_int]),
+    "mps_graph_stats": (ctypes.c_int, [_h, _i64p, _i64p, _i64p]),
+    "mps_set_autotune": (ctypes.c_int, [_h, ctypes.c_int]),
+    "mps_autotune_stats": (ctypes.c_int, [_i64p, _i64p, _i64p]),
+    "mps_autotune_table": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, _intp]),
+    "mps_autotune_clear": (ctypes.c_int, []),
+    "mps_autotune_min_flops": (ctypes.c_int, [ctypes.c_double]),
+    "mps_autotune_freeze": (ctypes.c_int, [ctypes.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -330,6 +338,17 @@ class MPS:
     def reset_kernel_stats(self):
         self._check(lib.mps_reset_kernel_stats(self._h), "mps_reset_kernel_stats")
 
+    def set_graphs(self, on: bool = True):
+        """Capture each update call's launch phases into CUDA graphs (mps_set_graphs)."""
+        self._check(lib.mps_set_graphs(self._h, int(bool(on))), "mps_set_graphs")
+
+    def graph_stats(self) -> dict:
+        return _graph_stats(self._h)
+
+    def set_autotune(self, on: bool = True):
+        """Choose the SVD tile shape per sector-size histogram (mps_set_autotune)."""
+        self._check(lib.mps_set_autotune(self._h, int(bool(on))), "mps_set_autotune")
+
     def stats(self) -> dict:
         a, b, c, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         na, nk = ctypes.c_double(), ctypes.c_double()
@@ -361,6 +380,19 @@ class Executor:
         except Exception:
             pass
 
+    def set_graphs(self, on: bool = True):
+        rc = lib.mps_set_graphs(self._h, int(bool(on)))
+        if rc != MPS_OK:
+            raise MPSError(rc, "mps_set_graphs")
+
+    def graph_stats(self) -> dict:
+        return _graph_stats(self._h)
+
+    def set_autotune(self, on: bool = True):
+        rc = lib.mps_set_autotune(self._h, int(bool(on)))
+        if rc != MPS_OK:
+            raise MPSError(rc, "mps_set_autotune")
+
     def apply(self, items):
         """items = [(mps, site, flat_gate, chi, cutoff), ...]; returns (trunc_err, status) arrays."""
         n = len(items)
@@ -379,6 +411,45 @@ class Executor:
         if rc not in (MPS_OK, MPS_ENOCONV):
             raise MPSError(rc, "mps_exec_apply: " + lib.mps_last_error(self._h).decode())
         return te, st
+
+
+def _graph_stats(h) -> dict:
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lib.mps_graph_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return dict(launches=a.value, updates=b.value, instantiations=c.value)
+
+
+def autotune_stats() -> dict:
+    """Process-wide SVD tile-shape table: keys, tuning runs, reuses."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lib.mps_autotune_stats(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return dict(keys=a.value, tuning_runs=b.value, hits=c.value)
+
+
+def autotune_table() -> str:
+    n = ctypes.c_int()
+    lib.mps_autotune_table(None, 0, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    rc = lib.mps_autotune_table(buf, n.value + 1, ctypes.byref(n))
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_autotune_table")
+    return buf.value.decode()
+
+
+def autotune_clear() -> None:
+    lib.mps_autotune_clear()
+
+
+def autotune_freeze(frozen: bool = True) -> None:
+    """Frozen: sector-size histograms not yet in the table keep the default shape, untuned."""
+    lib.mps_autotune_freeze(int(bool(frozen)))
+
+
+def autotune_min_flops(flops: float) -> None:
+    """Nominal SVD flops below which a batch keeps the default tile shape."""
+    rc = lib.mps_autotune_min_flops(float(flops))
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_autotune_min_flops")
 
 
 def footprint_bytes(L: int, d: int, N: int, chi_max: int) -> tuple[int, int]:

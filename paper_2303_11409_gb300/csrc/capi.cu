@@ -14,6 +14,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -84,19 +86,51 @@ void resolve_pending(mps_s* h) {
   for (auto& p : h->pending) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) h->kstat[p.kind].ms += ms;
-    h->event_pool.push_back(p.a);
-    h->event_pool.push_back(p.b);
+    if (p.pooled) {
+      h->event_pool.push_back(p.a);
+      h->event_pool.push_back(p.b);
+    }
   }
+  cudaGetLastError();
   h->pending.clear();
+}
+
+// Inside a stream capture a timing event must be an external event-record node of the
+// graph; those use one fixed event pair per kernel kind, so that the graph's event nodes
+// stay the same from one update call to the next (each kind is timed at most once per
+// phase, and pending pairs are read back before the phase that records them again).
+cudaError_t ensure_kind_events(mps_s* h) {
+  for (int k = 0; k < MPS_K_COUNT; ++k)
+    for (int j = 0; j < 2; ++j)
+      if (!h->kind_ev[k][j]) {
+        cudaError_t e = cudaEventCreate(&h->kind_ev[k][j]);
+        if (e != cudaSuccess) return e;
+      }
+  return cudaSuccess;
 }
 
 template <class F>
 cudaError_t timed(mps_s* h, int kind, bool nonempty, double flops, double bytes, F&& launch) {
   const bool prof = h->profiling && nonempty;
   cudaEvent_t a = nullptr, b = nullptr;
-  if (prof) { a = pool_event(h); b = pool_event(h); cudaEventRecord(a, h->stream); }
+  const bool pooled = !h->capturing;
+  if (prof) {
+    if (pooled) {
+      a = pool_event(h);
+      b = pool_event(h);
+      cudaEventRecord(a, h->stream);
+    } else {
+      a = h->kind_ev[kind][0];
+      b = h->kind_ev[kind][1];
+      cudaEventRecordWithFlags(a, h->stream, cudaEventRecordExternal);
+    }
+  }
   cudaError_t e = launch();
-  if (prof) { cudaEventRecord(b, h->stream); h->pending.push_back(PendingTiming{kind, a, b}); }
+  if (prof) {
+    if (pooled) cudaEventRecord(b, h->stream);
+    else cudaEventRecordWithFlags(b, h->stream, cudaEventRecordExternal);
+    h->pending.push_back(PendingTiming{kind, a, b, pooled});
+  }
   if (nonempty) {
     KStat& k = h->kstat[kind];
     k.launches++;
@@ -104,6 +138,102 @@ cudaError_t timed(mps_s* h, int kind, bool nonempty, double flops, double bytes,
     k.bytes += bytes;
   }
   return e;
+}
+
+// Runs one launch phase of an update call.  With graphs on (and a stream that can be
+// captured), the phase's copies and kernels are captured into a CUDA graph and replayed
+// through the handle's executable graph for that phase, updated in place
+// (cudaGraphExecUpdate) when only parameters changed and re-instantiated when the
+// topology changed (for example a different number of SVD kernel groups).
+template <class F>
+cudaError_t run_phase(mps_s* o, int slot, F&& body) {
+  cudaStream_t st = o->stream;
+  if (!o->graphs || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return body();
+  if (o->profiling) {
+    cudaError_t e = ensure_kind_events(o);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  o->capturing = true;
+  const cudaError_t eb = body();
+  o->capturing = false;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(st, &g);
+  if (eb != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return eb != cudaSuccess ? eb : ee;
+  }
+  bool updated = false;
+  if (o->gexec[slot]) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(o->gexec[slot], g, &info) == cudaSuccess) {
+      updated = true;
+      o->graph_updates++;
+    } else {
+      cudaGetLastError();
+      cudaGraphExecDestroy(o->gexec[slot]);
+      o->gexec[slot] = nullptr;
+    }
+  }
+  if (!updated) {
+    e = cudaGraphInstantiate(&o->gexec[slot], g, 0);
+    if (e != cudaSuccess) {
+      o->gexec[slot] = nullptr;
+      cudaGraphDestroy(g);
+      return e;
+    }
+    o->graph_instantiations++;
+  }
+  cudaGraphDestroy(g);
+  o->graph_launches++;
+  return cudaGraphLaunch(o->gexec[slot], st);
+}
+
+// ---- SVD tile-shape autotuner ----------------------------------------------------------
+// Key: the histogram of the batch's cluster-mode sectors over octaves of K = min(m, n),
+// counts rounded to powers of two, leaving out octaves that hold under 5% of the batch's
+// nominal SVD work (so that a few edge sectors do not split otherwise equal batches).
+// On the first batch with a new key (enough SVD work, tuning not frozen) every candidate
+// tile shape runs the batch's SVD phase on the same inputs (the phase reads Theta' and
+// writes only its own outputs and scratch, so it can be repeated), timed with CUDA
+// events, and the default shape runs once more at the end; a candidate replaces the
+// default only if it beats the faster of the default's two runs by more than 3%.  The
+// choice is stored and used for every later batch with that key.  The table is shared by
+// all handles of the process.
+struct TuneEntry {
+  int best = -1;
+  float ms[kTuneCands] = {};
+  int64_t hits = 0;
+};
+std::mutex g_tune_mu;
+std::map<std::vector<int>, TuneEntry> g_tune;
+int64_t g_tune_runs = 0;
+double g_tune_min_flops = 2e10;   // below this an SVD phase is too short to be worth tuning
+bool g_tune_frozen = false;       // frozen: unseen keys use the default shape without tuning
+constexpr int kTuneDefault = 1;   // svd_tune_candidate(1) is the default shape (bw 6, clusters from 2)
+
+std::vector<int> tune_key(const std::vector<SvdSector>& secs) {
+  std::map<int, std::pair<int, double>> hist;   // octave -> (count, nominal work)
+  double tot = 0.0;
+  for (const SvdSector& S : secs) {
+    if (S.mode == kSvdSmem) continue;
+    const double a = std::max(S.m, S.n), b = std::min(S.m, S.n);
+    const double w = 6.0 * a * b * b + 20.0 * b * b * b;
+    auto& e = hist[(int)std::floor(std::log2(b))];
+    e.first++;
+    e.second += w;
+    tot += w;
+  }
+  std::vector<int> key;
+  for (const auto& kv : hist) {
+    if (kv.second.second < 0.05 * tot) continue;
+    int q = 0;
+    for (int c = kv.second.first; c; c >>= 1) ++q;     // floor(log2(count)) + 1
+    key.push_back(kv.first);
+    key.push_back(q);
+  }
+  return key;
 }
 
 int gate_sn(int n, int d) { return std::min(d - 1, n) - std::max(0, n - d + 1) + 1; }
@@ -245,7 +375,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       }
   }
   const int64_t phase1_desc = a256((int64_t)sizeof(ThetaTask) * n_tasks) + a256(sizeof(TileRef) * (int64_t)n_tiles) +
-                              a256((int64_t)sizeof(SvdSector) * n_sec_total) +
+                              (owner->autotune ? kTuneCands : 1) * a256((int64_t)sizeof(SvdSector) * n_sec_total) +
                               a256((int64_t)sizeof(SelectSector) * n_sec_total) +
                               a256((int64_t)sizeof(SelectTask) * nreq) + gates_bytes +
                               a256((int64_t)sizeof(TcSegment) * n_tc_segs) + a256((int64_t)sizeof(TcTile) * n_tc_tiles);
@@ -399,24 +529,48 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     }
     seltask.push_back(SelectTask{W[u].sel_first, (int)selsec.size(), reqs[u].chi, reqs[u].cutoff});
   }
-  // largest sectors first so that the longest CTAs start earliest
+  // ---- SVD tile shape: the tuned choice for this sector-size histogram, or a tuning run ---
   // group the sectors by SVD kernel and cluster size, most expensive first inside a group
-  std::vector<SvdSector> svd_sorted = svd;
-  std::vector<SvdGroup> svd_groups;
-  CUDA_OR_FAIL(owner, svd_group(svd_sorted, svd_groups));
+  double svd_flops = 0, svd_bytes = 0, sel_bytes = 0;
+  for (const SvdSector& S : svd) {
+    const double a = std::max(S.m, S.n), b = std::min(S.m, S.n);
+    svd_flops += 4.0 * (6.0 * a * b * b + 20.0 * b * b * b);
+    svd_bytes += 16.0 * S.m * S.n + 16.0 * S.n * b + 8.0 * b + 8.0 * S.m;
+    sel_bytes += 8.0 * b;
+  }
+  std::vector<int> tkey;
+  int n_cand = 1, chosen = -1;       // n_cand > 1: this batch runs every candidate
+  if (owner->autotune) {
+    tkey = tune_key(svd);
+    if (!tkey.empty()) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(tkey);
+      if (it != g_tune.end() && it->second.best >= 0) {
+        chosen = it->second.best;
+        it->second.hits++;
+      } else if (!g_tune_frozen && svd_flops >= g_tune_min_flops) {
+        n_cand = kTuneCands;
+      }
+    }
+  }
+  std::vector<std::vector<SvdSector>> svd_sorted(n_cand, svd);
+  std::vector<std::vector<SvdGroup>> svd_groups(n_cand);
+  for (int c = 0; c < n_cand; ++c) {
+    const SvdTune tune = n_cand > 1 ? svd_tune_candidate(c) : (chosen >= 0 ? svd_tune_candidate(chosen) : SvdTune());
+    CUDA_OR_FAIL(owner, svd_group(svd_sorted[c], svd_groups[c], tune));
+  }
 
-  // ---- upload (one copy of all descriptors and gates) ---------------------------------
+  // ---- descriptors into the staging buffer (uploaded in one copy) ---------------------
   const int64_t o_tasks = sg.put(tasks.data(), (int64_t)tasks.size());
   const int64_t o_tiles = sg.put(tiles.data(), (int64_t)tiles.size());
-  const int64_t o_svd = sg.put(svd_sorted.data(), (int64_t)svd_sorted.size());
+  std::vector<int64_t> o_svd(n_cand);
+  for (int c = 0; c < n_cand; ++c) o_svd[c] = sg.put(svd_sorted[c].data(), (int64_t)svd_sorted[c].size());
   const int64_t o_selsec = sg.put(selsec.data(), (int64_t)selsec.size());
   const int64_t o_seltask = sg.put(seltask.data(), (int64_t)seltask.size());
   const int64_t o_tcseg = sg.put(tcseg.data(), (int64_t)tcseg.size());
   const int64_t o_tctile0 = sg.put(tctile[0].data(), (int64_t)tctile[0].size());
   const int64_t o_tctile1 = sg.put(tctile[1].data(), (int64_t)tctile[1].size());
   if (sg.size > desc_bytes) return fail(owner, MPS_EINVAL, "internal: descriptor bound exceeded");
-  CUDA_OR_FAIL(owner, cudaMemcpyAsync(dptr(desc_off), owner->pin_in.p, sg.size, cudaMemcpyHostToDevice, st));
-  CUDA_OR_FAIL(owner, cudaEventRecord(owner->staged, st));
 
   // ---- algorithmic work of the three kernels (flops: complex multiply-add = 8) -------
   double th_flops = 0, th_bytes = (double)(theta_bytes_end - theta_bytes_begin);   // Theta' written
@@ -429,43 +583,90 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     const int s = reqs[u].site;
     th_bytes += 16.0 * (double)(reqs[u].h->sites[s].nnz + reqs[u].h->sites[s + 1].nnz);
   }
-  double svd_flops = 0, svd_bytes = 0, sel_bytes = 0;
-  for (const SvdSector& S : svd) {
-    const double a = std::max(S.m, S.n), b = std::min(S.m, S.n);
-    svd_flops += 4.0 * (6.0 * a * b * b + 20.0 * b * b * b);
-    svd_bytes += 16.0 * S.m * S.n + 16.0 * S.n * b + 8.0 * b + 8.0 * S.m;
-    sel_bytes += 8.0 * b;
-  }
-  // ---- K1, K2, K3 ---------------------------------------------------------------------
-  CUDA_OR_FAIL(owner, cudaMemsetAsync(dptr(theta_bytes_begin), 0, theta_bytes_end - theta_bytes_begin, st));
-  const bool any_theta = !tiles.empty() || !tctile[0].empty() || !tctile[1].empty();
-  CUDA_OR_FAIL(owner, timed(owner, MPS_K_THETA, any_theta, th_flops, th_bytes, [&] {
-    cudaError_t e = launch_theta(reinterpret_cast<ThetaTask*>(dptr(desc_off + o_tasks)),
-                                 reinterpret_cast<TileRef*>(dptr(desc_off + o_tiles)), (int)tiles.size(), st);
-    const TcSegment* d_seg = reinterpret_cast<TcSegment*>(dptr(desc_off + o_tcseg));
-    if (e == cudaSuccess)
-      e = launch_tc_zgemm(MPS_TF32, reinterpret_cast<TcTile*>(dptr(desc_off + o_tctile0)), (int)tctile[0].size(),
-                          d_seg, owner->tc_flag, st);
-    if (e == cudaSuccess)
-      e = launch_tc_zgemm(MPS_BF16X3, reinterpret_cast<TcTile*>(dptr(desc_off + o_tctile1)), (int)tctile[1].size(),
-                          d_seg, owner->tc_flag, st);
-    return e;
-  }));
-  CUDA_OR_FAIL(owner, timed(owner, MPS_K_SVD, !svd_sorted.empty(), svd_flops, svd_bytes, [&] {   // one or more kernels
-    const SvdSector* d_svd = reinterpret_cast<SvdSector*>(dptr(desc_off + o_svd));
-    return launch_svd_groups(d_svd, svd_groups, st, owner->side, kSvdSideStreams, owner->fork, owner->join);
-  }));
-  CUDA_OR_FAIL(owner, timed(owner, MPS_K_SELECT, nreq > 0, 0.0, sel_bytes, [&] {
-    return launch_select(reinterpret_cast<SelectSector*>(dptr(desc_off + o_selsec)),
-                         reinterpret_cast<SelectTask*>(dptr(desc_off + o_seltask)), nreq,
-                         reinterpret_cast<int*>(dptr(kept_off)), reinterpret_cast<SelectResult*>(dptr(res_off)), st);
-  }));
   const int64_t out_bytes = res_off + (int64_t)sizeof(SelectResult) * nreq - kept_off;
-  CUDA_OR_FAIL(owner, cudaMemcpyAsync(owner->pin_out.p, dptr(kept_off), out_bytes, cudaMemcpyDeviceToHost, st));
   int* tc_err_host = reinterpret_cast<int*>((char*)owner->pin_out.p + a256(out_bytes));
   *tc_err_host = 0;
-  if (owner->tc_flag)   // this update's Theta' GEMM, or the reassembly GEMM of the previous one
-    CUDA_OR_FAIL(owner, cudaMemcpyAsync(tc_err_host, owner->tc_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+
+  // ---- phase 1: upload, K1 (Theta'), K2 (SVD), K3 (top-chi), read-back ------------------
+  auto upload_and_theta = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(dptr(desc_off), owner->pin_in.p, sg.size, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(dptr(theta_bytes_begin), 0, theta_bytes_end - theta_bytes_begin, st);
+    if (e != cudaSuccess) return e;
+    const bool any_theta = !tiles.empty() || !tctile[0].empty() || !tctile[1].empty();
+    return timed(owner, MPS_K_THETA, any_theta, th_flops, th_bytes, [&] {
+      cudaError_t e2 = launch_theta(reinterpret_cast<ThetaTask*>(dptr(desc_off + o_tasks)),
+                                    reinterpret_cast<TileRef*>(dptr(desc_off + o_tiles)), (int)tiles.size(), st);
+      const TcSegment* d_seg = reinterpret_cast<TcSegment*>(dptr(desc_off + o_tcseg));
+      if (e2 == cudaSuccess)
+        e2 = launch_tc_zgemm(MPS_TF32, reinterpret_cast<TcTile*>(dptr(desc_off + o_tctile0)),
+                             (int)tctile[0].size(), d_seg, owner->tc_flag, st);
+      if (e2 == cudaSuccess)
+        e2 = launch_tc_zgemm(MPS_BF16X3, reinterpret_cast<TcTile*>(dptr(desc_off + o_tctile1)),
+                             (int)tctile[1].size(), d_seg, owner->tc_flag, st);
+      return e2;
+    });
+  };
+  auto svd_launch = [&](int c) -> cudaError_t {   // one or more kernels
+    const SvdSector* d_svd = reinterpret_cast<SvdSector*>(dptr(desc_off + o_svd[c]));
+    return launch_svd_groups(d_svd, svd_groups[c], st, owner->side, kSvdSideStreams, owner->fork, owner->join);
+  };
+  auto select_and_readback = [&]() -> cudaError_t {
+    cudaError_t e = timed(owner, MPS_K_SELECT, nreq > 0, 0.0, sel_bytes, [&] {
+      return launch_select(reinterpret_cast<SelectSector*>(dptr(desc_off + o_selsec)),
+                           reinterpret_cast<SelectTask*>(dptr(desc_off + o_seltask)), nreq,
+                           reinterpret_cast<int*>(dptr(kept_off)), reinterpret_cast<SelectResult*>(dptr(res_off)), st);
+    });
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(owner->pin_out.p, dptr(kept_off), out_bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && owner->tc_flag)   // this update's Theta' GEMM, or the previous reassembly GEMM
+      e = cudaMemcpyAsync(tc_err_host, owner->tc_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    return e;
+  };
+  if (n_cand == 1) {
+    CUDA_OR_FAIL(owner, run_phase(owner, 0, [&]() -> cudaError_t {
+      cudaError_t e = upload_and_theta();
+      if (e == cudaSuccess)
+        e = timed(owner, MPS_K_SVD, !svd.empty(), svd_flops, svd_bytes, [&] { return svd_launch(0); });
+      if (e == cudaSuccess) e = select_and_readback();
+      return e;
+    }));
+  } else {
+    // tuning run: every candidate tile shape on the same inputs, timed on the stream
+    CUDA_OR_FAIL(owner, upload_and_theta());
+    std::vector<cudaEvent_t> ev(2 * (n_cand + 1));
+    for (auto& x : ev) x = pool_event(owner);
+    for (int r = 0; r <= n_cand; ++r) {         // every candidate, then the default once more
+      const int c = r < n_cand ? r : kTuneDefault;
+      CUDA_OR_FAIL(owner, cudaEventRecord(ev[2 * r], st));
+      CUDA_OR_FAIL(owner, svd_launch(c));
+      CUDA_OR_FAIL(owner, cudaEventRecord(ev[2 * r + 1], st));
+    }
+    CUDA_OR_FAIL(owner, cudaStreamSynchronize(st));
+    float ms[kTuneCands + 1] = {};
+    for (int r = 0; r <= n_cand; ++r) CUDA_OR_FAIL(owner, cudaEventElapsedTime(&ms[r], ev[2 * r], ev[2 * r + 1]));
+    ms[kTuneDefault] = std::min(ms[kTuneDefault], ms[n_cand]);
+    int best = kTuneDefault;
+    for (int c = 0; c < n_cand; ++c)
+      if (ms[c] < 0.97f * ms[kTuneDefault] && ms[c] < ms[best]) best = c;
+    for (auto& x : ev) owner->event_pool.push_back(x);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      TuneEntry& te = g_tune[tkey];
+      te.best = best;
+      for (int c = 0; c < n_cand; ++c) te.ms[c] = ms[c];
+      g_tune_runs++;
+    }
+    // the outputs must come from the chosen shape: rerun it unless it ran last
+    if (best != kTuneDefault) CUDA_OR_FAIL(owner, svd_launch(best));
+    KStat& k = owner->kstat[MPS_K_SVD];
+    k.launches++;
+    k.flops += svd_flops;
+    k.bytes += svd_bytes;
+    if (owner->profiling) k.ms += ms[best];
+    CUDA_OR_FAIL(owner, select_and_readback());
+  }
+  CUDA_OR_FAIL(owner, cudaEventRecord(owner->staged, st));
   CUDA_OR_FAIL(owner, cudaStreamSynchronize(st));
   resolve_pending(owner);
   if (*tc_err_host) {
@@ -628,33 +829,40 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     const int64_t o_gtile0 = s2.put(gtile[0].data(), (int64_t)gtile[0].size());
     const int64_t o_gtile1 = s2.put(gtile[1].data(), (int64_t)gtile[1].size());
     if (s2.size > desc_bytes) return fail(owner, MPS_EINVAL, "internal: descriptor bound exceeded");
-    CUDA_OR_FAIL(owner, cudaMemcpyAsync(dptr(desc_off), owner->pin_in.p, s2.size, cudaMemcpyHostToDevice, st));
-    CUDA_OR_FAIL(owner, cudaEventRecord(owner->staged, st));
     double lam_bytes = 0, gm_flops = tc_gm_flops, gm_bytes = tc_gm_bytes;
     for (const LambdaTask& T : lam) lam_bytes += 16.0 * T.k;
     for (const GemmTask& T : gm) {
       gm_flops += 8.0 * T.M * T.N * T.K;
       gm_bytes += 16.0 * ((double)T.M * T.K + (double)T.K * T.N + (double)T.M * T.N);
     }
-    CUDA_OR_FAIL(owner, timed(owner, MPS_K_LAMBDA, true, 0.0, lam_bytes, [&] {
-      return launch_lambda(reinterpret_cast<LambdaTask*>(dptr(desc_off + o_lam)), (int)lam.size(), st);
-    }));
-    CUDA_OR_FAIL(owner, timed(owner, MPS_K_SCATTER, sc_elems > 0, 0.0, 32.0 * (double)sc_elems, [&] {
-      return launch_scatter(reinterpret_cast<ScatterTask*>(dptr(desc_off + o_sc)), (int)sc.size(), sc_elems, st);
-    }));
-    const bool any_gemm = !gt.empty() || !gtile[0].empty() || !gtile[1].empty();
-    CUDA_OR_FAIL(owner, timed(owner, MPS_K_GEMM, any_gemm, gm_flops, gm_bytes, [&] {
-      cudaError_t e = launch_gemm(reinterpret_cast<GemmTask*>(dptr(desc_off + o_gm)),
-                                  reinterpret_cast<TileRef*>(dptr(desc_off + o_gt)), (int)gt.size(), st);
-      const TcSegment* d_seg = reinterpret_cast<TcSegment*>(dptr(desc_off + o_gseg));
+    // ---- phase 2: upload, K4/K5 (lambda, B^[s+1] scatter, B^[s] product) ----------------
+    CUDA_OR_FAIL(owner, run_phase(owner, 1, [&]() -> cudaError_t {
+      cudaError_t e = cudaMemcpyAsync(dptr(desc_off), owner->pin_in.p, s2.size, cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess)
-        e = launch_tc_zgemm(MPS_TF32, reinterpret_cast<TcTile*>(dptr(desc_off + o_gtile0)), (int)gtile[0].size(),
-                            d_seg, owner->tc_flag, st);
+        e = timed(owner, MPS_K_LAMBDA, true, 0.0, lam_bytes, [&] {
+          return launch_lambda(reinterpret_cast<LambdaTask*>(dptr(desc_off + o_lam)), (int)lam.size(), st);
+        });
       if (e == cudaSuccess)
-        e = launch_tc_zgemm(MPS_BF16X3, reinterpret_cast<TcTile*>(dptr(desc_off + o_gtile1)), (int)gtile[1].size(),
-                            d_seg, owner->tc_flag, st);
+        e = timed(owner, MPS_K_SCATTER, sc_elems > 0, 0.0, 32.0 * (double)sc_elems, [&] {
+          return launch_scatter(reinterpret_cast<ScatterTask*>(dptr(desc_off + o_sc)), (int)sc.size(), sc_elems, st);
+        });
+      const bool any_gemm = !gt.empty() || !gtile[0].empty() || !gtile[1].empty();
+      if (e == cudaSuccess)
+        e = timed(owner, MPS_K_GEMM, any_gemm, gm_flops, gm_bytes, [&] {
+          cudaError_t e2 = launch_gemm(reinterpret_cast<GemmTask*>(dptr(desc_off + o_gm)),
+                                       reinterpret_cast<TileRef*>(dptr(desc_off + o_gt)), (int)gt.size(), st);
+          const TcSegment* d_seg = reinterpret_cast<TcSegment*>(dptr(desc_off + o_gseg));
+          if (e2 == cudaSuccess)
+            e2 = launch_tc_zgemm(MPS_TF32, reinterpret_cast<TcTile*>(dptr(desc_off + o_gtile0)),
+                                 (int)gtile[0].size(), d_seg, owner->tc_flag, st);
+          if (e2 == cudaSuccess)
+            e2 = launch_tc_zgemm(MPS_BF16X3, reinterpret_cast<TcTile*>(dptr(desc_off + o_gtile1)),
+                                 (int)gtile[1].size(), d_seg, owner->tc_flag, st);
+          return e2;
+        });
       return e;
     }));
+    CUDA_OR_FAIL(owner, cudaEventRecord(owner->staged, st));
   }
   for (int u = 0; u < nreq; ++u) {
     if (!apply[u]) continue;
@@ -778,6 +986,11 @@ int mps_destroy(mps_t h) {
   for (auto& p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   if (h->tc_flag) cudaFree(h->tc_flag);
+  for (auto& g : h->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto& kk : h->kind_ev)
+    for (auto& e : kk)
+      if (e) cudaEventDestroy(e);
   h->work.release();
   h->pin_in.release();
   h->pin_out.release();
@@ -1131,6 +1344,91 @@ int mps_reset_kernel_stats(mps_t h) {
 }
 
 int64_t mps_launch_count(void) { return g_launches.load(); }
+
+int mps_set_graphs(mps_t h, int on) {
+  if (!h) return MPS_EINVAL;
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  h->graphs = on != 0;
+  if (!h->graphs)
+    for (auto& g : h->gexec)
+      if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  return MPS_OK;
+}
+
+int mps_graph_stats(mps_t h, int64_t* launches, int64_t* updates, int64_t* instantiations) {
+  if (!h) return MPS_EINVAL;
+  if (launches) *launches = h->graph_launches;
+  if (updates) *updates = h->graph_updates;
+  if (instantiations) *instantiations = h->graph_instantiations;
+  return MPS_OK;
+}
+
+int mps_set_autotune(mps_t h, int on) {
+  if (!h) return MPS_EINVAL;
+  h->autotune = on != 0;
+  return MPS_OK;
+}
+
+int mps_autotune_stats(int64_t* keys, int64_t* tuning_runs, int64_t* hits) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int64_t nh = 0;
+  for (const auto& kv : g_tune) nh += kv.second.hits;
+  if (keys) *keys = (int64_t)g_tune.size();
+  if (tuning_runs) *tuning_runs = g_tune_runs;
+  if (hits) *hits = nh;
+  return MPS_OK;
+}
+
+int mps_autotune_table(char* buf, int cap, int* len) {
+  std::string t;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    char line[256];
+    for (const auto& kv : g_tune) {
+      std::string key;
+      for (size_t i = 0; i + 1 < kv.first.size(); i += 2) {
+        std::snprintf(line, sizeof(line), "%sK~2^%d:%d", key.empty() ? "" : ",", kv.first[i],
+                      kv.first[i + 1] ? 1 << (kv.first[i + 1] - 1) : 0);
+        key += line;
+      }
+      const TuneEntry& e = kv.second;
+      if (e.best < 0) continue;
+      const SvdTune b = svd_tune_candidate(e.best);
+      std::snprintf(line, sizeof(line), "%s -> bw=%d cl_min=%d hits=%lld ms=", key.c_str(), b.bw, b.cl_min,
+                    (long long)e.hits);
+      t += line;
+      for (int c = 0; c < kTuneCands; ++c) {
+        std::snprintf(line, sizeof(line), "%s%.2f", c ? "/" : "", e.ms[c]);
+        t += line;
+      }
+      t += "\n";
+    }
+  }
+  if (len) *len = (int)t.size();
+  if (!buf || cap <= (int)t.size()) return buf ? MPS_EINVAL : MPS_OK;
+  std::memcpy(buf, t.c_str(), t.size() + 1);
+  return MPS_OK;
+}
+
+int mps_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  g_tune_runs = 0;
+  return MPS_OK;
+}
+
+int mps_autotune_freeze(int frozen) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_frozen = frozen != 0;
+  return MPS_OK;
+}
+
+int mps_autotune_min_flops(double flops) {
+  if (!(flops >= 0.0) || !std::isfinite(flops)) return MPS_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_min_flops = flops;
+  return MPS_OK;
+}
 
 int mps_last_batch_sweeps(mps_t h, int* n_sectors, int64_t* sweeps_sum, int* sweeps_max) {
   if (!h) return MPS_EINVAL;

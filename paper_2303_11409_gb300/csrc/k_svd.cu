@@ -878,7 +878,7 @@ cudaError_t launch_group(const SvdSector* d_secs, const SvdGroup& g, int max_swe
 
 }  // namespace
 
-cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& groups) {
+cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& groups, const SvdTune& tune) {
   cudaError_t e = set_attrs();
   if (e != cudaSuccess) return e;
   // every sector gets a kernel and a cluster size
@@ -891,20 +891,22 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
       smem[k] = svd_smem_need(S.m, S.n);
       continue;
     }
-    // blocks of about 6 columns; the smallest cluster (2, 4 or 8 CTAs) whose CTAs can
-    // stage all of their block pairs of a round at once, so that a step offers the warp
-    // groups about 3 K / (2 cl) disjoint pairs; failing that, 8 CTAs staging as many
-    // pairs as fit, with more pairs per CTA when a single one does not fit
+    // blocks of about tune.bw columns (6 by default); the smallest cluster (tune.cl_min,
+    // then doubling up to 8 CTAs) whose CTAs can stage all of their block pairs of a round
+    // at once, so that a step offers the warp groups about K / (2 cl) * bw / 2 disjoint
+    // pairs; failing that, 8 CTAs staging as many pairs as fit, with more pairs per CTA
+    // when a single one does not fit
+    const int bw = std::max(2, tune.bw);
     int pick_cl = 0, pick_g = 0, pick_gs = 0;
-    for (int cl = 2; cl <= kBigCluster && !pick_cl; cl *= 2) {
-      const int g = std::max(1, (std::min(S.m, S.n) + 6 * cl) / (12 * cl));
+    for (int cl = std::max(2, std::min(tune.cl_min, kBigCluster)); cl <= kBigCluster && !pick_cl; cl *= 2) {
+      const int g = std::max(1, (std::min(S.m, S.n) + bw * cl) / (2 * bw * cl));
       if (g <= kMaxStaged && block_smem_need(S.m, S.n, cl, g, g) <= kBlockSmemMax) {
         pick_cl = cl; pick_g = g; pick_gs = g;
       }
     }
     if (!pick_cl) {
       const int cl = kBigCluster;
-      int g = std::max(1, (std::min(S.m, S.n) + 6 * cl) / (12 * cl));
+      int g = std::max(1, (std::min(S.m, S.n) + bw * cl) / (2 * bw * cl));
       while (g < 64 && block_smem_need(S.m, S.n, cl, g, 1) > kBlockSmemMax) ++g;
       int gs = 1;
       while (gs < std::min(g, kMaxStaged) && block_smem_need(S.m, S.n, cl, g, gs + 1) <= kBlockSmemMax) ++gs;

@@ -160,7 +160,7 @@ struct Stats {
 };
 
 struct KStat { int64_t launches = 0; double ms = 0, flops = 0, bytes = 0; };
-struct PendingTiming { int kind; cudaEvent_t a, b; };
+struct PendingTiming { int kind; cudaEvent_t a, b; bool pooled; };
 
 // Kernel launches made by the library in this process (all handles).
 void count_launch();
@@ -192,6 +192,15 @@ struct mps_s {
   std::vector<mps::PendingTiming> pending;   // event pairs not yet read back
   std::vector<cudaEvent_t> event_pool;
   int* tc_flag = nullptr;                 // set by a tensor-core GEMM whose bounded wait expired
+  // CUDA graphs: the two launch phases of an update call are captured and replayed
+  // through one executable graph each, updated in place while the topology holds
+  bool graphs = false;
+  bool capturing = false;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int64_t graph_launches = 0, graph_updates = 0, graph_instantiations = 0;
+  cudaEvent_t kind_ev[MPS_K_COUNT][2] = {};   // per-kind timing events used inside captured graphs
+  // autotuning of the SVD tile shape per sector-size histogram
+  bool autotune = false;
 
   double2* slot_ptr(int s, int slot) { return d_sites + site_base[s] + (slot ? site_cap[s] : 0); }
   double* lambda_ptr(int b) { return d_lambda + lam_base[b]; }
@@ -203,8 +212,20 @@ namespace mps {
 cudaError_t launch_theta(const ThetaTask* d_tasks, const TileRef* d_tiles, int n_tiles, cudaStream_t st);
 // Sectors grouped by kernel and cluster size (a group is a contiguous run of the array).
 struct SvdGroup { int kind, cl, smem, first, count; };
+// Tile shape of the block-Jacobi cluster kernel: target column-block width and the
+// smallest cluster size tried.  The autotuner picks one per sector-size histogram.
+struct SvdTune { int bw = 6; int cl_min = 2; };
+constexpr int kTuneCands = 8;
+inline SvdTune svd_tune_candidate(int k) {   // bw in {4, 6, 8, 12} x cl_min in {2, 4}
+  static const int bws[4] = {4, 6, 8, 12};
+  SvdTune t;
+  t.bw = bws[k & 3];
+  t.cl_min = (k & 4) ? 4 : 2;
+  return t;
+}
 // Orders `secs` into groups (costliest first inside each) and fills `groups`.
-cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& groups);
+cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& groups,
+                      const SvdTune& tune = SvdTune());
 // Group 0 on st, group g > 0 on side[g-1] when n_side >= groups - 1; st then waits for all.
 cudaError_t launch_svd_groups(const SvdSector* d_secs, const std::vector<SvdGroup>& groups, cudaStream_t st,
                               const cudaStream_t* side, int n_side, cudaEvent_t fork, const cudaEvent_t* join);

@@ -79,6 +79,28 @@ def random_positive(n: int, rng: np.random.Generator) -> np.ndarray:
     return np.sort(v)[::-1].copy()
 
 
+def haar_unitary(n: int, rng: np.random.Generator) -> np.ndarray:
+    """An n x n unitary drawn from the Haar measure: Q of the QR decomposition of a
+    complex Gaussian matrix, each column multiplied by the phase of R's diagonal entry
+    (Mezzadri's recipe)."""
+    z = random_complex((n, n), rng) / np.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    dg = np.diag(r)
+    return q * (dg / np.abs(dg))[None, :]
+
+
+def random_u1_gate(d: int, rng: np.random.Generator) -> list[np.ndarray]:
+    """A charge-conserving two-site gate with Haar-random charge blocks.
+
+    Block n (n = 0..2(d-1)) acts on the states (i, n - i) of two sites of local
+    dimension d, so its size is the number of such i in [0, d-1]."""
+    blocks = []
+    for n in range(2 * (d - 1) + 1):
+        size = min(d - 1, n) - max(0, n - d + 1) + 1
+        blocks.append(haar_unitary(size, rng))
+    return blocks
+
+
 def random_occupations(L: int, d: int, N: int, rng: np.random.Generator) -> list[int]:
     """A random product state of L sites, local dimension d, total charge N."""
     if N > L * (d - 1):
