@@ -652,10 +652,77 @@ __device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int ncta
     Mem::st(a, make_double2(x.x, -x.y));
   }
   sync();
+
+  // ---- wide sectors (K = m < n): R^dag = Q2 [R2; 0] by unpivoted Householder QR of its
+  // K columns.  Rotations that orthogonalise the columns of R^dag orthogonalise those of
+  // R2 alike (Q2 has orthonormal columns), so the Jacobi sweeps run on R2's columns,
+  // length K instead of n, and Y = P Q2 [normalised columns; 0] at the end. --------------
+  double2* J = W;        // the Jacobi matrix: column j at J + j * jld, length jlen
+  int jlen = n, jld = ld;
+  double* tau = w.nu;    // reflector scales (w.nu is free after the pivoted QR; n >= K)
+  const bool wide = Mem::kCache && S.wide;   // cluster kernels only (their scratch holds R2)
+  if constexpr (Mem::kCache) if (wide) {
+    double2* W2 = S.work2;
+    const int ld2 = odd_ld(K);
+    for (int64_t e = tid_all; e < (int64_t)K * ld2; e += threads_all) Mem::st(W2 + e, make_double2(0.0, 0.0));
+    sync();
+    for (int k = 0; k < K; ++k) {
+      double2* xk = W + (int64_t)k * ld;
+      if (worker == 0) {   // H_k = I - tau_k v v^dag maps x_k[k:] to beta e_k; v overwrites x_k[k:]
+        double x2 = 0.0;
+        for (int i = k + lane; i < n; i += 32) {
+          const double2 x = Mem::ld(xk + i);
+          x2 = fma(x.x, x.x, fma(x.y, x.y, x2));
+        }
+        x2 = warp_sum(x2);
+        const double xn = sqrt(x2);
+        const double2 x0 = Mem::ld(xk + k);
+        const double a0 = hypot(x0.x, x0.y);
+        double2 beta;
+        if (a0 > 0.0) beta = make_double2(-x0.x / a0 * xn, -x0.y / a0 * xn);
+        else beta = make_double2(-xn, 0.0);
+        const double uu = 2.0 * x2 + 2.0 * xn * a0;
+        if (lane == 0) {
+          Mem::st(xk + k, make_double2(x0.x - beta.x, x0.y - beta.y));
+          Mem::st(tau + k, uu > 0.0 ? 2.0 / uu : 0.0);
+          Mem::st(W2 + (int64_t)k * ld2 + k, beta);          // R2[k][k]
+        }
+      }
+      sync();
+      const double tk = Mem::ld(tau + k);
+      for (int j = k + 1 + worker; j < K; j += workers) {
+        double2* xj = W + (int64_t)j * ld;
+        double pr = 0.0, pim = 0.0;
+        if (tk != 0.0) {
+          for (int i = k + lane; i < n; i += 32) {
+            const double2 v = Mem::ld(xk + i), x = Mem::ld(xj + i);
+            pr = fma(v.x, x.x, fma(v.y, x.y, pr));         // conj(v) x
+            pim = fma(v.x, x.y, fma(-v.y, x.x, pim));
+          }
+          pr = warp_sum(pr) * tk;
+          pim = warp_sum(pim) * tk;
+        }
+        for (int i = k + lane; i < n; i += 32) {
+          double2 x = Mem::ld(xj + i);
+          if (tk != 0.0) {
+            const double2 v = Mem::ld(xk + i);
+            x.x -= v.x * pr - v.y * pim;
+            x.y -= v.x * pim + v.y * pr;
+            Mem::st(xj + i, x);
+          }
+          if (i == k) Mem::st(W2 + (int64_t)j * ld2 + k, x);   // R2[k][j], final after H_k
+        }
+      }
+      sync();
+    }
+    J = W2;
+    jlen = K;
+    jld = ld2;
+  }
   for (int j = worker; j < K; j += workers) {
-    const double2* a = W + (int64_t)j * ld;
+    const double2* a = J + (int64_t)j * jld;
     double acc = 0.0;
-    for (int i = lane; i < n; i += 32) {
+    for (int i = lane; i < jlen; i += 32) {
       const double2 x = Mem::ld(a + i);
       acc = fma(x.x, x.x, fma(x.y, x.y, acc));
     }
@@ -664,18 +731,18 @@ __device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int ncta
   }
   sync();
 
-  // ---- one-sided Jacobi on the K columns (length n) of R^dag -----------------------------
+  // ---- one-sided Jacobi on the K columns of R^dag (or R2) --------------------------------
   const double tol = kEps * (double)max(n, 32);
   const double tol2 = tol * tol;
   const double floor2 = (32.0 * kEps) * (32.0 * kEps) * fro2;
   bool converged = false;
-  const int sweep = jacobi(W, n, ld, K, w, rank, nctas, sync, tol2, floor2, max_sweeps, converged);
+  const int sweep = jacobi(J, jlen, jld, K, w, rank, nctas, sync, tol2, floor2, max_sweeps, converged);
 
   // ---- singular values (noise floor -> 0), descending, ties by column index -----------
   for (int j = worker; j < K; j += workers) {
-    const double2* a = W + (int64_t)j * ld;
+    const double2* a = J + (int64_t)j * jld;
     double acc = 0.0;
-    for (int i = lane; i < n; i += 32) {
+    for (int i = lane; i < jlen; i += 32) {
       const double2 x = Mem::ld(a + i);
       acc = fma(x.x, x.x, fma(x.y, x.y, acc));
     }
@@ -696,17 +763,62 @@ __device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int ncta
   }
   sync();
   for (int r = tid_all; r < K; r += threads_all) S.sigma[r] = Mem::ld(w.nrm + Mem::ld(w.ord + r));
-  // Y[perm[j], r] = column ord[r] of R^dag, row j, divided by its norm
-  for (int64_t e = tid_all; e < kn; e += threads_all) {
-    const int r = (int)(e / n), j = (int)(e % n);
-    const int c = Mem::ld(w.ord + r);
-    const double sv = Mem::ld(w.nrm + c);
-    double2 y = make_double2(0.0, 0.0);
-    if (sv > 0.0) {
-      const double2 a = Mem::ld(W + (int64_t)c * ld + j);
-      y = make_double2(a.x / sv, a.y / sv);
+  if (wide) {
+    // Y[perm[j], r] = (Q2 [R2 column ord[r] / sigma_r; 0])[j]; Q2 = H_0 ... H_{K-1}, one warp per column
+    for (int r = worker; r < K; r += workers) {
+      const int c = Mem::ld(w.ord + r);
+      const double sv = Mem::ld(w.nrm + c);
+      double2* y = S.ytmp + (int64_t)r * n;
+      if (sv > 0.0) {
+        const double2* a = J + (int64_t)c * jld;
+        for (int i = lane; i < n; i += 32) {
+          double2 val = make_double2(0.0, 0.0);
+          if (i < K) {
+            const double2 x = Mem::ld(a + i);
+            val = make_double2(x.x / sv, x.y / sv);
+          }
+          Mem::st(y + i, val);
+        }
+        __syncwarp();
+        for (int k = K - 1; k >= 0; --k) {
+          const double tk = Mem::ld(tau + k);
+          if (tk == 0.0) continue;
+          const double2* v = W + (int64_t)k * ld;
+          double pr = 0.0, pim = 0.0;
+          for (int i = k + lane; i < n; i += 32) {
+            const double2 vv = Mem::ld(v + i), x = Mem::ld(y + i);
+            pr = fma(vv.x, x.x, fma(vv.y, x.y, pr));
+            pim = fma(vv.x, x.y, fma(-vv.y, x.x, pim));
+          }
+          pr = warp_sum(pr) * tk;
+          pim = warp_sum(pim) * tk;
+          for (int i = k + lane; i < n; i += 32) {
+            const double2 vv = Mem::ld(v + i);
+            double2 x = Mem::ld(y + i);
+            x.x -= vv.x * pr - vv.y * pim;
+            x.y -= vv.x * pim + vv.y * pr;
+            Mem::st(y + i, x);
+          }
+          __syncwarp();
+        }
+        for (int j = lane; j < n; j += 32) S.Y[(int64_t)r * n + Mem::ld(w.perm + j)] = Mem::ld(y + j);
+      } else {
+        for (int j = lane; j < n; j += 32) S.Y[(int64_t)r * n + j] = make_double2(0.0, 0.0);
+      }
     }
-    S.Y[(int64_t)r * n + Mem::ld(w.perm + j)] = y;
+  } else {
+    // Y[perm[j], r] = column ord[r] of R^dag, row j, divided by its norm
+    for (int64_t e = tid_all; e < kn; e += threads_all) {
+      const int r = (int)(e / n), j = (int)(e % n);
+      const int c = Mem::ld(w.ord + r);
+      const double sv = Mem::ld(w.nrm + c);
+      double2 y = make_double2(0.0, 0.0);
+      if (sv > 0.0) {
+        const double2 a = Mem::ld(W + (int64_t)c * ld + j);
+        y = make_double2(a.x / sv, a.y / sv);
+      }
+      S.Y[(int64_t)r * n + Mem::ld(w.perm + j)] = y;
+    }
   }
   if (tid_all == 0) *S.status = converged ? sweep : -1;
 }
@@ -796,7 +908,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) jacobi_cluster_block_kernel(
   jb.gs = S.staged;
   jb.bsmax = (K + 2 * cluster * jb.g - 1) / (2 * cluster * jb.g);
   jb.sm = reinterpret_cast<double2*>(smem_raw);
-  jb.smn = reinterpret_cast<double*>(smem_raw + 16LL * 2 * jb.gs * jb.bsmax * S.n);
+  jb.smn = reinterpret_cast<double*>(smem_raw + 16LL * 2 * jb.gs * jb.bsmax * (S.wide ? K : S.n));
   svd_sector<L2Mem>(S, cluster_work(S), rank, cluster, ClusterSync{}, max_sweeps, jb);
 }
 
@@ -897,26 +1009,27 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
     // pairs; failing that, 8 CTAs staging as many pairs as fit, with more pairs per CTA
     // when a single one does not fit
     const int bw = std::max(2, tune.bw);
+    const int cn = S.wide ? std::min(S.m, S.n) : S.n;   // Jacobi column length
     int pick_cl = 0, pick_g = 0, pick_gs = 0;
     for (int cl = std::max(2, std::min(tune.cl_min, kBigCluster)); cl <= kBigCluster && !pick_cl; cl *= 2) {
       const int g = std::max(1, (std::min(S.m, S.n) + bw * cl) / (2 * bw * cl));
-      if (g <= kMaxStaged && block_smem_need(S.m, S.n, cl, g, g) <= kBlockSmemMax) {
+      if (g <= kMaxStaged && block_smem_need(S.m, cn, cl, g, g) <= kBlockSmemMax) {
         pick_cl = cl; pick_g = g; pick_gs = g;
       }
     }
     if (!pick_cl) {
       const int cl = kBigCluster;
       int g = std::max(1, (std::min(S.m, S.n) + bw * cl) / (2 * bw * cl));
-      while (g < 64 && block_smem_need(S.m, S.n, cl, g, 1) > kBlockSmemMax) ++g;
+      while (g < 64 && block_smem_need(S.m, cn, cl, g, 1) > kBlockSmemMax) ++g;
       int gs = 1;
-      while (gs < std::min(g, kMaxStaged) && block_smem_need(S.m, S.n, cl, g, gs + 1) <= kBlockSmemMax) ++gs;
-      if (block_smem_need(S.m, S.n, cl, g, gs) <= kBlockSmemMax) {
+      while (gs < std::min(g, kMaxStaged) && block_smem_need(S.m, cn, cl, g, gs + 1) <= kBlockSmemMax) ++gs;
+      if (block_smem_need(S.m, cn, cl, g, gs) <= kBlockSmemMax) {
         pick_cl = cl; pick_g = g; pick_gs = gs;
       }
     }
     if (pick_cl) {
       key[k] = {kSvdClusterBlock, pick_cl};
-      smem[k] = block_smem_need(S.m, S.n, pick_cl, pick_g, pick_gs);
+      smem[k] = block_smem_need(S.m, cn, pick_cl, pick_g, pick_gs);
       secs[k].groups = pick_g;
       secs[k].staged = pick_gs;
     } else {
@@ -989,6 +1102,9 @@ bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L) {
   L.ord_off.assign(ns, -1);
   L.flag_off.assign(ns, -1);
   L.piv_off.assign(ns, -1);
+  L.wide.assign(ns, 0);
+  L.w2_off.assign(ns, -1);
+  L.yt_off.assign(ns, -1);
   L.smem = 0;
   int64_t off = 0;
   auto a256 = [](int64_t x) { return (x + 255) & ~int64_t(255); };
@@ -1007,6 +1123,11 @@ bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L) {
     L.ord_off[k] = off;  off = a256(off + 4 * (N + Kk));                // perm, ord
     L.flag_off[k] = off; off = a256(off + 4 * (kJacobiMaxSweeps + 1 + kMaxCluster));   // flags, pivot index
     L.piv_off[k] = off;  off = a256(off + 8 * (kMaxCluster + 2));       // pivot value, scalars
+    if (4LL * n[k] >= 5LL * m[k]) {   // wide: the Jacobi sweeps run on the K x K factor R2
+      L.wide[k] = 1;
+      L.w2_off[k] = off; off = a256(off + 16 * Kk * odd_ld((int)Kk));     // R2 / Jacobi matrix
+      L.yt_off[k] = off; off = a256(off + 16 * N * Kk);                   // Q2 applied to its columns
+    }
   }
   L.total = off;
   return true;
@@ -1021,6 +1142,11 @@ void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base
   S.order = reinterpret_cast<int*>(base + L.ord_off[k]);
   S.flags = reinterpret_cast<int*>(base + L.flag_off[k]);
   S.pivv = reinterpret_cast<double*>(base + L.piv_off[k]);
+  S.wide = L.wide[k];
+  if (S.wide) {
+    S.work2 = reinterpret_cast<double2*>(base + L.w2_off[k]);
+    S.ytmp = reinterpret_cast<double2*>(base + L.yt_off[k]);
+  }
 }
 
 }  // namespace mps

@@ -96,12 +96,16 @@ struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   int mode;                   // kSvdSmem, kSvdCluster or kSvdClusterBlock
   int groups;                 // block Jacobi: block pairs per CTA and round
   int staged;                 // block Jacobi: block pairs staged in shared memory at once
+  int wide;                   // cluster mode, m < n: Jacobi on R2 of R^dag = Q2 R2 (K x K)
+  double2* work2;             // wide: R2 / the Jacobi matrix, K x (K | 1) column-major
+  double2* ytmp;              // wide: n x K, Q2 applied to the normalised columns
 };
 
 // Scratch layout of a batch of sector SVDs (cluster-mode sectors only need global scratch).
 struct SvdScratchLayout {
   std::vector<int> mode;
-  std::vector<int64_t> work_off, v_off, norm_off, ord_off, flag_off, piv_off;
+  std::vector<int64_t> work_off, v_off, norm_off, ord_off, flag_off, piv_off, w2_off, yt_off;
+  std::vector<int> wide;
   int smem = 0;               // dynamic shared memory of the one-CTA kernel
   int64_t total = 0;
 };

@@ -25,7 +25,7 @@ def _check(M, sig, Y, sweeps, tol=1e-12):
 # one-CTA shared-memory sectors (wide and tall), cluster sectors (wide, tall with V, and
 # more than 512 rows, the register-cache limit)
 SHAPES = [(1, 1), (1, 7), (7, 1), (2, 2), (5, 5), (30, 20), (20, 30), (64, 64), (100, 110),
-          (150, 170), (200, 90), (33, 257), (600, 300), (300, 600), (420, 410)]
+          (150, 170), (200, 90), (33, 257), (600, 300), (300, 600), (420, 410), (130, 600), (64, 1100)]
 
 
 def test_svd_random_shapes(gpu_lib):
@@ -42,6 +42,9 @@ def test_svd_rowscale_graded_and_rank_deficient(gpu_lib):
     A = W.random_complex((60, 50), rng)
     mats.append(A)
     scales.append(np.logspace(0, -12, 60))
+    # wide cluster sector (Jacobi on the K x K factor of R^dag) with graded rows
+    mats.append(W.random_complex((110, 320), rng))
+    scales.append(np.logspace(0, -10, 110))
     # exact rank 3
     B = W.random_complex((40, 3), rng) @ W.random_complex((3, 45), rng)
     mats.append(B)
@@ -58,7 +61,14 @@ def test_svd_rowscale_graded_and_rank_deficient(gpu_lib):
         k = min(Ms.shape)
         assert np.max(np.abs(sig - ref[:k])) <= 1e-13 * ref[0]
     # rank 3: everything past the third value is at rounding level
-    assert np.all(out[1][0][3:] < 1e-13 * out[1][0][0])
+    assert np.all(out[2][0][3:] < 1e-13 * out[2][0][0])
+    # graded wide sector: right singular vectors orthonormal and M y_j = sigma_j to relative accuracy
+    Ms = scales[1][:, None] * mats[1]
+    sig, Y, _ = out[1]
+    good = sig > 1e-6 * sig[0]      # where numpy's own product M y is accurate to 1e-10 relative
+    Yg = Y[:, good]
+    assert np.max(np.abs(Yg.conj().T @ Yg - np.eye(Yg.shape[1]))) < 1e-10
+    assert np.max(np.abs(np.linalg.norm(Ms @ Yg, axis=0) / sig[good] - 1.0)) < 1e-8
 
 
 def test_svd_many_sectors_one_launch(gpu_lib):

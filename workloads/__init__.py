@@ -136,3 +136,58 @@ def serving_requests(n: int, seed: int = 0, rate_hz: float = 1.0, L_choices=(32,
         param = float(rng.uniform(0.0, 2.0)) if model == "xxz" else float(rng.uniform(1.0, 10.0))
         out.append(dict(id=k, arrival=float(t[k]), model=model, L=L, chi=chi, steps=steps, param=param))
     return out
+
+
+def _strings(n_sites: int, d: int, q: int) -> int:
+    """Number of occupation strings of n_sites sites (0..d-1 each) summing to q."""
+    if q < 0 or q > n_sites * (d - 1):
+        return 0
+    ways = [1] + [0] * q
+    for _ in range(n_sites):
+        ways = [sum(ways[q2 - i] for i in range(d) if q2 - i >= 0) for q2 in range(q + 1)]
+    return ways[q]
+
+
+def saturated_sector_dims(L: int, d: int, N: int, b: int, chi: int) -> dict:
+    """Sector dimensions {charge: dim} of bond b of a chain at saturation: chi spread over
+    the charges c the bond can carry in proportion to min(#strings of the left part with
+    N - c particles, #strings of the right part with c), each capped by that bound."""
+    lo, hi = max(0, N - (d - 1) * b), min(N, (d - 1) * (L - b))
+    bound = {c: min(_strings(b, d, N - c), _strings(L - b, d, c)) for c in range(lo, hi + 1)}
+    bound = {c: v for c, v in bound.items() if v > 0}
+    tot = sum(bound.values())
+    if tot <= chi:
+        return bound
+    dims = {c: min(v, int(chi * v / tot)) for c, v in bound.items()}
+    dims = {c: v for c, v in dims.items() if v > 0}
+    return dims or {max(bound, key=bound.get): 1}
+
+
+def saturated_random_state(L: int, d: int, N: int, chi: int, seed: int):
+    """A synthetic saturated chain: every inner bond at saturated_sector_dims, positive
+    Schmidt-like weights (unit norm per bond, descending per sector) and complex normal
+    blocks for every allowed (l, m) pair (0 <= l - m <= d - 1) scaled by 1/sqrt(max dim).
+    Not canonical; it gives an update the sector sizes and the cost of a saturated one.
+    Returns (lam, blocks): lam[b] = {c: weights} for b = 1..L-1 (index 0 and L unused),
+    blocks[s] = {(l, m): array}."""
+    rng = np.random.default_rng(seed)
+    bonds = [None] * (L + 1)
+    bonds[0], bonds[L] = {N: 1}, {0: 1}
+    lam = [None] * (L + 1)
+    for b in range(1, L):
+        bonds[b] = dict(sorted(saturated_sector_dims(L, d, N, b, chi).items()))
+        w = random_positive(sum(bonds[b].values()), rng)
+        w /= np.linalg.norm(w)
+        lam[b], off = {}, 0
+        for c, D in bonds[b].items():
+            lam[b][c] = np.sort(w[off:off + D])[::-1].copy()
+            off += D
+    blocks = []
+    for s in range(L):
+        blk = {}
+        for l, Dl in bonds[s].items():
+            for m, Dm in bonds[s + 1].items():
+                if 0 <= l - m <= d - 1:
+                    blk[(l, m)] = random_complex((Dl, Dm), rng) / np.sqrt(max(Dl, Dm))
+        blocks.append(blk)
+    return lam, blocks
