@@ -453,65 +453,84 @@ def run_serving(args, world, rank, local):
     form's, and p50/p99 latency under Poisson arrivals at 0.8 x the served capacity.
     The request mix is the serving configuration scaled down so that the whole run
     takes minutes: L in {16, 32}, chi in {32, 64, 128}, 5..40 Trotter steps (the full
-    mix has L up to 128, chi up to 1024 and up to 500 steps per request).
+    mix has L up to 128, chi up to 1024 and up to 500 steps per request).  The plain
+    form is FP64 with direct launches; the served form runs at --precision (sector GEMMs
+    on the tensor cores for tf32 / bf16x3, SVD and truncation FP64) with CUDA graphs
+    (--graphs), and the largest deviation of its <n_i> from the plain FP64 results is
+    reported beside the speed-up.
     """
     import numpy as np
     import torch
     torch.cuda.set_device(local)
     import paper_2303_11409_gb300 as m
     import workloads as W
+    stream = torch.cuda.Stream()          # capturable (the legacy default stream is not)
+    torch.cuda.set_stream(stream)
+    prec_name = args.precision.split(",")[0]
+    prec = {"fp64": m.MPS_FP64, "tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[prec_name]
+    graphs = bool(args.graphs)
     mix = dict(L_choices=(16, 32), chi_choices=(32, 64, 128), steps_range=(5, 40))
     raw = W.serving_requests(args.serve_requests, seed=rank, rate_hz=1.0, **mix)
     reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=0.0)
             for r in raw]
     budget = 64 << 30
-    # plain form: one request at a time, no merging
+    # plain form: FP64, one request at a time, no merging, direct launches
     t0 = time.perf_counter()
     plain_updates = 0
+    plain_obs = {}
     for q in reqs:
-        srv = m.serve.Server(budget_bytes=budget, max_slots=1)
+        srv = m.serve.Server(budget_bytes=budget, max_slots=1, stream=stream.cuda_stream)
         res = srv.run([q])
         srv.close()
         plain_updates += res[0].updates
+        plain_obs[q.id] = res[0].observables
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
     plain_rate = plain_updates / plain_s                    # updates/s
     # served capacity: every request queued at t = 0, merged launches across requests
-    srv = m.serve.Server(budget_bytes=budget, max_slots=64)
+    srv = m.serve.Server(budget_bytes=budget, max_slots=64, stream=stream.cuda_stream, precision=prec,
+                         graphs=graphs)
     t0 = time.perf_counter()
     res = srv.run(reqs)
     torch.cuda.synchronize()
     cap_s = time.perf_counter() - t0
     srv.close()
     served_cap = sum(r.updates for r in res) / cap_s
+    # accuracy of the served form against the plain FP64 form, per observable <n_i>
+    obs_err = max(float(np.max(np.abs(r.observables - plain_obs[r.id]))) for r in res)
     # latency under load: Poisson arrivals at 0.8 x the served capacity (in requests/s)
     req_rate = 0.8 * len(reqs) / cap_s
     raw = W.serving_requests(args.serve_requests, seed=rank, rate_hz=req_rate, **mix)
     reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=r["arrival"])
             for r in raw]
-    srv = m.serve.Server(budget_bytes=budget, max_slots=64)
+    srv = m.serve.Server(budget_bytes=budget, max_slots=64, stream=stream.cuda_stream, precision=prec,
+                         graphs=graphs)
     launches0 = m.launch_count()
     t0 = time.perf_counter()
     res = srv.run(reqs)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    gstats = srv.executor.graph_stats()
     srv.close()
     summ = m.serve.summarize(res, wall)
     if rank == 0:
         line = {"metric": "serving two-site updates/s (p50/p99 request latency)", "value": served_cap,
                 "unit": "updates/s", "n_gpus": world, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64" if prec_name == "fp64" else f"{prec_name}+f64",
+                "data": "synthetic",
                 "p50_latency_s": summ["p50_latency_s"], "p99_latency_s": summ["p99_latency_s"],
                 "requests": len(res), "updates": summ["updates"], "loaded_wall_s": wall,
                 "loaded_updates_per_s": summ["updates_per_s"],
                 "plain_updates_per_s": plain_rate, "served_over_plain": served_cap / plain_rate,
+                "max_observable_error_vs_plain_fp64": obs_err,
                 "arrival_rate_hz": req_rate, "max_active_under_load": srv.max_active_seen,
-                "gpu_launches": m.launch_count() - launches0,
+                "gpu_launches": m.launch_count() - launches0, "graphs": gstats,
                 "config": {"workload": "serving_mix_scaled", "requests": len(reqs), **{k: list(v) for k, v in mix.items()},
                            "models": "xxz Delta~U[0,2] (Neel) / bh U~U[1,10] J=1 (Mott), 50/50",
                            "value": "served capacity (all requests queued at t=0, merged launches)",
                            "latency": "Poisson arrivals at 0.8 x the served capacity",
-                           "plain": "each request alone, one after another", "budget_bytes": budget,
+                           "plain": "FP64, each request alone, one after another, direct launches",
+                           "served_precision": prec_name, "cuda_graphs": graphs, "budget_bytes": budget,
                            "max_slots": 64}}
         print(json.dumps(line), flush=True)
 

@@ -18,7 +18,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import models
-from ._binding import MPS, Executor, footprint_bytes
+from ._binding import MPS, MPS_FP64, Executor, footprint_bytes
 from .tebd import GateTable, strang_layers
 
 
@@ -99,10 +99,13 @@ class Server:
     max_slots: int = 64
     stream: object = None
     clock: object = time.perf_counter
+    precision: int = MPS_FP64      # sector-GEMM precision of every admitted request's MPS
+    graphs: bool = False           # capture the merged update calls in CUDA graphs
     executor: Executor = field(init=False)
 
     def __post_init__(self):
         self.executor = Executor(self.stream)
+        self.executor.set_graphs(self.graphs)
         self.max_active_seen = 0
         self.max_bytes_seen = 0
 
@@ -123,7 +126,7 @@ class Server:
                     break
                 req = pending.pop(0)
                 d, occ, gates = _setup(req)
-                psi = MPS(d, occ, req.chi, stream=self.executor.stream)
+                psi = MPS(d, occ, req.chi, precision=self.precision, stream=self.executor.stream)
                 layers = [lay for _ in range(req.steps) for lay in strang_layers(req.L)]
                 active.append(Job(req, psi, gates, layers, need, now))
                 used += need
