@@ -105,7 +105,10 @@ MPS_API int mps_info(mps_t h, int* L, int* d, int* N, int* chi_max, int* precisi
  * middle charge c, an FP64 SVD of diag(lambda^[s]) Theta'(c) per c, a global
  * top-chi truncation across all c (ties within 1e-11 sigma_max at the cut go to
  * the lower charge), then B^[s+1] = Y^dag_kept, B^[s] = Theta' Y_kept / |S_kept|
- * and lambda^[s+1] = S_kept / |S_kept|.
+ * and lambda^[s+1] = S_kept / |S_kept|.  Within a sector the SVD does not resolve
+ * singular values below 0.01 * cutoff * |M(c)|_F (at least 100x under the cutoff
+ * threshold cutoff * |sigma|_2, so discarded in any case): their columns are not
+ * rotated and they count as zero.
  * Errors: MPS_EINVAL, MPS_ENOMEM, MPS_ENOCONV (state updated), MPS_ECUDA.
  */
 MPS_API int mps_apply_gate2(mps_t h, int site, const double* gate_blocks, int chi,

@@ -520,6 +520,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       S.rowscale = h->lambda_ptr(s) + Lb.off[E.l0];
       S.m = E.rows;
       S.n = E.cols;
+      S.floor_rel = kDeflateRel * reqs[u].cutoff;
       svd_fill_scratch(S, JL, sec_global, dptr(jac_base));
       S.sigma = reinterpret_cast<double*>(dptr(W[u].sig_off[si]));
       S.Y = reinterpret_cast<double2*>(dptr(W[u].y_off[si]));

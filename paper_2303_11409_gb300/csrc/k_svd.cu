@@ -26,8 +26,10 @@
 //                          hardware cluster barrier.
 // Jacobi pairs follow the round-robin ordering (disjoint pairs per round, one
 // warp per pair).  A pair is rotated when |a_p^dag a_q|^2 > tol^2 |a_p|^2 |a_q|^2,
-// tol = eps * max(n, 32), and both columns are above the noise floor 32 eps
-// |M|_F; singular values at or below the floor are reported as exactly 0.
+// tol = eps * max(n, 32), and both columns are above the floor: the noise level
+// 32 eps |M|_F, or a higher deflation level the caller sets (SvdSector::floor_rel,
+// a fraction of the truncation cutoff); singular values at or below the floor are
+// reported as exactly 0.
 // Convergence is a sweep without a rotation; a sector that does not converge
 // within the sweep limit reports -1.  FP64 costs a warp 64 cycles per
 // instruction here, so per-pair scalar work is kept small (no square root in the
@@ -734,7 +736,9 @@ __device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int ncta
   // ---- one-sided Jacobi on the K columns of R^dag (or R2) --------------------------------
   const double tol = kEps * (double)max(n, 32);
   const double tol2 = tol * tol;
-  const double floor2 = (32.0 * kEps) * (32.0 * kEps) * fro2;
+  // floor: the rounding-noise level 32 eps |M|_F, or the caller's deflation level when higher
+  const double frel = fmax(32.0 * kEps, S.floor_rel);
+  const double floor2 = frel * frel * fro2;
   bool converged = false;
   const int sweep = jacobi(J, jlen, jld, K, w, rank, nctas, sync, tol2, floor2, max_sweeps, converged);
 

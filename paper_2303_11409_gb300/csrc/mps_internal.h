@@ -96,6 +96,8 @@ struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   int mode;                   // kSvdSmem, kSvdCluster or kSvdClusterBlock
   int groups;                 // block Jacobi: block pairs per CTA and round
   int staged;                 // block Jacobi: block pairs staged in shared memory at once
+  double floor_rel;           // columns below floor_rel |M|_F are not rotated, their sigma is 0
+                              // (0: the rounding-noise level 32 eps)
   int wide;                   // cluster mode, m < n: Jacobi on R2 of R^dag = Q2 R2 (K x K)
   double2* work2;             // wide: R2 / the Jacobi matrix, K x (K | 1) column-major
   double2* ytmp;              // wide: n x K, Q2 applied to the normalised columns
@@ -272,6 +274,10 @@ constexpr int kSvdSmemMax = 200 * 1024;
 int64_t svd_smem_need(int m, int n);
 constexpr int kJacobiMaxSweeps = 40;
 constexpr double kTieRel = 1e-11;
+// Deflation of an update's SVDs: columns whose norm falls below kDeflateRel * cutoff * |M(c)|_F
+// are left unrotated and reported as zero.  |M(c)|_F <= |sigma|_2 of the whole update, so they
+// lie at least 100x below the cutoff threshold cutoff * |sigma|_2 and are discarded either way.
+constexpr double kDeflateRel = 0.01;
 
 // GEMM tiling shared by the Theta build and the reassembly GEMM.
 constexpr int kTile = 64;
