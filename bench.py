@@ -358,6 +358,7 @@ def run_ours(args, world, rank, local):
     barrier(world)
     launches = m.launch_count() - launches0
     graph_stats = psi.graph_stats()
+    deflation = psi.deflation_stats()
     psi.set_profiling(False)
     ks = psi.kernel_stats()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -439,6 +440,7 @@ def run_ours(args, world, rank, local):
                                   "precision": args.precision, "cuda_graphs": bool(args.graphs),
                                   "autotune": bool(args.autotune)}, case=args.case),
                 "graphs": graph_stats, "autotune": {**m.autotune_stats(), "table": m.autotune_table()},
+                "svd_deflation": deflation,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary(), "step_ms": [round(x, 3) for x in step_ms]}
         print(json.dumps(line), flush=True)

@@ -107,8 +107,13 @@ MPS_API int mps_info(mps_t h, int* L, int* d, int* N, int* chi_max, int* precisi
  * the lower charge), then B^[s+1] = Y^dag_kept, B^[s] = Theta' Y_kept / |S_kept|
  * and lambda^[s+1] = S_kept / |S_kept|.  Within a sector the SVD does not resolve
  * singular values below 0.01 * cutoff * |M(c)|_F (at least 100x under the cutoff
- * threshold cutoff * |sigma|_2, so discarded in any case): their columns are not
- * rotated and they count as zero.
+ * threshold cutoff * |sigma|_2, so discarded in any case), nor, when chi set the cut
+ * of the previous update of the same bond, below 3e-4 times that relative cut
+ * (smallest kept value / |sigma|_2): their columns are not rotated and they count as
+ * zero.  When the new cut falls
+ * under half that previous one, the call redoes its SVDs and selection without the
+ * second level, so an unresolved value always lies >= 1600x under the kept ones.
+ * mps_deflation_stats counts updates that used the second level and those redone.
  * Errors: MPS_EINVAL, MPS_ENOMEM, MPS_ENOCONV (state updated), MPS_ECUDA.
  */
 MPS_API int mps_apply_gate2(mps_t h, int site, const double* gate_blocks, int chi,
@@ -224,6 +229,13 @@ MPS_API int mps_set_site(mps_t h, int site, int n_blocks, const int32_t* lcharge
  */
 MPS_API int mps_last_update_stats(mps_t h, int* n_sectors, int* n_triples, int* max_sweeps,
                           int* tie_band, double* norm_all, double* norm_kept);
+
+/*
+ * mps_deflation_stats - updates on h (cumulative) whose SVDs used the previous cut of
+ * their bond as a deflation level, and how many of those were redone without it
+ * (see mps_apply_gate2).  Either pointer may be NULL.
+ */
+MPS_API int mps_deflation_stats(mps_t h, int64_t* deflated_updates, int64_t* redos);
 
 /*
  * Kernel kinds reported by mps_kernel_stats.

@@ -78,6 +78,7 @@ _SIGS = {
     "mps_set_bond": (ctypes.c_int, [_h, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _dblp]),
     "mps_set_site": (ctypes.c_int, [_h, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _dblp]),
     "mps_last_update_stats": (ctypes.c_int, [_h, _intp, _intp, _intp, _intp, _dblp, _dblp]),
+    "mps_deflation_stats": (ctypes.c_int, [_h, _i64p, _i64p]),
     "mps_plan_sectors": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.c_int, _i32p, _i32p,
                                         ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_int, _intp, _i32p,
                                         ctypes.c_int, _intp]),
@@ -337,6 +338,12 @@ class MPS:
 
     def reset_kernel_stats(self):
         self._check(lib.mps_reset_kernel_stats(self._h), "mps_reset_kernel_stats")
+
+    def deflation_stats(self) -> dict:
+        """Updates that deflated their SVDs from the bond's previous cut, and those redone."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._check(lib.mps_deflation_stats(self._h, ctypes.byref(a), ctypes.byref(b)), "mps_deflation_stats")
+        return dict(deflated_updates=a.value, redos=b.value)
 
     def set_graphs(self, on: bool = True):
         """Capture each update call's launch phases into CUDA graphs (mps_set_graphs)."""

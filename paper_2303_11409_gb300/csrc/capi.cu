@@ -283,6 +283,7 @@ struct UpdWork {
   std::vector<int64_t> theta_off, y_off, sig_off;   // byte offsets into the workspace per sector
   int sel_first = 0;                                // index of the first sector in the select arrays
   int64_t gate_off = 0;                             // byte offset of this update's staged gate
+  double cut_est = 0.0;                             // the bond's previous relative cut (0: none)
 };
 
 int run_batch(std::vector<Req>& reqs, mps_s* owner) {
@@ -302,6 +303,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     mps_s* h = reqs[u].h;
     const int s = reqs[u].site;
     plan_update(h->bonds[s], h->bonds[s + 1], h->bonds[s + 2], h->d, W[u].plan);
+    if ((int)h->cut_est.size() == h->L + 1) W[u].cut_est = h->cut_est[s + 1];
     max_tri = std::max<int>(max_tri, (int)W[u].plan.triple_l.size());
     n_sec_total += (int)W[u].plan.sectors.size();
     if (W[u].plan.sectors.empty()) return fail(owner, MPS_EINVAL, "update has no charge sectors");
@@ -521,6 +523,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       S.m = E.rows;
       S.n = E.cols;
       S.floor_rel = kDeflateRel * reqs[u].cutoff;
+      S.floor_abs = kChiDeflate * W[u].cut_est;
       svd_fill_scratch(S, JL, sec_global, dptr(jac_base));
       S.sigma = reinterpret_cast<double*>(dptr(W[u].sig_off[si]));
       S.Y = reinterpret_cast<double2*>(dptr(W[u].y_off[si]));
@@ -624,6 +627,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       e = cudaMemcpyAsync(tc_err_host, owner->tc_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
     return e;
   };
+  int c_used = 0;                    // the tile shape whose outputs the batch keeps
   if (n_cand == 1) {
     CUDA_OR_FAIL(owner, run_phase(owner, 0, [&]() -> cudaError_t {
       cudaError_t e = upload_and_theta();
@@ -660,6 +664,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     }
     // the outputs must come from the chosen shape: rerun it unless it ran last
     if (best != kTuneDefault) CUDA_OR_FAIL(owner, svd_launch(best));
+    c_used = best;
     KStat& k = owner->kstat[MPS_K_SVD];
     k.launches++;
     k.flops += svd_flops;
@@ -677,6 +682,31 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   const int* kept = (const int*)owner->pin_out.p;
   const int* sstat = (const int*)((char*)owner->pin_out.p + (status_off - kept_off));
   const SelectResult* res = (const SelectResult*)((char*)owner->pin_out.p + (res_off - kept_off));
+
+  // ---- deflation check: an update whose new cut fell below kChiVerify x the estimate its
+  // SVDs were deflated with has the batch's SVDs and selection redone without that level ----
+  {
+    bool redo = false;
+    for (int u = 0; u < nreq; ++u) {
+      if (W[u].cut_est <= 0.0) continue;
+      reqs[u].h->stats.deflated_updates++;
+      if (res[u].status == 0 && res[u].cut < kChiVerify * W[u].cut_est) redo = true;
+    }
+    if (redo) {
+      std::vector<SvdSector>& v = svd_sorted[c_used];
+      for (SvdSector& S : v) S.floor_abs = 0.0;
+      char* hsrc = (char*)owner->pin_in.p + o_svd[c_used];
+      std::memcpy(hsrc, v.data(), sizeof(SvdSector) * v.size());
+      CUDA_OR_FAIL(owner, cudaMemcpyAsync(dptr(desc_off + o_svd[c_used]), hsrc, sizeof(SvdSector) * v.size(),
+                                          cudaMemcpyHostToDevice, st));
+      CUDA_OR_FAIL(owner, timed(owner, MPS_K_SVD, true, svd_flops, svd_bytes, [&] { return svd_launch(c_used); }));
+      CUDA_OR_FAIL(owner, select_and_readback());
+      CUDA_OR_FAIL(owner, cudaStreamSynchronize(st));
+      resolve_pending(owner);
+      for (int u = 0; u < nreq; ++u)
+        if (W[u].cut_est > 0.0) reqs[u].h->stats.deflation_redos++;
+    }
+  }
 
   // ---- host: new bond tables and block layouts; phase-2 descriptors -------------------
   std::vector<LambdaTask> lam;
@@ -872,6 +902,11 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     h->bonds[s + 1] = newmid[u];
     h->sites[s] = newL[u];
     h->sites[s + 1] = newR[u];
+    // the next update of this bond deflates from this cut when chi set it (more candidates
+    // than kept); a cut set by the cutoff lies under the cutoff deflation level anyway
+    if ((int)h->cut_est.size() == h->L + 1)
+      h->cut_est[s + 1] = (res[u].n_candidates > reqs[u].chi && res[u].norm_all > 0.0)
+                              ? res[u].cut / res[u].norm_all : 0.0;
     h->cur[s] ^= 1;
     h->cur[s + 1] ^= 1;
   }
@@ -934,6 +969,7 @@ int mps_create(mps_t* out, int L, int d, const int32_t* site_charges, int precis
   }
   h->sites.resize(L);
   h->cur.assign(L, 0);
+  h->cut_est.assign(L + 1, 0.0);
   h->dirty.assign(L, 0);
   h->site_cap.resize(L);
   h->site_base.resize(L);
@@ -1293,6 +1329,7 @@ int mps_set_bond(mps_t h, int bond, int n_sectors, const int32_t* charges, const
   h->bonds[bond] = t;
   h->dirty[bond - 1] = 1;
   h->dirty[bond] = 1;
+  std::fill(h->cut_est.begin(), h->cut_est.end(), 0.0);   // a loaded state has no deflation history
   return MPS_OK;
 }
 
@@ -1315,6 +1352,7 @@ int mps_set_site(mps_t h, int site, int n_blocks, const int32_t* lcharges, const
                                cudaMemcpyHostToDevice));
   h->sites[site] = t;
   h->dirty[site] = 0;
+  std::fill(h->cut_est.begin(), h->cut_est.end(), 0.0);
   return MPS_OK;
 }
 
@@ -1436,6 +1474,13 @@ int mps_last_batch_sweeps(mps_t h, int* n_sectors, int64_t* sweeps_sum, int* swe
   if (n_sectors) *n_sectors = h->stats.batch_sectors;
   if (sweeps_sum) *sweeps_sum = h->stats.batch_sweeps_sum;
   if (sweeps_max) *sweeps_max = h->stats.batch_sweeps_max;
+  return MPS_OK;
+}
+
+int mps_deflation_stats(mps_t h, int64_t* deflated_updates, int64_t* redos) {
+  if (!h) return MPS_EINVAL;
+  if (deflated_updates) *deflated_updates = h->stats.deflated_updates;
+  if (redos) *redos = h->stats.deflation_redos;
   return MPS_OK;
 }
 

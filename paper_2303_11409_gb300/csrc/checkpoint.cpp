@@ -6,11 +6,14 @@
 //
 // File layout (little-endian, all integers int32 unless noted):
 //   "U1MPSCK1"                                   8-byte magic
-//   version (1), L, d, N, chi_max, precision
+//   version (2), L, d, N, chi_max, precision
 //   per bond b = 0..L:  n, charge[n], dim[n], lambda[sum dim] (float64)
 //   per site s = 0..L-1: n_blocks (int32), nnz (int64), block (l, m) pairs
 //                        [2 n_blocks], data[2 nnz] (float64, interleaved complex)
+//   cut[L + 1] (float64): per bond, the relative cut of its last update, which
+//                        sets the next update's SVD deflation level (version 2 only)
 //   "U1MPSEND"                                   8-byte trailer
+// Version 1 files (without the cut record) load with no deflation history.
 // The block order is the library's (l ascending, then m ascending), which the
 // loader checks against the order the bond tables imply.
 #include <cstdint>
@@ -54,7 +57,7 @@ int mps_save(mps_t h, const char* path) {
   File out;
   out.f = std::fopen(path, "wb");
   if (!out.f) return save_fail(h, std::string("cannot open ") + path + " for writing");
-  const int32_t hdr[6] = {1, h->L, h->d, h->N, h->chi_max, h->precision};
+  const int32_t hdr[6] = {2, h->L, h->d, h->N, h->chi_max, h->precision};
   bool ok = put(out.f, kMagic, 8) && put(out.f, hdr, 6);
   std::vector<int32_t> ch, dm;
   std::vector<double> lam;
@@ -88,7 +91,9 @@ int mps_save(mps_t h, const char* path) {
     ok = put(out.f, &nb, 1) && put(out.f, &nnz, 1) && put(out.f, pairs.data(), pairs.size()) &&
          put(out.f, data.data(), data.size());
   }
-  ok = ok && put(out.f, kTrailer, 8);
+  std::vector<double> cut(h->L + 1, 0.0);
+  if ((int)h->cut_est.size() == h->L + 1) cut = h->cut_est;
+  ok = ok && put(out.f, cut.data(), cut.size()) && put(out.f, kTrailer, 8);
   if (!ok) return save_fail(h, std::string("write to ") + path + " failed");
   if (std::fclose(out.f) != 0) {
     out.f = nullptr;
@@ -106,8 +111,10 @@ int mps_load(mps_t* out, const char* path, void* cuda_stream) {
   if (!in.f) return MPS_EINVAL;
   char magic[8];
   int32_t hdr[6];
-  if (!get(in.f, magic, 8) || std::memcmp(magic, kMagic, 8) != 0 || !get(in.f, hdr, 6) || hdr[0] != 1)
+  if (!get(in.f, magic, 8) || std::memcmp(magic, kMagic, 8) != 0 || !get(in.f, hdr, 6) ||
+      (hdr[0] != 1 && hdr[0] != 2))
     return MPS_EINVAL;
+  const int version = hdr[0];
   const int L = hdr[1], d = hdr[2], N = hdr[3], chi_max = hdr[4], precision = hdr[5];
   if (L < 2 || d < 2 || d > MPS_MAX_D || N < 0 || N > L * (d - 1) || chi_max < 1) return MPS_EINVAL;
   // a product state with the same total charge; every bond and site is then overwritten
@@ -158,8 +165,15 @@ int mps_load(mps_t* out, const char* path, void* cuda_stream) {
     rc = mps_set_site(h, s, nb, lc.data(), mc.data(), data.data());
     if (rc != MPS_OK) return rc;
   }
+  std::vector<double> cut(L + 1, 0.0);
+  if (version >= 2) {
+    if (!get(in.f, cut.data(), cut.size())) return MPS_EINVAL;
+    for (double c : cut)
+      if (!(c >= 0.0 && c <= 1.0)) return MPS_EINVAL;
+  }
   char trailer[8];
   if (!get(in.f, trailer, 8) || std::memcmp(trailer, kTrailer, 8) != 0) return MPS_EINVAL;
+  h->cut_est = cut;   // after every mps_set_bond / mps_set_site, which clear it
   *out = guard.release();
   return MPS_OK;
 }

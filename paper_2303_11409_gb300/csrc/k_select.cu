@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const SelectSector*
   R.pad = 0;
   if (!(total2 > 0.0)) {
     if (tid == 0) {
-      R.norm_kept = 0.0; R.trunc_err = 1.0; R.n_candidates = 0; R.status = -1;
+      R.norm_kept = 0.0; R.trunc_err = 1.0; R.n_candidates = 0; R.status = -1; R.cut = 0.0;
       res[blockIdx.x] = R;
     }
     for (int s = tid; s < ns; s += kSelThreads) kept[T.s0 + s] = 0;
@@ -147,7 +147,21 @@ __global__ void __launch_bounds__(kSelThreads) select_kernel(const SelectSector*
   }
   const double kept2 = block_sum(kp, dred);
   const double disc2 = block_sum(dp, dred);
+  // the cut: smallest kept value (fixed-order reduction: min is order independent anyway)
+  double cmin = 1.0e308;
+  for (int s = tid; s < ns; s += kSelThreads) {
+    const int k = kept[T.s0 + s];
+    if (k > 0) cmin = fmin(cmin, secs[T.s0 + s].sigma[k - 1]);
+  }
+  dred[tid] = cmin;
+  __syncthreads();
+  for (int s = kSelThreads / 2; s; s >>= 1) {
+    if (tid < s) dred[tid] = fmin(dred[tid], dred[tid + s]);
+    __syncthreads();
+  }
+  const double cut = dred[0];
   if (tid == 0) {
+    R.cut = cut >= 1.0e308 ? 0.0 : cut;
     R.norm_kept = sqrt(kept2);
     R.trunc_err = disc2 / total2;
     R.band = band_total;

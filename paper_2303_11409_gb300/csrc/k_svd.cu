@@ -738,7 +738,7 @@ __device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int ncta
   const double tol2 = tol * tol;
   // floor: the rounding-noise level 32 eps |M|_F, or the caller's deflation level when higher
   const double frel = fmax(32.0 * kEps, S.floor_rel);
-  const double floor2 = frel * frel * fro2;
+  const double floor2 = fmax(frel * frel * fro2, S.floor_abs * S.floor_abs);
   bool converged = false;
   const int sweep = jacobi(J, jlen, jld, K, w, rank, nctas, sync, tol2, floor2, max_sweeps, converged);
 

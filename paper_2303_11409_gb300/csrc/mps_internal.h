@@ -98,6 +98,7 @@ struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   int staged;                 // block Jacobi: block pairs staged in shared memory at once
   double floor_rel;           // columns below floor_rel |M|_F are not rotated, their sigma is 0
                               // (0: the rounding-noise level 32 eps)
+  double floor_abs;           // the same for an absolute level (0: none)
   int wide;                   // cluster mode, m < n: Jacobi on R2 of R^dag = Q2 R2 (K x K)
   double2* work2;             // wide: R2 / the Jacobi matrix, K x (K | 1) column-major
   double2* ytmp;              // wide: n x K, Q2 applied to the normalised columns
@@ -126,6 +127,7 @@ struct SelectTask {           // one update: its sectors are [s0, s1) of the sec
 };
 struct SelectResult {         // per update
   double norm_all, norm_kept, trunc_err;
+  double cut;                 // smallest kept singular value (0 if none)
   int band, n_candidates, status, pad;
 };
 
@@ -163,6 +165,7 @@ struct Stats {
   double norm_all = 0, norm_kept = 0;
   int batch_sectors = 0, batch_sweeps_max = 0;   // over every update of the last call
   int64_t batch_sweeps_sum = 0;
+  int64_t deflated_updates = 0, deflation_redos = 0;   // cut-estimate deflation, cumulative
 };
 
 struct KStat { int64_t launches = 0; double ms = 0, flops = 0, bytes = 0; };
@@ -198,6 +201,7 @@ struct mps_s {
   std::vector<mps::PendingTiming> pending;   // event pairs not yet read back
   std::vector<cudaEvent_t> event_pool;
   int* tc_flag = nullptr;                 // set by a tensor-core GEMM whose bounded wait expired
+  std::vector<double> cut_est;            // per bond: smallest kept sigma of its last update (0: none)
   // CUDA graphs: the two launch phases of an update call are captured and replayed
   // through one executable graph each, updated in place while the topology holds
   bool graphs = false;
@@ -278,6 +282,13 @@ constexpr double kTieRel = 1e-11;
 // are left unrotated and reported as zero.  |M(c)|_F <= |sigma|_2 of the whole update, so they
 // lie at least 100x below the cutoff threshold cutoff * |sigma|_2 and are discarded either way.
 constexpr double kDeflateRel = 0.01;
+// Deflation from the bond's previous cut: when chi set the last cut of a bond, columns below
+// kChiDeflate * (the smallest singular value that update kept) are not resolved either.  The update is redone
+// without it when its new cut falls below kChiVerify * that estimate, which keeps the level at
+// or under 6e-4 of the actual cut (deflated values stay far below the cut; the kept values and
+// vectors move by < 1e-13 on graded sectors).
+constexpr double kChiDeflate = 3e-4;
+constexpr double kChiVerify = 0.5;
 
 // GEMM tiling shared by the Theta build and the reassembly GEMM.
 constexpr int kTile = 64;

@@ -49,7 +49,8 @@ def test_graph_mode_is_bit_identical(gpu_lib):
     assert gs["updates"] > 0                         # parameters changed, topology held
     assert gs["instantiations"] + gs["updates"] == gs["launches"]
     ks = b.kernel_stats()
-    assert ks["svd"]["launches"] == 3 * steps and ks["svd"]["ms"] > 0   # events inside the graph
+    redos = b.deflation_stats()["redos"]            # a redone SVD phase is one more launch
+    assert ks["svd"]["launches"] == 3 * steps + redos and ks["svd"]["ms"] > 0   # events inside the graph
     assert a.graph_stats()["launches"] == 0
     a.close()
     b.close()

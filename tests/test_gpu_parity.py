@@ -278,3 +278,24 @@ def test_load_rejects_missing_and_damaged_files(gpu_lib, tmp_path):
             break
         dims = struct.unpack_from(f"<{n}i", raw, off + 4 + 4 * n)
         off += 4 + 8 * n + 8 * sum(dims)
+
+
+def test_deflation_from_the_previous_cut_and_its_redo(gpu_lib):
+    """The second update of a bond deflates its SVDs from the first one's cut.  With a
+    much larger chi the new cut falls far below that estimate, so the update must be
+    redone without the deflation level; both updates match the oracle."""
+    L, d, N = 8, 3, 8
+    st = random_state(L, d, N, 60, seed=5)
+    g = _gpu(gpu_lib, d, [1] * L, 80)
+    load_state(g, st)
+    G = gates.bh_gate(L, 3, d, 1.0, 2.0, 0.4)
+    s = 3
+    seen = []
+    for chi in (6, 6, 40):        # no history, then a similar cut, then a far lower cut
+        g.apply_gate2(s, G, chi, 1e-10)
+        st.apply_gate2(s, G, chi, 1e-10)
+        compare_update(g, st, s)
+        seen.append(g.deflation_stats())
+    assert seen[0] == dict(deflated_updates=0, redos=0), seen
+    assert seen[2]["deflated_updates"] == 2, seen
+    assert seen[2]["redos"] - seen[1]["redos"] == 1, seen      # the 40th value is far below the 6th
