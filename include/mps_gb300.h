@@ -287,11 +287,13 @@ MPS_API int mps_graph_stats(mps_t h, int64_t* launches, int64_t* updates, int64_
 
 /*
  * mps_set_autotune - when on, update calls on h choose the tile shape of the cluster
- * SVD kernel (target column-block width 4, 6, 8 or 12 and smallest cluster 2 or 4 CTAs)
- * from a process-wide table keyed on the histogram of the batch's large sectors
+ * SVD (block-Jacobi column-block width 4, 6, 8 or 12 and smallest cluster 2 or 4 CTAs,
+ * or clusters of 16 CTAs for sectors from min(m, n) = 512 or 256 up, where the device
+ * places them; ten candidates) from a process-wide table keyed on the histogram of the
+ * batch's large sectors
  * (octaves of min(m, n) holding at least 5% of the nominal SVD work, counts rounded to
  * powers of two).  The first batch with a new key whose nominal SVD work is at least
- * the tuning threshold (2e10 flops unless set) runs all eight shapes on its own inputs,
+ * the tuning threshold (2e10 flops unless set) runs all ten shapes on its own inputs,
  * timed with CUDA events, and stores the fastest (the default shape, width 6 from
  * 2 CTAs, unless another beats it by more than 3%); its outputs come from the stored
  * shape.  Shapes differ only in rounding (the Jacobi pair order changes), so a tuned run
@@ -305,12 +307,18 @@ MPS_API int mps_graph_stats(mps_t h, int64_t* launches, int64_t* updates, int64_
  *   default shape and are not tuned (stored keys are still used).
  * mps_autotune_min_flops - the nominal SVD work (flops, >= 0) below which a batch is
  *   not tuned and uses the default shape.
+ * mps_autotune_force - candidate 0..9 makes every update call of the process use that
+ *   shape, whether or not autotuning is on (for tests and measurements); -1 ends it.
+ *   Candidates 0..7: width {4, 6, 8, 12}[k & 3], clusters from 2 << (k >> 2); 8 and 9:
+ *   width 6 from 2 CTAs, 16-CTA clusters from min(m, n) = 512 and 256.  MPS_EINVAL for
+ *   any other value.
  */
 MPS_API int mps_set_autotune(mps_t h, int on);
 MPS_API int mps_autotune_stats(int64_t* keys, int64_t* tuning_runs, int64_t* hits);
 MPS_API int mps_autotune_table(char* buf, int cap, int* len);
 MPS_API int mps_autotune_clear(void);
 MPS_API int mps_autotune_freeze(int frozen);
+MPS_API int mps_autotune_force(int candidate);
 MPS_API int mps_autotune_min_flops(double flops);
 
 /*

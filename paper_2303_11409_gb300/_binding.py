@@ -103,6 +103,7 @@ _SIGS = {
     "mps_autotune_clear": (ctypes.c_int, []),
     "mps_autotune_min_flops": (ctypes.c_int, [ctypes.c_double]),
     "mps_autotune_freeze": (ctypes.c_int, [ctypes.c_int]),
+    "mps_autotune_force": (ctypes.c_int, [ctypes.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -445,6 +446,13 @@ def autotune_table() -> str:
 
 def autotune_clear() -> None:
     lib.mps_autotune_clear()
+
+
+def autotune_force(candidate: int) -> None:
+    """Every update call uses SVD tile-shape candidate 0..9 (-1: back to normal)."""
+    rc = lib.mps_autotune_force(int(candidate))
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_autotune_force")
 
 
 def autotune_freeze(frozen: bool = True) -> None:

@@ -211,6 +211,7 @@ std::map<std::vector<int>, TuneEntry> g_tune;
 int64_t g_tune_runs = 0;
 double g_tune_min_flops = 2e10;   // below this an SVD phase is too short to be worth tuning
 bool g_tune_frozen = false;       // frozen: unseen keys use the default shape without tuning
+int g_tune_force = -1;            // >= 0: every batch uses this candidate (tests, experiments)
 constexpr int kTuneDefault = 1;   // svd_tune_candidate(1) is the default shape (bw 6, clusters from 2)
 
 std::vector<int> tune_key(const std::vector<SvdSector>& secs) {
@@ -544,7 +545,14 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   }
   std::vector<int> tkey;
   int n_cand = 1, chosen = -1;       // n_cand > 1: this batch runs every candidate
-  if (owner->autotune) {
+  int forced;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    forced = g_tune_force;
+  }
+  if (forced >= 0) {
+    chosen = forced;
+  } else if (owner->autotune) {
     tkey = tune_key(svd);
     if (!tkey.empty()) {
       std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1433,8 +1441,12 @@ int mps_autotune_table(char* buf, int cap, int* len) {
       const TuneEntry& e = kv.second;
       if (e.best < 0) continue;
       const SvdTune b = svd_tune_candidate(e.best);
-      std::snprintf(line, sizeof(line), "%s -> bw=%d cl_min=%d hits=%lld ms=", key.c_str(), b.bw, b.cl_min,
-                    (long long)e.hits);
+      if (b.c16_min_k < (1 << 30))
+        std::snprintf(line, sizeof(line), "%s -> 16-CTA clusters from K=%d hits=%lld ms=", key.c_str(), b.c16_min_k,
+                      (long long)e.hits);
+      else
+        std::snprintf(line, sizeof(line), "%s -> bw=%d cl_min=%d hits=%lld ms=", key.c_str(), b.bw, b.cl_min,
+                      (long long)e.hits);
       t += line;
       for (int c = 0; c < kTuneCands; ++c) {
         std::snprintf(line, sizeof(line), "%s%.2f", c ? "/" : "", e.ms[c]);
@@ -1453,6 +1465,13 @@ int mps_autotune_clear(void) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.clear();
   g_tune_runs = 0;
+  return MPS_OK;
+}
+
+int mps_autotune_force(int candidate) {
+  if (candidate < -1 || candidate >= kTuneCands) return MPS_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_force = candidate;
   return MPS_OK;
 }
 

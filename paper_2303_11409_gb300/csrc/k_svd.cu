@@ -1031,6 +1031,16 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
         pick_cl = cl; pick_g = g; pick_gs = gs;
       }
     }
+    if (std::min(S.m, S.n) >= tune.c16_min_k && g_big_cluster >= 16) {   // a 16-CTA cluster
+      const int cl = 16;
+      int g = std::max(1, (std::min(S.m, S.n) + bw * cl) / (2 * bw * cl));
+      while (g < 64 && block_smem_need(S.m, cn, cl, g, 1) > kBlockSmemMax) ++g;
+      int gs = 1;
+      while (gs < std::min(g, kMaxStaged) && block_smem_need(S.m, cn, cl, g, gs + 1) <= kBlockSmemMax) ++gs;
+      if (block_smem_need(S.m, cn, cl, g, gs) <= kBlockSmemMax) {
+        pick_cl = cl; pick_g = g; pick_gs = gs;
+      }
+    }
     if (pick_cl) {
       key[k] = {kSvdClusterBlock, pick_cl};
       smem[k] = block_smem_need(S.m, cn, pick_cl, pick_g, pick_gs);

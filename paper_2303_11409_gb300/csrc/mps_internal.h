@@ -222,13 +222,19 @@ namespace mps {
 cudaError_t launch_theta(const ThetaTask* d_tasks, const TileRef* d_tiles, int n_tiles, cudaStream_t st);
 // Sectors grouped by kernel and cluster size (a group is a contiguous run of the array).
 struct SvdGroup { int kind, cl, smem, first, count; };
-// Tile shape of the block-Jacobi cluster kernel: target column-block width and the
-// smallest cluster size tried.  The autotuner picks one per sector-size histogram.
-struct SvdTune { int bw = 6; int cl_min = 2; };
-constexpr int kTuneCands = 8;
-inline SvdTune svd_tune_candidate(int k) {   // bw in {4, 6, 8, 12} x cl_min in {2, 4}
+// Tile shape of the cluster SVD: target column-block width of the block-Jacobi kernel, the
+// smallest cluster size tried, and the sector size (min(m, n)) from which a sector gets a
+// cluster of 16 CTAs (the largest sectors of a layer set its critical path).  The autotuner
+// picks one per sector-size histogram.
+struct SvdTune { int bw = 6; int cl_min = 2; int c16_min_k = 1 << 30; };
+constexpr int kTuneCands = 10;
+inline SvdTune svd_tune_candidate(int k) {   // bw in {4, 6, 8, 12} x cl_min in {2, 4}; 16 CTAs from 512 or 256
   static const int bws[4] = {4, 6, 8, 12};
   SvdTune t;
+  if (k >= 8) {
+    t.c16_min_k = k == 8 ? 512 : 256;
+    return t;
+  }
   t.bw = bws[k & 3];
   t.cl_min = (k & 4) ? 4 : 2;
   return t;
