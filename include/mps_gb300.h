@@ -272,6 +272,23 @@ MPS_API int mps_reset_kernel_stats(mps_t h);
 MPS_API int64_t mps_launch_count(void);
 
 /*
+ * mps_set_sweep_limit - the Jacobi sweep limit (1..40, default 40) of the update calls
+ * whose owner or executor is h.  A sector that has not converged within it returns
+ * MPS_ENOCONV and the state is updated with the last iterate (its singular values are
+ * still exact column norms, but the vectors are not fully orthogonal).  A low limit is
+ * how the non-convergence path is exercised in tests.  MPS_EINVAL outside 1..40.
+ *
+ * mps_tc_inject_stall - when on, the tensor-core GEMM kernels launched afterwards (in
+ * any handle, and mps_zgemm_tc) issue no MMA, so their bounded mbarrier waits run out
+ * after about 50 ms instead of 2 s: each such launch reports MPS_ETIMEOUT (an update
+ * call returns it with the state unchanged).  For tests of the timeout path without
+ * faulting or hanging the GPU; nothing is in flight when the kernel frees its tensor
+ * memory.  The paper has no counterpart.
+ */
+MPS_API int mps_set_sweep_limit(mps_t h, int max_sweeps);
+MPS_API int mps_tc_inject_stall(int on);
+
+/*
  * mps_set_graphs - when on, each update call on h (mps_apply_gate2/_layer, and the
  * merged calls whose owner or executor is h) captures its two launch phases (upload,
  * Theta' build, SVD, top-chi selection and read-back; upload and reassembly) into CUDA

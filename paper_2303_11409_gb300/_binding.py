@@ -96,6 +96,8 @@ _SIGS = {
     "mps_svd_sectors": (ctypes.c_int, [ctypes.c_int, _intp, _intp, _vp, _i64p, _vp, _i64p, _vp, _i64p, _vp,
                                        _i64p, _vp, _vp, ctypes.c_int64, _vp]),
     "mps_set_graphs": (ctypes.c_int, [_h, ctypes.c_int]),
+    "mps_set_sweep_limit": (ctypes.c_int, [_h, ctypes.c_int]),
+    "mps_tc_inject_stall": (ctypes.c_int, [ctypes.c_int]),
     "mps_graph_stats": (ctypes.c_int, [_h, _i64p, _i64p, _i64p]),
     "mps_set_autotune": (ctypes.c_int, [_h, ctypes.c_int]),
     "mps_autotune_stats": (ctypes.c_int, [_i64p, _i64p, _i64p]),
@@ -340,6 +342,10 @@ class MPS:
     def reset_kernel_stats(self):
         self._check(lib.mps_reset_kernel_stats(self._h), "mps_reset_kernel_stats")
 
+    def set_sweep_limit(self, max_sweeps: int):
+        """Jacobi sweep limit (1..40) of this handle's update calls (mps_set_sweep_limit)."""
+        self._check(lib.mps_set_sweep_limit(self._h, int(max_sweeps)), "mps_set_sweep_limit")
+
     def deflation_stats(self) -> dict:
         """Updates that deflated their SVDs from the bond's previous cut, and those redone."""
         a, b = ctypes.c_int64(), ctypes.c_int64()
@@ -446,6 +452,11 @@ def autotune_table() -> str:
 
 def autotune_clear() -> None:
     lib.mps_autotune_clear()
+
+
+def tc_inject_stall(on: bool) -> None:
+    """Tensor-core GEMMs launched afterwards issue no MMA and report a bounded-wait expiry."""
+    lib.mps_tc_inject_stall(int(bool(on)))
 
 
 def autotune_force(candidate: int) -> None:

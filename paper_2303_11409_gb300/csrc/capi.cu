@@ -20,6 +20,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mps_internal.h"
 
 using namespace mps;
@@ -54,6 +56,13 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace mps
 
 namespace {
+
+// NVTX range over a scope (no-op unless a profiler is attached): the phases of an update call
+// (plan, launch phase 1, host layout, launch phase 2) show up by name in a timeline.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 int fail(mps_s* h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -147,6 +156,7 @@ cudaError_t timed(mps_s* h, int kind, bool nonempty, double flops, double bytes,
 // topology changed (for example a different number of SVD kernel groups).
 template <class F>
 cudaError_t run_phase(mps_s* o, int slot, F&& body) {
+  Range range(slot == 0 ? "mps.phase1 theta-svd-select" : "mps.phase2 reassembly");
   cudaStream_t st = o->stream;
   if (!o->graphs || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return body();
   if (o->profiling) {
@@ -293,6 +303,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   const int nreq = (int)reqs.size();
   std::vector<UpdWork> W(nreq);
 
+  Range batch_range("mps.update_call");
   // ---- K0: plan every update and size the workspace --------------------------------
   int64_t ws = 0;
   int n_sec_total = 0, n_tiles = 0, n_tasks = 0, max_tri = 0;
@@ -621,7 +632,8 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   };
   auto svd_launch = [&](int c) -> cudaError_t {   // one or more kernels
     const SvdSector* d_svd = reinterpret_cast<SvdSector*>(dptr(desc_off + o_svd[c]));
-    return launch_svd_groups(d_svd, svd_groups[c], st, owner->side, kSvdSideStreams, owner->fork, owner->join);
+    return launch_svd_groups(d_svd, svd_groups[c], st, owner->side, kSvdSideStreams, owner->fork, owner->join,
+                             owner->sweep_limit);
   };
   auto select_and_readback = [&]() -> cudaError_t {
     cudaError_t e = timed(owner, MPS_K_SELECT, nreq > 0, 0.0, sel_bytes, [&] {
@@ -1391,6 +1403,12 @@ int mps_reset_kernel_stats(mps_t h) {
 }
 
 int64_t mps_launch_count(void) { return g_launches.load(); }
+
+int mps_set_sweep_limit(mps_t h, int max_sweeps) {
+  if (!h || max_sweeps < 1 || max_sweeps > kJacobiMaxSweeps) return MPS_EINVAL;
+  h->sweep_limit = max_sweeps;
+  return MPS_OK;
+}
 
 int mps_set_graphs(mps_t h, int on) {
   if (!h) return MPS_EINVAL;

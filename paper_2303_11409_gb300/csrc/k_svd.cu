@@ -1084,7 +1084,9 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
 }
 
 cudaError_t launch_svd_groups(const SvdSector* d_secs, const std::vector<SvdGroup>& groups, cudaStream_t st,
-                              const cudaStream_t* side, int n_side, cudaEvent_t fork, const cudaEvent_t* join) {
+                              const cudaStream_t* side, int n_side, cudaEvent_t fork, const cudaEvent_t* join,
+                              int max_sweeps) {
+  max_sweeps = std::max(1, std::min(max_sweeps, kJacobiMaxSweeps));   // the flag arrays hold 40 sweeps
   // group 0 on st, the others on side streams when given, all joined back into st
   cudaError_t e = cudaSuccess;
   const int ng = (int)groups.size();
@@ -1097,7 +1099,7 @@ cudaError_t launch_svd_groups(const SvdSector* d_secs, const std::vector<SvdGrou
   }
   for (int g = 0; g < ng; ++g) {
     cudaStream_t s = (fan && g > 0) ? side[g - 1] : st;
-    if ((e = launch_group(d_secs, groups[g], kJacobiMaxSweeps, s)) != cudaSuccess) return e;
+    if ((e = launch_group(d_secs, groups[g], max_sweeps, s)) != cudaSuccess) return e;
   }
   if (fan) {
     for (int g = 1; g < ng; ++g) {

@@ -24,6 +24,7 @@
 // The epilogue stages the accumulator through shared memory so that the FP64
 // stores of each output row are contiguous.
 #include <cuda_bf16.h>
+#include <atomic>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <vector>
@@ -41,6 +42,7 @@ constexpr int kTcThreads = 128;
 constexpr int kTcStages = 2;
 constexpr uint32_t kStageBytes = 32 * 1024;          // TF32: A, B (16 KB each); BF16x3: A hi, A lo, B hi, B lo
 constexpr long long kWaitCycles = 4000000000LL;      // bound of every mbarrier wait (~2 s)
+constexpr long long kStallWaitCycles = 100000000LL;  // the bound in stall-injection mode (~50 ms)
 constexpr int kEpiLd = 17;                           // padded row stride (double2) of the epilogue staging
 
 static_assert(kTcM == kTcTileM && kTcNc == kTcTileN, "tile shape");
@@ -70,10 +72,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 }
 
 // Bounded wait for the phase with the given parity; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long bound) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
-  while (clock64() - t0 < kWaitCycles) {
+  while (clock64() - t0 < bound) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -137,7 +139,7 @@ struct Lanes {
 template <int P>
 __global__ void __launch_bounds__(kTcThreads) tc_zgemm_kernel(const TcTile* __restrict__ tiles,
                                                               const TcSegment* __restrict__ segs,
-                                                              int* __restrict__ error_flag) {
+                                                              int* __restrict__ error_flag, int stall) {
   constexpr bool kTF32 = (P == MPS_TF32);
   using Ln = Lanes<kTF32>;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -161,6 +163,10 @@ __global__ void __launch_bounds__(kTcThreads) tc_zgemm_kernel(const TcTile* __re
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   constexpr uint32_t idesc = idesc_f32acc(kTF32 ? 2 : 1, kTcM, kTcN);
+  // stall injection (tests of the bounded-wait path): no MMA and no commit is issued, so no
+  // mbarrier phase completes and every wait runs out after the short bound; nothing is in
+  // flight when the tensor memory is freed
+  const long long wait_bound = stall ? kStallWaitCycles : kWaitCycles;
 
   int nsteps = 0;
   for (int sg = 0; sg < T.nseg; ++sg) nsteps += (max(segs[T.seg0 + sg].Kc, 0) + kTcKc - 1) / kTcKc;
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_zgemm_kernel(const TcTile* __re
   for (; step < nsteps;) {
     const int st = step % kTcStages;
     if (step >= kTcStages) {      // the MMAs that last read this stage must have completed
-      const bool w = mbar_wait(&bar_mma[st], (uint32_t)((step / kTcStages - 1) & 1));
+      const bool w = mbar_wait(&bar_mma[st], (uint32_t)((step / kTcStages - 1) & 1), wait_bound);
       ok = __syncthreads_and(w);  // every thread takes the same branch
       if (!ok) break;
     }
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_zgemm_kernel(const TcTile* __re
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (tid == 0) {
+    if (tid == 0 && !stall) {
       const uint32_t s0 = smem_u32(stage);
       if constexpr (kTF32) {
 #pragma unroll
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_zgemm_kernel(const TcTile* __re
   // tensor memory is freed); a commit completes after every earlier MMA of the thread
   if (step > 0) {
     const int last = (step - 1) % kTcStages;
-    const bool w = mbar_wait(&bar_mma[last], (uint32_t)(((step - 1) / kTcStages) & 1));
+    const bool w = mbar_wait(&bar_mma[last], (uint32_t)(((step - 1) / kTcStages) & 1), wait_bound);
     ok = __syncthreads_and(ok && w);
   }
   tc_fence_after();
@@ -334,6 +340,8 @@ __global__ void __launch_bounds__(kTcThreads) tc_zgemm_kernel(const TcTile* __re
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)kTcN));
 }
 
+std::atomic<bool> g_tc_stall{false};   // mps_tc_inject_stall
+
 template <int P>
 cudaError_t launch_tc(const TcTile* d_tiles, int n_tiles, const TcSegment* d_segs, int* d_err, cudaStream_t st) {
   static bool attr = false;
@@ -345,7 +353,7 @@ cudaError_t launch_tc(const TcTile* d_tiles, int n_tiles, const TcSegment* d_seg
     attr = true;
   }
   count_launch();
-  tc_zgemm_kernel<P><<<n_tiles, kTcThreads, smem, st>>>(d_tiles, d_segs, d_err);
+  tc_zgemm_kernel<P><<<n_tiles, kTcThreads, smem, st>>>(d_tiles, d_segs, d_err, g_tc_stall.load() ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -362,6 +370,11 @@ cudaError_t launch_tc_zgemm(int precision, const TcTile* d_tiles, int n_tiles, c
 }  // namespace mps
 
 using namespace mps;
+
+extern "C" int mps_tc_inject_stall(int on) {
+  g_tc_stall.store(on != 0);
+  return MPS_OK;
+}
 
 // Standalone entry point: C = A B on the tensor cores (see the header).
 extern "C" int mps_zgemm_tc(int precision, int M, int N, int K, const double* d_A, int lda, const double* d_B,

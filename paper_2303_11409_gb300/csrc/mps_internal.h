@@ -202,6 +202,7 @@ struct mps_s {
   std::vector<cudaEvent_t> event_pool;
   int* tc_flag = nullptr;                 // set by a tensor-core GEMM whose bounded wait expired
   std::vector<double> cut_est;            // per bond: smallest kept sigma of its last update (0: none)
+  int sweep_limit = 40;                   // Jacobi sweep limit of this handle's update calls
   // CUDA graphs: the two launch phases of an update call are captured and replayed
   // through one executable graph each, updated in place while the topology holds
   bool graphs = false;
@@ -244,7 +245,8 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
                       const SvdTune& tune = SvdTune());
 // Group 0 on st, group g > 0 on side[g-1] when n_side >= groups - 1; st then waits for all.
 cudaError_t launch_svd_groups(const SvdSector* d_secs, const std::vector<SvdGroup>& groups, cudaStream_t st,
-                              const cudaStream_t* side, int n_side, cudaEvent_t fork, const cudaEvent_t* join);
+                              const cudaStream_t* side, int n_side, cudaEvent_t fork, const cudaEvent_t* join,
+                              int max_sweeps = 40);
 
 cudaError_t launch_select(const SelectSector* d_secs, const SelectTask* d_tasks, int n_tasks,
                           int* d_kept, SelectResult* d_res, cudaStream_t st);
