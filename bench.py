@@ -255,6 +255,7 @@ def run_reference(args, world, rank):
 # the CUDA path
 # ---------------------------------------------------------------------------
 def run_ours(args, world, rank, local):
+    global _BH128_STATE
     import numpy as np
     import torch
     torch.cuda.set_device(local)
@@ -297,7 +298,6 @@ def run_ours(args, world, rank, local):
         if args.case == "bh128":
             # a synthetic saturated chain (Hilbert-proportional sector sizes, random blocks) loaded
             # through mps_set_bond / mps_set_site, at the run's precision
-            global _BH128_STATE
             psi = new_psi(W.mott_occupations(L), prec)
             if _BH128_STATE is None:
                 _BH128_STATE = W.saturated_random_state(L, D, N_PART, CHI, seed=0)
