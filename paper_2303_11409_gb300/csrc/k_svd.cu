@@ -14,27 +14,40 @@
 // lambda-graded sectors of an MPS (singular values over 10-15 decades) need
 // 20-35 plain Jacobi sweeps but 6-8 after it.
 //
+// Wide sectors (cluster kernels, n >= 1.25 m): R^dag has m columns of length n; an
+// unpivoted Householder QR R^dag = Q2 [R2; 0] lets the sweeps rotate the columns of the
+// m x m factor R2 instead (the same rotations orthogonalise both), and
+// Y = P Q2 [normalised columns; 0] is formed at the end, one warp per column.
+//
 // Storage: M is kept row-major with an odd leading dimension ld >= n, so the QR
 // rank-1 updates are coalesced (32 consecutive columns per warp) and, once R's
 // rows are conjugated in place, they are the contiguous columns of R^dag.
 // GB300 runs FP64 at 2 FMA/clk/SM, so one SM per large sector would leave a
-// layer waiting on its largest sectors.  Two kernels share the work:
-//   jacobi_cta_kernel:     one CTA per sector, all of it in shared memory;
-//   jacobi_cluster_kernel: a thread-block cluster of 8 or 16 CTAs per large
-//                          sector, data in L2 (ld.global.cg / st.global.cg, no
-//                          stale L1 lines across SMs), steps separated by the
-//                          hardware cluster barrier.
-// Jacobi pairs follow the round-robin ordering (disjoint pairs per round, one
-// warp per pair).  A pair is rotated when |a_p^dag a_q|^2 > tol^2 |a_p|^2 |a_q|^2,
+// layer waiting on its largest sectors.  Three kernels share the work:
+//   jacobi_cta_kernel:           one CTA per sector, all of it in shared memory,
+//                                round-robin pair ordering;
+//   jacobi_cluster_block_kernel: a thread-block cluster of 2, 4, 8 (or 16) CTAs per
+//                                large sector, data in L2 (ld.global.cg /
+//                                st.global.cg, no stale L1 lines across SMs), block
+//                                Jacobi with the block pairs of a round staged in
+//                                shared memory, CTA barriers between the steps of a
+//                                round and the hardware cluster barrier between rounds;
+//   jacobi_cluster_kernel:       the same data placement with round-robin pairs and
+//                                register-cached columns, for sectors whose blocks do
+//                                not fit in shared memory.
+// Column pairs of a step are shared by groups of 8, 16 or 32 lanes (an FP64 warp
+// instruction costs the same at any lane count on this part, so a warp does several
+// pairs at once).  A pair is rotated when |a_p^dag a_q|^2 > tol^2 |a_p|^2 |a_q|^2,
 // tol = eps * max(n, 32), and both columns are above the floor: the noise level
 // 32 eps |M|_F, or a higher deflation level the caller sets (SvdSector::floor_rel,
-// a fraction of the truncation cutoff); singular values at or below the floor are
-// reported as exactly 0.
+// a fraction of the truncation cutoff, and SvdSector::floor_abs, a fraction of the
+// bond's previous cut); singular values at or below the floor are reported as
+// exactly 0.
 // Convergence is a sweep without a rotation; a sector that does not converge
 // within the sweep limit reports -1.  FP64 costs a warp 64 cycles per
 // instruction here, so per-pair scalar work is kept small (no square root in the
-// test; two rsqrt, one sqrt and one division per rotation; column norms tracked
-// through the exact 2x2 relations within a sweep).
+// test; at most two rsqrt, one sqrt and one division per rotation; column norms tracked through the
+// exact 2x2 relations within a sweep).
 #include <algorithm>
 #include <mutex>
 #include <vector>
