@@ -90,16 +90,40 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 
-__device__ __forceinline__ float to_tf32(double x) {   // round to nearest (ties away) in TF32
+// FP64 -> FP32, round to nearest even, in integer operations only.  GB300 runs FP64 (and the
+// FP64-to-FP32 conversion) at 2 operations per clock per SM, and staging two operand tiles per
+// K step converts 48 values per thread: with hardware conversions and the coefficient applied
+// in FP64 the kernel was bound by the FP64 pipe (87% busy, tensor pipe 3%).  From the IEEE-754
+// binary64 and binary32 layouts: rebias the exponent, keep the top 23 of the 52 fraction bits,
+// round on the 29 dropped bits (a carry into the exponent is the correct result).  Magnitudes
+// below 2^-126 (FP32 subnormals) become signed zero, overflow becomes infinity, NaN stays NaN.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const int fe = e - 1023 + 127;
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+  const uint32_t fm = (uint32_t)(m >> 29);
+  const uint32_t rem = (uint32_t)(m & 0x1FFFFFFFu);
+  uint32_t r = ((uint32_t)fe << 23) | fm;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (fm & 1u))) ++r;
+  if (r > 0x7F800000u) r = 0x7F800000u;
+  return __uint_as_float(sign | r);
+}
+
+__device__ __forceinline__ float to_tf32(float x) {   // round to nearest (ties away) in TF32
   uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"((float)x));
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
 
-// x = hi + lo to about 2^-17 relative: hi = bf16(x), lo = bf16(x - hi)
-__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn((float)x);
-  lo = __float2bfloat16_rn((float)(x - (double)__bfloat162float(hi)));
+// x = hi + lo to about 2^-17 relative: hi = bf16(x), lo = bf16(x - hi) (x - hi exact in FP32)
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
 __device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc,
@@ -193,21 +217,24 @@ __global__ void __launch_bounds__(kTcThreads) tc_zgemm_kernel(const TcTile* __re
     ralpha = S.alpha;
     cur_k0 += kTcKc;
   };
+  // operands are converted to FP32 first (d2f_rn) and scaled by the segment's complex
+  // coefficient in FP32: the FP32 rounding (2^-24) is far below the TF32 / BF16x3 one
   auto store_step = [&](unsigned char* stage) {
+    const float alr = d2f_rn(ralpha.x), ali = d2f_rn(ralpha.y);
     if constexpr (kTF32) {
       unsigned char* a_s = stage;
       unsigned char* b_s = stage + 16 * 1024;
 #pragma unroll
       for (int g = 0; g < kTcM / 8; ++g) {
-        const double2 x = ra[g];
-        const double xr = ralpha.x * x.x - ralpha.y * x.y, xi = ralpha.x * x.y + ralpha.y * x.x;
-        *reinterpret_cast<float2*>(a_s + Ln::off(g, r7, kc)) = make_float2(to_tf32(xr), to_tf32(xi));
+        const float xr = d2f_rn(ra[g].x), xi = d2f_rn(ra[g].y);
+        const float vr = fmaf(alr, xr, -ali * xi), vi = fmaf(alr, xi, ali * xr);
+        *reinterpret_cast<float2*>(a_s + Ln::off(g, r7, kc)) = make_float2(to_tf32(vr), to_tf32(vi));
       }
 #pragma unroll
       for (int g = 0; g < kTcNc / 8; ++g) {
-        const double2 y = rb[g];
-        *reinterpret_cast<float2*>(b_s + Ln::off(g, r7, kc)) = make_float2(to_tf32(y.x), to_tf32(-y.y));
-        *reinterpret_cast<float2*>(b_s + Ln::off(g + kTcNc / 8, r7, kc)) = make_float2(to_tf32(y.y), to_tf32(y.x));
+        const float yr = to_tf32(d2f_rn(rb[g].x)), yi = to_tf32(d2f_rn(rb[g].y));
+        *reinterpret_cast<float2*>(b_s + Ln::off(g, r7, kc)) = make_float2(yr, -yi);
+        *reinterpret_cast<float2*>(b_s + Ln::off(g + kTcNc / 8, r7, kc)) = make_float2(yi, yr);
       }
     } else {
       unsigned char* ah = stage;
@@ -217,16 +244,16 @@ __global__ void __launch_bounds__(kTcThreads) tc_zgemm_kernel(const TcTile* __re
       __nv_bfloat16 h0, l0, h1, l1;
 #pragma unroll
       for (int g = 0; g < kTcM / 8; ++g) {
-        const double2 x = ra[g];
-        split_bf16(ralpha.x * x.x - ralpha.y * x.y, h0, l0);
-        split_bf16(ralpha.x * x.y + ralpha.y * x.x, h1, l1);
+        const float xr = d2f_rn(ra[g].x), xi = d2f_rn(ra[g].y);
+        split_bf16(fmaf(alr, xr, -ali * xi), h0, l0);
+        split_bf16(fmaf(alr, xi, ali * xr), h1, l1);
         const uint32_t o = Ln::off(g, r7, kc);
         *reinterpret_cast<__nv_bfloat162*>(ah + o) = __halves2bfloat162(h0, h1);
         *reinterpret_cast<__nv_bfloat162*>(al + o) = __halves2bfloat162(l0, l1);
       }
 #pragma unroll
       for (int g = 0; g < kTcNc / 8; ++g) {
-        const double2 y = rb[g];
+        const float2 y = make_float2(d2f_rn(rb[g].x), d2f_rn(rb[g].y));
         const uint32_t o_re = Ln::off(g, r7, kc), o_im = Ln::off(g + kTcNc / 8, r7, kc);
         split_bf16(y.x, h0, l0);
         split_bf16(-y.y, h1, l1);
