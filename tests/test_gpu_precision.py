@@ -7,7 +7,9 @@ the rounding of Theta' shows up as small singular values that the cutoff keeps a
 chi cap trims like any others.
 
 Stated error against the FP64 oracle, after the whole run (max over sites/bonds);
-measured on GB300 in brackets:
+measured on GB300 in brackets (with FP64 operand staging; the tests pass unchanged with the
+FP32 staging of the tensor-core kernel, whose two-site products measure 5.4e-4 (TF32) and
+1.3e-5 (BF16x3)):
     XXZ L=16, Neel, dt=0.05 x 20 steps, chi<=64, cutoff 1e-10 (600 updates)
         TF32:   <Sz_i> 5e-3 [1.5e-3]   bond entropy 5e-3 [1.6e-3]   amplitude 1.5e-3 [3.1e-4]
         BF16x3: <Sz_i> 8e-5 [2.1e-5]   bond entropy 1e-4 [2.7e-5]   amplitude 2e-5 [3.9e-6]
