@@ -7,7 +7,7 @@ the rounding of Theta' shows up as small singular values that the cutoff keeps a
 chi cap trims like any others.
 
 Stated error against the FP64 oracle, after the whole run (max over sites/bonds);
-measured on GB300 in brackets (with FP64 operand staging; the tests pass unchanged with the
+measured on GB300 in brackets (with FP64 operand staging; the stated tolerances hold with the
 FP32 staging of the tensor-core kernel, whose two-site products measure 5.4e-4 (TF32) and
 1.3e-5 (BF16x3)):
     XXZ L=16, Neel, dt=0.05 x 20 steps, chi<=64, cutoff 1e-10 (600 updates)
