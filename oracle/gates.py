@@ -8,7 +8,7 @@ charge).  Block n acts on the basis (i, n - i), i ascending, with
 Models are the paper's examples of U(1) symmetry (Sec. I): the XXZ chain, the
 Bose-Hubbard chain and boson-sampling beam splitters.  Conventions the paper
 leaves open (J = 1, spin-1/2 operators, on-site weights, the beam-splitter
-matrix) are readings listed in the design doc.
+matrix) are readings made here; the CUDA path's gate builders use the same ones.
 """
 from __future__ import annotations
 

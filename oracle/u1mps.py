@@ -20,7 +20,7 @@ What it follows (arXiv:2303.11409, Sec. II):
   * the CPU algorithm "loops over allowed charge values to construct Theta(c)"
     (Sec. II, CPU/GPU implementation paragraph): update() does exactly that.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent (the CUDA path follows the same ones):
   * sites are 0-based s = 0..L-1, bond b sits left of site b (b = 0..L), so site
     s joins bond s (left) and bond s+1 (right);
   * the state is kept right-canonical (B = Gamma lambda); the update is the
