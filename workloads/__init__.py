@@ -1,9 +1,11 @@
 """Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmarks.
 
-This module only draws numbers and lays out initial occupations; it holds none of
-the two-site update's arithmetic (no contraction, no SVD, no truncation), so the
-CUDA path and the float64 oracle can both take their inputs from it without
-sharing any of the method.
+This module only draws numbers and lays out inputs: initial occupations, Haar
+angles and Haar-random unitaries, random blocks and weights, the request mix, and
+the recipe of a synthetic saturated chain (sector sizes in proportion to a count of
+occupation strings).  It holds none of the two-site update's arithmetic (no
+contraction, no SVD, no truncation), so the CUDA path and the float64 oracle can
+both take their inputs from it without sharing any of the method.
 
 Workloads follow the model families the paper names for U(1)-symmetric tensor
 networks (Sec. I: Bose-Hubbard chains, XXZ spin chains, boson-sampling
@@ -24,6 +26,10 @@ __all__ = [
     "random_positive",
     "random_occupations",
     "serving_requests",
+    "haar_unitary",
+    "random_u1_gate",
+    "saturated_sector_dims",
+    "saturated_random_state",
 ]
 
 
