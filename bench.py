@@ -1,19 +1,25 @@
 #!/usr/bin/env python
 """Two-site TEBD update throughput of the U(1) block-sparse MPS on one GB300.
 
-Workload: Bose-Hubbard chain L=64, local cutoff n_max=4 (d=5), N=64 bosons
-(unit filling), J=1, U=2, Mott initial state, second-order Trotter steps of
-dt=0.02, chi<=512, cutoff 1e-10, FP64.  A "step" is one Trotter step: three
-layers (odd dt/2, even dt, odd dt/2), 95 two-site updates, each running the
-whole update path (planner, Theta build, per-sector SVD, global top-chi,
-reassembly, renormalisation).  The timed steps are taken in the saturated
-regime: the chain is first evolved from the Mott state by the same Trotter
-steps until its middle bond reaches chi (untimed), then W warm-up and K timed
-steps follow.  The L2 cache is flushed (256 MiB write) between timed steps,
-outside the timed events.
+Default workload (the largest single-GPU configuration): Bose-Hubbard chain L=128,
+local cutoff n_max=4 (d=5), N=128 bosons, J=1, U=2, second-order Trotter layers of
+dt=0.02, chi<=2048, cutoff 1e-10, sector GEMMs (the Theta' build and the reassembly
+product) in TF32 on the tensor cores with FP32 accumulation, SVD, truncation and
+renormalisation in FP64.  The chain starts saturated: every inner bond at chi spread
+over its charges in proportion to the Hilbert-space bound of each charge, random
+complex blocks (seeded), positive Schmidt weights (evolving the Mott state to
+saturation at chi=2048 would take hours).  A "step" is one whole Strang layer of
+that chain: the odd bonds with dt/2, the even bonds with dt, the odd bonds with dt/2,
+in turn (64, 63, 64 two-site updates), each update running the whole path (planner,
+Theta' build, per-sector SVD, global top-chi, reassembly, renormalisation).  The
+chain's 17 GB of site tensors exceed the 129 MB L2 many times over; the L2 is also
+flushed (256 MiB write) between timed steps, outside the timed events.
 
-Prints one JSON line (rank 0).  --impl reference times the float64 oracle on the
-host cores instead (a bounded sample of the same workload per step).
+Prints one JSON line (rank 0).  --impl reference times the float64 oracle on the host
+cores instead (a bounded sample of the same chain's updates per step).  --serve runs
+the serving workload (continuous batching) instead.  --case selects the other
+configurations (bh64: L=64, chi<=512, FP64, evolved from the Mott state; small:
+L=32 for profiler captures; boson: boson sampling M=100, chi<=1024).
 """
 from __future__ import annotations
 
@@ -23,97 +29,112 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-L, D, N_PART, J, U, DT, CHI, CUTOFF = 64, 5, 64, 1.0, 2.0, 0.02, 512, 1e-10
-UPDATES_PER_STEP = 32 + 31 + 32
+D, J, U, DT, CUTOFF = 5, 1.0, 2.0, 0.02, 1e-10
 METRIC = "two-site updates/s"
-WORKLOAD = "bose_hubbard_L64_nmax4_N64_J1_U2_dt0.02_chi512_cutoff1e-10_fp64"
-# --case small: the same model on L=32, chi=512 (half the chain, same sector sizes), for profiler captures
-SMALL = dict(L=32, N=32, CHI=512, WORKLOAD="bose_hubbard_L32_nmax4_N32_J1_U2_dt0.02_chi512_cutoff1e-10_fp64")
-# --case bh128: Bose-Hubbard L=128, N=128, chi<=2048 (the mixed-precision configuration), timed on
-# Strang layers of Bose-Hubbard gates applied to a synthetic saturated chain (evolving the Mott
-# state to saturation at chi=2048 would take far longer than a benchmark run)
-BH128 = dict(L=128, N=128, CHI=2048, SAMPLE=8,
-             WORKLOAD="bose_hubbard_L128_nmax4_N128_J1_U2_dt0.02_chi2048_cutoff1e-10_fp64")
-_BH128_STATE = None
-# --case boson: boson sampling, M=100 modes, single photons in modes 0..49, per-mode cutoff 4
-# (d=5), brickwork of seeded Haar beam splitters, chi<=1024; a step is one brickwork layer
-BOSON = dict(L=100, N=50, CHI=1024, DEPTH=100,
-             WORKLOAD="boson_sampling_M100_photons50_d5_brickwork100_chi1024_cutoff1e-10_fp64")
-# FP64 peak of the GB300 CUDA cores: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz.
-# (An FMA-chain probe measured 1.195 TFLOP/s, i.e. 2 FMA/clk/SM at the clock it ran.)
+CASES = {
+    # the configuration of record: L=128, chi<=2048, mixed-precision sector GEMMs
+    "bh128": dict(L=128, N=128, CHI=2048, precision="tf32", start="saturated",
+                  workload="bose_hubbard_L128_nmax4_N128_J1_U2_dt0.02_chi2048_cutoff1e-10"),
+    # L=64, chi<=512, FP64, evolved from the Mott state until the middle bond reaches chi
+    "bh64": dict(L=64, N=64, CHI=512, precision="fp64", start="evolved",
+                 workload="bose_hubbard_L64_nmax4_N64_J1_U2_dt0.02_chi512_cutoff1e-10"),
+    # half the L=64 chain at the same chi and sector sizes, for profiler captures
+    "small": dict(L=32, N=32, CHI=512, precision="fp64", start="evolved",
+                  workload="bose_hubbard_L32_nmax4_N32_J1_U2_dt0.02_chi512_cutoff1e-10"),
+    # boson sampling: M=100 modes, photons in modes 0..49, per-mode cutoff 4, Haar brickwork
+    "boson": dict(L=100, N=50, CHI=1024, precision="fp64", start="brickwork", depth=100,
+                  workload="boson_sampling_M100_photons50_d5_brickwork100_chi1024_cutoff1e-10"),
+}
+# FP64 peak of the GB300 CUDA cores: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (unit counts and
+# the maximum clock; an FMA-chain probe, run by every bench, measures 1.19-1.26 TFLOP/s)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
-# DRAM bytes per launch of the SVD phase of a saturated layer of this workload (all SVD kernels
-# of one layer), from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum with the
-# default tile shape; emptied whenever those kernels change.
-NCU_TRAFFIC = {"svd": 22.57e9}
-# Tensor peaks of the reduced-precision GEMMs, from the measured dense BF16 rate times the nominal
-# ratio of the format (TF32 1.1 / BF16 2.25 PFLOP/s dense); BF16x3 issues three BF16 MMAs per product.
-BF16_MEASURED_TFLOPS = 1913.8
-TENSOR_PEAK_TFLOPS = {"tf32": BF16_MEASURED_TFLOPS * 1.1 / 2.25, "bf16x3": BF16_MEASURED_TFLOPS / 3.0}
+# fallback of the measured peaks when MEASURED_PEAKS.json is absent (one earlier GB300 measurement)
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 KERNEL_BOUND = {"theta": "alu", "svd": "alu", "gemm": "alu", "select": "hbm", "lambda": "hbm",
                 "scatter": "hbm", "expect": "hbm", "amplitude": "alu"}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            p = json.load(fh)
+        return {k: float(p[k]) for k in FALLBACK_PEAKS}, "MEASURED_PEAKS.json (measured on this pool's GB300)"
+    except Exception:
+        return dict(FALLBACK_PEAKS), "fallback peaks (MEASURED_PEAKS.json absent)"
+
+
+def tensor_peak_tflops(precision: str, peaks: dict) -> tuple[float, str]:
+    """Peak of a sector GEMM timed inside the long step: the sustained BF16 rate times the
+    nominal ratio of the format (TF32 1.1 / BF16 2.25 PFLOP/s dense); BF16x3 issues three
+    BF16 MMAs per product."""
+    bf = peaks["bf16_tflops_sustained"]
+    if precision == "tf32":
+        return bf * 1.1 / 2.25, "sustained bf16 x 1.1/2.25 (nominal TF32/BF16 ratio)"
+    return bf / 3.0, "sustained bf16 / 3 (three BF16 MMAs per product)"
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=8)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--case", default="bh128", choices=sorted(CASES))
+    p.add_argument("--precision", default=None,
+                   help="sector GEMMs in fp64, tf32 or bf16x3 (tensor cores); SVD and truncation stay FP64; "
+                        "default: the case's (tf32 for bh128, fp64 otherwise); a comma-separated list runs each")
     p.add_argument("--max-prep", type=int, default=120)
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement (at most --steps)")
     p.add_argument("--serve", action="store_true",
                    help="serving workload instead: continuous batching vs the plain one-request-at-a-time form")
     p.add_argument("--serve-requests", type=int, default=48)
-    p.add_argument("--case", default="full", choices=["full", "small", "bh128", "boson"],
-                   help="full: the benchmark workload; small: L=32, chi=512 (for profiler captures); "
-                        "bh128: L=128, chi=2048; boson: boson sampling M=100, chi=1024")
-    p.add_argument("--precision", default="fp64",
-                   help="sector GEMMs in fp64 (default), tf32 or bf16x3 (tensor cores); SVD and truncation stay "
-                        "FP64; a comma-separated list runs each in turn from the same start state")
+    p.add_argument("--serve-seconds", type=float, default=25.0,
+                   help="wall-time bound of the serving sub-measurement of the main line (0: none)")
     p.add_argument("--graphs", type=int, default=1, help="capture each update call's launch phases in CUDA graphs")
     p.add_argument("--autotune", type=int, default=0,
                    help="SVD tile shape chosen per sector-size histogram (tuning runs happen before the timed steps)")
     a = p.parse_args()
-    global L, N_PART, CHI, WORKLOAD, UPDATES_PER_STEP
-    if a.case != "full":
-        c = {"small": SMALL, "bh128": BH128, "boson": BOSON}[a.case]
-        L, N_PART, CHI, WORKLOAD = c["L"], c["N"], c["CHI"], c["WORKLOAD"]
-        UPDATES_PER_STEP = (L // 2) + (L - 1) // 2 + (L // 2)
-        a.no_cpu_baseline = True
-    if a.case == "bh128":
-        UPDATES_PER_STEP = BH128["SAMPLE"]
+    a.cfg = CASES[a.case]
+    if a.precision is None:
+        a.precision = a.cfg["precision"]
+    if a.case != "bh128":
+        a.serve_seconds = 0.0
     return a
 
 
-def config(extra=None, case="full"):
-    if case == "boson":
-        c = {"workload": WORKLOAD, "model": "boson_sampling", "M": L, "d": D, "photons": N_PART,
-             "depth": BOSON["DEPTH"], "chi": CHI, "cutoff": CUTOFF,
-             "step": "one brickwork layer of Haar beam splitters (49 or 50 two-site updates)",
-             "regime": "the brickwork from the input state; timed layers follow the layers that bring the largest bond to chi"}
+def config_of(a, extra=None):
+    c = a.cfg
+    if a.case == "boson":
+        out = {"workload": c["workload"] + "_" + a.precision, "model": "boson_sampling", "M": c["L"], "d": D,
+               "photons": c["N"], "depth": c["depth"], "chi": c["CHI"], "cutoff": CUTOFF,
+               "step": "one brickwork layer of Haar beam splitters (49 or 50 two-site updates)",
+               "regime": "the brickwork from the input state; timed layers follow the layers that bring "
+                         "the largest bond to chi"}
     else:
-        c = {"workload": WORKLOAD, "model": "bose_hubbard", "L": L, "d": D, "N": N_PART, "J": J, "U": U,
-             "dt": DT, "chi": CHI, "cutoff": CUTOFF, "updates_per_step": UPDATES_PER_STEP,
-             "regime": ("synthetic saturated chain (every inner bond at chi spread over its charges in proportion "
-                        "to the Hilbert bound, random blocks, not canonical); a timed step is the 8 central updates "
-                        "of the odd (dt/2) layer, a bounded sample of the 127 updates of a Strang layer"
-                        if case == "bh128" else
-                        "saturated (timed steps follow untimed Trotter steps from the Mott state until the middle "
-                        "bond reaches chi)")}
-    c["l2"] = "flushed between timed steps (256 MiB device write outside the timed events)"
+        out = {"workload": c["workload"] + "_" + a.precision, "model": "bose_hubbard", "L": c["L"], "d": D,
+               "N": c["N"], "J": J, "U": U, "dt": DT, "chi": c["CHI"], "cutoff": CUTOFF,
+               "step": "one Strang layer (odd dt/2, even dt, odd dt/2 in turn): all of its two-site updates",
+               "regime": ("synthetic saturated chain (every inner bond at chi spread over its charges in proportion "
+                          "to the Hilbert bound; seeded random complex blocks and positive Schmidt weights; not "
+                          "canonical)" if c["start"] == "saturated" else
+                          "saturated (timed layers follow untimed Trotter steps from the Mott state until the "
+                          "middle bond reaches chi)")}
+    out["sector_gemms"] = a.precision
+    out["svd_truncation_renorm"] = "fp64"
+    out["l2"] = "inputs (site tensors) larger than L2; also flushed between timed steps (256 MiB write)"
     if extra:
-        c.update(extra)
-        if extra.get("precision", "fp64") != "fp64":
-            c["workload"] = WORKLOAD.replace("_fp64", "_" + extra["precision"])
-    return c
+        out.update(extra)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -124,11 +145,10 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        import torch
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        dist.init_process_group(backend)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return world, rank, local
 
 
@@ -149,7 +169,7 @@ def max_over_ranks(x, world):
 
 
 # ---------------------------------------------------------------------------
-# clocks during the timed region
+# clocks during the timed region (samples go to a temporary file)
 # ---------------------------------------------------------------------------
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -160,12 +180,11 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.fh = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
+            self.fh = tempfile.NamedTemporaryFile("w+", prefix="clocks_", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
@@ -180,14 +199,21 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if self.fh is not None:
             self.fh.close()
 
     def summary(self):
-        if self.proc is None or not os.path.exists(self.path):
+        if self.proc is None or self.fh is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.fh.name) as fh:
+            lines = fh.readlines()
+        try:
+            os.unlink(self.fh.name)
+        except OSError:
+            pass
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -206,45 +232,103 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# the oracle on the host cores (cpu_baseline and the reference arm)
+# the saturated chain, and the oracle on the host cores (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(seconds: float, max_updates: int | None = None):
-    """Oracle updates of the odd layer on a saturated synthetic chain, for about `seconds`."""
-    from oracle import synth, tebd as otebd
+_STATE = {}
+
+
+def saturated_chain(cfg):
+    """(lam, blocks) of the seeded synthetic saturated chain (built once per process)."""
     import workloads as W
-    st = synth.random_state(L, D, N_PART, CHI, seed=0, occ=W.mott_occupations(L))
+    key = (cfg["L"], cfg["N"], cfg["CHI"])
+    if key not in _STATE:
+        _STATE[key] = W.saturated_random_state(cfg["L"], D, cfg["N"], cfg["CHI"], seed=0)
+    return _STATE[key]
+
+
+def oracle_state(cfg):
+    """The oracle's copy of the same chain (the generated inputs, no arithmetic)."""
+    import numpy as np
+    from oracle import U1MPS
+    L, N = cfg["L"], cfg["N"]
+    lam, blocks = saturated_chain(cfg)
+    st = U1MPS(L, D, N)
+    st.bond = [None] * (L + 1)
+    st.lam = [None] * (L + 1)
+    st.bond[0], st.bond[L] = {N: 1}, {0: 1}
+    st.lam[0], st.lam[L] = {N: np.ones(1)}, {0: np.ones(1)}
+    for b in range(1, L):
+        st.lam[b] = {c: np.array(v) for c, v in lam[b].items()}
+        st.bond[b] = {c: len(v) for c, v in lam[b].items()}
+    st.B = [dict(bl) for bl in blocks]
+    return st
+
+
+def oracle_updates(cfg, seconds: float, max_updates: int | None = None):
+    """Oracle updates of the chain's odd layer (middle bonds first, dt/2 gates) for about
+    `seconds`; each update starts from the chain as generated (the sites are restored)."""
+    from oracle import tebd as otebd
+    L, chi = cfg["L"], cfg["CHI"]
+    st = oracle_state(cfg)
     gate_of = otebd.bh_gates(L, D, J, U, DT)
-    odd = list(range(0, L - 1, 2))
-    order = sorted(odd, key=lambda s: (abs(s - (L // 2 - 1)), s))     # middle bonds first
-    n, t0 = 0, time.perf_counter()
+    order = sorted(range(0, L - 1, 2), key=lambda s: (abs(s - (L // 2 - 1)), s))
+    n, el = 0, 0.0
     for s in order * 4:
-        st.apply_gate2(s, gate_of(s, 0.5), CHI, CUTOFF)
+        keep = (dict(st.bond[s + 1]), dict(st.lam[s + 1]), dict(st.B[s]), dict(st.B[s + 1]))
+        t0 = time.perf_counter()
+        st.apply_gate2(s, gate_of(s, 0.5), chi, CUTOFF)
+        el += time.perf_counter() - t0
+        st.bond[s + 1], st.lam[s + 1], st.B[s], st.B[s + 1] = keep
         n += 1
-        el = time.perf_counter() - t0
         if (max_updates is not None and n >= max_updates) or el >= seconds:
             break
-    el = time.perf_counter() - t0
-    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)))
-    return n, el, cores
+    return n, el
+
+
+def blas_threads() -> int:
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count() or 1
+
+
+def oracle_single_thread(case: str, seconds: float):
+    """The same sample in a fresh process with one BLAS thread (the thread count is fixed
+    when numpy loads, so it needs a process of its own)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "n, el = bench.oracle_updates(bench.CASES[%r], %r); print(json.dumps([n, el]))" % (ROOT, case, seconds))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        n, el = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": n / el, "unit": "updates/s", "cores": 1, "sample": f"{n} oracle updates ({el:.1f} s)"}
+    except Exception as e:  # pragma: no cover - reported, not fatal
+        return {"value": None, "error": str(e)[:200]}
 
 
 def run_reference(args, world, rank):
+    """The float64 oracle on the host cores, on the same chain and metric: each step is a
+    bounded sample of the configuration's updates (two updates of the odd layer)."""
     if rank != 0:
         return
-    per_step = 4
+    if args.case != "bh128":
+        print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the default configuration"}))
+        return
+    per_step = 2
     times = []
     for i in range(args.warmup + args.steps):
-        n, el, cores = oracle_sample(1e9, max_updates=per_step)
+        n, el = oracle_updates(args.cfg, 1e9, max_updates=per_step)
         if i >= args.warmup:
             times.append(el)
     tot = sum(times)
     value = per_step * len(times) / tot
-    sample = (f"{per_step} oracle updates per step on the odd layer (middle bonds first) of a saturated "
-              f"synthetic chi={CHI} chain (random blocks at Hilbert-proportional sector dims)")
+    cores = blas_threads()
+    sample = (f"{per_step} oracle updates per step on the odd layer (middle bonds first) of the saturated "
+              f"synthetic chi={args.cfg['CHI']} chain")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config({"oracle": "float64 numpy/scipy (zgesvd)"}),
+            "data": "synthetic", "config": config_of(args, {"oracle": "float64 numpy/scipy (zgesvd)"}),
             "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -254,19 +338,11 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
-def run_ours(args, world, rank, local):
-    global _BH128_STATE
+def build_workload(args, m, W, stream, prec):
+    """The state on the device and a step function (returns the updates it made)."""
     import numpy as np
-    import torch
-    torch.cuda.set_device(local)
-    import paper_2303_11409_gb300 as m
-    import workloads as W
-
-    # a stream of its own: the legacy default stream cannot be captured into CUDA graphs
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    fp64_measured = m.fp64_peak_probe(stream.cuda_stream)
-    prec = {"fp64": m.MPS_FP64, "tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[args.precision]
+    cfg = args.cfg
+    L, CHI = cfg["L"], cfg["CHI"]
 
     def new_psi(occ, precision):
         p = m.MPS(D, occ, CHI, precision=precision, stream=stream.cuda_stream)
@@ -275,11 +351,11 @@ def run_ours(args, world, rank, local):
         return p
 
     prep = 0
-    if args.case == "boson":
-        layers = W.brickwork_pairs(L, BOSON["DEPTH"])
+    if cfg["start"] == "brickwork":
+        layers = W.brickwork_pairs(L, cfg["depth"])
         ang = W.haar_beam_splitter_angles(sum(map(len, layers)), seed=0)
         first = np.cumsum([0] + [len(x) for x in layers])
-        psi = new_psi(W.single_photon_occupations(L, N_PART), prec)
+        psi = new_psi(W.single_photon_occupations(L, cfg["N"]), prec)
         pos = [0]
 
         def step():                      # the next brickwork layer (wrapping round after the last)
@@ -293,51 +369,62 @@ def run_ours(args, world, rank, local):
         while prep < args.max_prep and max(sum(psi.bond_dims(b).values()) for b in range(L + 1)) < CHI:
             step()
             prep += 1
+        return psi, step, prep
+
+    gates = m.tebd.GateTable("bh", L, D, DT, J=J, U=U)
+    if cfg["start"] == "saturated":
+        psi = new_psi(W.mott_occupations(L), prec)
+        lam, blocks = saturated_chain(cfg)
+        for b in range(1, L):
+            psi.set_bond(b, lam[b])
+        for s_ in range(L):
+            psi.set_site(s_, blocks[s_])
     else:
-        gates = m.tebd.GateTable("bh", L, D, DT, J=J, U=U)
-        if args.case == "bh128":
-            # a synthetic saturated chain (Hilbert-proportional sector sizes, random blocks) loaded
-            # through mps_set_bond / mps_set_site, at the run's precision
-            psi = new_psi(W.mott_occupations(L), prec)
-            if _BH128_STATE is None:
-                _BH128_STATE = W.saturated_random_state(L, D, N_PART, CHI, seed=0)
-            lam, blocks = _BH128_STATE
+        psi = new_psi(W.mott_occupations(L), m.MPS_FP64)
+        while prep < args.max_prep and sum(psi.bond_dims(L // 2).values()) < CHI:
+            m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
+            prep += 1
+        if prec != m.MPS_FP64:
+            # the same saturated state, continued with the sector GEMMs on the tensor cores
+            low = new_psi(W.mott_occupations(L), prec)
             for b in range(1, L):
-                psi.set_bond(b, lam[b])
+                low.set_bond(b, psi.bond(b))
             for s_ in range(L):
-                psi.set_site(s_, blocks[s_])
-        else:
-            psi = new_psi(W.mott_occupations(L), m.MPS_FP64)
-            while prep < args.max_prep and sum(psi.bond_dims(L // 2).values()) < CHI:
-                m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
-                prep += 1
-            if args.precision != "fp64":
-                # the same saturated state, continued with the sector GEMMs on the tensor cores
-                low = new_psi(W.mott_occupations(L), prec)
-                for b in range(1, L):
-                    low.set_bond(b, psi.bond(b))
-                for s_ in range(L):
-                    low.set_site(s_, psi.site(s_))
-                psi.close()
-                psi = low
+                low.set_site(s_, psi.site(s_))
+            psi.close()
+            psi = low
+    layers = m.tebd.strang_layers(L)
+    pos = [0]
 
-        if args.case == "bh128":
-            sample = list(range(L // 2 - BH128["SAMPLE"], L // 2 + BH128["SAMPLE"], 2))
+    def step():                          # the next Strang layer: odd dt/2, even dt, odd dt/2, ...
+        sites, f = layers[pos[0] % 3]
+        psi.apply_layer(sites, [gates(s_, f) for s_ in sites], CHI, CUTOFF)
+        pos[0] += 1
+        return len(sites)
 
-            def step():                  # the central updates of the odd (dt/2) layer
-                t0 = time.perf_counter()
-                psi.apply_layer(sample, [gates(s_, 0.5) for s_ in sample], CHI, CUTOFF)
-                print(f"{len(sample)} updates: {time.perf_counter() - t0:.2f} s", file=sys.stderr, flush=True)
-                return len(sample)
-        else:
-            def step():
-                m.tebd.trotter_step(psi, gates, CHI, CUTOFF)
-                return UPDATES_PER_STEP
+    return psi, step, prep
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2303_11409_gb300 as m
+    import workloads as W
+
+    peaks, peak_src = measured_peaks()
+    # a stream of its own: the legacy default stream cannot be captured into CUDA graphs
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    fp64_measured = m.fp64_peak_probe(stream.cuda_stream)
+    prec = {"fp64": m.MPS_FP64, "tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[args.precision]
+    psi, step, prep = build_workload(args, m, W, stream, prec)
+    L = args.cfg["L"]
 
     for _ in range(args.warmup):
         step()
-    # tile shapes are tuned during the evolution to saturation and the warm-up steps; a
-    # sector-size histogram first seen inside the timed steps keeps the default shape
+    # tile shapes are tuned during the preparation and the warm-up steps; a sector-size
+    # histogram first seen inside the timed steps keeps the default shape
     m.autotune_freeze(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
@@ -364,87 +451,132 @@ def run_ours(args, world, rank, local):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), world)
     value = world * n_upd / (total_ms / 1000.0)
-    mid_dims = max(sum(psi.bond_dims(b).values()) for b in range(L + 1))
+    largest = max(sum(psi.bond_dims(b).values()) for b in range(L + 1))
 
     # roofline of the dominant kernel (largest device time in the timed region)
+    tot_ms = max(sum(v["ms"] for v in ks.values()), 1e-12)
     dom = max(ks, key=lambda k: ks[k]["ms"])
     kd = ks[dom]
+    per_launch_ms = kd["ms"] / max(kd["launches"], 1)
     if KERNEL_BOUND[dom] == "hbm":
         achieved = kd["bytes"] / (kd["ms"] / 1000.0) / 1e9
-        peak, unit, traffic_unit = 6790.3, "GB/s", kd["bytes"] / max(kd["launches"], 1)
+        peak, unit = peaks["hbm_gbs"], "GB/s"
+        src = peak_src + " hbm_gbs"
     else:
         achieved = kd["flops"] / (kd["ms"] / 1000.0) / 1e9
         peak, unit = FP64_PEAK_GFLOPS, "GFLOP/s"
+        src = "FP64 CUDA-core peak from unit counts and the 2070 MHz max clock (152 SMs x 2 FMA/clk x 2 flop)"
     roofline = {"kernel": dom, "bound": KERNEL_BOUND[dom], "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak,
-                "traffic": (NCU_TRAFFIC.get(dom) if args.case == "full" and args.precision == "fp64"
-                            and not args.autotune else None),
-                "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the phase",
+                "frac": achieved / peak, "traffic": None,
+                "traffic_note": "null: no ncu DRAM capture of this kernel at this configuration's current build",
                 "per_launch": {"flops" if unit == "GFLOP/s" else "bytes":
                                (kd["flops"] if unit == "GFLOP/s" else kd["bytes"]) / max(kd["launches"], 1),
-                               "ms": kd["ms"] / max(kd["launches"], 1)},
-                "peak_source": ("FP64 CUDA-core peak from unit counts and the 2070 MHz max clock "
-                                "(152 SMs x 2 FMA/clk x 2 flop)")
-                if unit == "GFLOP/s" else "MEASURED_PEAKS.json hbm_gbs (measured copy)",
-                "fp64_peak_measured_gflops": fp64_measured,
-                "precision": args.precision,
+                               "ms": per_launch_ms},
+                "peak_source": src, "fp64_peak_measured_gflops": fp64_measured,
                 "frac_of_measured_fp64": achieved / fp64_measured if unit == "GFLOP/s" else None,
-                "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                                "share": v["ms"] / max(sum(x["ms"] for x in ks.values()), 1e-12)}
+                "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share": v["ms"] / tot_ms}
                             for k, v in ks.items() if v["launches"]}}
     if args.precision != "fp64":
         # the tensor-core sector GEMMs (Theta' build and reassembly) against the format's peak
+        tpk, tsrc = tensor_peak_tflops(args.precision, peaks)
         tc = {}
         for k in ("theta", "gemm"):
             v = ks[k]
             if v["launches"] and v["ms"] > 0:
                 tf = v["flops"] / (v["ms"] / 1000.0) / 1e12
-                tc[k] = {"achieved": tf, "unit": "TFLOP/s", "peak": TENSOR_PEAK_TFLOPS[args.precision],
-                         "frac": tf / TENSOR_PEAK_TFLOPS[args.precision],
-                         "bytes_per_s_gb": v["bytes"] / (v["ms"] / 1000.0) / 1e9}
+                tc[k] = {"achieved": tf, "unit": "TFLOP/s", "peak": tpk, "frac": tf / tpk,
+                         "flops_per_launch": v["flops"] / v["launches"], "ms_per_launch": v["ms"] / v["launches"],
+                         "share_of_device_time": v["ms"] / tot_ms}
         roofline["tensor_gemms"] = tc
-        roofline["tensor_peak_source"] = ("MEASURED_PEAKS.json bf16_tflops x nominal TF32/BF16 ratio (1.1/2.25)"
-                                          if args.precision == "tf32" else
-                                          "MEASURED_PEAKS.json bf16_tflops / 3 (three BF16 MMAs per product)")
+        roofline["tensor_peak_source"] = peak_src + ": " + tsrc
 
-    # e2e: the public API with host buffers, host wall clock, one observable read back per step
+    # e2e: the public API with host buffers (gate blocks and descriptors go up, kept counts and
+    # one <n_i> come back), host wall clock
     glen = m.gate_length(D)
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
     e2e_upd = 0
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         e2e_upd += step()
         psi.expect(L // 2, np.arange(D, dtype=np.float64))
     t1 = time.perf_counter()
     e2e_s = max_over_ranks(t1 - t0, world)
-    per_step = e2e_upd / args.steps
-    e2e = {"value": world * e2e_upd / e2e_s, "unit": "updates/s",
+    per_step = e2e_upd / e2e_steps
+    e2e = {"value": world * e2e_upd / e2e_s, "unit": "updates/s", "steps": e2e_steps,
            "h2d_bytes_per_step": int(per_step * glen * 16),
            "d2h_bytes_per_step": int(per_step * 8 + 8),
-           "what": "steps through MPS.apply_layer with host gate buffers, plus one <n_i> read back per step"}
+           "what": "Strang layers through MPS.apply_layer (mps_apply_layer) with host gate buffers, "
+                   "plus one <n_i> read back per step"}
+    psi.close()
+    del flush
+
+    serving = None
+    if args.serve_seconds > 0:
+        serving = serving_sample(args, m, W, stream, prec)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n, el, cores = oracle_sample(args.cpu_seconds)
-        cpu = {"value": n / el, "unit": "updates/s", "cores": cores, "kind": "oracle",
-               "sample": (f"{n} oracle updates ({el:.1f} s) of the odd layer, middle bonds first, on a saturated "
-                          f"synthetic chi={CHI} chain (random blocks at Hilbert-proportional sector dims)")}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.case == "bh128":
+        n, el = oracle_updates(args.cfg, args.cpu_seconds)
+        cpu = {"value": n / el, "unit": "updates/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": (f"{n} oracle updates ({el:.1f} s) of the odd layer, middle bonds first, on the same "
+                          f"saturated chi={args.cfg['CHI']} chain"),
+               "single_thread": oracle_single_thread(args.case, max(5.0, args.cpu_seconds / 2))}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else f"{args.precision}+f64", "data": "synthetic",
-                "config": config({"prep_steps": prep, "largest_bond_dim": mid_dims, "updates_timed": n_upd,
-                                  "parallelism": "replicas" if world > 1 else "single",
-                                  "precision": args.precision, "cuda_graphs": bool(args.graphs),
-                                  "autotune": bool(args.autotune)}, case=args.case),
+                "config": config_of(args, {"prep_steps": prep, "largest_bond_dim": largest, "updates_timed": n_upd,
+                                           "parallelism": "replicas" if world > 1 else "single",
+                                           "cuda_graphs": bool(args.graphs), "autotune": bool(args.autotune)}),
                 "graphs": graph_stats, "autotune": {**m.autotune_stats(), "table": m.autotune_table()},
-                "svd_deflation": deflation,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk.summary(), "step_ms": [round(x, 3) for x in step_ms]}
+                "svd_deflation": deflation, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "serving": serving, "gpu_launches": launches, "clocks": clk.summary(),
+                "step_ms": [round(x, 3) for x in step_ms]}
         print(json.dumps(line), flush=True)
-    psi.close()
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+SERVE_MIX = dict(L_choices=(16, 32), chi_choices=(32, 64, 128), steps_range=(5, 40))
+
+
+def serving_sample(args, m, W, stream, prec):
+    """Bounded p50/p99 measurement for the main line: requests of the scaled serving mix
+    through the continuous-batching server at --precision, Poisson arrivals at 0.8 x the
+    capacity measured on the same requests queued at once, stopped after --serve-seconds
+    of arrivals (requests arriving later are not sent)."""
+    n = 24
+    raw = W.serving_requests(n, seed=1, rate_hz=1.0, **SERVE_MIX)
+    reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=0.0)
+            for r in raw]
+    srv = m.serve.Server(budget_bytes=64 << 30, max_slots=64, stream=stream.cuda_stream, precision=prec,
+                         graphs=bool(args.graphs))
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    cap_s = time.perf_counter() - t0
+    srv.close()
+    capacity = sum(r.updates for r in res) / cap_s
+    rate = 0.8 * len(reqs) / cap_s
+    raw = W.serving_requests(n, seed=1, rate_hz=rate, **SERVE_MIX)
+    raw = [r for r in raw if r["arrival"] <= args.serve_seconds]
+    reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=r["arrival"])
+            for r in raw]
+    srv = m.serve.Server(budget_bytes=64 << 30, max_slots=64, stream=stream.cuda_stream, precision=prec,
+                         graphs=bool(args.graphs))
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    srv.close()
+    s = m.serve.summarize(res, wall)
+    return {"p50_latency_s": s["p50_latency_s"], "p99_latency_s": s["p99_latency_s"], "requests": s["requests"],
+            "updates_per_s_under_load": s["updates_per_s"], "capacity_updates_per_s": capacity,
+            "arrival_rate_hz": rate,
+            "mix": {k: list(v) for k, v in SERVE_MIX.items()}, "precision": args.precision,
+            "what": "scaled serving mix (xxz / bose-hubbard quenches), Poisson arrivals at 0.8 x capacity"}
 
 
 def run_serving(args, world, rank, local):
@@ -471,12 +603,10 @@ def run_serving(args, world, rank, local):
     prec_name = args.precision.split(",")[0]
     prec = {"fp64": m.MPS_FP64, "tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[prec_name]
     graphs = bool(args.graphs)
-    mix = dict(L_choices=(16, 32), chi_choices=(32, 64, 128), steps_range=(5, 40))
-    raw = W.serving_requests(args.serve_requests, seed=rank, rate_hz=1.0, **mix)
+    raw = W.serving_requests(args.serve_requests, seed=rank, rate_hz=1.0, **SERVE_MIX)
     reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=0.0)
             for r in raw]
     budget = 64 << 30
-    # plain form: FP64, one request at a time, no merging, direct launches
     t0 = time.perf_counter()
     plain_updates = 0
     plain_obs = {}
@@ -488,8 +618,7 @@ def run_serving(args, world, rank, local):
         plain_obs[q.id] = res[0].observables
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
-    plain_rate = plain_updates / plain_s                    # updates/s
-    # served capacity: every request queued at t = 0, merged launches across requests
+    plain_rate = plain_updates / plain_s
     srv = m.serve.Server(budget_bytes=budget, max_slots=64, stream=stream.cuda_stream, precision=prec,
                          graphs=graphs)
     t0 = time.perf_counter()
@@ -498,11 +627,9 @@ def run_serving(args, world, rank, local):
     cap_s = time.perf_counter() - t0
     srv.close()
     served_cap = sum(r.updates for r in res) / cap_s
-    # accuracy of the served form against the plain FP64 form, per observable <n_i>
     obs_err = max(float(np.max(np.abs(r.observables - plain_obs[r.id]))) for r in res)
-    # latency under load: Poisson arrivals at 0.8 x the served capacity (in requests/s)
     req_rate = 0.8 * len(reqs) / cap_s
-    raw = W.serving_requests(args.serve_requests, seed=rank, rate_hz=req_rate, **mix)
+    raw = W.serving_requests(args.serve_requests, seed=rank, rate_hz=req_rate, **SERVE_MIX)
     reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=r["arrival"])
             for r in raw]
     srv = m.serve.Server(budget_bytes=budget, max_slots=64, stream=stream.cuda_stream, precision=prec,
@@ -527,7 +654,8 @@ def run_serving(args, world, rank, local):
                 "max_observable_error_vs_plain_fp64": obs_err,
                 "arrival_rate_hz": req_rate, "max_active_under_load": srv.max_active_seen,
                 "gpu_launches": m.launch_count() - launches0, "graphs": gstats,
-                "config": {"workload": "serving_mix_scaled", "requests": len(reqs), **{k: list(v) for k, v in mix.items()},
+                "config": {"workload": "serving_mix_scaled", "requests": len(reqs),
+                           **{k: list(v) for k, v in SERVE_MIX.items()},
                            "models": "xxz Delta~U[0,2] (Neel) / bh U~U[1,10] J=1 (Mott), 50/50",
                            "value": "served capacity (all requests queued at t=0, merged launches)",
                            "latency": "Poisson arrivals at 0.8 x the served capacity",

@@ -198,6 +198,15 @@ MPS_API int mps_bond_spectrum(mps_t h, int bond, int32_t* charges, int32_t* dims
                       int cap, int* n_out);
 
 /*
+ * mps_bond_entropy - the entanglement entropy of bond b (0..L) from its Schmidt values,
+ * S_b = -sum_a lambda_a^2 ln lambda_a^2 over all sectors (natural log; lambda are the
+ * Schmidt coefficients of the canonical form of Sec. II, unit 2-norm after every
+ * update).  Computed on the device (one reduction kernel); *out is written when the
+ * call returns.  Errors: MPS_EINVAL (bad bond, NULL out), MPS_ENOMEM, MPS_ECUDA.
+ */
+MPS_API int mps_bond_entropy(mps_t h, int bond, double* out);
+
+/*
  * mps_get_site - the blocks of site s in (l ascending, m ascending) order.
  *   lcharges, mcharges  block labels (capacity cap_blocks)
  *   data                complex128 interleaved, blocks concatenated, each row-major

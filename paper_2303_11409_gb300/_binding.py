@@ -71,6 +71,7 @@ _SIGS = {
     "mps_amplitude": (ctypes.c_int, [_h, _i32p, _dblp]),
     "mps_amplitude_batch": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _dblp]),
     "mps_bond_spectrum": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _i32p, _dblp, ctypes.c_int, _intp]),
+    "mps_bond_entropy": (ctypes.c_int, [_h, ctypes.c_int, _dblp]),
     "mps_save": (ctypes.c_int, [_h, ctypes.c_char_p]),
     "mps_load": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_char_p, _vp]),
     "mps_get_site": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _i32p, ctypes.c_int, _dblp, ctypes.c_int64,
@@ -277,9 +278,10 @@ class MPS:
         return {c: len(v) for c, v in self.bond(b).items()}
 
     def entropy(self, b: int) -> float:
-        p = np.concatenate([v ** 2 for v in self.bond(b).values()])
-        p = p[p > 0]
-        return float(-np.sum(p * np.log(p)))
+        """Bond entropy -sum lambda^2 ln lambda^2 of bond b (computed by the library)."""
+        out = ctypes.c_double(0.0)
+        self._check(lib.mps_bond_entropy(self._h, b, ctypes.byref(out)), "mps_bond_entropy")
+        return out.value
 
     def site(self, s: int) -> dict:
         """{(l, m): block} of site s (host copy)."""

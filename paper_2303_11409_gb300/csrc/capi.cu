@@ -1308,6 +1308,20 @@ int mps_bond_spectrum(mps_t h, int bond, int32_t* charges, int32_t* dims, double
   return MPS_OK;
 }
 
+int mps_bond_entropy(mps_t h, int bond, double* out) {
+  if (check_handle(h)) return MPS_EINVAL;
+  if (bond < 0 || bond > h->L || !out) return fail(h, MPS_EINVAL, "bad bond");
+  CUDA_OR_FAIL(h, cudaEventSynchronize(h->staged));
+  if (h->work.reserve(256) != cudaSuccess) return fail(h, MPS_ENOMEM, "workspace");
+  if (h->pin_out.reserve(256) != cudaSuccess) return fail(h, MPS_ENOMEM, "pinned staging");
+  double* d_out = reinterpret_cast<double*>(h->work.p);
+  CUDA_OR_FAIL(h, launch_entropy(h->lambda_ptr(bond), h->bonds[bond].total(), d_out, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->pin_out.p, d_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  *out = *reinterpret_cast<const double*>(h->pin_out.p);
+  return MPS_OK;
+}
+
 int mps_get_site(mps_t h, int site, int32_t* lcharges, int32_t* mcharges, int cap_blocks, double* data,
                  int64_t cap_values, int* n_blocks, int64_t* n_values) {
   if (check_handle(h)) return MPS_EINVAL;

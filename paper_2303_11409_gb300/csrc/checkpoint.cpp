@@ -20,6 +20,8 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -39,6 +41,19 @@ template <class T>
 bool put(FILE* f, const T* p, size_t n) { return n == 0 || std::fwrite(p, sizeof(T), n, f) == n; }
 template <class T>
 bool get(FILE* f, T* p, size_t n) { return n == 0 || std::fread(p, sizeof(T), n, f) == n; }
+
+// Bytes left between the read position and the end of the file (0 on error).  Every count
+// read from the file is checked against it before anything is sized by that count, so a
+// damaged or hostile file cannot make the loader allocate more than the file could hold.
+int64_t remaining(FILE* f) {
+  const long pos = std::ftell(f);
+  if (pos < 0 || std::fseek(f, 0, SEEK_END) != 0) return 0;
+  const long end = std::ftell(f);
+  if (end < 0 || std::fseek(f, pos, SEEK_SET) != 0) return 0;
+  return (int64_t)end - (int64_t)pos;
+}
+
+constexpr int64_t kMaxSites = int64_t(1) << 24;   // far above any chain a handle can hold
 
 int save_fail(mps_t h, const std::string& msg) {
   h->err = msg;
@@ -103,9 +118,23 @@ int mps_save(mps_t h, const char* path) {
   return MPS_OK;
 }
 
+static int load_body(mps_t* out, const char* path, void* cuda_stream);
+
 int mps_load(mps_t* out, const char* path, void* cuda_stream) {
   if (!out || !path) return MPS_EINVAL;
   *out = nullptr;
+  // nothing may escape the C boundary: allocation failures and any other exception of the
+  // host containers become status codes
+  try {
+    return load_body(out, path, cuda_stream);
+  } catch (const std::bad_alloc&) {
+    return MPS_ENOMEM;
+  } catch (...) {
+    return MPS_EINVAL;
+  }
+}
+
+static int load_body(mps_t* out, const char* path, void* cuda_stream) {
   File in;
   in.f = std::fopen(path, "rb");
   if (!in.f) return MPS_EINVAL;
@@ -116,7 +145,11 @@ int mps_load(mps_t* out, const char* path, void* cuda_stream) {
     return MPS_EINVAL;
   const int version = hdr[0];
   const int L = hdr[1], d = hdr[2], N = hdr[3], chi_max = hdr[4], precision = hdr[5];
-  if (L < 2 || d < 2 || d > MPS_MAX_D || N < 0 || N > L * (d - 1) || chi_max < 1) return MPS_EINVAL;
+  if (L < 2 || (int64_t)L > kMaxSites || d < 2 || d > MPS_MAX_D || N < 0 || (int64_t)N > (int64_t)L * (d - 1) ||
+      chi_max < 1)
+    return MPS_EINVAL;
+  // every bond record holds at least an int32 count, a charge, a dimension and one lambda
+  if (remaining(in.f) < (int64_t)(L + 1) * 20) return MPS_EINVAL;
   // a product state with the same total charge; every bond and site is then overwritten
   std::vector<int32_t> occ(L, 0);
   for (int s = 0, left = N; s < L; ++s) { occ[s] = left < d - 1 ? left : d - 1; left -= occ[s]; }
@@ -128,7 +161,7 @@ int mps_load(mps_t* out, const char* path, void* cuda_stream) {
   std::vector<double> lam;
   for (int b = 0; b <= L; ++b) {
     int32_t n = 0;
-    if (!get(in.f, &n, 1) || n < 1 || n > N + 1) return MPS_EINVAL;
+    if (!get(in.f, &n, 1) || n < 1 || n > N + 1 || (int64_t)n * 8 > remaining(in.f)) return MPS_EINVAL;
     ch.resize(n);
     dm.resize(n);
     if (!get(in.f, ch.data(), n) || !get(in.f, dm.data(), n)) return MPS_EINVAL;
@@ -137,6 +170,7 @@ int mps_load(mps_t* out, const char* path, void* cuda_stream) {
       if (dm[i] < 1 || dm[i] > chi_max) return MPS_EINVAL;
       tot += dm[i];
     }
+    if (tot * 8 > remaining(in.f)) return MPS_EINVAL;
     lam.resize(tot);
     if (!get(in.f, lam.data(), tot)) return MPS_EINVAL;
     if (b == 0 || b == L) {   // boundary bonds: one sector (N at the left end, 0 at the right), lambda = 1
@@ -153,6 +187,7 @@ int mps_load(mps_t* out, const char* path, void* cuda_stream) {
     int64_t nnz = 0;
     if (!get(in.f, &nb, 1) || !get(in.f, &nnz, 1) || nb < 0 || nnz < 0) return MPS_EINVAL;
     if (nnz > h->site_cap[s] || nb > (int64_t)h->site_cap[s]) return MPS_ENOMEM;
+    if ((int64_t)nb * 8 + nnz * 16 > remaining(in.f)) return MPS_EINVAL;
     pairs.resize(2 * (size_t)nb);
     data.resize(2 * (size_t)nnz);
     if (!get(in.f, pairs.data(), pairs.size()) || !get(in.f, data.data(), data.size())) return MPS_EINVAL;

@@ -10,6 +10,10 @@
 // amplitude formula (Sec. II), the product of exactly one block per site, the one
 // selected by the right-charges of the configuration.  One CTA per configuration
 // runs the vector-matrix chain with the row vector in shared memory.
+//
+// entropy_kernel: the bond entropy S_b = -sum_a lambda_a^2 ln lambda_a^2 over all
+// sectors of bond b (lambda are the Schmidt values of Sec. II; zero values add
+// nothing).  One CTA, a fixed-order tree reduction, so the result is deterministic.
 #include "mps_internal.h"
 
 namespace mps {
@@ -64,7 +68,29 @@ __global__ void amplitude_kernel(const AmpStep* __restrict__ steps, int L, int c
   if (threadIdx.x == 0) out[blockIdx.x] = (zero || dim != 1) ? make_double2(0.0, 0.0) : v[0];
 }
 
+__global__ void entropy_kernel(const double* __restrict__ lam, int n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double p = lam[i] * lam[i];
+    if (p > 0.0) acc -= p * log(p);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
 }  // namespace
+
+cudaError_t launch_entropy(const double* d_lambda, int n, double* d_out, cudaStream_t st) {
+  count_launch();
+  entropy_kernel<<<1, 256, 0, st>>>(d_lambda, n, d_out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_expect(const ExpectTask* d_tasks, int n_tasks, double* d_partial, cudaStream_t st) {
   if (n_tasks <= 0) return cudaSuccess;

@@ -940,17 +940,29 @@ constexpr int kBlockSmemMax = 110 * 1024;   // two block-Jacobi CTAs per SM
 // 8 CTAs per large sector: the GPU places about twice as many 8-CTA clusters as
 // 16-CTA ones, which keeps more SMs busy when a layer has hundreds of large sectors
 constexpr int kBigCluster = 8;
-bool g_attr_done = false;
-int g_big_cluster = 0;
+// Kernel attributes (dynamic shared memory, non-portable clusters) apply to the current device
+// only, so they are set once per device, under a lock, with that device's cluster size.
+constexpr int kMaxDevices = 64;
+std::mutex g_attr_mu;
+bool g_attr_done[kMaxDevices] = {};
+int g_big_cluster[kMaxDevices] = {};
 
 int64_t block_smem_need(int m, int n, int cl, int g, int gs) {
   const int64_t K = std::min(m, n), bs = (K + 2 * cl * g - 1) / (2 * cl * g);
   return 16 * 2 * gs * bs * n + 8 * 2 * gs * bs + 64;
 }
 
-cudaError_t set_attrs() {
-  if (g_attr_done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(jacobi_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSvdSmemMax);
+cudaError_t set_attrs(int* big_out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  if (g_attr_done[dev]) {
+    *big_out = g_big_cluster[dev];
+    return cudaSuccess;
+  }
+  e = cudaFuncSetAttribute(jacobi_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSvdSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(jacobi_cluster_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kBlockSmemMax);
@@ -976,8 +988,9 @@ cudaError_t set_attrs() {
     if (cudaOccupancyMaxActiveClusters(&n, jacobi_cluster_block_kernel, &cfg) == cudaSuccess && n >= 4) big = 16;
   }
   cudaGetLastError();
-  g_big_cluster = big;
-  g_attr_done = true;
+  g_big_cluster[dev] = big;
+  g_attr_done[dev] = true;
+  *big_out = big;
   return cudaSuccess;
 }
 
@@ -1008,7 +1021,8 @@ cudaError_t launch_group(const SvdSector* d_secs, const SvdGroup& g, int max_swe
 }  // namespace
 
 cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& groups, const SvdTune& tune) {
-  cudaError_t e = set_attrs();
+  int big_cluster = 0;
+  cudaError_t e = set_attrs(&big_cluster);
   if (e != cudaSuccess) return e;
   // every sector gets a kernel and a cluster size
   std::vector<std::pair<int, int>> key(secs.size());
@@ -1044,7 +1058,7 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
         pick_cl = cl; pick_g = g; pick_gs = gs;
       }
     }
-    if (std::min(S.m, S.n) >= tune.c16_min_k && g_big_cluster >= 16) {   // a 16-CTA cluster
+    if (std::min(S.m, S.n) >= tune.c16_min_k && big_cluster >= 16) {   // a 16-CTA cluster
       const int cl = 16;
       int g = std::max(1, (std::min(S.m, S.n) + bw * cl) / (2 * bw * cl));
       while (g < 64 && block_smem_need(S.m, cn, cl, g, 1) > kBlockSmemMax) ++g;
@@ -1060,7 +1074,7 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
       secs[k].groups = pick_g;
       secs[k].staged = pick_gs;
     } else {
-      key[k] = {kSvdCluster, g_big_cluster};
+      key[k] = {kSvdCluster, big_cluster};
     }
   }
   // group by (kind, cluster size); the most expensive sectors first inside a group

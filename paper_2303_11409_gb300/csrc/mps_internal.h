@@ -277,6 +277,8 @@ cudaError_t launch_lambda(const LambdaTask* d_tasks, int n_tasks, cudaStream_t s
 struct ExpectTask { const double2* blk; const double* lam; int Dl, Dm; double w; };
 cudaError_t launch_expect(const ExpectTask* d_tasks, int n_tasks, double* d_partial, cudaStream_t st);
 struct AmpStep { const double2* blk; int Dl, Dm; };
+// -sum lambda^2 ln lambda^2 over n values into *d_out (one CTA).
+cudaError_t launch_entropy(const double* d_lambda, int n, double* d_out, cudaStream_t st);
 cudaError_t launch_amplitude(const AmpStep* d_steps, int L, int n_cfg, double2* d_out, int chi_max,
                              cudaStream_t st);
 

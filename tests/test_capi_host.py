@@ -80,3 +80,25 @@ def test_svd_work_bytes_host(built):
     small = m.svd_work_bytes([10], [10])
     big = m.svd_work_bytes([300], [300])
     assert big >= 16 * 300 * 300 > small
+
+
+def test_load_rejects_impossible_headers_without_touching_the_gpu(built, tmp_path):
+    """mps_load checks the header and every size against the file before it creates a
+    handle or sizes anything: a damaged or hostile checkpoint is refused with MPS_EINVAL
+    (no exception crosses the C boundary, no device call is made)."""
+    import ctypes
+    import struct
+    import paper_2303_11409_gb300 as m
+    h = ctypes.c_void_p()
+    cases = {
+        "huge_L": struct.pack("<8s6i", b"U1MPSCK1", 2, 1 << 30, 5, 10, 64, 0),
+        "L_times_d_overflows": struct.pack("<8s6i", b"U1MPSCK1", 2, (1 << 24), 8, (1 << 31) - 1, 64, 0),
+        "short_file": struct.pack("<8s6i", b"U1MPSCK1", 2, 1000, 5, 10, 64, 0) + b"\0" * 64,
+        "negative_N": struct.pack("<8s6i", b"U1MPSCK1", 2, 8, 2, -1, 8, 0),
+    }
+    for name, blob in cases.items():
+        p = tmp_path / f"{name}.u1mps"
+        p.write_bytes(blob)
+        rc = m.lib.mps_load(ctypes.byref(h), str(p).encode(), None)
+        assert rc == m.MPS_EINVAL, (name, rc)
+        assert not h.value

@@ -299,3 +299,53 @@ def test_deflation_from_the_previous_cut_and_its_redo(gpu_lib):
     assert seen[0] == dict(deflated_updates=0, redos=0), seen
     assert seen[2]["deflated_updates"] == 2, seen
     assert seen[2]["redos"] - seen[1]["redos"] == 1, seen      # the 40th value is far below the 6th
+
+
+# ---------------------------------------------------------------------------
+# the benchmark chain's own trajectory: Bose-Hubbard L=64, n_max=4, N=64, J=1, U=2,
+# dt=0.02, chi<=512, cutoff 1e-10, evolved from the Mott state on both sides
+# ---------------------------------------------------------------------------
+BH64_STEPS = 30        # Strang steps the float64 oracle finishes in about a minute on 16 cores
+
+
+def test_bose_hubbard_L64_trajectory_from_mott(gpu_lib):
+    """Sec. II update, evolved the way the benchmark launches it (a stream of its own,
+    CUDA graphs on, one mps_apply_layer per Strang layer).  After every layer the kept
+    sector labels and dimensions of every bond equal the oracle's and every Schmidt
+    value agrees to 1e-12; after every step <n_i> and the bond entropies agree to
+    1e-9 * max(|ref|, |O|) (|O| = n_max for n, ln chi for the entropy)."""
+    import torch
+    m = gpu_lib
+    L, d, N, J, U, dt, chi, cutoff = 64, 5, 64, 1.0, 2.0, 0.02, 512, 1e-10
+    stream = torch.cuda.Stream()
+    g = m.MPS(d, W.mott_occupations(L), chi, stream=stream.cuda_stream)
+    g.set_graphs(True)
+    st = U1MPS.product(d, W.mott_occupations(L))
+    gate_of = tebd.bh_gates(L, d, J, U, dt)
+    n_op = np.arange(d)
+    worst_lam = worst_obs = 0.0
+    for step in range(BH64_STEPS):
+        for sites, f in tebd.strang_layers(L):
+            g.apply_layer(sites, [gate_of(s, f) for s in sites], chi, cutoff)
+            for s in sites:
+                st.apply_gate2(s, gate_of(s, f), chi, cutoff)
+            for b in range(L + 1):
+                gb = g.bond(b)
+                assert {c: len(v) for c, v in gb.items()} == st.bond[b], (step, b)
+                for c, v in gb.items():
+                    e = float(np.max(np.abs(v - st.lam[b][c])))
+                    worst_lam = max(worst_lam, e)
+                    assert e <= 1e-12, (step, b, c, e)
+        for s in range(L):
+            ref = st.expect_local(s, n_op)
+            e = abs(g.expect(s, n_op) - ref)
+            worst_obs = max(worst_obs, e / max(abs(ref), d - 1))
+            assert e <= 1e-9 * max(abs(ref), d - 1), (step, s, e)
+        for b in range(1, L):
+            ref = st.entropy(b)
+            e = abs(g.entropy(b) - ref)
+            assert e <= 1e-9 * max(abs(ref), math.log(chi)), (step, b, e)
+    print(f"L=64 trajectory, {BH64_STEPS} steps: largest bond {max(st.bond_dim(b) for b in range(L + 1))}, "
+          f"lambda err {worst_lam:.2e}, <n_i> rel err {worst_obs:.2e}")
+    assert g.graph_stats()["launches"] > 0
+    g.close()

@@ -21,10 +21,13 @@ FP32 staging of the tensor-core kernel, whose two-site products measure 5.4e-4 (
 Each update perturbs the state by about u times a small factor (the number of terms
 summed per element enters as sqrt, the rounding is unbiased), u = 2^-11 for TF32 and
 about 2^-17 for BF16x3, so the deviation grows like u sqrt(updates) to u * updates.
-On the XXZ run the bond tables (sector labels and dimensions) equal the oracle's after
-at least 90% of the layers (measured: BF16x3 all, TF32 58 of 60): the reduced modes
-guarantee the observable errors stated above, not the labels of values that their
-rounding moves across the truncation cut.
+Sector labels on the XXZ run: in BF16x3 every bond table (labels and dimensions) equals
+the oracle's after every layer.  In TF32 a bond may differ only where the oracle's own
+update of that bond had a singular value within the run's stated accuracy (5e-3 sigma_max,
+the <Sz_i> tolerance above) of its cut: the smallest kept and the largest discarded value
+when chi set the cut, or the cutoff threshold cutoff * |sigma|_2 when the cutoff did.  A
+TF32 rounding of Theta' moves singular values by about 2^-11 sigma_max per update, so such
+values can cross the cut; a label or dimension change anywhere else fails the test.
 """
 import numpy as np
 import pytest
@@ -45,30 +48,58 @@ def _prec(m, name):
     return {"tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[name]
 
 
+def _cut_distance(info, chi):
+    """Distance (relative to sigma_max) of the oracle update's nearest singular value to
+    its cut: the chi-th / (chi+1)-th gap when chi set the cut, else the distance of the
+    nearest value to the cutoff threshold."""
+    vals = np.sort(np.concatenate([np.asarray(v) for v in info["sigmas"].values()]))[::-1]
+    smax = vals[0]
+    cand = vals[vals > info["threshold"]]
+    if len(cand) > chi:
+        return (cand[chi - 1] - cand[chi]) / smax
+    return float(np.min(np.abs(vals - info["threshold"]))) / smax
+
+
 def _run(m, L, d, occ, gate_of, steps, chi, cutoff, prec):
-    """Both evolutions; returns them and the fraction of layers after which every bond
-    table (sector labels and dimensions) equals the oracle's."""
+    """Both evolutions; returns them and every (layer, bond, cut distance) at which a bond
+    table (sector labels and dimensions) differs from the oracle's."""
     g = m.MPS(d, occ, chi, precision=prec)
     st = U1MPS.product(d, occ)
-    same = layers = 0
+    mism = []
+    layer = 0
     for _ in range(steps):
         for sites, f in tebd.strang_layers(L):
             g.apply_layer(sites, [gate_of(s, f) for s in sites], chi, cutoff)
-            for s in sites:
-                st.apply_gate2(s, gate_of(s, f), chi, cutoff)
-            layers += 1
-            same += all(g.bond_dims(b) == st.bond[b] for b in range(L + 1))
-    return g, st, same / layers
+            infos = {s: st.apply_gate2(s, gate_of(s, f), chi, cutoff) for s in sites}
+            for b in range(L + 1):
+                if g.bond_dims(b) != st.bond[b]:
+                    # only the bonds this layer rewrote can differ first; an older difference
+                    # stays visible until its bond is updated again
+                    dist = _cut_distance(infos[b - 1], chi) if (b - 1) in infos else None
+                    mism.append((layer, b, dist))
+            layer += 1
+    return g, st, mism
 
 
 @pytest.mark.parametrize("name", ["tf32", "bf16x3"])
 def test_xxz_mixed_precision_observables(gpu_lib, name):
     L = 16
-    g, st, same = _run(gpu_lib, L, 2, W.neel_occupations(L), tebd.xxz_gates(L, 0.5, 0.05), 20, 64, 1e-10,
+    g, st, mism = _run(gpu_lib, L, 2, W.neel_occupations(L), tebd.xxz_gates(L, 0.5, 0.05), 20, 64, 1e-10,
                        _prec(gpu_lib, name))
-    print(f"XXZ {name}: fraction of layers with the oracle's bond tables {same:.3f}")
-    assert same >= 0.9
     t = TOL[name]
+    print(f"XXZ {name}: bonds differing from the oracle's tables (layer, bond, cut distance): {mism}")
+    if name == "bf16x3":
+        assert mism == []
+    else:
+        # every difference at a bond the layer rewrote comes from a cut the mode cannot
+        # resolve; a bond the layer did not touch (None) can only carry an earlier difference
+        seen = set()
+        for layer, b, dist in mism:
+            if dist is None:
+                assert b in seen, (layer, b)
+            else:
+                assert dist <= t["obs"], (layer, b, dist)
+            seen.add(b)
     dz = max(abs(g.expect(s, [-0.5, 0.5]) - st.expect_local(s, [-0.5, 0.5])) for s in range(L))
     dS = max(abs(g.entropy(b) - st.entropy(b)) for b in range(1, L))
     assert dz <= t["obs"], dz
@@ -85,9 +116,9 @@ def test_xxz_mixed_precision_observables(gpu_lib, name):
 @pytest.mark.parametrize("name", ["tf32", "bf16x3"])
 def test_bose_hubbard_mixed_precision_observables(gpu_lib, name):
     L, d = 12, 5
-    g, st, same = _run(gpu_lib, L, d, W.mott_occupations(L), tebd.bh_gates(L, d, 1.0, 2.0, 0.05), 8, 24, 1e-10,
+    g, st, mism = _run(gpu_lib, L, d, W.mott_occupations(L), tebd.bh_gates(L, d, 1.0, 2.0, 0.05), 8, 24, 1e-10,
                        _prec(gpu_lib, name))
-    print(f"Bose-Hubbard {name}: fraction of layers with the oracle's bond tables {same:.3f}")
+    print(f"Bose-Hubbard {name}: bonds differing from the oracle's tables: {len(mism)}")
     t = TOL[name]
     n_op = np.arange(d)
     dn = max(abs(g.expect(s, n_op) - st.expect_local(s, n_op)) for s in range(L))

@@ -14,6 +14,8 @@ synthetic and seeded (numpy PCG64).
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 __all__ = [
@@ -144,14 +146,25 @@ def serving_requests(n: int, seed: int = 0, rate_hz: float = 1.0, L_choices=(32,
     return out
 
 
+@functools.lru_cache(maxsize=None)
+def _string_table(n_sites: int, d: int) -> tuple:
+    """Row n of the table is the count of occupation strings of n sites (0..d-1 each)
+    for every total q = 0..n (d-1); built once per (n_sites, d) by adding one site at a
+    time (exact integers)."""
+    rows = [(1,)]
+    for n in range(1, n_sites + 1):
+        prev = rows[-1]
+        qmax = n * (d - 1)
+        rows.append(tuple(sum(prev[q - i] for i in range(d) if 0 <= q - i < len(prev))
+                          for q in range(qmax + 1)))
+    return tuple(rows)
+
+
 def _strings(n_sites: int, d: int, q: int) -> int:
     """Number of occupation strings of n_sites sites (0..d-1 each) summing to q."""
     if q < 0 or q > n_sites * (d - 1):
         return 0
-    ways = [1] + [0] * q
-    for _ in range(n_sites):
-        ways = [sum(ways[q2 - i] for i in range(d) if q2 - i >= 0) for q2 in range(q + 1)]
-    return ways[q]
+    return _string_table(max(n_sites, 1), d)[n_sites][q]
 
 
 def saturated_sector_dims(L: int, d: int, N: int, b: int, chi: int) -> dict:
