@@ -58,7 +58,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # fallback of the measured peaks when MEASURED_PEAKS.json is absent (one earlier GB300 measurement)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 KERNEL_BOUND = {"theta": "alu", "svd": "alu", "gemm": "alu", "select": "hbm", "lambda": "hbm",
-                "scatter": "hbm", "expect": "hbm", "amplitude": "alu"}
+                "scatter": "hbm", "expect": "hbm", "amplitude": "alu", "sample": "alu"}
 
 
 def measured_peaks():

@@ -86,6 +86,20 @@ typedef struct mps_s* mps_t;
 MPS_API int mps_create(mps_t* out, int L, int d, const int32_t* site_charges,
                int precision, int chi_max, void* cuda_stream);
 
+/*
+ * mps_create_segment - as mps_create, for a handle that holds only the sites
+ * site_lo..site_hi-1 of the chain (0 <= site_lo < site_hi <= L): every other site keeps
+ * the one element of its product-state block, so the arena is sized for the held sites
+ * only.  An update, mps_set_site or mps_load that would grow a site outside the range
+ * fails with MPS_ENOMEM (capacity exceeded) and leaves the state unchanged.  This is the
+ * per-rank handle of a chain split into contiguous segments (Sec. II distributes
+ * independent two-site updates across GPUs): a rank holds its own sites and one ghost
+ * site beyond each cut.  Errors: as mps_create, and MPS_EINVAL for an empty or
+ * out-of-range site range.
+ */
+MPS_API int mps_create_segment(mps_t* out, int L, int d, const int32_t* site_charges, int site_lo,
+                               int site_hi, int precision, int chi_max, void* cuda_stream);
+
 /* mps_destroy - frees the handle and its device memory (after its stream drains). */
 MPS_API int mps_destroy(mps_t h);
 
@@ -188,6 +202,30 @@ MPS_API int mps_amplitude(mps_t h, const int32_t* config, double out_complex[2])
 MPS_API int mps_amplitude_batch(mps_t h, int n, const int32_t* configs, double* out);
 
 /*
+ * mps_sample - n occupation patterns drawn from the state by sequential conditional
+ * sampling (a follow-on of the U(1) amplitude formula of Sec. II, where the charges pick
+ * one block per site).  In the right-canonical form the sites right of a bond form an
+ * isometry, so the probability of a prefix i_0..i_{s-1} is |v_s|^2 with
+ * v_s = B^[0][c_0, c_1] ... B^[s-1][c_{s-1}, c_s].  At site s every occupation i with a
+ * block (c_s, c_s - i) has weight w_i = |v_s B^[s][c_s, c_s - i]|^2; the conditional
+ * probability is w_i / sum_j w_j, and the drawn i is the first occupation, ascending,
+ * whose cumulative conditional probability exceeds uniforms[k L + s]; v is then advanced
+ * and rescaled to unit norm.
+ *   uniforms     host array of n x L numbers in [0, 1), row-major (sample k, site s):
+ *                the random draws are the caller's, so runs are reproducible
+ *   configs_out  host int32 array of n x L occupations (row-major)
+ *   probs_out    host array of n values (may be NULL): the product of the conditionals
+ *                of each drawn pattern; on an exactly canonical, untruncated state it is
+ *                |<pattern|psi>|^2
+ * Work is one CTA per sample on the device; the call returns when the results are on the
+ * host.  Errors: MPS_EINVAL (bad arguments, a site awaiting mps_set_site, a uniform
+ * outside [0, 1), or a prefix whose continuations all have zero weight: that sample's
+ * occupations from the failing site on are -1 and its probability 0), MPS_ENOMEM,
+ * MPS_ECUDA.
+ */
+MPS_API int mps_sample(mps_t h, int n, const double* uniforms, int32_t* configs_out, double* probs_out);
+
+/*
  * mps_bond_spectrum - the sectors of bond b (0..L): charges and dims ascending by
  * charge, and lambda values sector by sector (each sector descending).
  *   cap    capacity of charges/dims (sectors); lambda must hold the bond dimension
@@ -222,8 +260,11 @@ MPS_API int mps_get_site(mps_t h, int site, int32_t* lcharges, int32_t* mcharges
  * mps_set_site - replace the blocks of site s; the blocks must be exactly the
  *   allowed (l, m) pairs of the current tables of bonds s and s+1, in (l, m)
  *   ascending order, with data laid out as in mps_get_site.
- * Together they load an arbitrary state (for checkpoints and tests); set every
- * bond first, then every site whose neighbouring bonds changed.
+ * Together they load an arbitrary state (for checkpoints, tests and the ghost sites of
+ * a segmented chain); set every bond first, then every site whose neighbouring bonds
+ * changed.  mps_set_bond clears the deflation history of that bond only (the previous
+ * cut an update of the bond would deflate from, see mps_apply_gate2); mps_set_site
+ * keeps every bond's history.
  */
 MPS_API int mps_set_bond(mps_t h, int bond, int n_sectors, const int32_t* charges, const int32_t* dims,
                  const double* lambda);
@@ -253,6 +294,8 @@ MPS_API int mps_deflation_stats(mps_t h, int64_t* deflated_updates, int64_t* red
  *   SELECT  global top-chi truncation across sectors
  *   LAMBDA, SCATTER, GEMM  reassembly of lambda, B^[s+1] and B^[s]
  *   EXPECT, AMPLITUDE      measurements
+ *   SAMPLE                 sequential pattern sampling (mps_sample; its work depends on the
+ *                          drawn patterns and is counted as 0)
  */
 #define MPS_K_THETA 0
 #define MPS_K_SVD 1
@@ -262,7 +305,8 @@ MPS_API int mps_deflation_stats(mps_t h, int64_t* deflated_updates, int64_t* red
 #define MPS_K_GEMM 5
 #define MPS_K_EXPECT 6
 #define MPS_K_AMPLITUDE 7
-#define MPS_K_COUNT 8
+#define MPS_K_SAMPLE 8
+#define MPS_K_COUNT 9
 
 /*
  * mps_set_profiling - when on, every kernel launch of h is bracketed by CUDA events

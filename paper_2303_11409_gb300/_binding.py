@@ -19,7 +19,7 @@ MPS_OK, MPS_EINVAL, MPS_ECHARGE, MPS_ENOMEM, MPS_ENOCONV, MPS_ECUDA, MPS_ETIMEOU
 MPS_FP64, MPS_TF32, MPS_BF16X3 = 0, 1, 2
 MPS_MAX_D = 8
 MPS_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
-KERNEL_KINDS = ("theta", "svd", "select", "lambda", "scatter", "gemm", "expect", "amplitude")
+KERNEL_KINDS = ("theta", "svd", "select", "lambda", "scatter", "gemm", "expect", "amplitude", "sample")
 STATUS_NAMES = {0: "MPS_OK", -1: "MPS_EINVAL", -2: "MPS_ECHARGE", -3: "MPS_ENOMEM", -4: "MPS_ENOCONV",
                 -5: "MPS_ECUDA", -6: "MPS_ETIMEOUT"}
 
@@ -54,6 +54,8 @@ _h = ctypes.c_void_p
 _SIGS = {
     "mps_create": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int,
                                   ctypes.c_int, _vp]),
+    "mps_create_segment": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
     "mps_destroy": (ctypes.c_int, [_h]),
     "mps_last_error": (ctypes.c_char_p, [_h]),
     "mps_info": (ctypes.c_int, [_h, _intp, _intp, _intp, _intp, _intp]),
@@ -70,6 +72,7 @@ _SIGS = {
     "mps_expect": (ctypes.c_int, [_h, ctypes.c_int, _dblp, _dblp]),
     "mps_amplitude": (ctypes.c_int, [_h, _i32p, _dblp]),
     "mps_amplitude_batch": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _dblp]),
+    "mps_sample": (ctypes.c_int, [_h, ctypes.c_int, _dblp, _i32p, _dblp]),
     "mps_bond_spectrum": (ctypes.c_int, [_h, ctypes.c_int, _i32p, _i32p, _dblp, ctypes.c_int, _intp]),
     "mps_bond_entropy": (ctypes.c_int, [_h, ctypes.c_int, _dblp]),
     "mps_save": (ctypes.c_int, [_h, ctypes.c_char_p]),
@@ -257,6 +260,16 @@ class MPS:
         self._check(lib.mps_amplitude_batch(self._h, len(c), _ptr(c, _i32p), _ptr(out, _dblp)),
                     "mps_amplitude_batch")
         return out[:, 0] + 1j * out[:, 1]
+
+    def sample(self, uniforms):
+        """Patterns drawn by sequential conditional sampling (mps_sample) with the given
+        n x L uniform numbers in [0, 1); returns (patterns (n, L) int32, probabilities (n,))."""
+        u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64)).reshape(-1, self.L)
+        n = len(u)
+        cfg = np.zeros((n, self.L), np.int32)
+        pr = np.zeros(n)
+        self._check(lib.mps_sample(self._h, n, _ptr(u, _dblp), _ptr(cfg, _i32p), _ptr(pr, _dblp)), "mps_sample")
+        return cfg, pr
 
     def bond(self, b: int):
         """(charges, dims, lambda per charge) of bond b."""

@@ -704,27 +704,54 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   const SelectResult* res = (const SelectResult*)((char*)owner->pin_out.p + (res_off - kept_off));
 
   // ---- deflation check: an update whose new cut fell below kChiVerify x the estimate its
-  // SVDs were deflated with has the batch's SVDs and selection redone without that level ----
+  // SVDs were deflated with has its own SVDs redone without that level, then the selection
+  // of the batch is repeated (the other updates' spectra are unchanged, so their selections
+  // are too).  Redoing only the failing updates keeps every result independent of which
+  // other updates share the batch. ----
   {
+    std::vector<char> redo_upd(nreq, 0);
     bool redo = false;
     for (int u = 0; u < nreq; ++u) {
       if (W[u].cut_est <= 0.0) continue;
       reqs[u].h->stats.deflated_updates++;
-      if (res[u].status == 0 && res[u].cut < kChiVerify * W[u].cut_est) redo = true;
+      if (res[u].status == 0 && res[u].cut < kChiVerify * W[u].cut_est) redo = redo_upd[u] = 1;
     }
     if (redo) {
-      std::vector<SvdSector>& v = svd_sorted[c_used];
-      for (SvdSector& S : v) S.floor_abs = 0.0;
+      // the update of each sector, from the position of its status word
+      const int* status0 = reinterpret_cast<const int*>(dptr(status_off));
+      std::vector<int> upd_of(n_sec_total, 0);
+      for (int u = 0; u < nreq; ++u)
+        for (size_t si = 0; si < W[u].plan.sectors.size(); ++si) upd_of[W[u].sel_first + si] = u;
+      std::vector<SvdSector> sub;
+      double sub_flops = 0, sub_bytes = 0;
+      for (const SvdSector& S : svd_sorted[c_used]) {
+        if (!redo_upd[upd_of[S.status - status0]]) continue;
+        SvdSector T = S;
+        T.floor_abs = 0.0;
+        sub.push_back(T);
+        const double a = std::max(S.m, S.n), b = std::min(S.m, S.n);
+        sub_flops += 4.0 * (6.0 * a * b * b + 20.0 * b * b * b);
+        sub_bytes += 16.0 * S.m * S.n + 16.0 * S.n * b + 8.0 * b + 8.0 * S.m;
+      }
+      std::vector<SvdGroup> sub_groups;
+      // the tile shape the first run used for these sectors
+      const SvdTune tune = n_cand > 1 ? svd_tune_candidate(c_used) : (chosen >= 0 ? svd_tune_candidate(chosen) : SvdTune());
+      CUDA_OR_FAIL(owner, svd_group(sub, sub_groups, tune));
+      // the phase-1 SVD descriptors are no longer read (the stream is synchronised): reuse them
       char* hsrc = (char*)owner->pin_in.p + o_svd[c_used];
-      std::memcpy(hsrc, v.data(), sizeof(SvdSector) * v.size());
-      CUDA_OR_FAIL(owner, cudaMemcpyAsync(dptr(desc_off + o_svd[c_used]), hsrc, sizeof(SvdSector) * v.size(),
+      std::memcpy(hsrc, sub.data(), sizeof(SvdSector) * sub.size());
+      CUDA_OR_FAIL(owner, cudaMemcpyAsync(dptr(desc_off + o_svd[c_used]), hsrc, sizeof(SvdSector) * sub.size(),
                                           cudaMemcpyHostToDevice, st));
-      CUDA_OR_FAIL(owner, timed(owner, MPS_K_SVD, true, svd_flops, svd_bytes, [&] { return svd_launch(c_used); }));
+      const SvdSector* d_sub = reinterpret_cast<SvdSector*>(dptr(desc_off + o_svd[c_used]));
+      CUDA_OR_FAIL(owner, timed(owner, MPS_K_SVD, !sub.empty(), sub_flops, sub_bytes, [&] {
+        return launch_svd_groups(d_sub, sub_groups, st, owner->side, kSvdSideStreams, owner->fork, owner->join,
+                                 owner->sweep_limit);
+      }));
       CUDA_OR_FAIL(owner, select_and_readback());
       CUDA_OR_FAIL(owner, cudaStreamSynchronize(st));
       resolve_pending(owner);
       for (int u = 0; u < nreq; ++u)
-        if (W[u].cut_est > 0.0) reqs[u].h->stats.deflation_redos++;
+        if (redo_upd[u]) reqs[u].h->stats.deflation_redos++;
     }
   }
 
@@ -955,8 +982,25 @@ int check_gate_args(mps_s* h, int site, const double* gate, int chi, double cuto
 // ======================================================================================
 extern "C" {
 
+static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, int site_lo, int site_hi,
+                         int precision, int chi_max, void* cuda_stream);
+
 int mps_create(mps_t* out, int L, int d, const int32_t* site_charges, int precision, int chi_max,
                void* cuda_stream) {
+  return create_handle(out, L, d, site_charges, 0, L, precision, chi_max, cuda_stream);
+}
+
+int mps_create_segment(mps_t* out, int L, int d, const int32_t* site_charges, int site_lo, int site_hi,
+                       int precision, int chi_max, void* cuda_stream) {
+  if (site_lo < 0 || site_hi > L || site_hi - site_lo < 1) {
+    if (out) *out = nullptr;
+    return MPS_EINVAL;
+  }
+  return create_handle(out, L, d, site_charges, site_lo, site_hi, precision, chi_max, cuda_stream);
+}
+
+static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, int site_lo, int site_hi,
+                         int precision, int chi_max, void* cuda_stream) {
   if (!out) return MPS_EINVAL;
   *out = nullptr;
   if (L < 2 || d < 2 || d > MPS_MAX_D || chi_max < 1 || !site_charges) return MPS_EINVAL;
@@ -996,7 +1040,8 @@ int mps_create(mps_t* out, int L, int d, const int32_t* site_charges, int precis
   int64_t site_total = 0;
   for (int s = 0; s < L; ++s) {
     layout_site(h->bonds[s], h->bonds[s + 1], d, h->sites[s]);
-    h->site_cap[s] = std::max<int64_t>(1, h->bond_cap[s] * h->bond_cap[s + 1]);
+    // sites outside [site_lo, site_hi) keep their one product-state element and never grow
+    h->site_cap[s] = (s >= site_lo && s < site_hi) ? std::max<int64_t>(1, h->bond_cap[s] * h->bond_cap[s + 1]) : 1;
     h->site_base[s] = site_total;
     site_total += 2 * ((h->site_cap[s] + 15) / 16 * 16);
   }
@@ -1291,6 +1336,72 @@ int mps_amplitude_batch(mps_t h, int n, const int32_t* configs, double* out) {
   return MPS_OK;
 }
 
+int mps_sample(mps_t h, int n, const double* uniforms, int32_t* configs_out, double* probs_out) {
+  if (check_handle(h)) return MPS_EINVAL;
+  if (n < 0 || (n > 0 && (!uniforms || !configs_out))) return fail(h, MPS_EINVAL, "bad sample arguments");
+  if (n == 0) return MPS_OK;
+  for (int s = 0; s < h->L; ++s)
+    if (h->dirty[s]) return check_site_ready(h, s);
+  const int L = h->L, d = h->d;
+  for (int64_t k = 0; k < (int64_t)n * L; ++k)
+    if (!(uniforms[k] >= 0.0 && uniforms[k] < 1.0)) return fail(h, MPS_EINVAL, "uniforms must lie in [0, 1)");
+  // per site, per charge of its left bond, per occupation: the block and the next charge's index
+  std::vector<int> site_off(L);
+  std::vector<SampleEntry> table;
+  int cap = 1;
+  for (int s = 0; s < L; ++s) {
+    const BondTable &Lb = h->bonds[s], &Rb = h->bonds[s + 1];
+    cap = std::max(cap, std::max(Lb.total(), Rb.total()));
+    site_off[s] = (int)table.size();
+    const double2* slot = h->slot_ptr(s, h->cur[s]);
+    for (int li = 0; li < Lb.size(); ++li)
+      for (int i = 0; i < d; ++i) {
+        SampleEntry e{nullptr, 0, 0, -1, 0};
+        const int bi = h->sites[s].find(Lb.charge[li], Lb.charge[li] - i);
+        if (bi >= 0) {
+          const SiteBlock& B = h->sites[s].blocks[bi];
+          e.blk = slot + B.off;
+          e.Dl = B.Dl;
+          e.Dm = B.Dm;
+          e.next = B.im;
+        }
+        table.push_back(e);
+      }
+  }
+  const int64_t b_table = a256(sizeof(SampleEntry) * (int64_t)table.size());
+  const int64_t b_off = a256(sizeof(int) * (int64_t)L);
+  const int64_t b_u = a256(8 * (int64_t)n * L);
+  const int64_t b_cfg = a256(4 * (int64_t)n * L);
+  const int64_t b_prob = a256(8 * (int64_t)n);
+  const int64_t in_bytes = b_table + b_off + b_u;
+  CUDA_OR_FAIL(h, cudaEventSynchronize(h->staged));
+  if (h->work.reserve(in_bytes + b_cfg + b_prob) != cudaSuccess) return fail(h, MPS_ENOMEM, "workspace");
+  if (h->pin_in.reserve(in_bytes) != cudaSuccess || h->pin_out.reserve(b_cfg + b_prob) != cudaSuccess)
+    return fail(h, MPS_ENOMEM, "pinned staging");
+  char* hp = (char*)h->pin_in.p;
+  std::memcpy(hp, table.data(), sizeof(SampleEntry) * table.size());
+  std::memcpy(hp + b_table, site_off.data(), sizeof(int) * L);
+  std::memcpy(hp + b_table + b_off, uniforms, 8 * (size_t)n * L);
+  char* base = (char*)h->work.p;
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(base, hp, in_bytes, cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaEventRecord(h->staged, h->stream));
+  int* d_cfg = reinterpret_cast<int*>(base + in_bytes);
+  double* d_prob = reinterpret_cast<double*>(base + in_bytes + b_cfg);
+  // the work depends on the drawn patterns (the blocks visited), so none is counted
+  CUDA_OR_FAIL(h, timed(h, MPS_K_SAMPLE, true, 0.0, 0.0, [&] {
+    return launch_sample(reinterpret_cast<SampleEntry*>(base), reinterpret_cast<int*>(base + b_table), L, d, cap,
+                         reinterpret_cast<double*>(base + b_table + b_off), n, d_cfg, d_prob, h->stream);
+  }));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->pin_out.p, d_cfg, b_cfg + b_prob, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  std::memcpy(configs_out, h->pin_out.p, 4 * (size_t)n * L);
+  const double* pr = reinterpret_cast<const double*>((char*)h->pin_out.p + b_cfg);
+  if (probs_out) std::memcpy(probs_out, pr, 8 * (size_t)n);
+  for (int k = 0; k < n; ++k)
+    if (pr[k] == 0.0) return fail(h, MPS_EINVAL, "a sample reached a prefix whose continuations have zero weight");
+  return MPS_OK;
+}
+
 int mps_amplitude(mps_t h, const int32_t* config, double out_complex[2]) {
   return mps_amplitude_batch(h, 1, config, out_complex);
 }
@@ -1363,7 +1474,7 @@ int mps_set_bond(mps_t h, int bond, int n_sectors, const int32_t* charges, const
   h->bonds[bond] = t;
   h->dirty[bond - 1] = 1;
   h->dirty[bond] = 1;
-  std::fill(h->cut_est.begin(), h->cut_est.end(), 0.0);   // a loaded state has no deflation history
+  h->cut_est[bond] = 0.0;   // a loaded bond has no deflation history (the other bonds keep theirs)
   return MPS_OK;
 }
 
@@ -1386,7 +1497,6 @@ int mps_set_site(mps_t h, int site, int n_blocks, const int32_t* lcharges, const
                                cudaMemcpyHostToDevice));
   h->sites[site] = t;
   h->dirty[site] = 0;
-  std::fill(h->cut_est.begin(), h->cut_est.end(), 0.0);
   return MPS_OK;
 }
 

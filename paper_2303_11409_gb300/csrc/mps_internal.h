@@ -277,6 +277,12 @@ cudaError_t launch_lambda(const LambdaTask* d_tasks, int n_tasks, cudaStream_t s
 struct ExpectTask { const double2* blk; const double* lam; int Dl, Dm; double w; };
 cudaError_t launch_expect(const ExpectTask* d_tasks, int n_tasks, double* d_partial, cudaStream_t st);
 struct AmpStep { const double2* blk; int Dl, Dm; };
+// Sequential pattern sampling: entry [site_off[s] + li * d + i] is the block (c, c - i) of site
+// s for the li-th charge c of bond s (blk == nullptr when absent) and the index of c - i in
+// bond s+1's table.
+struct SampleEntry { const double2* blk; int Dl, Dm; int next; int pad; };
+cudaError_t launch_sample(const SampleEntry* d_table, const int* d_site_off, int L, int d, int cap,
+                          const double* d_uniforms, int n, int* d_configs, double* d_probs, cudaStream_t st);
 // -sum lambda^2 ln lambda^2 over n values into *d_out (one CTA).
 cudaError_t launch_entropy(const double* d_lambda, int n, double* d_out, cudaStream_t st);
 cudaError_t launch_amplitude(const AmpStep* d_steps, int L, int n_cfg, double2* d_out, int chi_max,

@@ -86,14 +86,19 @@ def test_tf32_operand_rounding(gpu_lib):
     C = m.zgemm_tc(A, np.ones((1, 1), np.complex128), precision=m.MPS_TF32)
     got = C[:, 0].real
     want = _tf32_rna(_f32_rn_flush(x)).astype(np.float64)
-    nan = np.isnan(want)
-    assert np.array_equal(np.isnan(got), nan)
-    bad = np.nonzero(got[~nan] != want[~nan])[0]
-    assert bad.size == 0, [(x[~nan][i], got[~nan][i], want[~nan][i]) for i in bad[:8]]
+    # an operand the conversion makes infinite or NaN gives a non-finite product (how the
+    # tensor core combines inf and NaN with the zero terms of the lowered GEMM is its own
+    # business); every finite operand must come out exactly as modelled
+    fin = np.isfinite(want)
+    assert np.all(~np.isfinite(got[~fin])), [(x[i], got[i]) for i in np.nonzero(~fin)[0]]
+    bad = np.nonzero(got[fin] != want[fin])[0]
+    assert bad.size == 0, [(x[fin][i], got[fin][i], want[fin][i]) for i in bad[:8]]
+    # the overflow cases are among the non-finite ones, the subnormal ones among the zeros
+    assert np.count_nonzero(~fin) >= 7
     # the tie cases do decide: truncating instead of rounding would change some results
     trunc = (x.view(np.uint64) & np.uint64(0xFFFFFFFFE0000000)).view(np.float64)
     alt = _tf32_rna(_f32_rn_flush(trunc)).astype(np.float64)
-    assert np.any((alt != want) & ~nan)
+    assert np.any((alt != want) & fin)
 
 
 def test_bf16x3_operand_rounding(gpu_lib):

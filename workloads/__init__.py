@@ -32,6 +32,7 @@ __all__ = [
     "random_u1_gate",
     "saturated_sector_dims",
     "saturated_random_state",
+    "uniforms",
 ]
 
 
@@ -107,6 +108,13 @@ def random_u1_gate(d: int, rng: np.random.Generator) -> list[np.ndarray]:
         size = min(d - 1, n) - max(0, n - d + 1) + 1
         blocks.append(haar_unitary(size, rng))
     return blocks
+
+
+def uniforms(n: int, L: int, seed: int = 0) -> np.ndarray:
+    """n x L uniform numbers in [0, 1) (numpy PCG64(seed)): the random draws of pattern
+    sampling, one per site per sample, handed to both the CUDA path and the oracle."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.random((n, L))
 
 
 def random_occupations(L: int, d: int, N: int, rng: np.random.Generator) -> list[int]:
