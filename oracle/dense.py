@@ -77,3 +77,27 @@ def bond_entropy(psi: np.ndarray, b: int) -> float:
 def schmidt_values(psi: np.ndarray, b: int) -> np.ndarray:
     d = psi.shape[0]
     return np.linalg.svd(psi.reshape(d ** b, -1), compute_uv=False)
+
+
+def clock_ops(n: int):
+    """Z_n clock operators in the charge basis: X = diag(w^k), Z|k> = |k+1 mod n>."""
+    X = np.diag(np.exp(2j * np.pi * np.arange(n) / n))
+    Z = np.roll(np.eye(n), 1, axis=0)
+    return X, Z
+
+
+def clock_two_site(n: int, J: float, f: float, w_left: float, w_right: float) -> np.ndarray:
+    """-J (Z1 Z2^dag + h.c.) - f (w1 (X1 + X1^dag) + w2 (X2 + X2^dag)) by Kronecker products."""
+    X, Z = clock_ops(n)
+    eye = np.eye(n)
+    zz = np.kron(Z, Z.conj().T)
+    xx = X + X.conj().T
+    return -J * (zz + zz.conj().T) - f * (w_left * np.kron(xx, eye) + w_right * np.kron(eye, xx))
+
+
+def mean_op(psi: np.ndarray, s: int, diag: np.ndarray) -> float:
+    """<psi| O_s |psi> / <psi|psi> for O diagonal in the local basis."""
+    p = np.abs(psi) ** 2
+    axes = tuple(a for a in range(psi.ndim) if a != s)
+    marg = p.sum(axis=axes)
+    return float(np.dot(marg, diag) / p.sum())

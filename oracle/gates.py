@@ -124,3 +124,36 @@ def beam_splitter_gate(theta: float, phi: float, d: int):
 def flatten_blocks(blocks) -> np.ndarray:
     """Blocks n = 0..2(d-1), each row-major, concatenated as complex128."""
     return np.concatenate([np.asarray(b, dtype=np.complex128).reshape(-1) for b in blocks])
+
+
+# ---------------------------------------------------------------------------
+# Z_n clock chain (the Z_n-symmetric example; n = 2 is the transverse-field Ising chain)
+# ---------------------------------------------------------------------------
+
+def clock_h_blocks(n: int, J: float, f: float, w_left: float, w_right: float):
+    """h = -J (Z1 Z2^dag + Z1^dag Z2) - f (w1 (X1 + X1^dag) + w2 (X2 + X2^dag)) by Z_n charge.
+
+    Local basis |k>, k = 0..n-1, is the Z_n charge: X|k> = w^k |k> (w = exp(2 pi i / n)),
+    so X + X^dag = diag(2 cos(2 pi k / n)), and Z|k> = |k+1 mod n> shifts the charge, so
+    Z1 Z2^dag conserves the pair's total (i + j) mod n.  Block q acts on (i, (q - i) mod n),
+    i ascending.  w1, w2 count each on-site term once per step (as for Bose-Hubbard).
+    """
+    xs = 2.0 * np.cos(2.0 * np.pi * np.arange(n) / n)
+    blocks = []
+    for q in range(n):
+        basis = [(i, (q - i) % n) for i in range(n)]
+        idx = {b: a for a, b in enumerate(basis)}
+        h = np.zeros((n, n))
+        for a, (i, j) in enumerate(basis):
+            h[a, a] = -f * (w_left * xs[i] + w_right * xs[j])
+            for di in (1, -1):           # Z1 Z2^dag: (i, j) -> (i+1, j-1); its adjoint the reverse
+                b = idx[((i + di) % n, (j - di) % n)]
+                h[b, a] += -J
+        blocks.append(h)
+    return blocks
+
+
+def clock_gate(L: int, s: int, n: int, J: float, f: float, tau: float):
+    """exp(-i h tau) per Z_n block for the bond (s, s+1), chain-end weights as bh_weights."""
+    wl, wr = bh_weights(L, s)
+    return [_expm_hermitian(h, tau) for h in clock_h_blocks(n, J, f, wl, wr)]
