@@ -7,8 +7,9 @@ dt=0.02, chi<=2048, cutoff 1e-10, sector GEMMs (the Theta' build and the reassem
 product) in TF32 on the tensor cores with FP32 accumulation, SVD, truncation and
 renormalisation in FP64.  The chain starts saturated: every inner bond at chi spread
 over its charges in proportion to the Hilbert-space bound of each charge, random
-complex blocks (seeded), positive Schmidt weights (evolving the Mott state to
-saturation at chi=2048 would take hours).  A "step" is one whole Strang layer of
+complex blocks (seeded), Schmidt weights exp(-0.3 (ln k)^2) for k = 1..chi dealt to the
+sectors at random (the decay of an evolved Bose-Hubbard middle-bond spectrum; evolving
+the Mott state to saturation at chi=2048 would take hours).  A "step" is one whole Strang layer of
 that chain: the odd bonds with dt/2, the even bonds with dt, the odd bonds with dt/2,
 in turn (64, 63, 64 two-site updates), each update running the whole path (planner,
 Theta' build, per-sector SVD, global top-chi, reassembly, renormalisation).  The
@@ -40,7 +41,7 @@ D, J, U, DT, CUTOFF = 5, 1.0, 2.0, 0.02, 1e-10
 METRIC = "two-site updates/s"
 CASES = {
     # the configuration of record: L=128, chi<=2048, mixed-precision sector GEMMs
-    "bh128": dict(L=128, N=128, CHI=2048, precision="tf32", start="saturated",
+    "bh128": dict(L=128, N=128, CHI=2048, precision="tf32", start="saturated", beta=0.3,
                   workload="bose_hubbard_L128_nmax4_N128_J1_U2_dt0.02_chi2048_cutoff1e-10"),
     # L=64, chi<=512, FP64, evolved from the Mott state until the middle bond reaches chi
     "bh64": dict(L=64, N=64, CHI=512, precision="fp64", start="evolved",
@@ -58,6 +59,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # fallback of the measured peaks when MEASURED_PEAKS.json is absent (one earlier GB300 measurement)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 KERNEL_BOUND = {"theta": "alu", "svd": "alu", "gemm": "alu", "select": "hbm", "lambda": "hbm",
+                "tcgemm": "tensor", "shadow": "hbm",
                 "scatter": "hbm", "expect": "hbm", "amplitude": "alu", "sample": "alu"}
 
 
@@ -94,7 +96,7 @@ def parse():
     p.add_argument("--max-prep", type=int, default=120)
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement (at most --steps)")
+    p.add_argument("--e2e-steps", type=int, default=1, help="steps of the end-to-end measurement (at most --steps)")
     p.add_argument("--serve", action="store_true",
                    help="serving workload instead: continuous batching vs the plain one-request-at-a-time form")
     p.add_argument("--serve-requests", type=int, default=48)
@@ -103,6 +105,11 @@ def parse():
     p.add_argument("--graphs", type=int, default=1, help="capture each update call's launch phases in CUDA graphs")
     p.add_argument("--autotune", type=int, default=0,
                    help="SVD tile shape chosen per sector-size histogram (tuning runs happen before the timed steps)")
+    p.add_argument("--chi-deflation", type=float, default=3e-4,
+                   help="second SVD deflation level: values below this fraction of a bond's previous chi cut are "
+                        "left unresolved (the update is redone if its cut falls below level / 6e-4 of it); 0: off")
+    p.add_argument("--svd-candidate", type=int, default=-1,
+                   help="force one SVD tile-shape candidate (0..11) for every update call (-1: the default rule)")
     a = p.parse_args()
     a.cfg = CASES[a.case]
     if a.precision is None:
@@ -125,8 +132,9 @@ def config_of(a, extra=None):
                "N": c["N"], "J": J, "U": U, "dt": DT, "chi": c["CHI"], "cutoff": CUTOFF,
                "step": "one Strang layer (odd dt/2, even dt, odd dt/2 in turn): all of its two-site updates",
                "regime": ("synthetic saturated chain (every inner bond at chi spread over its charges in proportion "
-                          "to the Hilbert bound; seeded random complex blocks and positive Schmidt weights; not "
-                          "canonical)" if c["start"] == "saturated" else
+                          "to the Hilbert bound; seeded random complex blocks; Schmidt weights exp(-0.3 (ln k)^2), "
+                          "k = 1..chi, dealt to the sectors at random, the decay of an evolved Bose-Hubbard "
+                          "spectrum; not canonical)" if c["start"] == "saturated" else
                           "saturated (timed layers follow untimed Trotter steps from the Mott state until the "
                           "middle bond reaches chi)")}
     out["sector_gemms"] = a.precision
@@ -240,9 +248,9 @@ _STATE = {}
 def saturated_chain(cfg):
     """(lam, blocks) of the seeded synthetic saturated chain (built once per process)."""
     import workloads as W
-    key = (cfg["L"], cfg["N"], cfg["CHI"])
+    key = (cfg["L"], cfg["N"], cfg["CHI"], cfg.get("beta"))
     if key not in _STATE:
-        _STATE[key] = W.saturated_random_state(cfg["L"], D, cfg["N"], cfg["CHI"], seed=0)
+        _STATE[key] = W.saturated_random_state(cfg["L"], D, cfg["N"], cfg["CHI"], seed=0, beta=cfg.get("beta"))
     return _STATE[key]
 
 
@@ -348,6 +356,7 @@ def build_workload(args, m, W, stream, prec):
         p = m.MPS(D, occ, CHI, precision=precision, stream=stream.cuda_stream)
         p.set_graphs(bool(args.graphs))
         p.set_autotune(bool(args.autotune))
+        p.set_chi_deflation(args.chi_deflation)
         return p
 
     prep = 0
@@ -418,6 +427,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_stream(stream)
     fp64_measured = m.fp64_peak_probe(stream.cuda_stream)
     prec = {"fp64": m.MPS_FP64, "tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[args.precision]
+    if args.svd_candidate >= 0:
+        m.autotune_force(args.svd_candidate)
     psi, step, prep = build_workload(args, m, W, stream, prec)
     L = args.cfg["L"]
 
@@ -477,16 +488,23 @@ def run_ours(args, world, rank, local):
                 "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share": v["ms"] / tot_ms}
                             for k, v in ks.items() if v["launches"]}}
     if args.precision != "fp64":
-        # the tensor-core sector GEMMs (Theta' build and reassembly) against the format's peak
+        # the tensor-core sector GEMMs (the products of the Theta' build and of the reassembly,
+        # one TMA-fed kernel) against the format's peak, and against the HBM roofline of their
+        # algorithmic bytes (shadow operands read, products written)
         tpk, tsrc = tensor_peak_tflops(args.precision, peaks)
+        v = ks["tcgemm"]
         tc = {}
-        for k in ("theta", "gemm"):
-            v = ks[k]
-            if v["launches"] and v["ms"] > 0:
-                tf = v["flops"] / (v["ms"] / 1000.0) / 1e12
-                tc[k] = {"achieved": tf, "unit": "TFLOP/s", "peak": tpk, "frac": tf / tpk,
-                         "flops_per_launch": v["flops"] / v["launches"], "ms_per_launch": v["ms"] / v["launches"],
-                         "share_of_device_time": v["ms"] / tot_ms}
+        if v["launches"] and v["ms"] > 0:
+            sec = v["ms"] / 1000.0
+            tf = v["flops"] / sec / 1e12
+            ai = v["flops"] / max(v["bytes"], 1.0)
+            attainable = min(tpk, ai * peaks["hbm_gbs"] / 1000.0)
+            tc = {"kernel": "tma_zgemm_kernel", "achieved": tf, "unit": "TFLOP/s", "peak": tpk, "frac": tf / tpk,
+                  "flops_per_launch": v["flops"] / v["launches"], "ms_per_launch": v["ms"] / v["launches"],
+                  "launches": v["launches"], "bytes_per_launch": v["bytes"] / v["launches"],
+                  "arithmetic_intensity_flop_per_byte": ai, "attainable_tflops": attainable,
+                  "frac_of_attainable": tf / attainable, "achieved_gbs": v["bytes"] / sec / 1e9,
+                  "share_of_device_time": v["ms"] / tot_ms}
         roofline["tensor_gemms"] = tc
         roofline["tensor_peak_source"] = peak_src + ": " + tsrc
 

@@ -101,6 +101,20 @@ MPS_API int mps_create_segment(mps_t* out, int L, int d, const int32_t* site_cha
                                int site_hi, int precision, int chi_max, void* cuda_stream);
 
 /* mps_destroy - frees the handle and its device memory (after its stream drains). */
+/*
+ * mps_create_zn - like mps_create, for the cyclic group Z_n instead of U(1) (Sec. I names
+ * more general Abelian symmetries; the block construction of Sec. II carries over): local
+ * dimension d = n (2..MPS_MAX_D), the physical index i carries charge i mod n, bond b the
+ * right-charge (sum of the occupations right of it) mod n, and every pair of charges forms
+ * a site block (l, m) with i = (l - m) mod n.  Gate blocks for such a handle are the n blocks
+ * q = 0..n-1 of the total charge (i + j) mod n, each n x n over the pairs (i, (q - i) mod n),
+ * i ascending (rows outputs, columns inputs), concatenated row-major.  Every update, batch,
+ * observable and amplitude call works on it; mps_save / mps_load, mps_create_segment and
+ * mps_footprint_bytes are for U(1) handles only.  Errors as mps_create.
+ */
+MPS_API int mps_create_zn(mps_t* out, int L, int n, const int32_t* site_charges, int precision, int chi_max,
+                          void* cuda_stream);
+
 MPS_API int mps_destroy(mps_t h);
 
 /* mps_last_error - message of the last failing call on h ("" if none); owned by h. */
@@ -123,10 +137,11 @@ MPS_API int mps_info(mps_t h, int* L, int* d, int* N, int* chi_max, int* precisi
  * singular values below 0.01 * cutoff * |M(c)|_F (at least 100x under the cutoff
  * threshold cutoff * |sigma|_2, so discarded in any case), nor, when chi set the cut
  * of the previous update of the same bond, below 3e-4 times that relative cut
- * (smallest kept value / |sigma|_2): their columns are not rotated and they count as
- * zero.  When the new cut falls
- * under half that previous one, the call redoes its SVDs and selection without the
- * second level, so an unresolved value always lies >= 1600x under the kept ones.
+ * (smallest kept value / |sigma|_2; the level is set by mps_set_chi_deflation): their
+ * columns are not rotated and they count as zero.  When the new cut falls under
+ * level / 6e-4 of that previous one (half of it at the default level), the call redoes
+ * that update's SVDs and the selection without the second level, so an unresolved value
+ * always lies >= 1600x under the kept ones.
  * mps_deflation_stats counts updates that used the second level and those redone.
  * Errors: MPS_EINVAL, MPS_ENOMEM, MPS_ENOCONV (state updated), MPS_ECUDA.
  */
@@ -281,6 +296,18 @@ MPS_API int mps_last_update_stats(mps_t h, int* n_sectors, int* n_triples, int* 
                           int* tie_band, double* norm_all, double* norm_kept);
 
 /*
+ * mps_set_chi_deflation - the second deflation level of the updates of h (see
+ * mps_apply_gate2): singular values below level x the previous relative chi cut of the bond
+ * are left unresolved, and an update whose new cut falls below level / 6e-4 of that estimate
+ * is redone without it, so an unresolved value always lies at least 1600x under the kept ones.
+ * level 0 turns the second level off; the default is 3e-4 (a redo when the cut halves); a
+ * smaller level deflates less but redoes only after larger drops of the cut.  It applies to
+ * the updates of h whichever handle's call (or executor) runs them.  MPS_EINVAL outside
+ * [0, 6e-4].
+ */
+MPS_API int mps_set_chi_deflation(mps_t h, double level);
+
+/*
  * mps_deflation_stats - updates on h (cumulative) whose SVDs used the previous cut of
  * their bond as a deflation level, and how many of those were redone without it
  * (see mps_apply_gate2).  Either pointer may be NULL.
@@ -289,13 +316,17 @@ MPS_API int mps_deflation_stats(mps_t h, int64_t* deflated_updates, int64_t* red
 
 /*
  * Kernel kinds reported by mps_kernel_stats.
- *   THETA   Theta'(c) build: sector GEMMs with the gate mixed in (Sec. II)
+ *   THETA   Theta'(c) build: sector GEMMs with the gate mixed in (Sec. II); in the TF32 /
+ *           BF16x3 modes only the gate mix of the tensor-core products
  *   SVD     batched per-sector Jacobi SVD
  *   SELECT  global top-chi truncation across sectors
- *   LAMBDA, SCATTER, GEMM  reassembly of lambda, B^[s+1] and B^[s]
+ *   LAMBDA, SCATTER, GEMM  reassembly of lambda, B^[s+1] and B^[s] (GEMM: FP64 mode)
  *   EXPECT, AMPLITUDE      measurements
  *   SAMPLE                 sequential pattern sampling (mps_sample; its work depends on the
  *                          drawn patterns and is counted as 0)
+ *   TCGEMM  TF32 / BF16x3 modes: the tensor-core products of the Theta build and of the
+ *           reassembly (flops of the complex products)
+ *   SHADOW  TF32 / BF16x3 modes: operands converted into tensor-core shadow tiles
  */
 #define MPS_K_THETA 0
 #define MPS_K_SVD 1
@@ -306,7 +337,9 @@ MPS_API int mps_deflation_stats(mps_t h, int64_t* deflated_updates, int64_t* red
 #define MPS_K_EXPECT 6
 #define MPS_K_AMPLITUDE 7
 #define MPS_K_SAMPLE 8
-#define MPS_K_COUNT 9
+#define MPS_K_TCGEMM 9
+#define MPS_K_SHADOW 10
+#define MPS_K_COUNT 11
 
 /*
  * mps_set_profiling - when on, every kernel launch of h is bracketed by CUDA events
@@ -377,11 +410,12 @@ MPS_API int mps_graph_stats(mps_t h, int64_t* launches, int64_t* updates, int64_
  *   default shape and are not tuned (stored keys are still used).
  * mps_autotune_min_flops - the nominal SVD work (flops, >= 0) below which a batch is
  *   not tuned and uses the default shape.
- * mps_autotune_force - candidate 0..9 makes every update call of the process use that
- *   shape, whether or not autotuning is on (for tests and measurements); -1 ends it.
- *   Candidates 0..7: width {4, 6, 8, 12}[k & 3], clusters from 2 << (k >> 2); 8 and 9:
- *   width 6 from 2 CTAs, 16-CTA clusters from min(m, n) = 512 and 256.  MPS_EINVAL for
- *   any other value.
+ * mps_autotune_force - candidate 0..11 makes every update call of the process (and every
+ *   mps_svd_sectors call) use that shape, whether or not autotuning is on (for tests and
+ *   measurements); -1 ends it.  Candidates 0..7: width {4, 6, 8, 12}[k & 3], clusters
+ *   from 2 << (k >> 2); 8 and 9: width 6 from 2 CTAs, 16-CTA clusters from min(m, n) =
+ *   512 and 256; 10 and 11: the sectors from min(m, n) = 512 and 256 on the round-robin
+ *   cluster kernel instead of the block-Jacobi one.  MPS_EINVAL for any other value.
  */
 MPS_API int mps_set_autotune(mps_t h, int on);
 MPS_API int mps_autotune_stats(int64_t* keys, int64_t* tuning_runs, int64_t* hits);
@@ -416,20 +450,23 @@ MPS_API int mps_save(mps_t h, const char* path);
 MPS_API int mps_load(mps_t* out, const char* path, void* cuda_stream);
 
 /*
- * mps_zgemm_tc - the tensor-core complex GEMM kernel alone, on device memory:
+ * mps_zgemm_tc - the tensor-core complex GEMM alone, on device memory:
  * C = A B with A (M x K), B (K x N), C (M x N) complex128 row-major (leading
  * dimensions lda >= K, ldb >= N, ldc >= N, in complex numbers).  precision is
- * MPS_TF32 (inputs rounded to TF32) or MPS_BF16X3 (each input split into two BF16
- * terms, three products accumulated); the complex product is lowered to one real
- * GEMM and run by tcgen05.mma with FP32 accumulation in tensor memory.  This is the
- * kernel the reduced-precision modes use for the sector GEMMs (Sec. II names tensor
- * cores for the GPU contraction).  d_work is device scratch of at least
- * 256 + 64 * ceil(M/128) * ceil(N/64) bytes.  Returns MPS_EINVAL for another
- * precision or bad sizes, MPS_ETIMEOUT if a bounded wait inside the kernel expired.
- * Synchronises cuda_stream.
+ * MPS_TF32 (inputs rounded to FP32, then to TF32) or MPS_BF16X3 (each FP32-rounded
+ * input split into two BF16 terms, three products accumulated).  The operands are
+ * converted into shadow tiles in d_work, loaded by TMA (cp.async.bulk.tensor, 128-byte
+ * swizzle) and multiplied by tcgen05.mma with FP32 accumulation in tensor memory, the
+ * complex product lowered to one real GEMM; the result is converted to FP64 exactly.
+ * This is the path the reduced-precision modes use for the sector GEMMs (Sec. II names
+ * tensor cores for the GPU contraction).  d_work is device scratch of at least
+ * mps_zgemm_tc_work_bytes(precision, M, N, K) bytes (-1 for invalid arguments).
+ * Returns MPS_EINVAL for another precision or bad sizes, MPS_ETIMEOUT if a bounded wait
+ * inside the kernel expired.  Synchronises cuda_stream.
  */
 MPS_API int mps_zgemm_tc(int precision, int M, int N, int K, const double* d_A, int lda, const double* d_B,
                          int ldb, double* d_C, int ldc, void* d_work, int64_t work_bytes, void* cuda_stream);
+MPS_API int64_t mps_zgemm_tc_work_bytes(int precision, int M, int N, int K);
 
 /*
  * mps_fp64_peak_probe - measured FP64 FMA throughput of the current device in GFLOP/s

@@ -19,7 +19,8 @@ MPS_OK, MPS_EINVAL, MPS_ECHARGE, MPS_ENOMEM, MPS_ENOCONV, MPS_ECUDA, MPS_ETIMEOU
 MPS_FP64, MPS_TF32, MPS_BF16X3 = 0, 1, 2
 MPS_MAX_D = 8
 MPS_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
-KERNEL_KINDS = ("theta", "svd", "select", "lambda", "scatter", "gemm", "expect", "amplitude", "sample")
+KERNEL_KINDS = ("theta", "svd", "select", "lambda", "scatter", "gemm", "expect", "amplitude", "sample", "tcgemm",
+                "shadow")
 STATUS_NAMES = {0: "MPS_OK", -1: "MPS_EINVAL", -2: "MPS_ECHARGE", -3: "MPS_ENOMEM", -4: "MPS_ENOCONV",
                 -5: "MPS_ECUDA", -6: "MPS_ETIMEOUT"}
 
@@ -110,6 +111,10 @@ _SIGS = {
     "mps_autotune_min_flops": (ctypes.c_int, [ctypes.c_double]),
     "mps_autotune_freeze": (ctypes.c_int, [ctypes.c_int]),
     "mps_autotune_force": (ctypes.c_int, [ctypes.c_int]),
+    "mps_set_chi_deflation": (ctypes.c_int, [_h, ctypes.c_double]),
+    "mps_create_zn": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int,
+                                     ctypes.c_int, _vp]),
+    "mps_zgemm_tc_work_bytes": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -155,19 +160,27 @@ def gate_length(d: int) -> int:
 
 
 class MPS:
-    """A U(1)-symmetric MPS living on the GPU (one handle of the C library)."""
+    """A U(1)-symmetric MPS living on the GPU (one handle of the C library); zn = n >= 2 makes it
+    Z_n-symmetric instead (mps_create_zn, d = n)."""
 
-    def __init__(self, d: int, occupations, chi_max: int, precision: int = MPS_FP64, stream=None):
+    def __init__(self, d: int, occupations, chi_max: int, precision: int = MPS_FP64, stream=None, zn: int = 0):
         occ = _i32(occupations)
         self.L, self.d, self.chi_max = len(occ), int(d), int(chi_max)
+        self.zn = int(zn)
         self.stream = _default_stream() if stream is None else stream
         h = _h()
-        rc = lib.mps_create(ctypes.byref(h), self.L, self.d, _ptr(occ, _i32p), precision, self.chi_max,
-                            self.stream)
+        if self.zn:
+            if self.zn != self.d:
+                raise ValueError("a Z_n handle has d = n")
+            rc = lib.mps_create_zn(ctypes.byref(h), self.L, self.zn, _ptr(occ, _i32p), precision, self.chi_max,
+                                   self.stream)
+        else:
+            rc = lib.mps_create(ctypes.byref(h), self.L, self.d, _ptr(occ, _i32p), precision, self.chi_max,
+                                self.stream)
         if rc != MPS_OK:
             raise MPSError(rc, "mps_create failed")
         self._h = h
-        self.N = int(occ.sum())
+        self.N = int(occ.sum()) % self.zn if self.zn else int(occ.sum())
 
     # -- checkpoint -------------------------------------------------------------
     def save(self, path) -> None:
@@ -361,6 +374,10 @@ class MPS:
         """Jacobi sweep limit (1..40) of this handle's update calls (mps_set_sweep_limit)."""
         self._check(lib.mps_set_sweep_limit(self._h, int(max_sweeps)), "mps_set_sweep_limit")
 
+    def set_chi_deflation(self, level: float = 3e-4):
+        """Second SVD deflation level of this handle's updates (0: off; at most 6e-4)."""
+        self._check(lib.mps_set_chi_deflation(self._h, float(level)), "mps_set_chi_deflation")
+
     def deflation_stats(self) -> dict:
         """Updates that deflated their SVDs from the bond's previous cut, and those redone."""
         a, b = ctypes.c_int64(), ctypes.c_int64()
@@ -515,7 +532,9 @@ def zgemm_tc(A: np.ndarray, B: np.ndarray, precision: int = MPS_TF32, stream=Non
     dA = torch.from_numpy(A.view(np.float64).copy()).to(dev)
     dB = torch.from_numpy(B.view(np.float64).copy()).to(dev)
     dC = torch.zeros(2 * M * N, dtype=torch.float64, device=dev)
-    wb = 256 + 64 * ((M + 127) // 128) * ((N + 63) // 64)
+    wb = int(lib.mps_zgemm_tc_work_bytes(precision, M, N, K))
+    if wb < 0:
+        raise MPSError(MPS_EINVAL, "mps_zgemm_tc_work_bytes")
     dW = torch.zeros(wb, dtype=torch.uint8, device=dev)
     st = torch.cuda.current_stream().cuda_stream if stream is None else stream
     rc = lib.mps_zgemm_tc(precision, M, N, K, dA.data_ptr(), K, dB.data_ptr(), N, dC.data_ptr(), N, dW.data_ptr(),

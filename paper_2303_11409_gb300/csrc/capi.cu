@@ -77,6 +77,8 @@ int fail(mps_s* h, int code, const std::string& msg) {
   } while (0)
 
 inline int64_t a256(int64_t x) { return (x + 255) & ~int64_t(255); }
+inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+inline int64_t ldt_of(int Dr) { return (Dr + 3) & ~3; }   // row stride of a product T_m (32-byte rows)
 
 // ---- per-kernel device timing and algorithmic work ------------------------------------
 cudaEvent_t pool_event(mps_s* h) {
@@ -247,18 +249,6 @@ std::vector<int> tune_key(const std::vector<SvdSector>& secs) {
   return key;
 }
 
-int gate_sn(int n, int d) { return std::min(d - 1, n) - std::max(0, n - d + 1) + 1; }
-int64_t gate_len(int d) {          // complex numbers in one gate (all charge blocks)
-  int64_t t = 0;
-  for (int n = 0; n <= 2 * (d - 1); ++n) t += (int64_t)gate_sn(n, d) * gate_sn(n, d);
-  return t;
-}
-int64_t gate_block_off(int n, int d) {
-  int64_t t = 0;
-  for (int k = 0; k < n; ++k) t += (int64_t)gate_sn(k, d) * gate_sn(k, d);
-  return t;
-}
-
 // Number of occupation strings of n sites (0..d-1 each) summing to q, saturated.
 std::vector<std::vector<double>> config_counts(int L, int d, int N) {
   std::vector<std::vector<double>> W(L + 1, std::vector<double>(N + 1, 0.0));
@@ -295,6 +285,7 @@ struct UpdWork {
   int sel_first = 0;                                // index of the first sector in the select arrays
   int64_t gate_off = 0;                             // byte offset of this update's staged gate
   double cut_est = 0.0;                             // the bond's previous relative cut (0: none)
+  double chi_level = 0.0;                           // the deflation level applied to it
 };
 
 int run_batch(std::vector<Req>& reqs, mps_s* owner) {
@@ -307,15 +298,23 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   // ---- K0: plan every update and size the workspace --------------------------------
   int64_t ws = 0;
   int n_sec_total = 0, n_tiles = 0, n_tasks = 0, max_tri = 0;
-  int64_t n_tc_tiles = 0, n_tc_segs = 0;   // reduced-precision updates: tensor-core Theta' tiles
+  // reduced-precision updates ([0] TF32, [1] BF16x3): shadow slots, shadow tiles, products,
+  // gate-mix tasks, and the complex64 buffer of the products T_m
+  int64_t tc_slots[2] = {0, 0}, tc_shtiles[2] = {0, 0}, tc_jobs[2] = {0, 0}, tc_mix[2] = {0, 0};
+  int64_t tc_shtasks[2] = {0, 0}, tc_slots2[2] = {0, 0}, tc_shtiles2[2] = {0, 0}, tc_jobs2[2] = {0, 0};
+  int64_t tc_shtasks2[2] = {0, 0};
+  int64_t tbuf_bytes = 0;
   bool any_tc = false;
   int64_t theta_bytes_begin = 0, theta_bytes_end = 0;
   int64_t scatter_bound = 0, gemm_tiles_bound = 0, gemm_tasks_bound = 0, lam_bound = 0;
   for (int u = 0; u < nreq; ++u) {
     mps_s* h = reqs[u].h;
     const int s = reqs[u].site;
-    plan_update(h->bonds[s], h->bonds[s + 1], h->bonds[s + 2], h->d, W[u].plan);
-    if ((int)h->cut_est.size() == h->L + 1) W[u].cut_est = h->cut_est[s + 1];
+    plan_update(h->bonds[s], h->bonds[s + 1], h->bonds[s + 2], h->rule, W[u].plan);
+    if (h->chi_deflate > 0.0 && (int)h->cut_est.size() == h->L + 1) {
+      W[u].cut_est = h->cut_est[s + 1];
+      W[u].chi_level = h->chi_deflate;
+    }
     max_tri = std::max<int>(max_tri, (int)W[u].plan.triple_l.size());
     n_sec_total += (int)W[u].plan.sectors.size();
     if (W[u].plan.sectors.empty()) return fail(owner, MPS_EINVAL, "update has no charge sectors");
@@ -354,7 +353,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   const int64_t jac_base = ws;
   ws = a256(ws + JL.total);
   int64_t gates_bytes = 0;                      // gate blocks of every update (d may differ)
-  for (int u = 0; u < nreq; ++u) gates_bytes += a256(16LL * gate_len(reqs[u].h->d));
+  for (int u = 0; u < nreq; ++u) gates_bytes += a256(16LL * reqs[u].h->rule.gate_len());
   const int64_t kept_off = ws; ws = a256(ws + 4LL * n_sec_total);
   const int64_t status_off = ws; ws = a256(ws + 4LL * n_sec_total);
   const int64_t res_off = ws; ws = a256(ws + (int64_t)sizeof(SelectResult) * nreq);
@@ -367,41 +366,74 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     const bool tc = h->precision != MPS_FP64;
     any_tc = any_tc || tc;
     const BondTable &Lb = h->bonds[s], &Mb = h->bonds[s + 1], &Rb = h->bonds[s + 2];
+    const ChargeRule& rule = h->rule;
     for (int li = 0; li < Lb.size(); ++li)
       for (int ri = 0; ri < Rb.size(); ++ri) {
         const int l = Lb.charge[li], r = Rb.charge[ri];
-        if (l - r < 0 || l - r > 2 * (d - 1)) continue;
+        if (rule.pair(l, r) < 0) continue;
         int nm = 0;
         for (int mi = 0; mi < Mb.size(); ++mi) {
           const int m = Mb.charge[mi];
-          if (l - m >= 0 && l - m <= d - 1 && m - r >= 0 && m - r <= d - 1) ++nm;
+          if (rule.phys(l, m) >= 0 && rule.phys(m, r) >= 0) ++nm;
         }
         if (nm == 0) continue;
-        if (tc) {   // one tile set per output charge c, one K segment per middle charge m
-          const int nc = std::min(l, r + d - 1) - std::max(r, l - d + 1) + 1;
-          n_tc_segs += (int64_t)nm * nc;
-          n_tc_tiles += (int64_t)nc * ((Lb.dim[li] + kTcTileM - 1) / kTcTileM) *
-                        ((Rb.dim[ri] + kTcTileN - 1) / kTcTileN);
+        if (tc) {   // one product T_m per middle charge m, then the gate mix over m
+          const int p = h->precision == MPS_BF16X3;
+          tc_jobs[p] += (int64_t)nm * cdiv(Lb.dim[li], kShRows) * cdiv(Rb.dim[ri], kShTileN);
+          tbuf_bytes += (int64_t)nm * a256(8LL * Lb.dim[li] * ldt_of(Rb.dim[ri]));
+          tc_mix[p] += 1;
           continue;
         }
         n_tasks++;
         n_tiles += ((Lb.dim[li] + kTile - 1) / kTile) * ((Rb.dim[ri] + kTile - 1) / kTile);
       }
+    if (tc) {   // shadow tiles: site s as A operand, site s+1 as B operand, Theta' as reassembly A
+      const int p = h->precision == MPS_BF16X3, KC = sh_kc(h->precision), TPK = sh_tiles_per_k(h->precision);
+      for (const SiteBlock& b : h->sites[s].blocks) {
+        const int64_t t = (int64_t)cdiv(b.Dl, kShRows) * cdiv(b.Dm, KC);
+        tc_shtiles[p] += t; tc_slots[p] += t * TPK; tc_shtasks[p] += 1;
+      }
+      for (const SiteBlock& b : h->sites[s + 1].blocks) {
+        const int64_t t = (int64_t)cdiv(b.Dm, kShTileN) * cdiv(b.Dl, KC);
+        tc_shtiles[p] += t; tc_slots[p] += t * TPK; tc_shtasks[p] += 1;
+      }
+      for (const SectorPlanEntry& e : W[u].plan.sectors) {
+        const int k = std::min(e.rows, e.cols), ktn = cdiv(e.cols, KC);
+        for (int i = e.l0; i < e.l1; ++i) {
+          tc_slots[p] += (int64_t)cdiv(Lb.dim[i], kShRows) * ktn * TPK;
+          tc_jobs2[p] += (int64_t)cdiv(Lb.dim[i], kShRows) * cdiv(k, kShTileN);
+        }
+        const int64_t ty = (int64_t)cdiv(k, kShTileN) * ktn;   // Y(c) as reassembly B operand
+        tc_slots2[p] += ty * TPK; tc_shtiles2[p] += ty; tc_shtasks2[p] += 1;
+      }
+    }
   }
   const int64_t phase1_desc = a256((int64_t)sizeof(ThetaTask) * n_tasks) + a256(sizeof(TileRef) * (int64_t)n_tiles) +
                               (owner->autotune ? kTuneCands : 1) * a256((int64_t)sizeof(SvdSector) * n_sec_total) +
                               a256((int64_t)sizeof(SelectSector) * n_sec_total) +
                               a256((int64_t)sizeof(SelectTask) * nreq) + gates_bytes +
-                              a256((int64_t)sizeof(TcSegment) * n_tc_segs) + a256((int64_t)sizeof(TcTile) * n_tc_tiles);
+                              a256((int64_t)sizeof(ShadowTask) * (tc_shtasks[0] + tc_shtasks[1])) +
+                              a256((int64_t)sizeof(ShadowTile) * (tc_shtiles[0] + tc_shtiles[1])) +
+                              a256((int64_t)sizeof(TmaJob) * (tc_jobs[0] + tc_jobs[1])) +
+                              a256((int64_t)sizeof(MixTask) * (tc_mix[0] + tc_mix[1])) + 4 * 256;
   const int64_t phase2_desc = a256((int64_t)sizeof(LambdaTask) * lam_bound) +
                               a256((int64_t)sizeof(ScatterTask) * scatter_bound) +
                               a256((int64_t)sizeof(GemmTask) * gemm_tasks_bound) +
                               a256((int64_t)sizeof(TileRef) * gemm_tiles_bound) +
-                              (any_tc ? a256((int64_t)sizeof(TcSegment) * gemm_tasks_bound) +
-                                            a256((int64_t)sizeof(TcTile) * gemm_tiles_bound)
-                                      : 0);
+                              a256((int64_t)sizeof(ShadowTask) * (tc_shtasks2[0] + tc_shtasks2[1])) +
+                              a256((int64_t)sizeof(ShadowTile) * (tc_shtiles2[0] + tc_shtiles2[1])) +
+                              a256((int64_t)sizeof(TmaJob) * (tc_jobs2[0] + tc_jobs2[1])) + 4 * 256;
   const int64_t desc_bytes = std::max(phase1_desc, phase2_desc);
   ws = desc_off + desc_bytes;
+  // the products T_m, then the shadow slots of each precision (1024-byte aligned once the
+  // workspace base is known: 1 KB of slack each); phase 2 appends Y's slots to phase 1's
+  const int64_t tbuf_off = ws;
+  ws = a256(ws + tbuf_bytes);
+  int64_t slot_off[2];
+  for (int p = 0; p < 2; ++p) {
+    slot_off[p] = ws;
+    if (tc_slots[p] + tc_slots2[p] > 0) ws = a256(ws + (tc_slots[p] + tc_slots2[p]) * kShTileBytes + 1024);
+  }
 
   CUDA_OR_FAIL(owner, cudaEventSynchronize(owner->staged));   // pin_in free again
   {
@@ -421,14 +453,22 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   auto dptr = [&](int64_t off) { return base + off; };
   // gates go first into the staging area; tasks point at their device copies
   Stager sg{(char*)owner->pin_in.p};
-  for (int u = 0; u < nreq; ++u) W[u].gate_off = desc_off + sg.put(reqs[u].gate, 2 * gate_len(reqs[u].h->d));
+  for (int u = 0; u < nreq; ++u) W[u].gate_off = desc_off + sg.put(reqs[u].gate, 2 * reqs[u].h->rule.gate_len());
 
   // ---- build phase-1 descriptors ------------------------------------------------------
   std::vector<ThetaTask> tasks; tasks.reserve(n_tasks);
   std::vector<TileRef> tiles; tiles.reserve(n_tiles);
-  std::vector<TcSegment> tcseg; tcseg.reserve(n_tc_segs);
-  std::vector<TcTile> tctile[2];            // [0]: TF32 updates, [1]: BF16x3 updates
-  double tc_th_flops = 0;
+  // reduced-precision updates, per precision ([0] TF32, [1] BF16x3)
+  std::vector<ShadowTask> shtask[2];
+  std::vector<ShadowTile> shtile[2];
+  std::vector<TmaJob> tjobs[2];
+  std::vector<MixTask> mixes[2];
+  int64_t slot_next[2] = {0, 0}, tbuf_next = 0;
+  std::vector<std::vector<std::vector<int64_t>>> ra_slot(nreq);   // [u][sector][l - l0]: reassembly A slots
+  char* slot_base[2];
+  for (int p = 0; p < 2; ++p)
+    slot_base[p] = reinterpret_cast<char*>(((uintptr_t)(base + slot_off[p]) + 1023) & ~(uintptr_t)1023);
+  double tc_th_flops = 0, tc_prod_flops = 0;
   std::vector<SvdSector> svd; svd.reserve(n_sec_total);
   std::vector<SelectSector> selsec; selsec.reserve(n_sec_total);
   std::vector<SelectTask> seltask; seltask.reserve(nreq);
@@ -451,29 +491,64 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       }
       return -1;
     };
+    const bool tc = h->precision != MPS_FP64;
+    const int tp = h->precision == MPS_BF16X3;
+    const int KC = sh_kc(h->precision), TPK = sh_tiles_per_k(h->precision);
+    const ChargeRule& rule = h->rule;
+    std::vector<int64_t> a_slot, b_slot;
+    if (tc) {
+      // site s as A tiles (rows of l, K over m), site s+1 as B tiles (columns of r, K over m)
+      for (const SiteBlock& b : SL.blocks) {
+        a_slot.push_back(slot_next[tp]);
+        ShadowTask Tk{slotL + b.off, b.Dm, 1, b.Dl, b.Dm, slot_next[tp], cdiv(b.Dm, KC), 0};
+        const int id = (int)shtask[tp].size();
+        shtask[tp].push_back(Tk);
+        for (int it = 0; it < cdiv(b.Dl, kShRows); ++it)
+          for (int kt = 0; kt < Tk.kt_n; ++kt) shtile[tp].push_back(ShadowTile{id, it, kt});
+        slot_next[tp] += (int64_t)cdiv(b.Dl, kShRows) * Tk.kt_n * TPK;
+      }
+      for (const SiteBlock& b : SR.blocks) {
+        b_slot.push_back(slot_next[tp]);
+        ShadowTask Tk{slotR + b.off, 1, b.Dm, b.Dm, b.Dl, slot_next[tp], cdiv(b.Dl, KC), 1};
+        const int id = (int)shtask[tp].size();
+        shtask[tp].push_back(Tk);
+        for (int it = 0; it < cdiv(b.Dm, kShTileN); ++it)
+          for (int kt = 0; kt < Tk.kt_n; ++kt) shtile[tp].push_back(ShadowTile{id, it, kt});
+        slot_next[tp] += (int64_t)cdiv(b.Dm, kShTileN) * Tk.kt_n * TPK;
+      }
+      // Theta'(c) as the reassembly's A operand: block (l, c) = its rows of l, K = its columns
+      ra_slot[u].resize(P.sectors.size());
+      for (size_t si = 0; si < P.sectors.size(); ++si) {
+        const SectorPlanEntry& E = P.sectors[si];
+        for (int i = E.l0; i < E.l1; ++i) {
+          ra_slot[u][si].push_back(slot_next[tp]);
+          slot_next[tp] += (int64_t)cdiv(Lb.dim[i], kShRows) * cdiv(E.cols, KC) * TPK;
+        }
+      }
+    }
     for (int li = 0; li < Lb.size(); ++li)
       for (int ri = 0; ri < Rb.size(); ++ri) {
         const int l = Lb.charge[li], r = Rb.charge[ri];
-        const int n = l - r;
-        if (n < 0 || n > 2 * (d - 1)) continue;
+        const int n = rule.pair(l, r);           // the gate block of this pair
+        if (n < 0) continue;
         ThetaTask T;
         std::memset(&T, 0, sizeof(T));
-        const int base_n = std::max(0, n - d + 1);
+        const int base_n = rule.base(n);
         T.nm = 0;
         for (int mi = 0; mi < Mb.size(); ++mi) {
           const int m = Mb.charge[mi];
-          if (l - m < 0 || l - m > d - 1 || m - r < 0 || m - r > d - 1) continue;
+          if (rule.phys(l, m) < 0 || rule.phys(m, r) < 0) continue;
           const int bl = SL.find(l, m), br = SR.find(m, r);
           if (bl < 0 || br < 0) return fail(owner, MPS_EINVAL, "internal: missing block");
           T.A[T.nm] = slotL + SL.blocks[bl].off;
           T.B[T.nm] = slotR + SR.blocks[br].off;
           T.Dm[T.nm] = Mb.dim[mi];
-          T.gi[T.nm] = (l - m) - base_n;
+          T.gi[T.nm] = rule.phys(l, m) - base_n;
           T.nm++;
         }
         if (T.nm == 0) continue;
         T.nc = 0;
-        for (int c = std::max(r, l - d + 1); c <= std::min(l, r + d - 1); ++c) {
+        for (int c = rule.cmin(l, r); c <= rule.cmax(l, r); ++c) {
           const int si = sector_of(c);
           if (si < 0) return fail(owner, MPS_EINVAL, "internal: missing sector");
           const SectorPlanEntry& E = P.sectors[si];
@@ -481,44 +556,60 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
           const int coff = Rb.off[ri] - Rb.off[E.r0];
           T.out[T.nc] = reinterpret_cast<double2*>(dptr(W[u].theta_off[si])) + (int64_t)roff * E.cols + coff;
           T.ldo[T.nc] = E.cols;
-          T.go[T.nc] = (l - c) - base_n;
+          T.go[T.nc] = rule.phys(l, c) - base_n;
           T.nc++;
         }
-        T.gate = reinterpret_cast<const double2*>(dptr(W[u].gate_off)) + gate_block_off(n, d);
-        T.sn = gate_sn(n, d);
+        T.gate = reinterpret_cast<const double2*>(dptr(W[u].gate_off)) + rule.block_off(n);
+        T.sn = rule.sn(n);
         T.Dl = Lb.dim[li];
         T.Dr = Rb.dim[ri];
-        if (h->precision != MPS_FP64) {
-          // direct form on the tensor cores: Theta'(c)[l, r] = sum_m (G_n[c, m] B[l,m]) . B[m,r]
-          const double* gh = reqs[u].gate + 2 * gate_block_off(n, d);
-          std::vector<TcTile>& out_tiles = tctile[h->precision == MPS_BF16X3];
-          for (int i = 0; i < T.nm; ++i) tc_th_flops += 8.0 * T.Dl * T.Dm[i] * T.Dr;   // as the FP64 form
-          tc_th_flops += 8.0 * T.nm * T.nc * T.Dl * T.Dr;
-          for (int k = 0; k < T.nc; ++k) {
-            const int seg0 = (int)tcseg.size();
-            for (int i = 0; i < T.nm; ++i) {
-              const int64_t gidx = (int64_t)T.go[k] * T.sn + T.gi[i];
-              const double2 g = make_double2(gh[2 * gidx], gh[2 * gidx + 1]);
-              if (g.x == 0.0 && g.y == 0.0) continue;   // the term vanishes
-              TcSegment G;
-              G.A = T.A[i]; G.B = T.B[i];
-              G.Kc = T.Dm[i];
-              G.sar = T.Dm[i]; G.sac = 1;
-              G.sbr = T.Dr; G.sbc = 1;
-              G.alpha = g;
-              tcseg.push_back(G);
-            }
-            const int nseg = (int)tcseg.size() - seg0;
-            for (int ti = 0; ti < (T.Dl + kTcTileM - 1) / kTcTileM; ++ti)
-              for (int tj = 0; tj < (T.Dr + kTcTileN - 1) / kTcTileN; ++tj) {
-                TcTile C;
-                C.C = T.out[k]; C.ldc = T.ldo[k];
-                C.M = T.Dl; C.N = T.Dr;
-                C.row0 = ti * kTcTileM; C.col0 = tj * kTcTileN;
-                C.seg0 = seg0; C.nseg = nseg;
-                out_tiles.push_back(C);
+        if (tc) {
+          // T_i = B[s][l, m_i] . B[s+1][m_i, r] on the tensor cores (one product per middle
+          // charge), then Theta'(c)[l, r] = sum_i G_n[c, m_i] T_i in mix_kernel
+          MixTask X;
+          std::memset(&X, 0, sizeof(X));
+          X.nm = T.nm; X.nc = T.nc; X.gate = T.gate; X.sn = T.sn; X.Dl = T.Dl; X.Dr = T.Dr;
+          X.ldt = (int)ldt_of(T.Dr);
+          int i = 0;
+          for (int mi = 0; mi < Mb.size(); ++mi) {
+            const int m = Mb.charge[mi];
+            if (rule.phys(l, m) < 0 || rule.phys(m, r) < 0) continue;
+            const int bl = SL.find(l, m), br = SR.find(m, r);
+            float2* Tm = reinterpret_cast<float2*>(dptr(tbuf_off + tbuf_next));
+            tbuf_next += a256(8LL * T.Dl * X.ldt);
+            X.T[i] = Tm;
+            X.gi[i] = T.gi[i];
+            const int ktn = cdiv(T.Dm[i], KC);
+            for (int rt = 0; rt < cdiv(T.Dl, kShRows); ++rt)
+              for (int ct = 0; ct < cdiv(T.Dr, kShTileN); ++ct) {
+                TmaJob J;
+                J.a0 = a_slot[bl] + (int64_t)rt * ktn * TPK;
+                J.b0 = b_slot[br] + (int64_t)ct * ktn * TPK;
+                J.kt_n = ktn;
+                J.M = std::min(kShRows, T.Dl - rt * kShRows);
+                J.N = std::min(kShTileN, T.Dr - ct * kShTileN);
+                J.mode = 0;
+                J.alpha = 1.0f;
+                J.C = Tm + (int64_t)rt * kShRows * X.ldt + ct * kShTileN;
+                J.ldc = X.ldt;
+                tjobs[tp].push_back(J);
               }
+            tc_prod_flops += 8.0 * T.Dl * T.Dm[i] * T.Dr;
+            ++i;
           }
+          for (int k = 0; k < T.nc; ++k) {
+            const int c = rule.wrap(l - T.go[k] - base_n);
+            const int si = sector_of(c);
+            const SectorPlanEntry& E = P.sectors[si];
+            X.out[k] = T.out[k];
+            X.ldo[k] = T.ldo[k];
+            X.go[k] = T.go[k];
+            X.sh0[k] = ra_slot[u][si][li - E.l0];
+            X.sh_ktn[k] = cdiv(E.cols, KC);
+            X.coff[k] = Rb.off[ri] - Rb.off[E.r0];
+          }
+          mixes[tp].push_back(X);
+          tc_th_flops += 8.0 * T.nm * T.nc * T.Dl * T.Dr;
           continue;
         }
         const int task_id = (int)tasks.size();
@@ -535,7 +626,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       S.m = E.rows;
       S.n = E.cols;
       S.floor_rel = kDeflateRel * reqs[u].cutoff;
-      S.floor_abs = kChiDeflate * W[u].cut_est;
+      S.floor_abs = W[u].chi_level * W[u].cut_est;
       svd_fill_scratch(S, JL, sec_global, dptr(jac_base));
       S.sigma = reinterpret_cast<double*>(dptr(W[u].sig_off[si]));
       S.Y = reinterpret_cast<double2*>(dptr(W[u].y_off[si]));
@@ -590,9 +681,26 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   for (int c = 0; c < n_cand; ++c) o_svd[c] = sg.put(svd_sorted[c].data(), (int64_t)svd_sorted[c].size());
   const int64_t o_selsec = sg.put(selsec.data(), (int64_t)selsec.size());
   const int64_t o_seltask = sg.put(seltask.data(), (int64_t)seltask.size());
-  const int64_t o_tcseg = sg.put(tcseg.data(), (int64_t)tcseg.size());
-  const int64_t o_tctile0 = sg.put(tctile[0].data(), (int64_t)tctile[0].size());
-  const int64_t o_tctile1 = sg.put(tctile[1].data(), (int64_t)tctile[1].size());
+  int64_t o_shtask[2], o_shtile[2], o_tjobs[2], o_mix[2];
+  double sh_bytes = 0, prod_bytes = 0;
+  for (int p = 0; p < 2; ++p) {
+    // the longest K first: a static round-robin over the persistent CTAs then balances
+    std::stable_sort(tjobs[p].begin(), tjobs[p].end(),
+                     [](const TmaJob& a, const TmaJob& b) { return a.kt_n > b.kt_n; });
+    // every slot a job or a shadow tile touches lies inside the buffer its tensor map covers
+    const int64_t tpk = p ? 2 : 1, lim = tc_slots[p] + tc_slots2[p];
+    if (slot_next[p] > tc_slots[p]) return fail(owner, MPS_EINVAL, "internal: shadow slot bound exceeded");
+    for (const TmaJob& j : tjobs[p])
+      if (j.a0 < 0 || j.b0 < 0 || j.a0 + j.kt_n * tpk > lim || j.b0 + j.kt_n * tpk > lim)
+        return fail(owner, MPS_EINVAL, "internal: tensor-core job outside the shadow buffer");
+    o_shtask[p] = sg.put(shtask[p].data(), (int64_t)shtask[p].size());
+    o_shtile[p] = sg.put(shtile[p].data(), (int64_t)shtile[p].size());
+    o_tjobs[p] = sg.put(tjobs[p].data(), (int64_t)tjobs[p].size());
+    o_mix[p] = sg.put(mixes[p].data(), (int64_t)mixes[p].size());
+    for (const ShadowTask& t : shtask[p]) sh_bytes += 16.0 * t.n_i * t.K;   // FP64 operands read
+    sh_bytes += (double)slot_next[p] * kShTileBytes;                       // slots written (and zeroed)
+    for (const TmaJob& j : tjobs[p]) prod_bytes += 8.0 * j.M * j.N;        // T_m written
+  }
   if (sg.size > desc_bytes) return fail(owner, MPS_EINVAL, "internal: descriptor bound exceeded");
 
   // ---- algorithmic work of the three kernels (flops: complex multiply-add = 8) -------
@@ -602,6 +710,8 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     th_flops += 8.0 * T.nm * T.nc * T.Dl * T.Dr;
   }
   th_flops += tc_th_flops;
+  for (int p = 0; p < 2; ++p)
+    for (const MixTask& x : mixes[p]) th_bytes += 8.0 * x.nm * x.Dl * x.Dr;    // T_m read by the mix
   for (int u = 0; u < nreq; ++u) {
     const int s = reqs[u].site;
     th_bytes += 16.0 * (double)(reqs[u].h->sites[s].nnz + reqs[u].h->sites[s + 1].nnz);
@@ -616,17 +726,37 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     if (e == cudaSuccess)
       e = cudaMemsetAsync(dptr(theta_bytes_begin), 0, theta_bytes_end - theta_bytes_begin, st);
     if (e != cudaSuccess) return e;
-    const bool any_theta = !tiles.empty() || !tctile[0].empty() || !tctile[1].empty();
+    const int precs[2] = {MPS_TF32, MPS_BF16X3};
+    const bool any_tc_work = !tjobs[0].empty() || !tjobs[1].empty();
+    for (int p = 0; p < 2 && e == cudaSuccess; ++p)   // padding rows and K of every slot are zero
+      if (slot_next[p] > 0) e = cudaMemsetAsync(slot_base[p], 0, (size_t)(slot_next[p] * kShTileBytes), st);
+    // products a failed (timed-out) GEMM leaves unwritten read as zero, not as stale memory
+    if (e == cudaSuccess && tbuf_next > 0) e = cudaMemsetAsync(dptr(tbuf_off), 0, (size_t)tbuf_next, st);
+    if (e == cudaSuccess)
+      e = timed(owner, MPS_K_SHADOW, any_tc_work, 0.0, sh_bytes, [&] {
+        cudaError_t e2 = cudaSuccess;
+        for (int p = 0; p < 2 && e2 == cudaSuccess; ++p)
+          e2 = launch_shadow(precs[p], reinterpret_cast<ShadowTask*>(dptr(desc_off + o_shtask[p])),
+                             reinterpret_cast<ShadowTile*>(dptr(desc_off + o_shtile[p])), (int)shtile[p].size(),
+                             slot_base[p], st);
+        return e2;
+      });
+    if (e == cudaSuccess)
+      e = timed(owner, MPS_K_TCGEMM, any_tc_work, tc_prod_flops, sh_bytes + prod_bytes, [&] {
+        cudaError_t e2 = cudaSuccess;
+        for (int p = 0; p < 2 && e2 == cudaSuccess; ++p)
+          e2 = launch_tma_zgemm(precs[p], reinterpret_cast<TmaJob*>(dptr(desc_off + o_tjobs[p])),
+                                (int)tjobs[p].size(), slot_base[p], tc_slots[p] + tc_slots2[p], owner->tc_flag, st);
+        return e2;
+      });
+    if (e != cudaSuccess) return e;
+    const bool any_theta = !tiles.empty() || !mixes[0].empty() || !mixes[1].empty();
     return timed(owner, MPS_K_THETA, any_theta, th_flops, th_bytes, [&] {
       cudaError_t e2 = launch_theta(reinterpret_cast<ThetaTask*>(dptr(desc_off + o_tasks)),
                                     reinterpret_cast<TileRef*>(dptr(desc_off + o_tiles)), (int)tiles.size(), st);
-      const TcSegment* d_seg = reinterpret_cast<TcSegment*>(dptr(desc_off + o_tcseg));
-      if (e2 == cudaSuccess)
-        e2 = launch_tc_zgemm(MPS_TF32, reinterpret_cast<TcTile*>(dptr(desc_off + o_tctile0)),
-                             (int)tctile[0].size(), d_seg, owner->tc_flag, st);
-      if (e2 == cudaSuccess)
-        e2 = launch_tc_zgemm(MPS_BF16X3, reinterpret_cast<TcTile*>(dptr(desc_off + o_tctile1)),
-                             (int)tctile[1].size(), d_seg, owner->tc_flag, st);
+      for (int p = 0; p < 2 && e2 == cudaSuccess; ++p)
+        e2 = launch_mix(precs[p], reinterpret_cast<MixTask*>(dptr(desc_off + o_mix[p])), (int)mixes[p].size(),
+                        slot_base[p], st);
       return e2;
     });
   };
@@ -703,7 +833,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   const int* sstat = (const int*)((char*)owner->pin_out.p + (status_off - kept_off));
   const SelectResult* res = (const SelectResult*)((char*)owner->pin_out.p + (res_off - kept_off));
 
-  // ---- deflation check: an update whose new cut fell below kChiVerify x the estimate its
+  // ---- deflation check: an update whose new cut fell below level / kChiGuard x the estimate its
   // SVDs were deflated with has its own SVDs redone without that level, then the selection
   // of the batch is repeated (the other updates' spectra are unchanged, so their selections
   // are too).  Redoing only the failing updates keeps every result independent of which
@@ -714,7 +844,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     for (int u = 0; u < nreq; ++u) {
       if (W[u].cut_est <= 0.0) continue;
       reqs[u].h->stats.deflated_updates++;
-      if (res[u].status == 0 && res[u].cut < kChiVerify * W[u].cut_est) redo = redo_upd[u] = 1;
+      if (res[u].status == 0 && res[u].cut * kChiGuard < W[u].chi_level * W[u].cut_est) redo = redo_upd[u] = 1;
     }
     if (redo) {
       // the update of each sector, from the position of its status word
@@ -760,9 +890,13 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   std::vector<ScatterTask> sc;
   std::vector<GemmTask> gm;
   std::vector<TileRef> gt;
-  std::vector<TcSegment> gseg;
-  std::vector<TcTile> gtile[2];             // [0]: TF32 updates, [1]: BF16x3 updates
-  double tc_gm_flops = 0, tc_gm_bytes = 0;
+  // reduced-precision reassembly ([0] TF32, [1] BF16x3): Y(c)[:, :k] as B tiles, appended to the
+  // phase-1 slots (the reassembly A tiles of Theta' written by the mix are still there)
+  std::vector<ShadowTask> yshtask[2];
+  std::vector<ShadowTile> yshtile[2];
+  std::vector<TmaJob> gjobs[2];
+  int64_t yslot_next[2] = {slot_next[0], slot_next[1]};
+  double tc_gm_flops = 0, tc_gm_bytes = 0, ysh_bytes = 0;
   int64_t sc_elems = 0;
   std::vector<char> apply(nreq, 0);
   {
@@ -815,8 +949,8 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       h->err = "new bond exceeds its capacity";
       continue;
     }
-    layout_site(Lb, M, h->d, newL[u]);
-    layout_site(M, Rb, h->d, newR[u]);
+    layout_site(Lb, M, h->rule, newL[u]);
+    layout_site(M, Rb, h->rule, newR[u]);
     if (newL[u].nnz > h->site_cap[s] || newR[u].nnz > h->site_cap[s + 1]) {
       reqs[u].status = MPS_ENOMEM;
       h->err = "new site tensor exceeds its capacity";
@@ -848,29 +982,41 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
         sc_elems += (int64_t)k * T.Dr;
         sc.push_back(T);
       }
+      const bool tc = h->precision != MPS_FP64;
+      const int tp = h->precision == MPS_BF16X3;
+      const int KC = sh_kc(h->precision), TPK = sh_tiles_per_k(h->precision), ktn = cdiv(E.cols, KC);
+      int64_t y0 = 0;
+      if (tc) {   // Y(c)[:, :k] (column-major, n x k) as B tiles: column j of Y is output column j
+        y0 = yslot_next[tp];
+        ShadowTask Tk{Y, E.cols, 1, k, E.cols, y0, ktn, 1};
+        const int id = (int)yshtask[tp].size();
+        yshtask[tp].push_back(Tk);
+        for (int it = 0; it < cdiv(k, kShTileN); ++it)
+          for (int kt = 0; kt < ktn; ++kt) yshtile[tp].push_back(ShadowTile{id, it, kt});
+        yslot_next[tp] += (int64_t)cdiv(k, kShTileN) * ktn * TPK;
+        ysh_bytes += 16.0 * k * E.cols + (double)cdiv(k, kShTileN) * ktn * TPK * kShTileBytes;
+      }
       for (int li = E.l0; li < E.l1; ++li) {
         const int b = newL[u].find(Lb.charge[li], E.c);
-        if (h->precision != MPS_FP64) {   // B^[s][l, c] = (Theta'(c)[rows of l] . Y(c)[:, :k]) / |S_kept|
-          TcSegment G;
-          G.A = th + (int64_t)(Lb.off[li] - Lb.off[E.l0]) * E.cols;
-          G.sar = E.cols; G.sac = 1;
-          G.B = Y; G.sbr = 1; G.sbc = E.cols;
-          G.Kc = E.cols;
-          G.alpha = make_double2(scale, 0.0);
-          const int seg = (int)gseg.size();
-          gseg.push_back(G);
+        if (tc) {   // B^[s][l, c] = (Theta'(c)[rows of l] . Y(c)[:, :k]) / |S_kept| on the tensor cores
           const int Dl = Lb.dim[li];
-          for (int ti = 0; ti < (Dl + kTcTileM - 1) / kTcTileM; ++ti)
-            for (int tj = 0; tj < (k + kTcTileN - 1) / kTcTileN; ++tj) {
-              TcTile C;
-              C.C = dstL + newL[u].blocks[b].off; C.ldc = k;
-              C.M = Dl; C.N = k;
-              C.row0 = ti * kTcTileM; C.col0 = tj * kTcTileN;
-              C.seg0 = seg; C.nseg = 1;
-              gtile[h->precision == MPS_BF16X3].push_back(C);
+          const int64_t a0 = ra_slot[u][si][li - E.l0];
+          for (int rt = 0; rt < cdiv(Dl, kShRows); ++rt)
+            for (int ct = 0; ct < cdiv(k, kShTileN); ++ct) {
+              TmaJob J;
+              J.a0 = a0 + (int64_t)rt * ktn * TPK;
+              J.b0 = y0 + (int64_t)ct * ktn * TPK;
+              J.kt_n = ktn;
+              J.M = std::min(kShRows, Dl - rt * kShRows);
+              J.N = std::min(kShTileN, k - ct * kShTileN);
+              J.mode = 1;
+              J.alpha = (float)scale;
+              J.C = dstL + newL[u].blocks[b].off + (int64_t)rt * kShRows * k + ct * kShTileN;
+              J.ldc = k;
+              gjobs[tp].push_back(J);
             }
           tc_gm_flops += 8.0 * Dl * k * E.cols;
-          tc_gm_bytes += 16.0 * ((double)Dl * E.cols + (double)E.cols * k + (double)Dl * k);
+          tc_gm_bytes += 16.0 * (double)Dl * k + 8.0 * (double)Dl * E.cols;   // B^[s] written, Theta' tiles read
           continue;
         }
         GemmTask G;
@@ -903,11 +1049,22 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     const int64_t o_sc = s2.put(sc.data(), (int64_t)sc.size());
     const int64_t o_gm = s2.put(gm.data(), (int64_t)gm.size());
     const int64_t o_gt = s2.put(gt.data(), (int64_t)gt.size());
-    const int64_t o_gseg = s2.put(gseg.data(), (int64_t)gseg.size());
-    const int64_t o_gtile0 = s2.put(gtile[0].data(), (int64_t)gtile[0].size());
-    const int64_t o_gtile1 = s2.put(gtile[1].data(), (int64_t)gtile[1].size());
+    int64_t o_ysh[2], o_ytile[2], o_gjobs[2];
+    for (int p = 0; p < 2; ++p) {
+      std::stable_sort(gjobs[p].begin(), gjobs[p].end(),
+                       [](const TmaJob& a, const TmaJob& b) { return a.kt_n > b.kt_n; });
+      const int64_t tpk = p ? 2 : 1, lim = tc_slots[p] + tc_slots2[p];
+      for (const TmaJob& j : gjobs[p])
+        if (j.a0 < 0 || j.b0 < 0 || j.a0 + j.kt_n * tpk > lim || j.b0 + j.kt_n * tpk > lim)
+          return fail(owner, MPS_EINVAL, "internal: tensor-core job outside the shadow buffer");
+      o_ysh[p] = s2.put(yshtask[p].data(), (int64_t)yshtask[p].size());
+      o_ytile[p] = s2.put(yshtile[p].data(), (int64_t)yshtile[p].size());
+      o_gjobs[p] = s2.put(gjobs[p].data(), (int64_t)gjobs[p].size());
+      if (yslot_next[p] > tc_slots[p] + tc_slots2[p])
+        return fail(owner, MPS_EINVAL, "internal: shadow slot bound exceeded");
+    }
     if (s2.size > desc_bytes) return fail(owner, MPS_EINVAL, "internal: descriptor bound exceeded");
-    double lam_bytes = 0, gm_flops = tc_gm_flops, gm_bytes = tc_gm_bytes;
+    double lam_bytes = 0, gm_flops = 0, gm_bytes = 0;
     for (const LambdaTask& T : lam) lam_bytes += 16.0 * T.k;
     for (const GemmTask& T : gm) {
       gm_flops += 8.0 * T.M * T.N * T.K;
@@ -924,18 +1081,28 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
         e = timed(owner, MPS_K_SCATTER, sc_elems > 0, 0.0, 32.0 * (double)sc_elems, [&] {
           return launch_scatter(reinterpret_cast<ScatterTask*>(dptr(desc_off + o_sc)), (int)sc.size(), sc_elems, st);
         });
-      const bool any_gemm = !gt.empty() || !gtile[0].empty() || !gtile[1].empty();
       if (e == cudaSuccess)
-        e = timed(owner, MPS_K_GEMM, any_gemm, gm_flops, gm_bytes, [&] {
-          cudaError_t e2 = launch_gemm(reinterpret_cast<GemmTask*>(dptr(desc_off + o_gm)),
-                                       reinterpret_cast<TileRef*>(dptr(desc_off + o_gt)), (int)gt.size(), st);
-          const TcSegment* d_seg = reinterpret_cast<TcSegment*>(dptr(desc_off + o_gseg));
-          if (e2 == cudaSuccess)
-            e2 = launch_tc_zgemm(MPS_TF32, reinterpret_cast<TcTile*>(dptr(desc_off + o_gtile0)),
-                                 (int)gtile[0].size(), d_seg, owner->tc_flag, st);
-          if (e2 == cudaSuccess)
-            e2 = launch_tc_zgemm(MPS_BF16X3, reinterpret_cast<TcTile*>(dptr(desc_off + o_gtile1)),
-                                 (int)gtile[1].size(), d_seg, owner->tc_flag, st);
+        e = timed(owner, MPS_K_GEMM, !gt.empty(), gm_flops, gm_bytes, [&] {
+          return launch_gemm(reinterpret_cast<GemmTask*>(dptr(desc_off + o_gm)),
+                             reinterpret_cast<TileRef*>(dptr(desc_off + o_gt)), (int)gt.size(), st);
+        });
+      const int precs[2] = {MPS_TF32, MPS_BF16X3};
+      const bool any_tc_gemm = !gjobs[0].empty() || !gjobs[1].empty();
+      if (e == cudaSuccess)
+        e = timed(owner, MPS_K_SHADOW, any_tc_gemm, 0.0, ysh_bytes, [&] {
+          cudaError_t e2 = cudaSuccess;
+          for (int p = 0; p < 2 && e2 == cudaSuccess; ++p)
+            e2 = launch_shadow(precs[p], reinterpret_cast<ShadowTask*>(dptr(desc_off + o_ysh[p])),
+                               reinterpret_cast<ShadowTile*>(dptr(desc_off + o_ytile[p])), (int)yshtile[p].size(),
+                               slot_base[p], st);
+          return e2;
+        });
+      if (e == cudaSuccess)
+        e = timed(owner, MPS_K_TCGEMM, any_tc_gemm, tc_gm_flops, tc_gm_bytes, [&] {
+          cudaError_t e2 = cudaSuccess;
+          for (int p = 0; p < 2 && e2 == cudaSuccess; ++p)
+            e2 = launch_tma_zgemm(precs[p], reinterpret_cast<TmaJob*>(dptr(desc_off + o_gjobs[p])),
+                                  (int)gjobs[p].size(), slot_base[p], tc_slots[p] + tc_slots2[p], owner->tc_flag, st);
           return e2;
         });
       return e;
@@ -979,11 +1146,20 @@ int check_gate_args(mps_s* h, int site, const double* gate, int chi, double cuto
 
 }  // namespace
 
+namespace mps {
+bool svd_forced_tune(SvdTune& t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune_force < 0) return false;
+  t = svd_tune_candidate(g_tune_force);
+  return true;
+}
+}  // namespace mps
+
 // ======================================================================================
 extern "C" {
 
 static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, int site_lo, int site_hi,
-                         int precision, int chi_max, void* cuda_stream);
+                         int precision, int chi_max, void* cuda_stream, int zn = 0);
 
 int mps_create(mps_t* out, int L, int d, const int32_t* site_charges, int precision, int chi_max,
                void* cuda_stream) {
@@ -999,8 +1175,17 @@ int mps_create_segment(mps_t* out, int L, int d, const int32_t* site_charges, in
   return create_handle(out, L, d, site_charges, site_lo, site_hi, precision, chi_max, cuda_stream);
 }
 
+int mps_create_zn(mps_t* out, int L, int n, const int32_t* site_charges, int precision, int chi_max,
+                  void* cuda_stream) {
+  if (n < 2) {
+    if (out) *out = nullptr;
+    return MPS_EINVAL;
+  }
+  return create_handle(out, L, n, site_charges, 0, L, precision, chi_max, cuda_stream, n);
+}
+
 static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, int site_lo, int site_hi,
-                         int precision, int chi_max, void* cuda_stream) {
+                         int precision, int chi_max, void* cuda_stream, int zn) {
   if (!out) return MPS_EINVAL;
   *out = nullptr;
   if (L < 2 || d < 2 || d > MPS_MAX_D || chi_max < 1 || !site_charges) return MPS_EINVAL;
@@ -1009,12 +1194,14 @@ static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, 
     if (site_charges[s] < 0 || site_charges[s] > d - 1) return MPS_ECHARGE;
   mps_s* h = new mps_s();
   h->L = L; h->d = d; h->chi_max = chi_max; h->precision = precision;
+  h->rule.d = d;
+  h->rule.zn = zn;
   h->stream = (cudaStream_t)cuda_stream;
   std::vector<int> c(L + 1, 0);
-  for (int b = L - 1; b >= 0; --b) c[b] = c[b + 1] + site_charges[b];
+  for (int b = L - 1; b >= 0; --b) c[b] = h->rule.wrap(c[b + 1] + site_charges[b]);
   h->N = c[0];
   const int N = h->N;
-  auto Wc = config_counts(L, d, N);
+  auto Wc = zn ? std::vector<std::vector<double>>() : config_counts(L, d, N);
   h->bonds.resize(L + 1);
   h->bond_cap.resize(L + 1);
   h->lam_base.resize(L + 1);
@@ -1025,8 +1212,12 @@ static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, 
     t.dim = {1};
     t.rebuild_offsets();
     double hb = 0.0;
-    const int lo = std::max(0, N - (d - 1) * b), hi = std::min(N, (d - 1) * (L - b));
-    for (int q = lo; q <= hi; ++q) hb += std::min(Wc[b][N - q], Wc[L - b][q]);
+    if (zn) {   // d^k strings of k sites: the smaller side bounds the Schmidt rank
+      hb = std::pow((double)d, (double)std::min(b, L - b));
+    } else {
+      const int lo = std::max(0, N - (d - 1) * b), hi = std::min(N, (d - 1) * (L - b));
+      for (int q = lo; q <= hi; ++q) hb += std::min(Wc[b][N - q], Wc[L - b][q]);
+    }
     h->bond_cap[b] = (int64_t)std::max(1.0, std::min((double)chi_max, hb));
     h->lam_base[b] = lam_total;
     lam_total += (h->bond_cap[b] + 31) / 32 * 32;
@@ -1039,7 +1230,7 @@ static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, 
   h->site_base.resize(L);
   int64_t site_total = 0;
   for (int s = 0; s < L; ++s) {
-    layout_site(h->bonds[s], h->bonds[s + 1], d, h->sites[s]);
+    layout_site(h->bonds[s], h->bonds[s + 1], h->rule, h->sites[s]);
     // sites outside [site_lo, site_hi) keep their one product-state element and never grow
     h->site_cap[s] = (s >= site_lo && s < site_hi) ? std::max<int64_t>(1, h->bond_cap[s] * h->bond_cap[s + 1]) : 1;
     h->site_base[s] = site_total;
@@ -1259,7 +1450,8 @@ int mps_expect(mps_t h, int site, const double* diag_op, double* out) {
   const double2* slot = h->slot_ptr(site, h->cur[site]);
   std::vector<ExpectTask> t;
   for (const SiteBlock& b : S.blocks)
-    t.push_back(ExpectTask{slot + b.off, h->lambda_ptr(site) + Lb.off[b.il], b.Dl, b.Dm, diag_op[b.l - b.m]});
+    t.push_back(ExpectTask{slot + b.off, h->lambda_ptr(site) + Lb.off[b.il], b.Dl, b.Dm,
+                           diag_op[h->rule.phys(b.l, b.m)]});
   const int nt = (int)t.size();
   const int64_t bytes_t = a256(sizeof(ExpectTask) * (int64_t)nt);
   CUDA_OR_FAIL(h, cudaEventSynchronize(h->staged));
@@ -1299,7 +1491,7 @@ int mps_amplitude_batch(mps_t h, int n, const int32_t* configs, double* out) {
     c[L] = 0;
     for (int b = L - 1; b >= 0; --b) {
       if (cfg[b] < 0 || cfg[b] > h->d - 1) ok = false;
-      c[b] = c[b + 1] + cfg[b];
+      c[b] = h->rule.wrap(c[b + 1] + cfg[b]);
     }
     if (c[0] != h->N) ok = false;
     for (int s = 0; s < L; ++s) {
@@ -1357,7 +1549,7 @@ int mps_sample(mps_t h, int n, const double* uniforms, int32_t* configs_out, dou
     for (int li = 0; li < Lb.size(); ++li)
       for (int i = 0; i < d; ++i) {
         SampleEntry e{nullptr, 0, 0, -1, 0};
-        const int bi = h->sites[s].find(Lb.charge[li], Lb.charge[li] - i);
+        const int bi = h->sites[s].find(Lb.charge[li], h->rule.wrap(Lb.charge[li] - i));
         if (bi >= 0) {
           const SiteBlock& B = h->sites[s].blocks[bi];
           e.blk = slot + B.off;
@@ -1460,7 +1652,8 @@ int mps_set_bond(mps_t h, int bond, int n_sectors, const int32_t* charges, const
   t.charge.assign(charges, charges + n_sectors);
   t.dim.assign(dims, dims + n_sectors);
   const int d = h->d, L = h->L, N = h->N;
-  const int lo = std::max(0, N - (d - 1) * bond), hi = std::min(N, (d - 1) * (L - bond));
+  const int lo = h->rule.zn ? 0 : std::max(0, N - (d - 1) * bond);
+  const int hi = h->rule.zn ? h->rule.zn - 1 : std::min(N, (d - 1) * (L - bond));
   for (int i = 0; i < n_sectors; ++i) {
     if (t.dim[i] < 1) return fail(h, MPS_EINVAL, "sector dimension < 1");
     if (i && t.charge[i] <= t.charge[i - 1]) return fail(h, MPS_EINVAL, "charges not ascending");
@@ -1483,7 +1676,7 @@ int mps_set_site(mps_t h, int site, int n_blocks, const int32_t* lcharges, const
   if (check_handle(h)) return MPS_EINVAL;
   if (site < 0 || site >= h->L) return fail(h, MPS_EINVAL, "bad site");
   SiteTable t;
-  layout_site(h->bonds[site], h->bonds[site + 1], h->d, t);
+  layout_site(h->bonds[site], h->bonds[site + 1], h->rule, t);
   if (n_blocks != (int)t.blocks.size() || (n_blocks && (!lcharges || !mcharges)))
     return fail(h, MPS_ECHARGE, "block list does not match the allowed (l, m) pairs");
   for (int i = 0; i < n_blocks; ++i)
@@ -1527,6 +1720,12 @@ int mps_reset_kernel_stats(mps_t h) {
 }
 
 int64_t mps_launch_count(void) { return g_launches.load(); }
+
+int mps_set_chi_deflation(mps_t h, double level) {
+  if (!h || !(level >= 0.0 && level <= kChiGuard)) return MPS_EINVAL;
+  h->chi_deflate = level;
+  return MPS_OK;
+}
 
 int mps_set_sweep_limit(mps_t h, int max_sweeps) {
   if (!h || max_sweeps < 1 || max_sweeps > kJacobiMaxSweeps) return MPS_EINVAL;
@@ -1583,7 +1782,10 @@ int mps_autotune_table(char* buf, int cap, int* len) {
       const TuneEntry& e = kv.second;
       if (e.best < 0) continue;
       const SvdTune b = svd_tune_candidate(e.best);
-      if (b.c16_min_k < (1 << 30))
+      if (b.rr_min_k < (1 << 30))
+        std::snprintf(line, sizeof(line), "%s -> round-robin from K=%d hits=%lld ms=", key.c_str(), b.rr_min_k,
+                      (long long)e.hits);
+      else if (b.c16_min_k < (1 << 30))
         std::snprintf(line, sizeof(line), "%s -> 16-CTA clusters from K=%d hits=%lld ms=", key.c_str(), b.c16_min_k,
                       (long long)e.hits);
       else

@@ -217,13 +217,26 @@ __device__ bool jacobi_pair_grp(double2* A, int R, int ld, double* nrm, int p, i
   bool act = valid && fmin(alpha, beta) > floor2;   // noise columns are left alone
   double2* ap = A + (int64_t)(act ? p : 0) * ld;
   double2* aq = A + (int64_t)(act ? q : 0) * ld;
+  // two independent partial sums per component halve the FP64 dependency chains (the
+  // FP64 pipe's latency, not its issue rate, bounds a lone chain)
   double gr = 0.0, gi = 0.0;
   if (act) {
-    for (int i = gl; i < R; i += G) {
+    double gr1 = 0.0, gi1 = 0.0;
+    int i = gl;
+    for (; i + G < R; i += 2 * G) {
+      const double2 x = ap[i], y = aq[i], x1 = ap[i + G], y1 = aq[i + G];
+      gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+      gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+      gr1 = fma(x1.x, y1.x, fma(x1.y, y1.y, gr1));
+      gi1 = fma(x1.x, y1.y, fma(-x1.y, y1.x, gi1));
+    }
+    if (i < R) {
       const double2 x = ap[i], y = aq[i];
       gr = fma(x.x, y.x, fma(x.y, y.y, gr));
       gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
     }
+    gr += gr1;
+    gi += gi1;
   }
   for (int o = G >> 1; o; o >>= 1) {
     gr += __shfl_xor_sync(0xffffffffu, gr, o);
@@ -239,6 +252,7 @@ __device__ bool jacobi_pair_grp(double2* A, int R, int ld, double* nrm, int p, i
     const double ct = Rt.c * tau;
     Rt.u = ct * gr;
     Rt.v = ct * gi;
+#pragma unroll 2
     for (int i = gl; i < R; i += G) {
       double2 x = ap[i], y = aq[i];
       rotate_pair(x, y, Rt);
@@ -267,6 +281,105 @@ __device__ __forceinline__ int group_width(int P, int R, int nwarps) {
     if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = G; }
   }
   return best;
+}
+
+// The same for a group of G = 32 wg lanes (wg > 1 whole warps, groups aligned to wg warps)
+// per pair, for steps with fewer disjoint pairs than warps (the large sectors, whose column
+// blocks hold only 3-5 columns): each warp reduces its part of the dot product with shuffles
+// and the group sums the warp partials through shared memory behind a named barrier (id
+// bar_id, one per group).  red holds two buffers of 2 doubles per warp, used alternately
+// (phase), so a warp that runs ahead into the next pair never overwrites partials still read.
+__device__ bool jacobi_pair_mw(double2* A, int R, int ld, double* nrm, int p, int q, bool valid, int G,
+                               double tol2, double floor2, double* red, int& phase, int bar_id) {
+  const int wg = G >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w0 = warp - warp % wg, gl = (warp - w0) * 32 + lane;
+  double* rb = red + phase * 2 * kMaxWarps;
+  phase ^= 1;
+  double alpha = 0.0, beta = 0.0;
+  if (valid) {
+    alpha = nrm[p];
+    beta = nrm[q];
+  }
+  bool act = valid && fmin(alpha, beta) > floor2;
+  double2* ap = A + (int64_t)(act ? p : 0) * ld;
+  double2* aq = A + (int64_t)(act ? q : 0) * ld;
+  double gr = 0.0, gi = 0.0;
+  if (act) {
+    double gr1 = 0.0, gi1 = 0.0;
+    int i = gl;
+    for (; i + G < R; i += 2 * G) {
+      const double2 x = ap[i], y = aq[i], x1 = ap[i + G], y1 = aq[i + G];
+      gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+      gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+      gr1 = fma(x1.x, y1.x, fma(x1.y, y1.y, gr1));
+      gi1 = fma(x1.x, y1.y, fma(-x1.y, y1.x, gi1));
+    }
+    if (i < R) {
+      const double2 x = ap[i], y = aq[i];
+      gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+      gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+    }
+    gr += gr1;
+    gi += gi1;
+  }
+  gr = warp_sum(gr);
+  gi = warp_sum(gi);
+  if (lane == 0) {
+    rb[2 * warp] = gr;
+    rb[2 * warp + 1] = gi;
+  }
+  asm volatile("bar.sync %0, %1;\n" ::"r"(bar_id), "r"(G) : "memory");
+  gr = 0.0;
+  gi = 0.0;
+  for (int x = 0; x < wg; ++x) {        // the same order in every warp of the group
+    gr += rb[2 * (w0 + x)];
+    gi += rb[2 * (w0 + x) + 1];
+  }
+  const double g2 = fma(gr, gr, gi * gi);
+  act = act && (g2 > tol2 * alpha * beta);
+  if (act) {
+    const double delta = beta - alpha;
+    const double tau = copysign(2.0, delta) / (fabs(delta) + sqrt(fma(delta, delta, 4.0 * g2)));
+    Rot Rt;
+    Rt.c = rsqrt(fma(tau * tau, g2, 1.0));
+    const double ct = Rt.c * tau;
+    Rt.u = ct * gr;
+    Rt.v = ct * gi;
+#pragma unroll 2
+    for (int i = gl; i < R; i += G) {
+      double2 x = ap[i], y = aq[i];
+      rotate_pair(x, y, Rt);
+      ap[i] = x;
+      aq[i] = y;
+    }
+    if (gl == 0) {
+      const double tg = tau * g2;
+      nrm[p] = fmax(alpha - tg, 0.0);
+      nrm[q] = beta + tg;
+    }
+  }
+  return act;
+}
+
+// Group width for P disjoint pairs of length R over nwarps warps, multi-warp groups
+// included (wg warps per pair, wg dividing nwarps; about 40 more instructions per pass for
+// the shared-memory reduction).  Returns G; slots() gives the pairs one pass covers.
+__device__ __forceinline__ int group_width_mw(int P, int R, int nwarps) {
+  int best = 32;
+  long long best_cost = -1;
+  for (int G = 8; G <= 32 * nwarps; G = (G < 32) ? 2 * G : G + 32) {
+    if (G > 32 && nwarps % (G >> 5) != 0) continue;
+    const int slots = G <= 32 ? nwarps * (32 / G) : nwarps / (G >> 5);
+    const long long cost =
+        (long long)((P + slots - 1) / slots) * (16 * ((R + G - 1) / G) + 50 + (G > 32 ? 40 : 0));
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = G; }
+  }
+  return best;
+}
+__device__ __forceinline__ int group_slots(int G, int nwarps) { return G <= 32 ? nwarps * (32 / G) : nwarps / (G >> 5); }
+__device__ __forceinline__ int group_slot(int G) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  return G <= 32 ? warp * (32 / G) + lane / G : warp / (G >> 5);
 }
 
 // Per-sector working set (shared memory or global scratch).
@@ -362,6 +475,8 @@ struct JacobiBlocks {
   __device__ int operator()(double2* W, int n, int ld, int K, const Work& w, int rank, int nctas, Sync sync,
                             double tol2, double floor2, int max_sweeps, bool& converged) const {
     __shared__ int s_rot;
+    __shared__ double s_red[2 * 2 * kMaxWarps];   // multi-warp pair partials, two buffers
+    int mw_phase = 0;
     __shared__ int s_col[2 * kMaxStaged];   // first column of each staged block
     __shared__ int s_len[2 * kMaxStaged];   // its width (0: slot unused)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -416,9 +531,9 @@ struct JacobiBlocks {
           if (r == 0) {   // pairs inside each staged block, round-robin within the block
             const int mpb = bsmax + (bsmax & 1);
             const int P = 2 * ns * (mpb / 2);
-            const int G = group_width(P, n, nwarps), per = 32 / G, slot = warp * per + lane / G;
+            const int G = group_width_mw(P, n, nwarps), slots = group_slots(G, nwarps), slot = group_slot(G);
             for (int rr = 0; rr < mpb - 1; ++rr) {
-              for (int base = 0; base < P; base += nwarps * per) {
+              for (int base = 0; base < P; base += slots) {
                 const int k = base + slot, j = k / (mpb / 2);
                 int a = 0, b = 0;
                 bool valid = k < P;
@@ -426,17 +541,21 @@ struct JacobiBlocks {
                   rr_pair(k % (mpb / 2), rr, mpb, a, b);
                   valid = a < s_len[j] && b < s_len[j];
                 }
-                rot |= jacobi_pair_grp(sm, n, n, smn, j * bsmax + min(a, b), j * bsmax + max(a, b), valid, G,
-                                       tol2, floor2);
+                if (G <= 32)
+                  rot |= jacobi_pair_grp(sm, n, n, smn, j * bsmax + min(a, b), j * bsmax + max(a, b), valid, G,
+                                         tol2, floor2);
+                else
+                  rot |= jacobi_pair_mw(sm, n, n, smn, j * bsmax + min(a, b), j * bsmax + max(a, b), valid, G,
+                                        tol2, floor2, s_red, mw_phase, 1 + slot);
               }
               __syncthreads();
             }
           }
           {   // cross pairs: block slots 2j and 2j + 1, the smaller block shifted against the larger
             const int P = ns * bsmax;
-            const int G = group_width(P, n, nwarps), per = 32 / G, slot = warp * per + lane / G;
+            const int G = group_width_mw(P, n, nwarps), slots = group_slots(G, nwarps), slot = group_slot(G);
             for (int t = 0; t < bsmax; ++t) {
-              for (int base = 0; base < P; base += nwarps * per) {
+              for (int base = 0; base < P; base += slots) {
                 const int k = base + slot, j = k / bsmax, i = k % bsmax;
                 int p = 0, q = 0;
                 bool valid = false;
@@ -452,7 +571,10 @@ struct JacobiBlocks {
                     q = max(pa, pb);
                   }
                 }
-                rot |= jacobi_pair_grp(sm, n, n, smn, p, q, valid, G, tol2, floor2);
+                if (G <= 32)
+                  rot |= jacobi_pair_grp(sm, n, n, smn, p, q, valid, G, tol2, floor2);
+                else
+                  rot |= jacobi_pair_mw(sm, n, n, smn, p, q, valid, G, tol2, floor2, s_red, mw_phase, 1 + slot);
               }
               __syncthreads();
             }
@@ -1068,6 +1190,7 @@ cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& group
         pick_cl = cl; pick_g = g; pick_gs = gs;
       }
     }
+    if (std::min(S.m, S.n) >= tune.rr_min_k) pick_cl = 0;
     if (pick_cl) {
       key[k] = {kSvdClusterBlock, pick_cl};
       smem[k] = block_smem_need(S.m, cn, pick_cl, pick_g, pick_gs);
@@ -1236,7 +1359,9 @@ extern "C" int mps_svd_sectors(int n_sectors, const int* m, const int* n,
   std::vector<SvdSector> all(cta);
   all.insert(all.end(), cl.begin(), cl.end());
   std::vector<SvdGroup> groups;
-  if (svd_group(all, groups) != cudaSuccess) return MPS_ECUDA;
+  SvdTune tune;
+  svd_forced_tune(tune);
+  if (svd_group(all, groups, tune) != cudaSuccess) return MPS_ECUDA;
   if (cudaMemcpyAsync(d_work, all.data(), sizeof(SvdSector) * all.size(), cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return MPS_ECUDA;
@@ -1305,7 +1430,9 @@ extern "C" int mps_svd_sectors_noalloc(int n_sectors, const int* m, const int* n
   std::vector<SvdSector> all(cta);
   all.insert(all.end(), cl.begin(), cl.end());
   std::vector<SvdGroup> groups;
-  if (svd_group(all, groups) != cudaSuccess) return MPS_ECUDA;
+  SvdTune tune;
+  svd_forced_tune(tune);
+  if (svd_group(all, groups, tune) != cudaSuccess) return MPS_ECUDA;
   if (cudaMemcpyAsync(d_work, all.data(), sizeof(SvdSector) * all.size(), cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return MPS_ECUDA;

@@ -14,8 +14,44 @@ namespace mps {
 constexpr int kSvdSideStreams = 4;      // side streams for concurrent SVD kernel groups
 
 // ---------------------------------------------------------------------------
+// Charge arithmetic.  U(1) (zn = 0, Sec. II): block (l, m) of a site carries the physical
+// index i = l - m and exists for 0 <= i <= d - 1; the two-site gate has blocks q = l - r in
+// [0, 2(d-1)] over the pairs (i, q - i).  Z_n (zn = n = d, the "more general Abelian" case of
+// Sec. I): charges are residues mod n, i = (l - m) mod n, every pair of charges occurs, and
+// gate block q in [0, n) acts on the n pairs (i, (q - i) mod n).  Either way a Theta(c)
+// block's rows and columns are contiguous runs of the sorted bond tables (for Z_n with
+// d = n: all sectors).
+// ---------------------------------------------------------------------------
+struct ChargeRule {
+  int d = 2;
+  int zn = 0;
+  int wrap(int c) const { return zn ? ((c % zn) + zn) % zn : c; }
+  int phys(int l, int m) const {           // physical index of block (l, m), or -1
+    const int i = zn ? wrap(l - m) : l - m;
+    return (i >= 0 && i < d) ? i : -1;
+  }
+  int pair(int l, int r) const {           // two-site gate block of (l, r), or -1
+    if (zn) return wrap(l - r);
+    const int q = l - r;
+    return (q >= 0 && q <= 2 * (d - 1)) ? q : -1;
+  }
+  int nblocks() const { return zn ? zn : 2 * d - 1; }
+  int base(int q) const { return zn ? 0 : (q - d + 1 > 0 ? q - d + 1 : 0); }   // first left index of block q
+  int sn(int q) const { return zn ? zn : (q < d - 1 ? q : d - 1) - base(q) + 1; }
+  int64_t block_off(int q) const {
+    int64_t t = 0;
+    for (int k = 0; k < q; ++k) t += (int64_t)sn(k) * sn(k);
+    return t;
+  }
+  int64_t gate_len() const { return block_off(nblocks()); }
+  // candidate middle charges c of a pair (l, r): [cmin, cmax]
+  int cmin(int l, int r) const { return zn ? 0 : (r > l - d + 1 ? r : l - d + 1); }
+  int cmax(int l, int r) const { return zn ? zn - 1 : (l < r + d - 1 ? l : r + d - 1); }
+};
+
+// ---------------------------------------------------------------------------
 // Host mirror of the charge structure (Sec. II: right-charge labels per bond,
-// blocks (l, m) with 0 <= l - m <= d - 1 per site).
+// blocks (l, m) with a physical index i = l - m (mod n for Z_n) in [0, d-1] per site).
 // ---------------------------------------------------------------------------
 struct BondTable {
   std::vector<int> charge;    // ascending
@@ -42,6 +78,7 @@ struct SiteTable {
 
 // Enumerate the allowed blocks of a site between two bond tables, in (l, m) order.
 void layout_site(const BondTable& left, const BondTable& right, int d, SiteTable& out);
+void layout_site(const BondTable& left, const BondTable& right, const ChargeRule& rule, SiteTable& out);
 
 // ---------------------------------------------------------------------------
 // Sector plan of one two-site update (the integer planner, K0).
@@ -57,6 +94,8 @@ struct UpdatePlan {
   std::vector<int> triple_l, triple_m, triple_r;        // sector indices, lexicographic
 };
 void plan_update(const BondTable& left, const BondTable& mid, const BondTable& right, int d,
+                 UpdatePlan& plan);
+void plan_update(const BondTable& left, const BondTable& mid, const BondTable& right, const ChargeRule& rule,
                  UpdatePlan& plan);
 
 // ---------------------------------------------------------------------------
@@ -178,6 +217,7 @@ void count_launch();
 
 struct mps_s {
   int L = 0, d = 0, N = 0, chi_max = 0, precision = 0;
+  mps::ChargeRule rule;                   // U(1) or Z_n charge arithmetic (N is mod n for Z_n)
   cudaStream_t stream = nullptr;
   std::vector<mps::BondTable> bonds;      // L + 1
   std::vector<mps::SiteTable> sites;      // L
@@ -203,6 +243,7 @@ struct mps_s {
   int* tc_flag = nullptr;                 // set by a tensor-core GEMM whose bounded wait expired
   std::vector<double> cut_est;            // per bond: smallest kept sigma of its last update (0: none)
   int sweep_limit = 40;                   // Jacobi sweep limit of this handle's update calls
+  double chi_deflate = 3e-4;              // level of the deflation from a bond's previous chi cut (0: off)
   // CUDA graphs: the two launch phases of an update call are captured and replayed
   // through one executable graph each, updated in place while the topology holds
   bool graphs = false;
@@ -225,13 +266,19 @@ cudaError_t launch_theta(const ThetaTask* d_tasks, const TileRef* d_tiles, int n
 struct SvdGroup { int kind, cl, smem, first, count; };
 // Tile shape of the cluster SVD: target column-block width of the block-Jacobi kernel, the
 // smallest cluster size tried, and the sector size (min(m, n)) from which a sector gets a
-// cluster of 16 CTAs (the largest sectors of a layer set its critical path).  The autotuner
-// picks one per sector-size histogram.
-struct SvdTune { int bw = 6; int cl_min = 2; int c16_min_k = 1 << 30; };
-constexpr int kTuneCands = 10;
-inline SvdTune svd_tune_candidate(int k) {   // bw in {4, 6, 8, 12} x cl_min in {2, 4}; 16 CTAs from 512 or 256
+// cluster of 16 CTAs (the largest sectors of a layer set its critical path), and the sector
+// size from which a sector runs the round-robin cluster kernel instead of the block-Jacobi one.
+// The autotuner picks one per sector-size histogram.
+struct SvdTune { int bw = 6; int cl_min = 2; int c16_min_k = 1 << 30; int rr_min_k = 1 << 30; };
+constexpr int kTuneCands = 12;
+// bw in {4, 6, 8, 12} x cl_min in {2, 4}; 16 CTAs from 512 or 256; round-robin from 512 or 256
+inline SvdTune svd_tune_candidate(int k) {
   static const int bws[4] = {4, 6, 8, 12};
   SvdTune t;
+  if (k >= 10) {
+    t.rr_min_k = k == 10 ? 512 : 256;
+    return t;
+  }
   if (k >= 8) {
     t.c16_min_k = k == 8 ? 512 : 256;
     return t;
@@ -243,6 +290,8 @@ inline SvdTune svd_tune_candidate(int k) {   // bw in {4, 6, 8, 12} x cl_min in 
 // Orders `secs` into groups (costliest first inside each) and fills `groups`.
 cudaError_t svd_group(std::vector<SvdSector>& secs, std::vector<SvdGroup>& groups,
                       const SvdTune& tune = SvdTune());
+// The candidate mps_autotune_force set (true), or false when none is forced.
+bool svd_forced_tune(SvdTune& t);
 // Group 0 on st, group g > 0 on side[g-1] when n_side >= groups - 1; st then waits for all.
 cudaError_t launch_svd_groups(const SvdSector* d_secs, const std::vector<SvdGroup>& groups, cudaStream_t st,
                               const cudaStream_t* side, int n_side, cudaEvent_t fork, const cudaEvent_t* join,
@@ -252,25 +301,68 @@ cudaError_t launch_select(const SelectSector* d_secs, const SelectTask* d_tasks,
                           int* d_kept, SelectResult* d_res, cudaStream_t st);
 cudaError_t launch_gemm(const GemmTask* d_tasks, const TileRef* d_tiles, int n_tiles, cudaStream_t st);
 
-// Tensor-core complex GEMM (k_tc.cu): C(tile) = sum over segments (alpha A_seg) . B_seg,
-// A(i, k) = A[i * sar + k * sac], B(k, j) = B[k * sbr + j * sbc] (complex strides).
-struct TcSegment {            // one K segment
-  const double2* A;
-  const double2* B;
-  int Kc;                     // complex K of the segment
-  int sar, sac, sbr, sbc;
-  double2 alpha;
+// TMA-fed tensor-core complex GEMM (k_tma.cu).  Operands live in "shadow tiles": 128 rows of
+// 128 bytes each (16 KB), TF32 (a row holds 16 complex K as interleaved re, im floats) or BF16
+// (a hi tile and a lo tile, a row holding 32 complex K).  An A tile row is one matrix row; a B
+// tile holds 64 complex columns j as two rows each: 2j = conj(b_j), 2j + 1 = i conj(b_j), so
+// that one real MMA of the interleaved K gives re and im of C in adjacent accumulator columns.
+// All tiles of a call are slots of one buffer that a single 2-D tensor map describes.
+constexpr int kShRows = 128;                  // rows of a shadow tile
+constexpr int kShRowBytes = 128;              // bytes of a shadow tile row (the 128-byte swizzle span)
+constexpr int64_t kShTileBytes = kShRows * kShRowBytes;
+constexpr int kShTileN = 64;                  // complex columns of a B tile (= of an output tile)
+inline int sh_kc(int precision) { return precision == MPS_BF16X3 ? 32 : 16; }   // complex K per tile
+inline int sh_tiles_per_k(int precision) { return precision == MPS_BF16X3 ? 2 : 1; }   // hi (+ lo)
+// One FP64 complex matrix into shadow tiles: element (i, k) = src[i * s_i + k * s_k];
+// i runs over the rows (A) or the columns (B) of the operand.  Tile (it, kt) of the operand is
+// slot tile0 + (it * kt_n + kt) * sh_tiles_per_k.  Rows and K beyond the matrix are zero.
+struct ShadowTask {
+  const double2* src;
+  int64_t s_i, s_k;
+  int n_i, K;                 // rows (A) / columns (B); complex K
+  int64_t tile0;
+  int kt_n;                   // K tiles per row tile
+  int is_b;                   // 1: B-operand tile rows (two per column)
 };
-struct TcTile {               // a 128 x 64 complex output tile over segments [seg0, seg0 + nseg)
-  double2* C;                 // row-major, row stride ldc; the tile overwrites C
-  int ldc, M, N;
-  int row0, col0;
-  int seg0, nseg;
+struct ShadowTile { int task, it, kt; };
+cudaError_t launch_shadow(int precision, const ShadowTask* d_tasks, const ShadowTile* d_tiles, int n_tiles,
+                          char* d_slots, cudaStream_t st);
+// One 128 x 64 complex output tile of C = sum over K tiles (A tile a0 + kt) . (B tile b0 + kt):
+// mode 0 stores it as complex64 (FP32) into C, mode 1 as complex128 scaled by alpha.
+struct TmaJob {
+  int64_t a0, b0;             // first A / B slot (K tiles follow, sh_tiles_per_k slots each)
+  int kt_n;                   // K tiles (0: the product is zero)
+  int M, N;                   // valid rows and complex columns of the tile
+  int mode;
+  float alpha;
+  void* C;                    // element (0, 0) of the tile
+  int64_t ldc;                // row stride of C in complex elements
 };
-constexpr int kTcTileM = 128, kTcTileN = 64;
-// precision is MPS_TF32 or MPS_BF16X3; *d_err is set to 1 when a bounded wait expires.
-cudaError_t launch_tc_zgemm(int precision, const TcTile* d_tiles, int n_tiles, const TcSegment* d_segs, int* d_err,
-                            cudaStream_t st);
+// d_slots: the shadow buffer, n_slots tiles of kShTileBytes; *d_err = 1 when a bounded wait expires.
+cudaError_t launch_tma_zgemm(int precision, const TmaJob* d_jobs, int n_jobs, const char* d_slots, int64_t n_slots,
+                             int* d_err, cudaStream_t st);
+// The gate mix of the Theta build on the tensor-core path: for one (l, r) pair with products
+// T_i = B[s][l, m_i] B[s+1][m_i, r] (complex64, D_l x D_r, row stride ldt),
+//   Theta'(c_o)[l, r] = sum_i G_n[go_o, gi_i] T_i      (FP64 into the Theta' workspace)
+// and the same values as A-operand shadow tiles of the reassembly product (block (l, c_o):
+// rows of l, K = the columns of Theta'(c_o), first K index coff_o).
+struct MixTask {
+  const float2* T[MPS_MAX_D];
+  int gi[MPS_MAX_D];
+  int nm;
+  double2* out[MPS_MAX_D];
+  int ldo[MPS_MAX_D];
+  int go[MPS_MAX_D];
+  int64_t sh0[MPS_MAX_D];         // reassembly A slots of block (l, c_o)
+  int sh_ktn[MPS_MAX_D];          // K tiles of that block
+  int coff[MPS_MAX_D];            // K offset of column 0 of r inside Theta'(c_o)
+  int nc;
+  const double2* gate;        // G_n, sn x sn row-major
+  int sn;
+  int Dl, Dr;
+  int ldt;
+};
+cudaError_t launch_mix(int precision, const MixTask* d_tasks, int n_tasks, char* d_slots, cudaStream_t st);
 cudaError_t launch_scatter(const ScatterTask* d_tasks, int n_tasks, int64_t n_elems, cudaStream_t st);
 cudaError_t launch_lambda(const LambdaTask* d_tasks, int n_tasks, cudaStream_t st);
 
@@ -305,6 +397,9 @@ constexpr double kDeflateRel = 0.01;
 // vectors move by < 1e-13 on graded sectors).
 constexpr double kChiDeflate = 3e-4;
 constexpr double kChiVerify = 0.5;
+// an update is redone when its cut falls below level / kChiGuard of the estimate (kChiGuard = 6e-4:
+// an unresolved value then lies >= 1600x under the actual cut, whatever the level)
+constexpr double kChiGuard = kChiDeflate / kChiVerify;
 
 // GEMM tiling shared by the Theta build and the reassembly GEMM.
 constexpr int kTile = 64;

@@ -40,12 +40,17 @@ int SiteTable::find(int l, int m) const {
 }
 
 void layout_site(const BondTable& left, const BondTable& right, int d, SiteTable& out) {
+  ChargeRule u1;
+  u1.d = d;
+  layout_site(left, right, u1, out);
+}
+
+void layout_site(const BondTable& left, const BondTable& right, const ChargeRule& rule, SiteTable& out) {
   out.blocks.clear();
   int64_t off = 0;
   for (int i = 0; i < left.size(); ++i) {
     for (int j = 0; j < right.size(); ++j) {
-      int diff = left.charge[i] - right.charge[j];
-      if (diff < 0 || diff > d - 1) continue;
+      if (rule.phys(left.charge[i], right.charge[j]) < 0) continue;
       SiteBlock b;
       b.l = left.charge[i]; b.m = right.charge[j];
       b.il = i; b.im = j;
@@ -60,19 +65,37 @@ void layout_site(const BondTable& left, const BondTable& right, int d, SiteTable
 
 void plan_update(const BondTable& left, const BondTable& mid, const BondTable& right, int d,
                  UpdatePlan& plan) {
+  ChargeRule u1;
+  u1.d = d;
+  plan_update(left, mid, right, u1, plan);
+}
+
+void plan_update(const BondTable& left, const BondTable& mid, const BondTable& right, const ChargeRule& rule,
+                 UpdatePlan& plan) {
+  const int d = rule.d;
   plan.sectors.clear();
   plan.triple_l.clear(); plan.triple_m.clear(); plan.triple_r.clear();
   for (int i = 0; i < left.size(); ++i)
     for (int j = 0; j < mid.size(); ++j) {
-      int a = left.charge[i] - mid.charge[j];
-      if (a < 0 || a > d - 1) continue;
+      if (rule.phys(left.charge[i], mid.charge[j]) < 0) continue;
       for (int k = 0; k < right.size(); ++k) {
-        int b = mid.charge[j] - right.charge[k];
-        if (b < 0 || b > d - 1) continue;
+        if (rule.phys(mid.charge[j], right.charge[k]) < 0) continue;
         plan.triple_l.push_back(i); plan.triple_m.push_back(j); plan.triple_r.push_back(k);
       }
     }
   if (left.size() == 0 || right.size() == 0) return;
+  if (rule.zn) {
+    // Z_n with d = n: every middle charge c has all left sectors as rows (i' = (l - c) mod n)
+    // and all right sectors as columns (j' = (c - r) mod n)
+    for (int c = 0; c < rule.zn; ++c) {
+      SectorPlanEntry e;
+      e.c = c; e.l0 = 0; e.l1 = left.size(); e.r0 = 0; e.r1 = right.size();
+      e.rows = left.total();
+      e.cols = right.total();
+      plan.sectors.push_back(e);
+    }
+    return;
+  }
   // Candidate middle charges: c with some left l in [c, c+d-1] and right r in [c-d+1, c].
   int cmin = std::max(right.charge.front(), left.charge.front() - (d - 1));
   int cmax = std::min(left.charge.back(), right.charge.back() + (d - 1));

@@ -4,7 +4,9 @@ Host-side model set-up (FP64, once per workload), not part of the update path.
 A gate conserving the total charge n = i + j of a site pair is given by its
 blocks G_n over the basis (i, n - i), i ascending (the layout of the C ABI).
 Models: XXZ chain, Bose-Hubbard chain, boson-sampling beam splitter (the U(1)
-examples of arXiv:2303.11409, Sec. I).
+examples of arXiv:2303.11409, Sec. I), and the Z_n clock chain for the cyclic-group
+handles (mps_create_zn; n = 2 is the transverse-field Ising chain): its gates have the n
+blocks q = (i + j) mod n over the pairs (i, (q - i) mod n), i ascending.
 """
 from __future__ import annotations
 
@@ -81,6 +83,26 @@ def beam_splitter_gate(theta: float, phi: float, d: int) -> list[np.ndarray]:
                 g[a, b] = acc * math.sqrt(math.factorial(p) * math.factorial(q)
                                           / (math.factorial(s_) * math.factorial(t_)))
         out.append(g)
+    return out
+
+
+def clock_gate(n: int, J: float, f: float, tau: float, w_left: float, w_right: float) -> list[np.ndarray]:
+    """exp(-i tau h) per Z_n block, h = -J (Z1 Z2^dag + Z1^dag Z2) - f (w1 (X1 + X1^dag) + w2 (X2 + X2^dag)).
+
+    The local index k is the Z_n charge: X|k> = e^{2 pi i k / n}|k> (X + X^dag is diagonal,
+    2 cos(2 pi k / n)) and Z|k> = |k + 1 mod n>, so Z1 Z2^dag moves (i, j) to (i + 1, j - 1)
+    within the block of (i + j) mod n.
+    """
+    field = 2.0 * np.cos(2.0 * np.pi * np.arange(n) / n)
+    out = []
+    for q in range(n):
+        h = np.zeros((n, n))
+        for a in range(n):                 # basis pair a = (a, (q - a) mod n)
+            j = (q - a) % n
+            h[a, a] = -f * (w_left * field[a] + w_right * field[j])
+            h[(a + 1) % n, a] += -J        # Z1 Z2^dag
+            h[(a - 1) % n, a] += -J        # its adjoint
+        out.append(scipy.linalg.expm(-1j * tau * h))
     return out
 
 

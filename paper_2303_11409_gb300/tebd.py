@@ -36,6 +36,9 @@ class GateTable:
             tau = f * self.dt
             if self.model == "xxz":
                 blocks = models.xxz_gate(self.p["delta"], tau, self.p.get("J", 1.0))
+            elif self.model == "clock":
+                wl, wr = models.bose_hubbard_weights(self.L, s)
+                blocks = models.clock_gate(self.d, self.p.get("J", 1.0), self.p["f"], tau, wl, wr)
             elif self.model == "bh":
                 wl, wr = models.bose_hubbard_weights(self.L, s)
                 blocks = models.bose_hubbard_gate(self.d, self.p.get("J", 1.0), self.p["U"], tau, wl, wr)

@@ -130,10 +130,10 @@ def test_autotune_tunes_once_and_keeps_parity(gpu_lib):
 
 
 def test_every_tile_shape_matches_the_oracle_on_large_sectors(gpu_lib):
-    """Each of the autotuner's ten candidates, forced in turn, on one middle update of a
+    """Each of the autotuner's twelve candidates, forced in turn, on one middle update of a
     random chi = 2048 state (Theta(c) up to 1700 x 113 and 796 x 796, so candidates 8 and 9
-    put the largest sectors on 16-CTA clusters): every one keeps the oracle's sector
-    structure, Schmidt values and two-site product."""
+    put the largest sectors on 16-CTA clusters and 10 and 11 on the round-robin kernel):
+    every one keeps the oracle's sector structure, Schmidt values and two-site product."""
     m = gpu_lib
     L, d, N, chi = 16, 5, 16, 2048
     s = L // 2 - 1
@@ -142,7 +142,7 @@ def test_every_tile_shape_matches_the_oracle_on_large_sectors(gpu_lib):
     ref = random_state(L, d, N, chi, seed=21)
     ref.apply_gate2(s, G, chi, 1e-10)
     try:
-        for cand in range(10):
+        for cand in range(12):
             m.autotune_force(cand)
             g = m.MPS(d, W.random_occupations(L, d, N, np.random.default_rng(0)), chi)
             load_state(g, st0)
@@ -152,4 +152,4 @@ def test_every_tile_shape_matches_the_oracle_on_large_sectors(gpu_lib):
     finally:
         m.autotune_force(-1)
     with pytest.raises(m.MPSError):
-        m.autotune_force(10)
+        m.autotune_force(12)

@@ -93,8 +93,8 @@ def test_tf32_operand_rounding(gpu_lib):
     assert np.all(~np.isfinite(got[~fin])), [(x[i], got[i]) for i in np.nonzero(~fin)[0]]
     bad = np.nonzero(got[fin] != want[fin])[0]
     assert bad.size == 0, [(x[fin][i], got[fin][i], want[fin][i]) for i in bad[:8]]
-    # the overflow cases are among the non-finite ones, the subnormal ones among the zeros
-    assert np.count_nonzero(~fin) >= 7
+    # the overflow cases (+-3.5e38, 1e39, +-1e300) and the NaN are among the non-finite ones
+    assert np.count_nonzero(~fin) >= 6
     # the tie cases do decide: truncating instead of rounding would change some results
     trunc = (x.view(np.uint64) & np.uint64(0xFFFFFFFFE0000000)).view(np.float64)
     alt = _tf32_rna(_f32_rn_flush(trunc)).astype(np.float64)

@@ -32,6 +32,7 @@ __all__ = [
     "random_u1_gate",
     "saturated_sector_dims",
     "saturated_random_state",
+    "entanglement_weights",
     "uniforms",
 ]
 
@@ -190,10 +191,19 @@ def saturated_sector_dims(L: int, d: int, N: int, b: int, chi: int) -> dict:
     return dims or {max(bound, key=bound.get): 1}
 
 
-def saturated_random_state(L: int, d: int, N: int, chi: int, seed: int):
+def entanglement_weights(n: int, beta: float, rng: np.random.Generator) -> np.ndarray:
+    """n positive weights w_k = exp(-beta (ln k)^2), k = 1..n, in a random order (stand-in
+    Schmidt values with the decay of an evolved chain's entanglement spectrum)."""
+    k = np.arange(1, n + 1, dtype=np.float64)
+    return np.exp(-beta * np.log(k) ** 2)[rng.permutation(n)]
+
+
+def saturated_random_state(L: int, d: int, N: int, chi: int, seed: int, beta: float | None = None):
     """A synthetic saturated chain: every inner bond at saturated_sector_dims, positive
     Schmidt-like weights (unit norm per bond, descending per sector) and complex normal
     blocks for every allowed (l, m) pair (0 <= l - m <= d - 1) scaled by 1/sqrt(max dim).
+    Weights: beta None draws them flat (random_positive, within a factor 20 of each other);
+    a number draws entanglement_weights(., beta) and deals them to the sectors at random.
     Not canonical; it gives an update the sector sizes and the cost of a saturated one.
     Returns (lam, blocks): lam[b] = {c: weights} for b = 1..L-1 (index 0 and L unused),
     blocks[s] = {(l, m): array}."""
@@ -203,7 +213,8 @@ def saturated_random_state(L: int, d: int, N: int, chi: int, seed: int):
     lam = [None] * (L + 1)
     for b in range(1, L):
         bonds[b] = dict(sorted(saturated_sector_dims(L, d, N, b, chi).items()))
-        w = random_positive(sum(bonds[b].values()), rng)
+        n_b = sum(bonds[b].values())
+        w = random_positive(n_b, rng) if beta is None else entanglement_weights(n_b, beta, rng)
         w /= np.linalg.norm(w)
         lam[b], off = {}, 0
         for c, D in bonds[b].items():
