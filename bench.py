@@ -20,7 +20,8 @@ Prints one JSON line (rank 0).  --impl reference times the float64 oracle on the
 cores instead (a bounded sample of the same chain's updates per step).  --serve runs
 the serving workload (continuous batching) instead.  --case selects the other
 configurations (bh64: L=64, chi<=512, FP64, evolved from the Mott state; small:
-L=32 for profiler captures; boson: boson sampling M=100, chi<=1024).
+L=32 for profiler captures; small_tf32: a saturated L=24, chi<=1024 chain in TF32 for
+captures of the tensor-core kernels; boson: boson sampling M=100, chi<=1024).
 """
 from __future__ import annotations
 
@@ -49,6 +50,10 @@ CASES = {
     # half the L=64 chain at the same chi and sector sizes, for profiler captures
     "small": dict(L=32, N=32, CHI=512, precision="fp64", start="evolved",
                   workload="bose_hubbard_L32_nmax4_N32_J1_U2_dt0.02_chi512_cutoff1e-10"),
+    # a short saturated chain at chi<=1024 with TF32 sector GEMMs (about 1.5 GB), for profiler
+    # captures of the tensor-core kernels
+    "small_tf32": dict(L=24, N=24, CHI=1024, precision="tf32", start="saturated", beta=0.3,
+                       workload="bose_hubbard_L24_nmax4_N24_J1_U2_dt0.02_chi1024_cutoff1e-10"),
     # boson sampling: M=100 modes, photons in modes 0..49, per-mode cutoff 4, Haar brickwork
     "boson": dict(L=100, N=50, CHI=1024, precision="fp64", start="brickwork", depth=100,
                   workload="boson_sampling_M100_photons50_d5_brickwork100_chi1024_cutoff1e-10"),
@@ -429,8 +434,10 @@ def run_ours(args, world, rank, local):
     prec = {"fp64": m.MPS_FP64, "tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[args.precision]
     if args.svd_candidate >= 0:
         m.autotune_force(args.svd_candidate)
+    t_prep = time.perf_counter()
     psi, step, prep = build_workload(args, m, W, stream, prec)
     L = args.cfg["L"]
+    print(f"[bench] workload ready in {time.perf_counter() - t_prep:.1f} s", file=sys.stderr, flush=True)
 
     for _ in range(args.warmup):
         step()
