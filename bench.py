@@ -113,6 +113,8 @@ def parse():
     p.add_argument("--chi-deflation", type=float, default=3e-4,
                    help="second SVD deflation level: values below this fraction of a bond's previous chi cut are "
                         "left unresolved (the update is redone if its cut falls below level / 6e-4 of it); 0: off")
+    p.add_argument("--svd-mixed-min-k", type=int, default=0,
+                   help="cluster SVD sectors with min(m, n) >= this start with FP32 Jacobi sweeps (0: FP64 only)")
     p.add_argument("--svd-candidate", type=int, default=-1,
                    help="force one SVD tile-shape candidate (0..11) for every update call (-1: the default rule)")
     a = p.parse_args()
@@ -434,6 +436,7 @@ def run_ours(args, world, rank, local):
     prec = {"fp64": m.MPS_FP64, "tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[args.precision]
     if args.svd_candidate >= 0:
         m.autotune_force(args.svd_candidate)
+    m.svd_mixed_min_k(args.svd_mixed_min_k)
     t_prep = time.perf_counter()
     psi, step, prep = build_workload(args, m, W, stream, prec)
     L = args.cfg["L"]

@@ -515,6 +515,17 @@ MPS_API int mps_svd_sectors(int n_sectors, const int* m, const int* n,
                     int* d_status, void* d_work, int64_t work_bytes, void* cuda_stream);
 
 /*
+ * mps_svd_mixed_min_k - sectors of the cluster SVD kernels with min(m, n) >= min_k (0: none,
+ * the default) first run one-sided Jacobi sweeps in FP32 on the Jacobi matrix stacked on the
+ * identity, which accumulates the rotations V; V is then made unitary in FP64 (one Cholesky
+ * QR) and the FP64 sweeps start from the Jacobi matrix times V, converging in 2-3 sweeps.
+ * Results meet the same FP64 accuracy; FP32 runs at 64x the FP64 rate on this part.  A process
+ * setting, read when an update call or mps_svd_sectors lays out its scratch (more scratch per
+ * such sector: about 8 (jlen + K) K + 48 K^2 bytes).  MPS_EINVAL for min_k < 0.
+ */
+MPS_API int mps_svd_mixed_min_k(int min_k);
+
+/*
  * mps_svd_sectors_noalloc - the batched sector SVD of mps_svd_sectors for callers
  * that must not allocate device memory.  The paper has no counterpart to this
  * entry point; it exists for callers whose device memory is owned by someone

@@ -115,6 +115,7 @@ _SIGS = {
     "mps_create_zn": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int,
                                      ctypes.c_int, _vp]),
     "mps_zgemm_tc_work_bytes": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mps_svd_mixed_min_k": (ctypes.c_int, [ctypes.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -501,6 +502,13 @@ def autotune_force(candidate: int) -> None:
 def autotune_freeze(frozen: bool = True) -> None:
     """Frozen: sector-size histograms not yet in the table keep the default shape, untuned."""
     lib.mps_autotune_freeze(int(bool(frozen)))
+
+
+def svd_mixed_min_k(min_k: int) -> None:
+    """Cluster SVD sectors with min(m, n) >= min_k start with FP32 Jacobi sweeps (0: off)."""
+    rc = lib.mps_svd_mixed_min_k(int(min_k))
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_svd_mixed_min_k")
 
 
 def autotune_min_flops(flops: float) -> None:

@@ -49,6 +49,8 @@
 // test; at most two rsqrt, one sqrt and one division per rotation; column norms tracked through the
 // exact 2x2 relations within a sweep).
 #include <algorithm>
+#include <type_traits>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -602,9 +604,361 @@ struct JacobiBlocks {
   }
 };
 
-template <class Mem, class Sync, class Jacobi>
+// ---------------------------------------------------------------------------------------
+// Mixed-precision preconditioning of a cluster sector (after Gao, Ma and Shao, "A mixed
+// precision Jacobi SVD algorithm", 2022).  The Jacobi matrix J (jlen x K, FP64) is rounded to
+// FP32 and stacked on the identity, F = [fl32(J); I]; FP32 one-sided Jacobi sweeps rotate the
+// columns of both (the dot products run over the J rows only), so that the lower block
+// accumulates the rotations V.  One-sided Jacobi is column-wise relatively accurate, so J V has
+// relatively orthogonal columns to about FP32 precision even for columns 10-15 decades below
+// the largest.  The columns whose FP32 norm is above a tenth of the deflation floor are kept,
+// V is made unitary in FP64 by one Cholesky QR (V^dag V = U^dag U, V <- V U^-1; V is unitary to
+// about 1e-5, so one pass leaves it unitary to rounding), and A1 = J V (FP64) starts the FP64
+// sweeps, which then converge in 2-3 sweeps instead of 7-12.  The singular values of A1 are
+// those of J (V unitary), and the FP64 sweeps make them and the vectors FP64-accurate; columns
+// left out lie below the floor anyway.  FP32 runs at 64x the FP64 rate on this part.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// G lanes (8, 16 or 32) orthogonalise columns p, q of an FP32 matrix: the dot product over the
+// first R rows, the rotation over the first Rr rows.  Tests and parameters avoid squaring the
+// (possibly tiny) inner product: |g| against tol sqrt(alpha beta), t = tan(theta) from
+// zeta = (beta - alpha) / (2 |g|).
+__device__ bool jacobi_pair32(float2* A, int R, int Rr, int ld, float* nrm, int p, int q, bool valid, int G,
+                              float tol, float floor2) {
+  const int gl = threadIdx.x & (G - 1);
+  float alpha = 0.f, beta = 0.f;
+  if (valid) {
+    alpha = nrm[p];
+    beta = nrm[q];
+  }
+  bool act = valid && fminf(alpha, beta) > floor2;
+  float2* ap = A + (int64_t)(act ? p : 0) * ld;
+  float2* aq = A + (int64_t)(act ? q : 0) * ld;
+  float gr = 0.f, gi = 0.f;
+  if (act)
+    for (int i = gl; i < R; i += G) {
+      const float2 x = ap[i], y = aq[i];
+      gr = fmaf(x.x, y.x, fmaf(x.y, y.y, gr));
+      gi = fmaf(x.x, y.y, fmaf(-x.y, y.x, gi));
+    }
+  for (int o = G >> 1; o; o >>= 1) {
+    gr += __shfl_xor_sync(0xffffffffu, gr, o);
+    gi += __shfl_xor_sync(0xffffffffu, gi, o);
+  }
+  const float ag = hypotf(gr, gi);
+  act = act && (ag > tol * sqrtf(alpha) * sqrtf(beta));
+  if (act) {
+    const float zeta = (beta - alpha) / (2.f * ag), az = fabsf(zeta);
+    const float t = copysignf(1.f, zeta) / (az + (az < 1e18f ? sqrtf(fmaf(zeta, zeta, 1.f)) : az));
+    const float c = rsqrtf(fmaf(t, t, 1.f));
+    const float ct = c * t / ag;
+    const float u = ct * gr, v = ct * gi;
+    for (int i = gl; i < Rr; i += G) {
+      const float2 x = ap[i], y = aq[i];
+      ap[i] = make_float2(fmaf(c, x.x, -fmaf(u, y.x, v * y.y)), fmaf(c, x.y, -fmaf(u, y.y, -v * y.x)));
+      aq[i] = make_float2(fmaf(c, y.x, fmaf(u, x.x, -v * x.y)), fmaf(c, y.y, fmaf(u, x.y, v * x.x)));
+    }
+    if (gl == 0) {
+      const float tg = t * ag;
+      nrm[p] = fmaxf(alpha - tg, 0.f);
+      nrm[q] = beta + tg;
+    }
+  }
+  return act;
+}
+
+__device__ __forceinline__ int group_width32(int P, int R, int nwarps) {
+  int best = 32;
+  long long best_cost = -1;
+  for (int G = 32; G >= 8; G >>= 1) {
+    const int slots = nwarps * (32 / G);
+    const long long cost = (long long)((P + slots - 1) / slots) * (2 * ((R + G - 1) / G) + 30);
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = G; }
+  }
+  return best;
+}
+
+// FP32 block-Jacobi sweeps over the K columns of F (column c at F + c * ld): the same block
+// ordering as JacobiBlocks, columns of Rr FP32 complex staged whole in shared memory (the
+// FP64 kernel's staging area holds them: 8 (jlen + K) <= 16 jlen bytes per column), dot
+// products over the first R rows.  Returns the sweeps used (converged: a sweep without a
+// rotation).  flags: max_sweeps + 1 ints, zero on entry.
+struct JacobiBlocks32 {
+  float2* sm;
+  float* smn;
+  int bsmax, g, gs;
+  template <class Sync>
+  __device__ int operator()(float2* F, int R, int Rr, int ld, int K, float* nrm, int* flags, int rank, int nctas,
+                            Sync sync, float tol, float floor2, int max_sweeps, bool& converged) const {
+    __shared__ int s_rot32;
+    __shared__ int s_col32[2 * kMaxStaged];
+    __shared__ int s_len32[2 * kMaxStaged];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int worker = rank * nwarps + warp, workers = nctas * nwarps;
+    const int nb = 2 * nctas * g;
+    int sweep = 0;
+    converged = K < 2;
+    for (; !converged && sweep < max_sweeps; ++sweep) {
+      for (int j = worker; j < K; j += workers) {   // fresh squared norms over the J rows
+        const float2* a = F + (int64_t)j * ld;
+        float acc = 0.f;
+        for (int i = lane; i < R; i += 32) {
+          const float2 x = __ldcg(a + i);
+          acc = fmaf(x.x, x.x, fmaf(x.y, x.y, acc));
+        }
+        acc = warp_sum_f(acc);
+        if (lane == 0) __stcg(nrm + j, acc);
+      }
+      sync();
+      if (tid == 0) s_rot32 = 0;
+      bool rot = false;
+      for (int r = 0; r < nb - 1; ++r) {
+        for (int c0 = 0; c0 < g; c0 += gs) {
+          const int ns = min(gs, g - c0);
+          if (tid < 2 * gs) {
+            const int j = tid >> 1;
+            int col = 0, len = 0;
+            if (j < ns) {
+              int bp, bq;
+              rr_pair(rank + (c0 + j) * nctas, r, nb, bp, bq);
+              const int b = (tid & 1) ? bq : bp;
+              col = (int)((int64_t)K * b / nb);
+              len = (int)((int64_t)K * (b + 1) / nb) - col;
+            }
+            s_col32[tid] = col;
+            s_len32[tid] = len;
+          }
+          __syncthreads();
+          for (int j = 0; j < 2 * ns; ++j) {
+            const int col = s_col32[j], len = s_len32[j];
+            float2* dst = sm + (int64_t)j * bsmax * Rr;
+            for (int64_t e = tid; e < (int64_t)len * Rr; e += blockDim.x) {
+              const int c = (int)(e / Rr), i = (int)(e % Rr);
+              dst[e] = __ldcg(F + (int64_t)(col + c) * ld + i);
+            }
+            for (int c = tid; c < len; c += blockDim.x) smn[j * bsmax + c] = __ldcg(nrm + col + c);
+          }
+          __syncthreads();
+          if (r == 0) {
+            const int mpb = bsmax + (bsmax & 1);
+            const int P = 2 * ns * (mpb / 2);
+            const int G = group_width32(P, R, nwarps), per = 32 / G, slot = warp * per + lane / G;
+            for (int rr = 0; rr < mpb - 1; ++rr) {
+              for (int base = 0; base < P; base += nwarps * per) {
+                const int k = base + slot, j = k / (mpb / 2);
+                int a = 0, b = 0;
+                bool valid = k < P;
+                if (valid) {
+                  rr_pair(k % (mpb / 2), rr, mpb, a, b);
+                  valid = a < s_len32[j] && b < s_len32[j];
+                }
+                rot |= jacobi_pair32(sm, R, Rr, Rr, smn, j * bsmax + min(a, b), j * bsmax + max(a, b), valid, G,
+                                     tol, floor2);
+              }
+              __syncthreads();
+            }
+          }
+          {
+            const int P = ns * bsmax;
+            const int G = group_width32(P, R, nwarps), per = 32 / G, slot = warp * per + lane / G;
+            for (int t = 0; t < bsmax; ++t) {
+              for (int base = 0; base < P; base += nwarps * per) {
+                const int k = base + slot, j = k / bsmax, i = k % bsmax;
+                int p = 0, q = 0;
+                bool valid = false;
+                if (k < P) {
+                  const int la = s_len32[2 * j], lb = s_len32[2 * j + 1];
+                  const bool swap = la > lb;
+                  const int sa = swap ? lb : la, sb = swap ? la : lb;
+                  valid = i < sa && t < sb;
+                  if (valid) {
+                    const int pa = (2 * j + (swap ? 1 : 0)) * bsmax + i;
+                    const int pb = (2 * j + (swap ? 0 : 1)) * bsmax + (i + t) % sb;
+                    p = min(pa, pb);
+                    q = max(pa, pb);
+                  }
+                }
+                rot |= jacobi_pair32(sm, R, Rr, Rr, smn, p, q, valid, G, tol, floor2);
+              }
+              __syncthreads();
+            }
+          }
+          for (int j = 0; j < 2 * ns; ++j) {
+            const int col = s_col32[j], len = s_len32[j];
+            const float2* src = sm + (int64_t)j * bsmax * Rr;
+            for (int64_t e = tid; e < (int64_t)len * Rr; e += blockDim.x) {
+              const int c = (int)(e / Rr), i = (int)(e % Rr);
+              __stcg(F + (int64_t)(col + c) * ld + i, src[e]);
+            }
+            for (int c = tid; c < len; c += blockDim.x) __stcg(nrm + col + c, smn[j * bsmax + c]);
+          }
+          __syncthreads();
+        }
+        sync();
+      }
+      if (rot) s_rot32 = 1;
+      __syncthreads();
+      if (tid == 0 && s_rot32) __stcg(flags + sweep, 1);
+      sync();
+      converged = __ldcg(flags + sweep) == 0;
+    }
+    return sweep;
+  }
+};
+struct NoJacobi32 {};
+
+// The mixed-precision start of a cluster sector's sweeps (see above).  J: jlen x K, column c at
+// J + c * jld (FP64, L2).  On return the FP64 Jacobi matrix is S.a1 (same jld), its first
+// *nsel_out columns J V and the rest zero.  Every CTA of the cluster calls it.
+template <class Sync>
+__device__ void mixed_precondition(const SvdSector& S, const Work& w, const double2* J, int jlen, int jld, int K,
+                                   int rank, int nctas, Sync sync, double floor2, int max_sweeps,
+                                   const JacobiBlocks32& j32, int* nsel_out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int tid_all = rank * blockDim.x + tid, threads_all = nctas * blockDim.x;
+  const int worker = rank * nwarps + warp, workers = nctas * nwarps;
+  const int Rr = jlen + K, fld = odd_ld(Rr);
+  float2* F = S.f32;
+  // scale so that the largest column has norm 1 (keeps the FP32 squares far from underflow)
+  double cmax = 0.0;
+  for (int j = 0; j < K; ++j) cmax = fmax(cmax, L2Mem::ld(w.nrm + j));
+  const double sc = cmax > 0.0 ? 1.0 / sqrt(cmax) : 1.0;
+  for (int64_t e = tid_all; e < (int64_t)K * Rr; e += threads_all) {
+    const int c = (int)(e / Rr), i = (int)(e % Rr);
+    float2 v = make_float2(0.f, 0.f);
+    if (i < jlen) {
+      const double2 x = L2Mem::ld(J + (int64_t)c * jld + i);
+      v = make_float2((float)(x.x * sc), (float)(x.y * sc));
+    } else if (i - jlen == c) {
+      v.x = 1.f;
+    }
+    __stcg(F + (int64_t)c * fld + i, v);
+  }
+  for (int s = tid_all; s <= max_sweeps; s += threads_all) L2Mem::st(w.flags + s, 0);
+  sync();
+  // FP32 sweeps to FP32 convergence; the floor is a tenth of the FP64 one (in the scaled units)
+  const float tol32 = 1.1920929e-07f * (float)max(jlen, 32);
+  const float fl32 = (float)(0.01 * floor2 * sc * sc);
+  bool conv32 = false;
+  j32(F, jlen, Rr, fld, K, S.nrm32, w.flags, rank, nctas, sync, tol32, fl32, max_sweeps, conv32);
+  for (int j = worker; j < K; j += workers) {   // final FP32 norms
+    const float2* a = F + (int64_t)j * fld;
+    float acc = 0.f;
+    for (int i = lane; i < jlen; i += 32) {
+      const float2 x = __ldcg(a + i);
+      acc = fmaf(x.x, x.x, fmaf(x.y, x.y, acc));
+    }
+    acc = warp_sum_f(acc);
+    if (lane == 0) __stcg(S.nrm32 + j, acc);
+  }
+  sync();
+  if (tid_all == 0) {   // the kept columns, in column order
+    int ns = 0;
+    for (int c = 0; c < K; ++c)
+      if (__ldcg(S.nrm32 + c) > fl32) __stcg(S.sel + ns++, c);
+    __stcg(S.sel + K, ns);
+  }
+  sync();
+  const int ns = __ldcg(S.sel + K);
+  double2* Vd = S.vd;     // K x ns, column-major (ld K)
+  double2* G = S.gm;      // ns x ns, column-major
+  for (int64_t e = tid_all; e < (int64_t)K * ns; e += threads_all) {
+    const int t = (int)(e / K), k = (int)(e % K);
+    const float2 v = __ldcg(F + (int64_t)__ldcg(S.sel + t) * fld + jlen + k);
+    L2Mem::st(Vd + e, make_double2((double)v.x, (double)v.y));
+  }
+  sync();
+  // Gram matrix G = Vd^dag Vd (upper triangle; a warp per entry)
+  for (int64_t e = worker; e < (int64_t)ns * ns; e += workers) {
+    const int a = (int)(e % ns), b = (int)(e / ns);
+    if (a > b) continue;
+    const double2* va = Vd + (int64_t)a * K;
+    const double2* vb = Vd + (int64_t)b * K;
+    double gr = 0.0, gi = 0.0;
+    for (int k = lane; k < K; k += 32) {
+      const double2 x = L2Mem::ld(va + k), y = L2Mem::ld(vb + k);
+      gr = fma(x.x, y.x, fma(x.y, y.y, gr));      // conj(x) y
+      gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+    }
+    gr = warp_sum(gr);
+    gi = warp_sum(gi);
+    if (lane == 0) L2Mem::st(G + (int64_t)b * ns + a, make_double2(gr, gi));
+  }
+  sync();
+  // Cholesky G = U^dag U in place (upper triangle), column by column
+  for (int j = 0; j < ns; ++j) {
+    if (tid_all == 0) {
+      const double2 gjj = L2Mem::ld(G + (int64_t)j * ns + j);
+      L2Mem::st(G + (int64_t)j * ns + j, make_double2(sqrt(fmax(gjj.x, 1e-300)), 0.0));
+    }
+    sync();
+    const double d = L2Mem::ld(G + (int64_t)j * ns + j).x, id = 1.0 / d;
+    for (int c = j + 1 + tid_all; c < ns; c += threads_all) {   // row j of U
+      const double2 x = L2Mem::ld(G + (int64_t)c * ns + j);
+      L2Mem::st(G + (int64_t)c * ns + j, make_double2(x.x * id, x.y * id));
+    }
+    sync();
+    // trailing update G[a, c] -= conj(U[j, a]) U[j, c], j < a <= c
+    const int tr = ns - j - 1;
+    for (int64_t e = tid_all; e < (int64_t)tr * tr; e += threads_all) {
+      const int a = j + 1 + (int)(e % tr), c = j + 1 + (int)(e / tr);
+      if (a > c) continue;
+      const double2 ua = L2Mem::ld(G + (int64_t)a * ns + j), uc = L2Mem::ld(G + (int64_t)c * ns + j);
+      double2 x = L2Mem::ld(G + (int64_t)c * ns + a);
+      x.x -= ua.x * uc.x + ua.y * uc.y;
+      x.y -= ua.x * uc.y - ua.y * uc.x;
+      L2Mem::st(G + (int64_t)c * ns + a, x);
+    }
+    sync();
+  }
+  // V <- Vd U^-1, row by row (x U = v by forward substitution; a warp per row)
+  for (int k = worker; k < K; k += workers) {
+    for (int c = 0; c < ns; ++c) {
+      double sr = 0.0, si = 0.0;
+      for (int a = lane; a < c; a += 32) {
+        const double2 x = L2Mem::ld(Vd + (int64_t)a * K + k), u = L2Mem::ld(G + (int64_t)c * ns + a);
+        sr = fma(x.x, u.x, fma(-x.y, u.y, sr));
+        si = fma(x.x, u.y, fma(x.y, u.x, si));
+      }
+      sr = warp_sum(sr);
+      si = warp_sum(si);
+      if (lane == 0) {
+        const double2 v = L2Mem::ld(Vd + (int64_t)c * K + k);
+        const double id = 1.0 / L2Mem::ld(G + (int64_t)c * ns + c).x;
+        L2Mem::st(Vd + (int64_t)c * K + k, make_double2((v.x - sr) * id, (v.y - si) * id));
+      }
+      __syncwarp();
+    }
+  }
+  sync();
+  // A1 = J V (jlen x ns), the remaining columns zero
+  double2* A1 = S.a1;
+  for (int64_t e = tid_all; e < (int64_t)K * jlen; e += threads_all) {
+    const int t = (int)(e / jlen), i = (int)(e % jlen);
+    double ar = 0.0, ai = 0.0;
+    if (t < ns) {
+      const double2* vt = Vd + (int64_t)t * K;
+      for (int k = 0; k < K; ++k) {
+        const double2 x = L2Mem::ld(J + (int64_t)k * jld + i), v = L2Mem::ld(vt + k);
+        ar = fma(x.x, v.x, fma(-x.y, v.y, ar));
+        ai = fma(x.x, v.y, fma(x.y, v.x, ai));
+      }
+    }
+    L2Mem::st(A1 + (int64_t)t * jld + i, make_double2(ar, ai));
+  }
+  for (int s = tid_all; s <= max_sweeps; s += threads_all) L2Mem::st(w.flags + s, 0);
+  sync();
+  *nsel_out = ns;
+}
+
+template <class Mem, class Sync, class Jacobi, class J32 = NoJacobi32>
 __device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int nctas, Sync sync, int max_sweeps,
-                           Jacobi jacobi) {
+                           Jacobi jacobi, J32 j32 = J32()) {
   __shared__ double red_d[kMaxWarps][33];
   __shared__ double red_v[kMaxWarps];
   __shared__ int red_i[kMaxWarps];
@@ -875,7 +1229,27 @@ __device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int ncta
   const double frel = fmax(32.0 * kEps, S.floor_rel);
   const double floor2 = fmax(frel * frel * fro2, S.floor_abs * S.floor_abs);
   bool converged = false;
-  const int sweep = jacobi(J, jlen, jld, K, w, rank, nctas, sync, tol2, floor2, max_sweeps, converged);
+  int Kj = K;                    // columns the FP64 sweeps rotate
+  if constexpr (std::is_same<J32, JacobiBlocks32>::value) {
+    if (S.f32 && K >= 2) {       // FP32 sweeps first; the FP64 sweeps then start from J V
+      int ns = K;
+      mixed_precondition(S, w, J, jlen, jld, K, rank, nctas, sync, floor2, max_sweeps, j32, &ns);
+      J = S.a1;
+      Kj = ns;
+      for (int j = worker; j < K; j += workers) {   // column norms of the new Jacobi matrix
+        const double2* a = J + (int64_t)j * jld;
+        double acc = 0.0;
+        for (int i = lane; i < jlen; i += 32) {
+          const double2 x = Mem::ld(a + i);
+          acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) Mem::st(w.nrm + j, acc);
+      }
+      sync();
+    }
+  }
+  const int sweep = jacobi(J, jlen, jld, Kj, w, rank, nctas, sync, tol2, floor2, max_sweeps, converged);
 
   // ---- singular values (noise floor -> 0), descending, ties by column index -----------
   for (int j = worker; j < K; j += workers) {
@@ -953,7 +1327,7 @@ __device__ void svd_sector(const SvdSector& S, const Work& w, int rank, int ncta
       const double sv = Mem::ld(w.nrm + c);
       double2 y = make_double2(0.0, 0.0);
       if (sv > 0.0) {
-        const double2 a = Mem::ld(W + (int64_t)c * ld + j);
+        const double2 a = Mem::ld(J + (int64_t)c * jld + j);
         y = make_double2(a.x / sv, a.y / sv);
       }
       S.Y[(int64_t)r * n + Mem::ld(w.perm + j)] = y;
@@ -1048,7 +1422,15 @@ __global__ void __launch_bounds__(kBlockThreads, 2) jacobi_cluster_block_kernel(
   jb.bsmax = (K + 2 * cluster * jb.g - 1) / (2 * cluster * jb.g);
   jb.sm = reinterpret_cast<double2*>(smem_raw);
   jb.smn = reinterpret_cast<double*>(smem_raw + 16LL * 2 * jb.gs * jb.bsmax * (S.wide ? K : S.n));
-  svd_sector<L2Mem>(S, cluster_work(S), rank, cluster, ClusterSync{}, max_sweeps, jb);
+  // the FP32 sweeps of a mixed-precision sector stage columns of jlen + K <= 2 jlen FP32
+  // complex values in the same area
+  JacobiBlocks32 j32;
+  j32.g = jb.g;
+  j32.gs = jb.gs;
+  j32.bsmax = jb.bsmax;
+  j32.sm = reinterpret_cast<float2*>(smem_raw);
+  j32.smn = reinterpret_cast<float*>(smem_raw + 8LL * 2 * jb.gs * jb.bsmax * ((S.wide ? K : S.n) + K));
+  svd_sector<L2Mem>(S, cluster_work(S), rank, cluster, ClusterSync{}, max_sweeps, jb, j32);
 }
 
 
@@ -1271,7 +1653,9 @@ bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L) {
   L.wide.assign(ns, 0);
   L.w2_off.assign(ns, -1);
   L.yt_off.assign(ns, -1);
+  for (auto* v : {&L.f32_off, &L.n32_off, &L.vd_off, &L.gm_off, &L.a1_off, &L.sel_off}) v->assign(ns, -1);
   L.smem = 0;
+  const int mix_k = svd_mixed_min_k();
   int64_t off = 0;
   auto a256 = [](int64_t x) { return (x + 255) & ~int64_t(255); };
   for (int k = 0; k < ns; ++k) {
@@ -1294,6 +1678,15 @@ bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L) {
       L.w2_off[k] = off; off = a256(off + 16 * Kk * odd_ld((int)Kk));     // R2 / Jacobi matrix
       L.yt_off[k] = off; off = a256(off + 16 * N * Kk);                   // Q2 applied to its columns
     }
+    if (mix_k > 0 && Kk >= mix_k) {   // FP32 sweeps first (see mixed_precondition)
+      const int64_t jlen = L.wide[k] ? Kk : N, jld = L.wide[k] ? odd_ld((int)Kk) : odd_ld(n[k]);
+      L.f32_off[k] = off; off = a256(off + 8 * odd_ld((int)(jlen + Kk)) * Kk);
+      L.n32_off[k] = off; off = a256(off + 4 * Kk);
+      L.vd_off[k] = off;  off = a256(off + 16 * Kk * Kk);
+      L.gm_off[k] = off;  off = a256(off + 16 * Kk * Kk);
+      L.a1_off[k] = off;  off = a256(off + 16 * jld * Kk);
+      L.sel_off[k] = off; off = a256(off + 4 * (Kk + 1));
+    }
   }
   L.total = off;
   return true;
@@ -1313,7 +1706,31 @@ void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base
     S.work2 = reinterpret_cast<double2*>(base + L.w2_off[k]);
     S.ytmp = reinterpret_cast<double2*>(base + L.yt_off[k]);
   }
+  S.f32 = nullptr;
+  if (L.f32_off[k] >= 0) {
+    S.f32 = reinterpret_cast<float2*>(base + L.f32_off[k]);
+    S.nrm32 = reinterpret_cast<float*>(base + L.n32_off[k]);
+    S.vd = reinterpret_cast<double2*>(base + L.vd_off[k]);
+    S.gm = reinterpret_cast<double2*>(base + L.gm_off[k]);
+    S.a1 = reinterpret_cast<double2*>(base + L.a1_off[k]);
+    S.sel = reinterpret_cast<int*>(base + L.sel_off[k]);
+  }
 }
+
+namespace {
+std::atomic<int> g_mixed_min_k{0};
+}
+int svd_mixed_min_k() { return g_mixed_min_k.load(); }
+
+}  // namespace mps
+
+extern "C" int mps_svd_mixed_min_k(int min_k) {
+  if (min_k < 0) return MPS_EINVAL;
+  mps::g_mixed_min_k.store(min_k);
+  return MPS_OK;
+}
+
+namespace mps {
 
 }  // namespace mps
 

@@ -141,17 +141,28 @@ struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   int wide;                   // cluster mode, m < n: Jacobi on R2 of R^dag = Q2 R2 (K x K)
   double2* work2;             // wide: R2 / the Jacobi matrix, K x (K | 1) column-major
   double2* ytmp;              // wide: n x K, Q2 applied to the normalised columns
+  // mixed-precision preconditioning (cluster mode, K >= the threshold; f32 == nullptr: off):
+  float2* f32;                // the Jacobi matrix in FP32 stacked on V (identity), (jlen + K | 1) x K
+  float* nrm32;               // K FP32 squared column norms
+  double2* vd;                // K x K: the selected columns of V in FP64, then orthonormalised
+  double2* gm;                // K x K: their Gram matrix, then its Cholesky factor
+  double2* a1;                // jld x K: the Jacobi matrix times V, the start of the FP64 sweeps
+  int* sel;                   // K + 1: selected columns, then their count
 };
 
 // Scratch layout of a batch of sector SVDs (cluster-mode sectors only need global scratch).
 struct SvdScratchLayout {
   std::vector<int> mode;
   std::vector<int64_t> work_off, v_off, norm_off, ord_off, flag_off, piv_off, w2_off, yt_off;
+  std::vector<int64_t> f32_off, n32_off, vd_off, gm_off, a1_off, sel_off;   // mixed precision (-1: off)
   std::vector<int> wide;
   int smem = 0;               // dynamic shared memory of the one-CTA kernel
   int64_t total = 0;
 };
 bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L);
+// Cluster sectors with min(m, n) >= this run FP32 Jacobi sweeps first and finish in FP64
+// (0: every sector FP64 only); mps_svd_mixed_min_k sets it.
+int svd_mixed_min_k();
 // Points the cluster-mode scratch of sector k at base + the layout's offsets; sets S.mode.
 void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base);
 
