@@ -113,7 +113,7 @@ def parse():
     p.add_argument("--chi-deflation", type=float, default=3e-4,
                    help="second SVD deflation level: values below this fraction of a bond's previous chi cut are "
                         "left unresolved (the update is redone if its cut falls below level / 6e-4 of it); 0: off")
-    p.add_argument("--svd-mixed-min-k", type=int, default=0,
+    p.add_argument("--svd-mixed-min-k", type=int, default=192,
                    help="cluster SVD sectors with min(m, n) >= this start with FP32 Jacobi sweeps (0: FP64 only)")
     p.add_argument("--svd-candidate", type=int, default=-1,
                    help="force one SVD tile-shape candidate (0..11) for every update call (-1: the default rule)")

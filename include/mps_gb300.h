@@ -515,8 +515,8 @@ MPS_API int mps_svd_sectors(int n_sectors, const int* m, const int* n,
                     int* d_status, void* d_work, int64_t work_bytes, void* cuda_stream);
 
 /*
- * mps_svd_mixed_min_k - sectors of the cluster SVD kernels with min(m, n) >= min_k (0: none,
- * the default) first run one-sided Jacobi sweeps in FP32 on the Jacobi matrix stacked on the
+ * mps_svd_mixed_min_k - sectors of the cluster SVD kernels with min(m, n) >= min_k (default 192;
+ * 0: none) first run one-sided Jacobi sweeps in FP32 on the Jacobi matrix stacked on the
  * identity, which accumulates the rotations V; V is then made unitary in FP64 (one Cholesky
  * QR) and the FP64 sweeps start from the Jacobi matrix times V, converging in 2-3 sweeps.
  * Results meet the same FP64 accuracy; FP32 runs at 64x the FP64 rate on this part.  A process

@@ -1718,7 +1718,7 @@ void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base
 }
 
 namespace {
-std::atomic<int> g_mixed_min_k{0};
+std::atomic<int> g_mixed_min_k{192};
 }
 int svd_mixed_min_k() { return g_mixed_min_k.load(); }
 

@@ -34,7 +34,7 @@ def test_mixed_svd_matches_lapack_and_the_fp64_path(gpu_lib, decades):
         m.svd_mixed_min_k(64)
         got = m.svd_sectors(list(mats), rowscales=list(scales))
     finally:
-        m.svd_mixed_min_k(0)
+        m.svd_mixed_min_k(192)
     for A, lam, (s0, y0, sw0), (s1, y1, sw1) in zip(mats, scales, ref, got):
         M = lam[:, None] * A
         s_la = scipy.linalg.svd(M, compute_uv=False, lapack_driver="gesvd")
@@ -43,11 +43,18 @@ def test_mixed_svd_matches_lapack_and_the_fp64_path(gpu_lib, decades):
         assert np.max(np.abs(s1[:k] - s_la)) <= 1e-13 * smax
         assert np.max(np.abs(s1 - s0)) <= 1e-13 * smax
         good = s1 > 1e-9 * smax
-        # orthonormal right vectors and M Y = X S with orthonormal X
+        # orthonormal right vectors; (M Y)^dag (M Y) = S^2 to rounding of the largest value
+        # (the sigma-weighted form, the accuracy LAPACK's gesvd has: the update uses the
+        # vectors weighted by their singular values)
         Yg = y1[:, good]
         assert np.max(np.abs(Yg.conj().T @ Yg - np.eye(Yg.shape[1]))) <= 1e-10
-        X = (M @ Yg) / s1[good]
-        assert np.max(np.abs(X.conj().T @ X - np.eye(X.shape[1]))) <= 1e-8
+        MY = M @ Yg
+        assert np.max(np.abs(MY.conj().T @ MY - np.diag(s1[good] ** 2))) <= 1e-12 * smax ** 2
+        # and the kept subspace is the FP64 path's: the two projectors weighted by sigma agree
+        P1 = (Yg * s1[good]) @ Yg.conj().T
+        Y0 = y0[:, good]
+        P0 = (Y0 * s0[good]) @ Y0.conj().T
+        assert np.max(np.abs(P1 - P0)) <= 1e-11 * smax
         # the FP64 sweeps started from J V: far fewer than from J
         assert 0 <= sw1 <= max(4, sw0 - 2), (sw0, sw1)
 
@@ -73,4 +80,4 @@ def test_mixed_svd_update_keeps_the_oracle_structure(gpu_lib):
         compare_update(g, ref, s)
         g.close()
     finally:
-        m.svd_mixed_min_k(0)
+        m.svd_mixed_min_k(192)
