@@ -524,6 +524,9 @@ MPS_API int mps_svd_sectors(int n_sectors, const int* m, const int* n,
  * such sector: about 8 (jlen + K) K + 48 K^2 bytes).  MPS_EINVAL for min_k < 0.
  */
 MPS_API int mps_svd_mixed_min_k(int min_k);
+/* mps_svd_mixed_sweeps - the limit of those FP32 sweeps (1..40, default 8: on the chi = 2048 layer 6-10
+ * FP32 sweeps minimise the time; the FP64 sweeps finish either way); MPS_EINVAL outside. */
+MPS_API int mps_svd_mixed_sweeps(int max_sweeps);
 
 /*
  * mps_svd_sectors_noalloc - the batched sector SVD of mps_svd_sectors for callers

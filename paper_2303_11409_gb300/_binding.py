@@ -116,6 +116,7 @@ _SIGS = {
                                      ctypes.c_int, _vp]),
     "mps_zgemm_tc_work_bytes": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mps_svd_mixed_min_k": (ctypes.c_int, [ctypes.c_int]),
+    "mps_svd_mixed_sweeps": (ctypes.c_int, [ctypes.c_int]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -509,6 +510,13 @@ def svd_mixed_min_k(min_k: int) -> None:
     rc = lib.mps_svd_mixed_min_k(int(min_k))
     if rc != MPS_OK:
         raise MPSError(rc, "mps_svd_mixed_min_k")
+
+
+def svd_mixed_sweeps(max_sweeps: int) -> None:
+    """Limit of the FP32 sweeps of the mixed-precision SVD start (1..40)."""
+    rc = lib.mps_svd_mixed_sweeps(int(max_sweeps))
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_svd_mixed_sweeps")
 
 
 def autotune_min_flops(flops: float) -> None:

@@ -845,7 +845,8 @@ __device__ void mixed_precondition(const SvdSector& S, const Work& w, const doub
   const float tol32 = 1.1920929e-07f * (float)max(jlen, 32);
   const float fl32 = (float)(0.01 * floor2 * sc * sc);
   bool conv32 = false;
-  j32(F, jlen, Rr, fld, K, S.nrm32, w.flags, rank, nctas, sync, tol32, fl32, max_sweeps, conv32);
+  j32(F, jlen, Rr, fld, K, S.nrm32, w.flags, rank, nctas, sync, tol32, fl32, min(max_sweeps, S.fp32_sweeps),
+      conv32);
   for (int j = worker; j < K; j += workers) {   // final FP32 norms
     const float2* a = F + (int64_t)j * fld;
     float acc = 0.f;
@@ -1707,6 +1708,7 @@ void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base
     S.ytmp = reinterpret_cast<double2*>(base + L.yt_off[k]);
   }
   S.f32 = nullptr;
+  S.fp32_sweeps = svd_mixed_sweeps();
   if (L.f32_off[k] >= 0) {
     S.f32 = reinterpret_cast<float2*>(base + L.f32_off[k]);
     S.nrm32 = reinterpret_cast<float*>(base + L.n32_off[k]);
@@ -1719,14 +1721,22 @@ void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base
 
 namespace {
 std::atomic<int> g_mixed_min_k{192};
+std::atomic<int> g_mixed_sweeps{8};
 }
 int svd_mixed_min_k() { return g_mixed_min_k.load(); }
+int svd_mixed_sweeps() { return g_mixed_sweeps.load(); }
 
 }  // namespace mps
 
 extern "C" int mps_svd_mixed_min_k(int min_k) {
   if (min_k < 0) return MPS_EINVAL;
   mps::g_mixed_min_k.store(min_k);
+  return MPS_OK;
+}
+
+extern "C" int mps_svd_mixed_sweeps(int max_sweeps) {
+  if (max_sweeps < 1 || max_sweeps > mps::kJacobiMaxSweeps) return MPS_EINVAL;
+  mps::g_mixed_sweeps.store(max_sweeps);
   return MPS_OK;
 }
 

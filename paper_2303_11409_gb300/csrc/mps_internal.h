@@ -148,6 +148,7 @@ struct SvdSector {            // one Theta(c): M = diag(rowscale) * Theta, m x n
   double2* gm;                // K x K: their Gram matrix, then its Cholesky factor
   double2* a1;                // jld x K: the Jacobi matrix times V, the start of the FP64 sweeps
   int* sel;                   // K + 1: selected columns, then their count
+  int fp32_sweeps;            // limit of the FP32 sweeps
 };
 
 // Scratch layout of a batch of sector SVDs (cluster-mode sectors only need global scratch).
@@ -163,6 +164,7 @@ bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L);
 // Cluster sectors with min(m, n) >= this run FP32 Jacobi sweeps first and finish in FP64
 // (0: every sector FP64 only); mps_svd_mixed_min_k sets it.
 int svd_mixed_min_k();
+int svd_mixed_sweeps();      // limit of the FP32 sweeps (mps_svd_mixed_sweeps)
 // Points the cluster-mode scratch of sector k at base + the layout's offsets; sets S.mode.
 void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base);
 
