@@ -384,6 +384,52 @@ __device__ __forceinline__ int group_slot(int G) {
   return G <= 32 ? warp * (32 / G) + lane / G : warp / (G >> 5);
 }
 
+// Bulk copies (the TMA engine, no tensor map) of whole staged columns: a column of the Jacobi
+// matrix is contiguous in global memory and in the staging area, 16-byte aligned, a multiple of
+// 16 bytes long.  One thread issues them; the CTA waits on an mbarrier (loads) or the issuing
+// thread on the bulk group (stores).  Global data crosses between the generic and the async
+// proxy only behind fence.proxy.async and the cluster barrier.
+__device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void stage_bar_init(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sh_addr(b)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void stage_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sh_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   sh_addr(dst)),
+               "l"(src), "r"(bytes), "r"(sh_addr(b))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(sh_addr(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store_drain() {
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+  asm volatile("fence.proxy.async.global;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_to_async() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
+// Bounded wait (about 2 s) for the staging barrier's phase; false when it expired.
+__device__ __forceinline__ bool stage_wait(uint64_t* b, uint32_t parity) {
+  const uint32_t a = sh_addr(b);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 4000000000LL) return false;
+  }
+}
+
 // Per-sector working set (shared memory or global scratch).
 struct Work {
   double2* W;     // m x ld, row-major: M, then R (rows 0..K-1), then R^dag's columns
@@ -478,7 +524,11 @@ struct JacobiBlocks {
                             double tol2, double floor2, int max_sweeps, bool& converged) const {
     __shared__ int s_rot;
     __shared__ double s_red[2 * 2 * kMaxWarps];   // multi-warp pair partials, two buffers
+    __shared__ __align__(8) uint64_t s_bar;       // staging loads
     int mw_phase = 0;
+    uint32_t stage_parity = 0;
+    if (threadIdx.x == 0) stage_bar_init(&s_bar);
+    __syncthreads();
     __shared__ int s_col[2 * kMaxStaged];   // first column of each staged block
     __shared__ int s_len[2 * kMaxStaged];   // its width (0: slot unused)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -519,16 +569,22 @@ struct JacobiBlocks {
             s_len[tid] = len;
           }
           __syncthreads();
-          // stage: block slot j occupies columns [j * bsmax, j * bsmax + len) of sm
-          for (int j = 0; j < 2 * ns; ++j) {
-            const int col = s_col[j], len = s_len[j];
-            double2* dst = sm + (int64_t)j * bsmax * n;
-            for (int64_t e = tid; e < (int64_t)len * n; e += blockDim.x) {
-              const int c = (int)(e / n), i = (int)(e % n);
-              dst[e] = __ldcg(W + (int64_t)(col + c) * ld + i);
-            }
-            for (int c = tid; c < len; c += blockDim.x) smn[j * bsmax + c] = __ldcg(w.nrm + col + c);
+          // stage: block slot j occupies columns [j * bsmax, j * bsmax + len) of sm, one bulk
+          // copy per column
+          if (tid == 0) {
+            uint32_t bytes = 0;
+            for (int j = 0; j < 2 * ns; ++j) bytes += (uint32_t)s_len[j] * (uint32_t)n * 16u;
+            fence_to_async();
+            stage_expect(&s_bar, bytes);
+            for (int j = 0; j < 2 * ns; ++j)
+              for (int c = 0; c < s_len[j]; ++c)
+                bulk_load(sm + ((int64_t)j * bsmax + c) * n, W + (int64_t)(s_col[j] + c) * ld, (uint32_t)n * 16u,
+                          &s_bar);
           }
+          for (int j = 0; j < 2 * ns; ++j)
+            for (int c = tid; c < s_len[j]; c += blockDim.x) smn[j * bsmax + c] = __ldcg(w.nrm + s_col[j] + c);
+          stage_wait(&s_bar, stage_parity);
+          stage_parity ^= 1u;
           __syncthreads();
           if (r == 0) {   // pairs inside each staged block, round-robin within the block
             const int mpb = bsmax + (bsmax & 1);
@@ -581,15 +637,14 @@ struct JacobiBlocks {
               __syncthreads();
             }
           }
-          for (int j = 0; j < 2 * ns; ++j) {
-            const int col = s_col[j], len = s_len[j];
-            const double2* src = sm + (int64_t)j * bsmax * n;
-            for (int64_t e = tid; e < (int64_t)len * n; e += blockDim.x) {
-              const int c = (int)(e / n), i = (int)(e % n);
-              __stcg(W + (int64_t)(col + c) * ld + i, src[e]);
-            }
-            for (int c = tid; c < len; c += blockDim.x) __stcg(w.nrm + col + c, smn[j * bsmax + c]);
+          if (tid == 0) {   // write the staged columns back, one bulk copy each
+            for (int j = 0; j < 2 * ns; ++j)
+              for (int c = 0; c < s_len[j]; ++c)
+                bulk_store(W + (int64_t)(s_col[j] + c) * ld, sm + ((int64_t)j * bsmax + c) * n, (uint32_t)n * 16u);
+            bulk_store_drain();
           }
+          for (int j = 0; j < 2 * ns; ++j)
+            for (int c = tid; c < s_len[j]; c += blockDim.x) __stcg(w.nrm + s_col[j] + c, smn[j * bsmax + c]);
           __syncthreads();   // the next chunk reuses the staging buffers and block tables
         }
         sync();
@@ -698,6 +753,10 @@ struct JacobiBlocks32 {
     __shared__ int s_rot32;
     __shared__ int s_col32[2 * kMaxStaged];
     __shared__ int s_len32[2 * kMaxStaged];
+    __shared__ __align__(8) uint64_t s_bar32;
+    uint32_t stage_parity = 0;
+    if (threadIdx.x == 0) stage_bar_init(&s_bar32);
+    __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int worker = rank * nwarps + warp, workers = nctas * nwarps;
     const int nb = 2 * nctas * g;
@@ -734,15 +793,22 @@ struct JacobiBlocks32 {
             s_len32[tid] = len;
           }
           __syncthreads();
-          for (int j = 0; j < 2 * ns; ++j) {
-            const int col = s_col32[j], len = s_len32[j];
-            float2* dst = sm + (int64_t)j * bsmax * Rr;
-            for (int64_t e = tid; e < (int64_t)len * Rr; e += blockDim.x) {
-              const int c = (int)(e / Rr), i = (int)(e % Rr);
-              dst[e] = __ldcg(F + (int64_t)(col + c) * ld + i);
-            }
-            for (int c = tid; c < len; c += blockDim.x) smn[j * bsmax + c] = __ldcg(nrm + col + c);
+          // one bulk copy per column (ld is even: every column starts 16-byte aligned and is
+          // ld FP32 complex long, a multiple of 16 bytes; the staging stride is ld too)
+          if (tid == 0) {
+            uint32_t bytes = 0;
+            for (int j = 0; j < 2 * ns; ++j) bytes += (uint32_t)s_len32[j] * (uint32_t)ld * 8u;
+            fence_to_async();
+            stage_expect(&s_bar32, bytes);
+            for (int j = 0; j < 2 * ns; ++j)
+              for (int c = 0; c < s_len32[j]; ++c)
+                bulk_load(sm + ((int64_t)j * bsmax + c) * ld, F + (int64_t)(s_col32[j] + c) * ld, (uint32_t)ld * 8u,
+                          &s_bar32);
           }
+          for (int j = 0; j < 2 * ns; ++j)
+            for (int c = tid; c < s_len32[j]; c += blockDim.x) smn[j * bsmax + c] = __ldcg(nrm + s_col32[j] + c);
+          stage_wait(&s_bar32, stage_parity);
+          stage_parity ^= 1u;
           __syncthreads();
           if (r == 0) {
             const int mpb = bsmax + (bsmax & 1);
@@ -757,7 +823,7 @@ struct JacobiBlocks32 {
                   rr_pair(k % (mpb / 2), rr, mpb, a, b);
                   valid = a < s_len32[j] && b < s_len32[j];
                 }
-                rot |= jacobi_pair32(sm, R, Rr, Rr, smn, j * bsmax + min(a, b), j * bsmax + max(a, b), valid, G,
+                rot |= jacobi_pair32(sm, R, Rr, ld, smn, j * bsmax + min(a, b), j * bsmax + max(a, b), valid, G,
                                      tol, floor2);
               }
               __syncthreads();
@@ -783,20 +849,19 @@ struct JacobiBlocks32 {
                     q = max(pa, pb);
                   }
                 }
-                rot |= jacobi_pair32(sm, R, Rr, Rr, smn, p, q, valid, G, tol, floor2);
+                rot |= jacobi_pair32(sm, R, Rr, ld, smn, p, q, valid, G, tol, floor2);
               }
               __syncthreads();
             }
           }
-          for (int j = 0; j < 2 * ns; ++j) {
-            const int col = s_col32[j], len = s_len32[j];
-            const float2* src = sm + (int64_t)j * bsmax * Rr;
-            for (int64_t e = tid; e < (int64_t)len * Rr; e += blockDim.x) {
-              const int c = (int)(e / Rr), i = (int)(e % Rr);
-              __stcg(F + (int64_t)(col + c) * ld + i, src[e]);
-            }
-            for (int c = tid; c < len; c += blockDim.x) __stcg(nrm + col + c, smn[j * bsmax + c]);
+          if (tid == 0) {
+            for (int j = 0; j < 2 * ns; ++j)
+              for (int c = 0; c < s_len32[j]; ++c)
+                bulk_store(F + (int64_t)(s_col32[j] + c) * ld, sm + ((int64_t)j * bsmax + c) * ld, (uint32_t)ld * 8u);
+            bulk_store_drain();
           }
+          for (int j = 0; j < 2 * ns; ++j)
+            for (int c = tid; c < s_len32[j]; c += blockDim.x) __stcg(nrm + s_col32[j] + c, smn[j * bsmax + c]);
           __syncthreads();
         }
         sync();
@@ -822,7 +887,7 @@ __device__ void mixed_precondition(const SvdSector& S, const Work& w, const doub
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int tid_all = rank * blockDim.x + tid, threads_all = nctas * blockDim.x;
   const int worker = rank * nwarps + warp, workers = nctas * nwarps;
-  const int Rr = jlen + K, fld = odd_ld(Rr);
+  const int Rr = jlen + K, fld = (Rr + 1) & ~1;   // even: columns 16-byte aligned for bulk copies
   float2* F = S.f32;
   // scale so that the largest column has norm 1 (keeps the FP32 squares far from underflow)
   double cmax = 0.0;
@@ -1430,7 +1495,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2) jacobi_cluster_block_kernel(
   j32.gs = jb.gs;
   j32.bsmax = jb.bsmax;
   j32.sm = reinterpret_cast<float2*>(smem_raw);
-  j32.smn = reinterpret_cast<float*>(smem_raw + 8LL * 2 * jb.gs * jb.bsmax * ((S.wide ? K : S.n) + K));
+  j32.smn = reinterpret_cast<float*>(smem_raw + 8LL * 2 * jb.gs * jb.bsmax * ((((S.wide ? K : S.n) + K) + 1) & ~1));
   svd_sector<L2Mem>(S, cluster_work(S), rank, cluster, ClusterSync{}, max_sweeps, jb, j32);
 }
 
@@ -1454,7 +1519,7 @@ int g_big_cluster[kMaxDevices] = {};
 
 int64_t block_smem_need(int m, int n, int cl, int g, int gs) {
   const int64_t K = std::min(m, n), bs = (K + 2 * cl * g - 1) / (2 * cl * g);
-  return 16 * 2 * gs * bs * n + 8 * 2 * gs * bs + 64;
+  return 16 * 2 * gs * bs * n + 16 * 2 * gs * bs + 64;   // norms, and the FP32 staging's even-stride padding
 }
 
 cudaError_t set_attrs(int* big_out) {
@@ -1681,7 +1746,7 @@ bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L) {
     }
     if (mix_k > 0 && Kk >= mix_k) {   // FP32 sweeps first (see mixed_precondition)
       const int64_t jlen = L.wide[k] ? Kk : N, jld = L.wide[k] ? odd_ld((int)Kk) : odd_ld(n[k]);
-      L.f32_off[k] = off; off = a256(off + 8 * odd_ld((int)(jlen + Kk)) * Kk);
+      L.f32_off[k] = off; off = a256(off + 8 * (jlen + Kk + 2) * Kk);
       L.n32_off[k] = off; off = a256(off + 4 * Kk);
       L.vd_off[k] = off;  off = a256(off + 16 * Kk * Kk);
       L.gm_off[k] = off;  off = a256(off + 16 * Kk * Kk);
