@@ -477,6 +477,40 @@ MPS_API int64_t mps_zgemm_tc_work_bytes(int precision, int M, int N, int K);
 MPS_API int mps_fp64_peak_probe(double* gflops, void* cuda_stream);
 
 /*
+ * mps_dmrg - two-site DMRG sweeps on the state of h (ground states of the U(1) chains the
+ * paper cites DMRG for, Sec. I, on the block structure of Sec. II: the two-site wave function
+ * is split by its middle charge into the Theta(c) blocks of the TEBD update, each with its own
+ * SVD, truncated globally as mps_apply_gate2 does).
+ *   bond_terms   L-1 host pointers; bond_terms[k] is the Hermitian two-site term h_{k,k+1}
+ *                of H = sum_k h_{k,k+1} as charge blocks in the gate layout (block n over the
+ *                pairs (i, n - i), i ascending, rows outputs; interleaved complex128,
+ *                mps_gate_length(d) complex numbers); read during the call only
+ *   n_sweeps     sweeps; a sweep is a right-moving pass over the pairs (0,1) .. (L-2,L-1)
+ *                and a left-moving pass back (2 (L-1) local steps)
+ *   chi, cutoff  the truncation of every local step (the rule of mps_apply_gate2)
+ *   lanczos_dim  Krylov dimension of one Lanczos cycle (2..63); cycles restart from the
+ *                Ritz vector until the residual |H_eff psi - E psi| <= tol max(1, |E|)
+ *   energies     out (may be NULL): the Lanczos eigenvalue of every local step, in order;
+ *                energies_cap >= n_sweeps * 2 (L-1) when given
+ *   n_energies   out: local steps done
+ * The state must be right-canonical (any state the update calls produce, or a product
+ * state) and h an FP64 U(1) handle.  On return the state is right-canonical again with every
+ * lambda the Schmidt values of its bond (an inverse-free left-to-right pass), so the
+ * observables, sampling and update calls apply to it.  MPS_ENOCONV when a Lanczos
+ * or a Jacobi SVD stopped at its limit (the state is updated with the last iterate),
+ * MPS_EINVAL for bad arguments, a TF32/BF16x3 or Z_n handle, or a site set with mps_set_site
+ * but not yet valid; MPS_ENOMEM when a bond outgrows the handle's chi_max capacity.
+ * mps_dmrg_stats reports, for the last call, per kind (0: H_eff products, 1: environment
+ * updates, 2: Krylov vector work, 3: SVD, 4: other block contractions) the launches, the
+ * device milliseconds (with mps_set_profiling on) and the algorithmic flops; mps_dmrg_counts
+ * the H_eff products and Lanczos cycles.
+ */
+MPS_API int mps_dmrg(mps_t h, const double* const* bond_terms, int n_sweeps, int chi, double cutoff,
+                     int lanczos_dim, double tol, double* energies, int energies_cap, int* n_energies);
+MPS_API int mps_dmrg_stats(mps_t h, int kind, int64_t* launches, double* ms, double* flops);
+MPS_API int mps_dmrg_counts(mps_t h, int64_t* matvecs, int64_t* restarts);
+
+/*
  * mps_plan_sectors - the integer sector planner alone (host code, no GPU needed).
  * Given the charge tables of bonds s, s+1, s+2 (ascending charges), it lists every
  * compatible (l, m, r) with 0 <= l-m <= d-1 and 0 <= m-r <= d-1, and every

@@ -117,7 +117,12 @@ _SIGS = {
     "mps_zgemm_tc_work_bytes": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mps_svd_mixed_min_k": (ctypes.c_int, [ctypes.c_int]),
     "mps_svd_mixed_sweeps": (ctypes.c_int, [ctypes.c_int]),
+    "mps_dmrg": (ctypes.c_int, [_h, ctypes.POINTER(_dblp), ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                ctypes.c_double, _dblp, ctypes.c_int, _intp]),
+    "mps_dmrg_stats": (ctypes.c_int, [_h, ctypes.c_int, _i64p, _dblp, _dblp]),
+    "mps_dmrg_counts": (ctypes.c_int, [_h, _i64p, _i64p]),
 }
+DMRG_KINDS = ("heff", "env", "lanczos", "svd", "other")
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
     _f.restype = _res
@@ -396,6 +401,38 @@ class MPS:
     def set_autotune(self, on: bool = True):
         """Choose the SVD tile shape per sector-size histogram (mps_set_autotune)."""
         self._check(lib.mps_set_autotune(self._h, int(bool(on))), "mps_set_autotune")
+
+    # -- ground states ----------------------------------------------------------
+    def dmrg(self, bond_terms, n_sweeps: int, chi: int, cutoff: float, lanczos_dim: int = 24,
+             tol: float = 1e-12) -> np.ndarray:
+        """Two-site DMRG sweeps (mps_dmrg); bond_terms[k] holds the charge blocks of h_{k,k+1}.
+
+        Returns the Lanczos eigenvalue of every local step."""
+        hs = [_c128_flat(h) for h in bond_terms]
+        if len(hs) != self.L - 1:
+            raise ValueError("one bond term per bond (L - 1)")
+        if any(h.size != gate_length(self.d) for h in hs):
+            raise ValueError("a bond term has the wrong number of entries")
+        arr = (_dblp * len(hs))(*[h.ctypes.data_as(_dblp) for h in hs])
+        cap = n_sweeps * 2 * (self.L - 1)
+        en = np.zeros(max(cap, 1))
+        n = ctypes.c_int(0)
+        rc = lib.mps_dmrg(self._h, arr, n_sweeps, chi, cutoff, lanczos_dim, tol, _ptr(en, _dblp), cap,
+                          ctypes.byref(n))
+        self._check(rc, "mps_dmrg")
+        return en[:n.value].copy()
+
+    def dmrg_stats(self) -> dict:
+        """Per-kind launches, device ms (with profiling on) and flops of the last dmrg call."""
+        out = {}
+        for k, name in enumerate(DMRG_KINDS):
+            la, ms, fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+            lib.mps_dmrg_stats(self._h, k, ctypes.byref(la), ctypes.byref(ms), ctypes.byref(fl))
+            out[name] = dict(launches=la.value, ms=ms.value, flops=fl.value)
+        mv, rs = ctypes.c_int64(), ctypes.c_int64()
+        lib.mps_dmrg_counts(self._h, ctypes.byref(mv), ctypes.byref(rs))
+        out["matvecs"], out["lanczos_cycles"] = mv.value, rs.value
+        return out
 
     def stats(self) -> dict:
         a, b, c, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -221,6 +221,13 @@ struct Stats {
 };
 
 struct KStat { int64_t launches = 0; double ms = 0, flops = 0, bytes = 0; };
+// Work and device time of the last mps_dmrg call per kind (0: H_eff products, 1: environment
+// updates, 2: Krylov vector work, 3: SVD, 4: other block contractions).
+struct DmrgStats {
+  int64_t matvecs = 0, restarts = 0;
+  double ms[5] = {0, 0, 0, 0, 0}, flops[5] = {0, 0, 0, 0, 0};
+  int64_t launches[5] = {0, 0, 0, 0, 0};
+};
 struct PendingTiming { int kind; cudaEvent_t a, b; bool pooled; };
 
 // Kernel launches made by the library in this process (all handles).
@@ -251,6 +258,7 @@ struct mps_s {
   mps::Stats stats;
   bool profiling = false;
   mps::KStat kstat[MPS_K_COUNT];
+  mps::DmrgStats dmrg_last;               // the last mps_dmrg call
   std::vector<mps::PendingTiming> pending;   // event pairs not yet read back
   std::vector<cudaEvent_t> event_pool;
   int* tc_flag = nullptr;                 // set by a tensor-core GEMM whose bounded wait expired

@@ -106,5 +106,38 @@ def clock_gate(n: int, J: float, f: float, tau: float, w_left: float, w_right: f
     return out
 
 
+def xxz_bond_term(delta: float, J: float = 1.0) -> list[np.ndarray]:
+    """Charge blocks of h = J (S+S- + S-S+)/2 + Delta SzSz (the generator of xxz_gate), for mps_dmrg."""
+    return [np.array([[delta / 4.0]]), np.array([[-delta / 4.0, 0.5 * J], [0.5 * J, -delta / 4.0]]),
+            np.array([[delta / 4.0]])]
+
+
+def bose_hubbard_bond_term(d: int, J: float, U: float, w_left: float, w_right: float) -> list[np.ndarray]:
+    """Charge blocks of h = -J(b1^dag b2 + h.c.) + U/2 (w1 n1(n1-1) + w2 n2(n2-1)), for mps_dmrg."""
+    out = []
+    for n in range(2 * d - 1):
+        occ = list(basis(n, d))
+        k = len(occ)
+        h = np.zeros((k, k))
+        for a, i in enumerate(occ):
+            j = n - i
+            h[a, a] = 0.5 * U * (w_left * i * (i - 1) + w_right * j * (j - 1))
+            if a + 1 < k:
+                amp = -J * math.sqrt((i + 1) * j)
+                h[a + 1, a] = amp
+                h[a, a + 1] = amp
+        out.append(h)
+    return out
+
+
+def chain_bond_terms(model: str, L: int, d: int, **p) -> list[list[np.ndarray]]:
+    """The L - 1 bond terms of an XXZ ("xxz": delta, J) or Bose-Hubbard ("bh": J, U) chain."""
+    if model == "xxz":
+        t = xxz_bond_term(p.get("delta", 1.0), p.get("J", 1.0))
+        return [t for _ in range(L - 1)]
+    return [bose_hubbard_bond_term(d, p.get("J", 1.0), p.get("U", 0.0), *bose_hubbard_weights(L, s))
+            for s in range(L - 1)]
+
+
 def flatten(blocks) -> np.ndarray:
     return np.concatenate([np.asarray(b, dtype=np.complex128).reshape(-1) for b in blocks])
