@@ -21,7 +21,8 @@ cores instead (a bounded sample of the same chain's updates per step).  --serve 
 the serving workload (continuous batching) instead.  --case selects the other
 configurations (bh64: L=64, chi<=512, FP64, evolved from the Mott state; small:
 L=32 for profiler captures; small_tf32: a saturated L=24, chi<=1024 chain in TF32 for
-captures of the tensor-core kernels; boson: boson sampling M=100, chi<=1024).
+captures of the tensor-core kernels; boson: boson sampling M=100, chi<=1024; dmrg: two-site
+DMRG sweeps on the L=64 Bose-Hubbard chain at chi<=256).
 """
 from __future__ import annotations
 
@@ -54,6 +55,13 @@ CASES = {
     # captures of the tensor-core kernels
     "small_tf32": dict(L=24, N=24, CHI=1024, precision="tf32", start="saturated", beta=0.3,
                        workload="bose_hubbard_L24_nmax4_N24_J1_U2_dt0.02_chi1024_cutoff1e-10"),
+    # two-site DMRG ground state of the Bose-Hubbard chain (L=64, N=64, U=2), chi<=256: one step
+    # is one sweep (126 two-site updates) through mps_dmrg, after warm-up sweeps from the Mott state
+    "dmrg": dict(L=64, N=64, CHI=256, precision="fp64", start="dmrg",
+                 workload="dmrg_bose_hubbard_L64_nmax4_N64_J1_U2_chi256_cutoff1e-10"),
+    # the same at L=24, chi<=128, for profiler captures
+    "dmrg_small": dict(L=24, N=24, CHI=128, precision="fp64", start="dmrg",
+                       workload="dmrg_bose_hubbard_L24_nmax4_N24_J1_U2_chi128_cutoff1e-10"),
     # boson sampling: M=100 modes, photons in modes 0..49, per-mode cutoff 4, Haar brickwork
     "boson": dict(L=100, N=50, CHI=1024, precision="fp64", start="brickwork", depth=100,
                   workload="boson_sampling_M100_photons50_d5_brickwork100_chi1024_cutoff1e-10"),
@@ -421,6 +429,117 @@ def build_workload(args, m, W, stream, prec):
     return psi, step, prep
 
 
+def oracle_dmrg_sample(cfg, seconds: float):
+    """The oracle's DMRG on the same chain and schedule from the Mott state, timed for about
+    `seconds` of local steps.  Its bonds are still below chi during the sample, so the rate is
+    an upper bound on the oracle's rate at saturation."""
+    from oracle import U1MPS, dmrg as odmrg
+    import workloads as W
+    L, CHI = cfg["L"], cfg["CHI"]
+    dm = odmrg.DMRG(U1MPS.product(D, W.mott_occupations(L)), odmrg.bh_bonds(L, D, J, U))
+    order = [(s_, True) for s_ in range(L - 1)] + [(s_, False) for s_ in range(L - 2, -1, -1)]
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        s_, right = order[n % len(order)]
+        dm.step(s_, CHI, CUTOFF, right)
+        n += 1
+    el = time.perf_counter() - t0
+    largest = max(sum(b.values()) for b in dm.st.bond)
+    return {"value": n / el, "unit": "updates/s", "cores": blas_threads(), "kind": "oracle",
+            "sample": (f"the first {n} local steps ({el:.1f} s) of the oracle's DMRG on the same chain from the Mott "
+                       f"state (largest bond reached {largest} < chi: an upper bound on its rate at saturation)")}
+
+
+def run_dmrg_case(args, world, rank, local):
+    """Two-site DMRG sweeps (mps_dmrg) on the Bose-Hubbard chain: each timed step is one call of
+    one sweep (2 (L-1) two-site updates, then the canonical form), after warm-up sweeps from
+    the Mott state at the same chi.  The oracle's DMRG gives the CPU baseline on the same
+    chain (a bounded number of local steps)."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2303_11409_gb300 as m
+    import workloads as W
+    cfg = args.cfg
+    L, CHI = cfg["L"], cfg["CHI"]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    fp64_measured = m.fp64_peak_probe(stream.cuda_stream)
+    terms = m.models.chain_bond_terms("bh", L, D, J=J, U=U)
+    psi = m.MPS(D, W.mott_occupations(L), CHI, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        psi.dmrg(terms, 1, CHI, CUTOFF)
+    print(f"[bench] {args.warmup} warm-up sweeps in {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
+    psi.set_profiling(True)
+    torch.cuda.synchronize()
+    launches0 = m.launch_count()
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kinds = {}
+    energies = []
+    n_upd = 0
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            e = psi.dmrg(terms, 1, CHI, CUTOFF)
+            ev[k][1].record(stream)
+            n_upd += 2 * (L - 1)
+            energies.append(float(e[-1]))
+            for name, v in psi.dmrg_stats().items():
+                if isinstance(v, dict):
+                    a = kinds.setdefault(name, {"launches": 0, "ms": 0.0, "flops": 0.0})
+                    for kk in a:
+                        a[kk] += v[kk]
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = m.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    value = world * n_upd / (total_ms / 1000.0)
+    largest = max(sum(psi.bond_dims(b).values()) for b in range(L + 1))
+    tot = max(sum(v["ms"] for v in kinds.values()), 1e-12)
+    hv = kinds["heff"]
+    achieved = hv["flops"] / (hv["ms"] / 1000.0) / 1e9 if hv["ms"] > 0 else None
+    roofline = {"kernel": "heff (sumprod_kernel: H_eff products)", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS if achieved else None, "traffic": None,
+                "traffic_note": "null: no ncu DRAM capture of this kernel at this configuration",
+                "per_launch": {"flops": hv["flops"] / max(hv["launches"], 1), "ms": hv["ms"] / max(hv["launches"], 1)},
+                "peak_source": "FP64 CUDA-core peak from unit counts and the 2070 MHz max clock",
+                "fp64_peak_measured_gflops": fp64_measured,
+                "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share": v["ms"] / tot,
+                                "gflops": v["flops"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] > 0 else None}
+                            for k, v in kinds.items()}}
+    # e2e: the same call with host-resident bond terms and energies (mps_dmrg is host-in,
+    # host-out), timed on the host clock
+    t0 = time.perf_counter()
+    psi.dmrg(terms, 1, CHI, CUTOFF)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    glen = m.gate_length(D)
+    e2e = {"value": world * 2 * (L - 1) / e2e_s, "unit": "updates/s", "steps": 1,
+           "h2d_bytes_per_step": int((L - 1) * glen * 16), "d2h_bytes_per_step": int(2 * (L - 1) * 8),
+           "what": "one sweep through MPS.dmrg (mps_dmrg) with host bond terms, energies read back"}
+    psi.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_dmrg_sample(cfg, args.cpu_seconds)
+    if rank == 0:
+        line = {"metric": "two-site DMRG updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": cfg["workload"], "model": "bose_hubbard", "L": L, "d": D, "N": cfg["N"],
+                           "J": J, "U": U, "chi": CHI, "cutoff": CUTOFF,
+                           "step": f"one mps_dmrg call of one sweep ({2 * (L - 1)} two-site updates, then the canonical form)",
+                           "lanczos": "Krylov 24, residual tolerance 1e-12 |E|", "largest_bond_dim": largest,
+                           "l2": "no flush (one sweep streams the environments and Krylov vectors of 63 bonds)"},
+                "energy_per_site": energies[-1] / L, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk.summary(), "step_ms": [round(x, 3) for x in step_ms]}
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -700,6 +819,8 @@ def main():
         run_serving(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.case in ("dmrg", "dmrg_small"):
+        run_dmrg_case(args, world, rank, local)
     else:
         precisions = args.precision.split(",")
         for p_ in precisions:

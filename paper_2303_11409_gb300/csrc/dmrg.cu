@@ -77,7 +77,7 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__global__ void __launch_bounds__(kThr) sumprod_kernel(const SPTask* __restrict__ tasks,
+__global__ void __launch_bounds__(kThr, 2) sumprod_kernel(const SPTask* __restrict__ tasks,
                                                        const SPTerm* __restrict__ terms,
                                                        const SPTile* __restrict__ tiles,
                                                        const double2* __restrict__ X, double2* __restrict__ Y) {
@@ -113,6 +113,14 @@ __global__ void __launch_bounds__(kThr) sumprod_kernel(const SPTask* __restrict_
     }
     const double2* B = (P.flags & kBX) ? X + P.b : reinterpret_cast<const double2*>(P.b);
     const bool cb = (P.flags & kConjB) != 0;
+    // warp-uniform counts of the 16-row / 16-column groups that hold valid outputs: a
+    // block smaller than the tile spends no FP64 issue slots on its padding
+    const int warp_ty = (tid >> 5) * 2;
+    int ni = 0, nj = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ni += (row0 + warp_ty + 16 * i < T.M);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) nj += (col0 + 16 * j < T.N);
     for (int k0 = 0; k0 < P.K; k0 += kKc) {
       const int kc = min(kKc, P.K - k0);
       for (int e = tid; e < kT * kKc; e += kThr) {
@@ -144,9 +152,13 @@ __global__ void __launch_bounds__(kThr) sumprod_kernel(const SPTask* __restrict_
 #pragma unroll
         for (int j = 0; j < 4; ++j) b[j] = sm.B[kk][tx + 16 * j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i) {
+          if (i < ni) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+            for (int j = 0; j < 4; ++j)
+              if (j < nj) cfma(acc[i][j], a[i], b[j]);
+          }
+        }
       }
       __syncthreads();
     }
