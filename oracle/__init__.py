@@ -8,4 +8,4 @@ no code with the CUDA path.  Functions whose parity has no independent pin say
 """
 from .u1mps import (TIE_REL, U1MPS, SectorPlan, bond_charge_range, count_configs,  # noqa: F401
                     gate_basis, hilbert_dim, plan_update, select_kept)
-from . import gates, tebd, dense, freefermion, permanent, sampling, synth, dmrg  # noqa: F401
+from . import gates, tebd, dense, freefermion, permanent, sampling, synth, dmrg, multiu1  # noqa: F401
