@@ -477,6 +477,32 @@ MPS_API int64_t mps_zgemm_tc_work_bytes(int precision, int M, int N, int K);
 MPS_API int mps_fp64_peak_probe(double* gflops, void* cuda_stream);
 
 /*
+ * mps_create_multi - a handle whose physical index i carries several U(1) charges at once,
+ * the charge vector (phys_charges[i*ncomp + 0], ..., phys_charges[i*ncomp + ncomp-1]) (Sec. I
+ * lists "more general Abelian" symmetries beside U(1); e.g. two conserved particle species).
+ *   ncomp         1..4 charge components; every component >= 0; the vectors distinct and in
+ *                 ascending lexicographic order of i
+ *   site_indices  L physical indices in [0, d-1]: the initial product state
+ *   precision     MPS_FP64 only (other values: MPS_EINVAL)
+ * Bond charges are the vector sums to the right of each bond, encoded as one int32 in mixed
+ * radix (first component most significant; mps_charge_radix gives the radices, each more than
+ * twice the largest bond value, so differences decode uniquely and the integer order is the
+ * lexicographic one).  A block (l, m) exists iff l - m is a physical charge; the rows of a
+ * Theta(c) are the left sectors l with l - c a physical charge (in general not one contiguous
+ * run of the bond table; their lambdas are gathered before the SVD).  Gate and bond-term blocks
+ * are the distinct pair totals q_i + q_j in ascending order, each over its pairs (i, j), i
+ * ascending (rows outputs).  Every update, measurement and sampling call applies; mps_dmrg,
+ * mps_save and the tensor-core precisions are for single-U(1) handles.  Errors: MPS_EINVAL,
+ * MPS_ECHARGE (a negative component, vectors not ascending, or encoded charges beyond int32),
+ * MPS_ENOMEM.
+ * mps_charge_radix - *ncomp and the radix of each component (radix may be NULL); 1 and 0 for
+ * single-charge handles.
+ */
+MPS_API int mps_create_multi(mps_t* out, int L, int d, int ncomp, const int32_t* phys_charges,
+                             const int32_t* site_indices, int precision, int chi_max, void* cuda_stream);
+MPS_API int mps_charge_radix(mps_t h, int* ncomp, int32_t* radix);
+
+/*
  * mps_dmrg - two-site DMRG sweeps on the state of h (ground states of the U(1) chains the
  * paper cites DMRG for, Sec. I, on the block structure of Sec. II: the two-site wave function
  * is split by its middle charge into the Theta(c) blocks of the TEBD update, each with its own

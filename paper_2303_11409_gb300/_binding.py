@@ -121,6 +121,9 @@ _SIGS = {
                                 ctypes.c_double, _dblp, ctypes.c_int, _intp]),
     "mps_dmrg_stats": (ctypes.c_int, [_h, ctypes.c_int, _i64p, _dblp, _dblp]),
     "mps_dmrg_counts": (ctypes.c_int, [_h, _i64p, _i64p]),
+    "mps_create_multi": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p,
+                                        ctypes.c_int, ctypes.c_int, _vp]),
+    "mps_charge_radix": (ctypes.c_int, [_h, _intp, _i32p]),
 }
 DMRG_KINDS = ("heff", "env", "lanczos", "svd", "other")
 for _name, (_res, _args) in _SIGS.items():
@@ -166,16 +169,51 @@ def gate_length(d: int) -> int:
     return tot
 
 
+def multi_pair_blocks(charges):
+    """Two-site gate layout of a several-U(1) handle: the totals q_i + q_j (tuples) ascending,
+    each with its pairs (i, j), i ascending."""
+    tot = {}
+    for i, a in enumerate(charges):
+        for j, b in enumerate(charges):
+            tot.setdefault(tuple(x + y for x, y in zip(a, b)), []).append((i, j))
+    return {Q: sorted(tot[Q]) for Q in sorted(tot)}
+
+
 class MPS:
     """A U(1)-symmetric MPS living on the GPU (one handle of the C library); zn = n >= 2 makes it
-    Z_n-symmetric instead (mps_create_zn, d = n)."""
+    Z_n-symmetric instead (mps_create_zn, d = n); charges = [q_0, ..., q_{d-1}] (tuples, ascending)
+    gives physical index i the several-U(1) charge q_i (mps_create_multi, FP64): bond charges and
+    gate blocks are then keyed by tuples."""
 
-    def __init__(self, d: int, occupations, chi_max: int, precision: int = MPS_FP64, stream=None, zn: int = 0):
+    charges = None          # several-U(1) charge vectors (None: a single U(1) or Z_n charge)
+
+    def __init__(self, d: int, occupations, chi_max: int, precision: int = MPS_FP64, stream=None, zn: int = 0,
+                 charges=None):
         occ = _i32(occupations)
         self.L, self.d, self.chi_max = len(occ), int(d), int(chi_max)
         self.zn = int(zn)
+        self.charges = [tuple(int(v) for v in q) for q in charges] if charges is not None else None
         self.stream = _default_stream() if stream is None else stream
         h = _h()
+        if self.charges is not None:
+            nc = len(self.charges[0])
+            qa = _i32(np.asarray(self.charges, dtype=np.int32).reshape(-1))
+            rc = lib.mps_create_multi(ctypes.byref(h), self.L, self.d, nc, _ptr(qa, _i32p), _ptr(occ, _i32p),
+                                      precision, self.chi_max, self.stream)
+            if rc != MPS_OK:
+                raise MPSError(rc, "mps_create_multi failed")
+            self._h = h
+            ncomp = ctypes.c_int(0)
+            rad = np.zeros(4, np.int32)
+            lib.mps_charge_radix(h, ctypes.byref(ncomp), _ptr(rad, _i32p))
+            w, self._weights = 1, [0] * nc
+            for k in range(nc - 1, -1, -1):
+                self._weights[k] = w
+                w *= int(rad[k])
+            self._radix = [int(x) for x in rad[:nc]]
+            self._pairs = multi_pair_blocks(self.charges)
+            self.N = tuple(sum(self.charges[i][k] for i in occ) for k in range(nc))
+            return
         if self.zn:
             if self.zn != self.d:
                 raise ValueError("a Z_n handle has d = n")
@@ -188,6 +226,29 @@ class MPS:
             raise MPSError(rc, "mps_create failed")
         self._h = h
         self.N = int(occ.sum()) % self.zn if self.zn else int(occ.sum())
+
+    # -- several-U(1) charge keys -------------------------------------------------
+    def _enc(self, c):
+        return int(sum(x * w for x, w in zip(c, self._weights))) if self.charges is not None else int(c)
+
+    def _dec(self, v):
+        if self.charges is None:
+            return int(v)
+        out = []
+        for w in self._weights:
+            out.append(int(v) // w)
+            v = int(v) - out[-1] * w
+        return tuple(out)
+
+    def _gate_flat(self, gate):
+        if self.charges is not None and isinstance(gate, dict):
+            return _c128_flat([gate[Q] for Q in self._pairs])
+        return _c128_flat(gate)
+
+    def gate_length(self) -> int:
+        if self.charges is not None:
+            return sum(len(p) ** 2 for p in self._pairs.values())
+        return gate_length(self.d)
 
     # -- checkpoint -------------------------------------------------------------
     def save(self, path) -> None:
@@ -242,8 +303,8 @@ class MPS:
 
     # -- updates ----------------------------------------------------------------
     def apply_gate2(self, site: int, gate, chi: int, cutoff: float) -> float:
-        g = _c128_flat(gate)
-        if g.size != gate_length(self.d):
+        g = self._gate_flat(gate)
+        if g.size != self.gate_length():
             raise ValueError("gate has the wrong number of entries")
         te = ctypes.c_double(0.0)
         rc = lib.mps_apply_gate2(self._h, site, g.ctypes.data_as(_dblp), chi, cutoff, ctypes.byref(te))
@@ -252,7 +313,7 @@ class MPS:
 
     def apply_layer(self, sites, gates, chi: int, cutoff: float) -> np.ndarray:
         sites = np.ascontiguousarray(np.asarray(sites, dtype=np.intc))
-        gs = [_c128_flat(g) for g in gates]
+        gs = [self._gate_flat(g) for g in gates]
         if len(gs) != len(sites):
             raise ValueError("one gate per site")
         arr = (_dblp * len(gs))(*[g.ctypes.data_as(_dblp) for g in gs])
@@ -294,7 +355,7 @@ class MPS:
     def bond(self, b: int):
         """(charges, dims, lambda per charge) of bond b."""
         n = ctypes.c_int(0)
-        cap = self.L * (self.d - 1) + 2
+        cap = self.L * (self.d - 1) + 2 if self.charges is None else min(1 << 16, (self.L + 2) ** len(self.charges[0]))
         ch = np.zeros(cap, np.int32)
         dm = np.zeros(cap, np.int32)
         lam = np.zeros(max(1, self.chi_max) + 1)
@@ -303,7 +364,7 @@ class MPS:
         k = n.value
         out, off = {}, 0
         for c, D in zip(ch[:k], dm[:k]):
-            out[int(c)] = lam[off:off + D].copy()
+            out[self._dec(c)] = lam[off:off + D].copy()
             off += int(D)
         return out
 
@@ -330,22 +391,24 @@ class MPS:
         right = self.bond_dims(s + 1)
         out, off = {}, 0
         for l, m in zip(lc[:nb.value], mc[:nb.value]):
-            Dl, Dm = left[int(l)], right[int(m)]
-            out[(int(l), int(m))] = data[off:off + Dl * Dm].reshape(Dl, Dm).copy()
+            l, m = self._dec(l), self._dec(m)
+            Dl, Dm = left[l], right[m]
+            out[(l, m)] = data[off:off + Dl * Dm].reshape(Dl, Dm).copy()
             off += Dl * Dm
         return out
 
     def set_bond(self, b: int, lam: dict):
-        ch = _i32(sorted(lam))
-        dm = _i32([len(lam[c]) for c in sorted(lam)])
-        vals = np.ascontiguousarray(np.concatenate([np.asarray(lam[c], np.float64) for c in sorted(lam)]))
+        keys = sorted(lam)
+        ch = _i32([self._enc(c) for c in keys])
+        dm = _i32([len(lam[c]) for c in keys])
+        vals = np.ascontiguousarray(np.concatenate([np.asarray(lam[c], np.float64) for c in keys]))
         self._check(lib.mps_set_bond(self._h, b, len(ch), _ptr(ch, _i32p), _ptr(dm, _i32p), _ptr(vals, _dblp)),
                     "mps_set_bond")
 
     def set_site(self, s: int, blocks: dict):
         keys = sorted(blocks)
-        lc = _i32([k[0] for k in keys])
-        mc = _i32([k[1] for k in keys])
+        lc = _i32([self._enc(k[0]) for k in keys])
+        mc = _i32([self._enc(k[1]) for k in keys])
         if keys:
             data = np.ascontiguousarray(np.concatenate([np.asarray(blocks[k], np.complex128).reshape(-1)
                                                         for k in keys]))

@@ -11,6 +11,7 @@
 // launches with one host round trip.
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -334,10 +335,10 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       ws = a256(ws + 16LL * e.cols * k);
       W[u].sig_off.push_back(ws);
       ws = a256(ws + 8LL * k);
-      scatter_bound += (e.r1 - e.r0);
-      gemm_tasks_bound += (e.l1 - e.l0);
-      lam_bound += 1;
-      for (int i = e.l0; i < e.l1; ++i) {
+      scatter_bound += (int64_t)e.ri.size();
+      gemm_tasks_bound += (int64_t)e.li.size();
+      lam_bound += 1 + (e.contiguous ? 0 : (int64_t)e.li.size());
+      for (int i : e.li) {
         const int Dl = reqs[u].h->bonds[reqs[u].site].dim[i];
         gemm_tiles_bound += (int64_t)((Dl + kTile - 1) / kTile) * ((k + kTile - 1) / kTile);
       }
@@ -357,6 +358,13 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   const int64_t kept_off = ws; ws = a256(ws + 4LL * n_sec_total);
   const int64_t status_off = ws; ws = a256(ws + 4LL * n_sec_total);
   const int64_t res_off = ws; ws = a256(ws + (int64_t)sizeof(SelectResult) * nreq);
+  // the left lambdas of sectors whose rows are not one run of the bond table (several-U(1)
+  // handles), gathered so that the SVD reads its row scale contiguously
+  int64_t gather_rows = 0, n_gather = 0;
+  for (int u = 0; u < nreq; ++u)
+    for (auto& e : W[u].plan.sectors)
+      if (!e.contiguous) { gather_rows += e.rows; n_gather += (int64_t)e.li.size(); }
+  const int64_t gath_off = ws; ws = a256(ws + 8LL * gather_rows);
   const int64_t desc_off = ws;   // phase-1 descriptors start here; phase-2 reuses the same region
 
   // count theta tasks to size descriptors
@@ -399,7 +407,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       }
       for (const SectorPlanEntry& e : W[u].plan.sectors) {
         const int k = std::min(e.rows, e.cols), ktn = cdiv(e.cols, KC);
-        for (int i = e.l0; i < e.l1; ++i) {
+        for (int i : e.li) {
           tc_slots[p] += (int64_t)cdiv(Lb.dim[i], kShRows) * ktn * TPK;
           tc_jobs2[p] += (int64_t)cdiv(Lb.dim[i], kShRows) * cdiv(k, kShTileN);
         }
@@ -415,7 +423,8 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
                               a256((int64_t)sizeof(ShadowTask) * (tc_shtasks[0] + tc_shtasks[1])) +
                               a256((int64_t)sizeof(ShadowTile) * (tc_shtiles[0] + tc_shtiles[1])) +
                               a256((int64_t)sizeof(TmaJob) * (tc_jobs[0] + tc_jobs[1])) +
-                              a256((int64_t)sizeof(MixTask) * (tc_mix[0] + tc_mix[1])) + 4 * 256;
+                              a256((int64_t)sizeof(MixTask) * (tc_mix[0] + tc_mix[1])) +
+                              a256((int64_t)sizeof(LambdaTask) * n_gather) + 4 * 256;
   const int64_t phase2_desc = a256((int64_t)sizeof(LambdaTask) * lam_bound) +
                               a256((int64_t)sizeof(ScatterTask) * scatter_bound) +
                               a256((int64_t)sizeof(GemmTask) * gemm_tasks_bound) +
@@ -472,6 +481,8 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   std::vector<SvdSector> svd; svd.reserve(n_sec_total);
   std::vector<SelectSector> selsec; selsec.reserve(n_sec_total);
   std::vector<SelectTask> seltask; seltask.reserve(nreq);
+  std::vector<LambdaTask> gath;
+  int64_t gath_next = 0;
   int sec_global = 0;
   for (int u = 0; u < nreq; ++u) {
     mps_s* h = reqs[u].h;
@@ -520,7 +531,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       ra_slot[u].resize(P.sectors.size());
       for (size_t si = 0; si < P.sectors.size(); ++si) {
         const SectorPlanEntry& E = P.sectors[si];
-        for (int i = E.l0; i < E.l1; ++i) {
+        for (int i : E.li) {
           ra_slot[u][si].push_back(slot_next[tp]);
           slot_next[tp] += (int64_t)cdiv(Lb.dim[i], kShRows) * cdiv(E.cols, KC) * TPK;
         }
@@ -533,7 +544,6 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
         if (n < 0) continue;
         ThetaTask T;
         std::memset(&T, 0, sizeof(T));
-        const int base_n = rule.base(n);
         T.nm = 0;
         for (int mi = 0; mi < Mb.size(); ++mi) {
           const int m = Mb.charge[mi];
@@ -543,20 +553,24 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
           T.A[T.nm] = slotL + SL.blocks[bl].off;
           T.B[T.nm] = slotR + SR.blocks[br].off;
           T.Dm[T.nm] = Mb.dim[mi];
-          T.gi[T.nm] = rule.phys(l, m) - base_n;
+          T.gi[T.nm] = rule.gpos(n, rule.phys(l, m));
           T.nm++;
         }
         if (T.nm == 0) continue;
         T.nc = 0;
-        for (int c = rule.cmin(l, r); c <= rule.cmax(l, r); ++c) {
+        int cs[MPS_MAX_D];
+        const int ncs = rule.mids(l, r, cs);
+        for (int ci = 0; ci < ncs; ++ci) {
+          const int c = cs[ci];
           const int si = sector_of(c);
           if (si < 0) return fail(owner, MPS_EINVAL, "internal: missing sector");
           const SectorPlanEntry& E = P.sectors[si];
-          const int roff = Lb.off[li] - Lb.off[E.l0];
-          const int coff = Rb.off[ri] - Rb.off[E.r0];
+          const int roff = E.row_off(li);
+          const int coff = E.col_off(ri);
+          if (roff < 0 || coff < 0) return fail(owner, MPS_EINVAL, "internal: sector layout");
           T.out[T.nc] = reinterpret_cast<double2*>(dptr(W[u].theta_off[si])) + (int64_t)roff * E.cols + coff;
           T.ldo[T.nc] = E.cols;
-          T.go[T.nc] = rule.phys(l, c) - base_n;
+          T.go[T.nc] = rule.gpos(n, rule.phys(l, c));
           T.nc++;
         }
         T.gate = reinterpret_cast<const double2*>(dptr(W[u].gate_off)) + rule.block_off(n);
@@ -598,15 +612,17 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
             ++i;
           }
           for (int k = 0; k < T.nc; ++k) {
-            const int c = rule.wrap(l - T.go[k] - base_n);
+            const int c = cs[k];
             const int si = sector_of(c);
             const SectorPlanEntry& E = P.sectors[si];
             X.out[k] = T.out[k];
             X.ldo[k] = T.ldo[k];
             X.go[k] = T.go[k];
-            X.sh0[k] = ra_slot[u][si][li - E.l0];
+            int pos = 0;
+            while (E.li[pos] != li) ++pos;
+            X.sh0[k] = ra_slot[u][si][pos];
             X.sh_ktn[k] = cdiv(E.cols, KC);
-            X.coff[k] = Rb.off[ri] - Rb.off[E.r0];
+            X.coff[k] = E.col_off(ri);
           }
           mixes[tp].push_back(X);
           tc_th_flops += 8.0 * T.nm * T.nc * T.Dl * T.Dr;
@@ -622,7 +638,15 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       const SectorPlanEntry& E = P.sectors[si];
       SvdSector S = {};
       S.theta = reinterpret_cast<const double2*>(dptr(W[u].theta_off[si]));
-      S.rowscale = h->lambda_ptr(s) + Lb.off[E.l0];
+      if (E.contiguous) {
+        S.rowscale = h->lambda_ptr(s) + Lb.off[E.li.front()];
+      } else {
+        double* g = reinterpret_cast<double*>(dptr(gath_off)) + gath_next;
+        for (size_t a = 0; a < E.li.size(); ++a)
+          gath.push_back(LambdaTask{h->lambda_ptr(s) + Lb.off[E.li[a]], g + E.loff[a], Lb.dim[E.li[a]], 1.0});
+        gath_next += E.rows;
+        S.rowscale = g;
+      }
       S.m = E.rows;
       S.n = E.cols;
       S.floor_rel = kDeflateRel * reqs[u].cutoff;
@@ -681,6 +705,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   for (int c = 0; c < n_cand; ++c) o_svd[c] = sg.put(svd_sorted[c].data(), (int64_t)svd_sorted[c].size());
   const int64_t o_selsec = sg.put(selsec.data(), (int64_t)selsec.size());
   const int64_t o_seltask = sg.put(seltask.data(), (int64_t)seltask.size());
+  const int64_t o_gath = sg.put(gath.data(), (int64_t)gath.size());
   int64_t o_shtask[2], o_shtile[2], o_tjobs[2], o_mix[2];
   double sh_bytes = 0, prod_bytes = 0;
   for (int p = 0; p < 2; ++p) {
@@ -748,6 +773,11 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
           e2 = launch_tma_zgemm(precs[p], reinterpret_cast<TmaJob*>(dptr(desc_off + o_tjobs[p])),
                                 (int)tjobs[p].size(), slot_base[p], tc_slots[p] + tc_slots2[p], owner->tc_flag, st);
         return e2;
+      });
+    if (e != cudaSuccess) return e;
+    if (!gath.empty())
+      e = timed(owner, MPS_K_LAMBDA, true, 0.0, 16.0 * (double)gather_rows, [&] {
+        return launch_lambda(reinterpret_cast<LambdaTask*>(dptr(desc_off + o_gath)), (int)gath.size(), st);
       });
     if (e != cudaSuccess) return e;
     const bool any_theta = !tiles.empty() || !mixes[0].empty() || !mixes[1].empty();
@@ -969,13 +999,14 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       const double2* Y = reinterpret_cast<const double2*>(dptr(W[u].y_off[si]));
       const double2* th = reinterpret_cast<const double2*>(dptr(W[u].theta_off[si]));
       lam.push_back(LambdaTask{sig, h->lambda_ptr(s + 1) + M.off[mi], k, scale});
-      for (int ri = E.r0; ri < E.r1; ++ri) {
+      for (size_t ra = 0; ra < E.ri.size(); ++ra) {
+        const int ri = E.ri[ra];
         const int b = newR[u].find(E.c, Rb.charge[ri]);
         ScatterTask T;
         T.Y = Y;
         T.out = dstR + newR[u].blocks[b].off;
         T.n = E.cols;
-        T.coff = Rb.off[ri] - Rb.off[E.r0];
+        T.coff = E.coff[ra];
         T.k = k;
         T.Dr = Rb.dim[ri];
         T.first = sc_elems;
@@ -996,11 +1027,12 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
         yslot_next[tp] += (int64_t)cdiv(k, kShTileN) * ktn * TPK;
         ysh_bytes += 16.0 * k * E.cols + (double)cdiv(k, kShTileN) * ktn * TPK * kShTileBytes;
       }
-      for (int li = E.l0; li < E.l1; ++li) {
+      for (size_t la = 0; la < E.li.size(); ++la) {
+        const int li = E.li[la];
         const int b = newL[u].find(Lb.charge[li], E.c);
         if (tc) {   // B^[s][l, c] = (Theta'(c)[rows of l] . Y(c)[:, :k]) / |S_kept| on the tensor cores
           const int Dl = Lb.dim[li];
-          const int64_t a0 = ra_slot[u][si][li - E.l0];
+          const int64_t a0 = ra_slot[u][si][la];
           for (int rt = 0; rt < cdiv(Dl, kShRows); ++rt)
             for (int ct = 0; ct < cdiv(k, kShTileN); ++ct) {
               TmaJob J;
@@ -1020,7 +1052,7 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
           continue;
         }
         GemmTask G;
-        G.A = th + (int64_t)(Lb.off[li] - Lb.off[E.l0]) * E.cols;
+        G.A = th + (int64_t)E.loff[la] * E.cols;
         G.sar = E.cols; G.sac = 1;
         G.B = Y; G.sbr = 1; G.sbc = E.cols;
         G.C = dstL + newL[u].blocks[b].off;
@@ -1159,7 +1191,8 @@ bool svd_forced_tune(SvdTune& t) {
 extern "C" {
 
 static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, int site_lo, int site_hi,
-                         int precision, int chi_max, void* cuda_stream, int zn = 0);
+                         int precision, int chi_max, void* cuda_stream, int zn = 0,
+                         const ChargeRule* multi = nullptr);
 
 int mps_create(mps_t* out, int L, int d, const int32_t* site_charges, int precision, int chi_max,
                void* cuda_stream) {
@@ -1184,8 +1217,51 @@ int mps_create_zn(mps_t* out, int L, int n, const int32_t* site_charges, int pre
   return create_handle(out, L, n, site_charges, 0, L, precision, chi_max, cuda_stream, n);
 }
 
+int mps_create_multi(mps_t* out, int L, int d, int ncomp, const int32_t* phys_charges, const int32_t* site_indices,
+                     int precision, int chi_max, void* cuda_stream) {
+  if (out) *out = nullptr;
+  if (!out || L < 2 || d < 2 || d > MPS_MAX_D || ncomp < 1 || ncomp > 4 || !phys_charges) return MPS_EINVAL;
+  if (precision != MPS_FP64) return MPS_EINVAL;
+  ChargeRule r;
+  r.d = d;
+  r.multi = 1;
+  r.ncomp = ncomp;
+  // radix per component: more than twice the largest bond value (L * max charge), so that every
+  // difference of two charges decodes uniquely
+  int64_t w = 1;
+  std::vector<int64_t> weight(ncomp);
+  for (int k = ncomp - 1; k >= 0; --k) {
+    int mx = 0;
+    for (int i = 0; i < d; ++i) {
+      const int v = phys_charges[i * ncomp + k];
+      if (v < 0) return MPS_ECHARGE;
+      mx = std::max(mx, v);
+    }
+    r.radix[k] = (int)std::min<int64_t>(INT32_MAX, 2LL * L * mx + 3);
+    weight[k] = w;
+    w *= r.radix[k];
+    if (w > (int64_t)1 << 30) return MPS_EINVAL;     // encoded charges must fit in int32
+  }
+  for (int i = 0; i < d; ++i) {
+    int64_t e = 0;
+    for (int k = 0; k < ncomp; ++k) e += phys_charges[i * ncomp + k] * weight[k];
+    r.q[i] = (int)e;
+    if (i && r.q[i] <= r.q[i - 1]) return MPS_ECHARGE;   // distinct, in ascending order
+  }
+  r.init_multi();
+  return create_handle(out, L, d, site_indices, 0, L, precision, chi_max, cuda_stream, 0, &r);
+}
+
+int mps_charge_radix(mps_t h, int* ncomp, int32_t* radix) {
+  if (!h || !ncomp) return MPS_EINVAL;
+  *ncomp = h->rule.multi ? h->rule.ncomp : 1;
+  if (radix)
+    for (int k = 0; k < *ncomp; ++k) radix[k] = h->rule.multi ? h->rule.radix[k] : 0;
+  return MPS_OK;
+}
+
 static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, int site_lo, int site_hi,
-                         int precision, int chi_max, void* cuda_stream, int zn) {
+                         int precision, int chi_max, void* cuda_stream, int zn, const ChargeRule* multi) {
   if (!out) return MPS_EINVAL;
   *out = nullptr;
   if (L < 2 || d < 2 || d > MPS_MAX_D || chi_max < 1 || !site_charges) return MPS_EINVAL;
@@ -1194,14 +1270,15 @@ static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, 
     if (site_charges[s] < 0 || site_charges[s] > d - 1) return MPS_ECHARGE;
   mps_s* h = new mps_s();
   h->L = L; h->d = d; h->chi_max = chi_max; h->precision = precision;
+  if (multi) h->rule = *multi;
   h->rule.d = d;
   h->rule.zn = zn;
   h->stream = (cudaStream_t)cuda_stream;
   std::vector<int> c(L + 1, 0);
-  for (int b = L - 1; b >= 0; --b) c[b] = h->rule.wrap(c[b + 1] + site_charges[b]);
+  for (int b = L - 1; b >= 0; --b) c[b] = h->rule.wrap(c[b + 1] + h->rule.charge_of(site_charges[b]));
   h->N = c[0];
   const int N = h->N;
-  auto Wc = zn ? std::vector<std::vector<double>>() : config_counts(L, d, N);
+  auto Wc = (zn || multi) ? std::vector<std::vector<double>>() : config_counts(L, d, N);
   h->bonds.resize(L + 1);
   h->bond_cap.resize(L + 1);
   h->lam_base.resize(L + 1);
@@ -1212,7 +1289,7 @@ static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, 
     t.dim = {1};
     t.rebuild_offsets();
     double hb = 0.0;
-    if (zn) {   // d^k strings of k sites: the smaller side bounds the Schmidt rank
+    if (zn || multi) {   // d^k strings of k sites: the smaller side bounds the Schmidt rank
       hb = std::pow((double)d, (double)std::min(b, L - b));
     } else {
       const int lo = std::max(0, N - (d - 1) * b), hi = std::min(N, (d - 1) * (L - b));
@@ -1490,8 +1567,8 @@ int mps_amplitude_batch(mps_t h, int n, const int32_t* configs, double* out) {
     bool ok = true;
     c[L] = 0;
     for (int b = L - 1; b >= 0; --b) {
-      if (cfg[b] < 0 || cfg[b] > h->d - 1) ok = false;
-      c[b] = h->rule.wrap(c[b + 1] + cfg[b]);
+      if (cfg[b] < 0 || cfg[b] > h->d - 1) { ok = false; continue; }
+      c[b] = h->rule.wrap(c[b + 1] + h->rule.charge_of(cfg[b]));
     }
     if (c[0] != h->N) ok = false;
     for (int s = 0; s < L; ++s) {
@@ -1549,7 +1626,7 @@ int mps_sample(mps_t h, int n, const double* uniforms, int32_t* configs_out, dou
     for (int li = 0; li < Lb.size(); ++li)
       for (int i = 0; i < d; ++i) {
         SampleEntry e{nullptr, 0, 0, -1, 0};
-        const int bi = h->sites[s].find(Lb.charge[li], h->rule.wrap(Lb.charge[li] - i));
+        const int bi = h->sites[s].find(Lb.charge[li], h->rule.wrap(Lb.charge[li] - h->rule.charge_of(i)));
         if (bi >= 0) {
           const SiteBlock& B = h->sites[s].blocks[bi];
           e.blk = slot + B.off;
@@ -1652,8 +1729,10 @@ int mps_set_bond(mps_t h, int bond, int n_sectors, const int32_t* charges, const
   t.charge.assign(charges, charges + n_sectors);
   t.dim.assign(dims, dims + n_sectors);
   const int d = h->d, L = h->L, N = h->N;
-  const int lo = h->rule.zn ? 0 : std::max(0, N - (d - 1) * bond);
-  const int hi = h->rule.zn ? h->rule.zn - 1 : std::min(N, (d - 1) * (L - bond));
+  // several-U(1) handles: any encoded charge (the site layout keeps only blocks whose charge
+  // difference is a physical charge)
+  const int lo = h->rule.multi ? INT32_MIN : (h->rule.zn ? 0 : std::max(0, N - (d - 1) * bond));
+  const int hi = h->rule.multi ? INT32_MAX : (h->rule.zn ? h->rule.zn - 1 : std::min(N, (d - 1) * (L - bond)));
   for (int i = 0; i < n_sectors; ++i) {
     if (t.dim[i] < 1) return fail(h, MPS_EINVAL, "sector dimension < 1");
     if (i && t.charge[i] <= t.charge[i - 1]) return fail(h, MPS_EINVAL, "charges not ascending");

@@ -67,7 +67,7 @@ extern "C" {
 int mps_save(mps_t h, const char* path) {
   if (!h) return MPS_EINVAL;
   if (!path) return save_fail(h, "path is NULL");
-  if (h->rule.zn) return save_fail(h, "checkpoints hold U(1) handles only");
+  if (h->rule.zn || h->rule.multi) return save_fail(h, "checkpoints hold U(1) handles only");
   for (int s = 0; s < h->L; ++s)
     if (h->dirty[s]) return save_fail(h, "site " + std::to_string(s) + " needs mps_set_site before saving");
   File out;

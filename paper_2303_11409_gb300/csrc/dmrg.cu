@@ -1374,7 +1374,7 @@ int mps_dmrg(mps_t h, const double* const* bond_terms, int n_sweeps, int chi, do
   if (!h || !bond_terms || n_sweeps < 0 || chi < 1 || !(cutoff >= 0.0) || !n_energies) return MPS_EINVAL;
   *n_energies = 0;
   if (h->precision != MPS_FP64) { h->err = "DMRG runs on FP64 handles"; return MPS_EINVAL; }
-  if (h->rule.zn) { h->err = "DMRG is built for U(1) charges"; return MPS_EINVAL; }
+  if (h->rule.zn || h->rule.multi) { h->err = "DMRG is built for single U(1) charges"; return MPS_EINVAL; }
   if (lanczos_dim < 2 || lanczos_dim > 63 || !(tol > 0.0)) return MPS_EINVAL;
   const int L = h->L;
   if (L < 2) return MPS_EINVAL;

@@ -25,28 +25,79 @@ constexpr int kSvdSideStreams = 4;      // side streams for concurrent SVD kerne
 struct ChargeRule {
   int d = 2;
   int zn = 0;
+  // Several U(1) charges (multi = 1): physical index i carries the charge vector q_i, stored
+  // encoded as one integer q[i] (mixed radix, first component most significant, ascending in
+  // i); bond charges are encoded the same way.  The radix of every component exceeds twice
+  // its largest bond value, so differences of charges decode uniquely and the integer order
+  // of valid charges is their lexicographic order.  A Theta(c) block then has as rows the
+  // left sectors l with l - c among the q[i] (not always a contiguous run of the bond table).
+  // Two-site gate blocks are the distinct totals q[i] + q[j], ascending, each over its pairs
+  // (i, j) with i ascending.
+  int multi = 0;
+  int q[MPS_MAX_D] = {};
+  int ncomp = 1;
+  int radix[4] = {1, 1, 1, 1};
+  int nb2 = 0;
+  int q2[MPS_MAX_D * MPS_MAX_D] = {};
+  int sn2[MPS_MAX_D * MPS_MAX_D] = {};
+  int64_t off2[MPS_MAX_D * MPS_MAX_D + 1] = {};
+  signed char pos2[MPS_MAX_D * MPS_MAX_D][MPS_MAX_D] = {};
+  void init_multi();                       // fills the two-site block tables from q[]
   int wrap(int c) const { return zn ? ((c % zn) + zn) % zn : c; }
   int phys(int l, int m) const {           // physical index of block (l, m), or -1
+    if (multi) {
+      const int x = l - m;
+      for (int i = 0; i < d; ++i)
+        if (q[i] == x) return i;
+      return -1;
+    }
     const int i = zn ? wrap(l - m) : l - m;
     return (i >= 0 && i < d) ? i : -1;
   }
+  int charge_of(int i) const { return multi ? q[i] : i; }   // (encoded) charge of physical index i
   int pair(int l, int r) const {           // two-site gate block of (l, r), or -1
+    if (multi) {
+      const int x = l - r;
+      int lo = 0, hi = nb2 - 1;
+      while (lo <= hi) {
+        const int mid = (lo + hi) / 2;
+        if (q2[mid] == x) return mid;
+        if (q2[mid] < x) lo = mid + 1; else hi = mid - 1;
+      }
+      return -1;
+    }
     if (zn) return wrap(l - r);
-    const int q = l - r;
-    return (q >= 0 && q <= 2 * (d - 1)) ? q : -1;
+    const int q_ = l - r;
+    return (q_ >= 0 && q_ <= 2 * (d - 1)) ? q_ : -1;
   }
-  int nblocks() const { return zn ? zn : 2 * d - 1; }
-  int base(int q) const { return zn ? 0 : (q - d + 1 > 0 ? q - d + 1 : 0); }   // first left index of block q
-  int sn(int q) const { return zn ? zn : (q < d - 1 ? q : d - 1) - base(q) + 1; }
-  int64_t block_off(int q) const {
+  int nblocks() const { return multi ? nb2 : (zn ? zn : 2 * d - 1); }
+  int base(int q_) const { return zn ? 0 : (q_ - d + 1 > 0 ? q_ - d + 1 : 0); }   // first left index of block q (U(1))
+  int sn(int k) const {
+    if (multi) return sn2[k];
+    return zn ? zn : (k < d - 1 ? k : d - 1) - base(k) + 1;
+  }
+  int gpos(int k, int i) const { return multi ? pos2[k][i] : i - base(k); }   // row of left index i in block k
+  int64_t block_off(int k) const {
+    if (multi) return off2[k];
     int64_t t = 0;
-    for (int k = 0; k < q; ++k) t += (int64_t)sn(k) * sn(k);
+    for (int j = 0; j < k; ++j) t += (int64_t)sn(j) * sn(j);
     return t;
   }
   int64_t gate_len() const { return block_off(nblocks()); }
-  // candidate middle charges c of a pair (l, r): [cmin, cmax]
+  // candidate middle charges c of a pair (l, r): [cmin, cmax] (U(1), Z_n)
   int cmin(int l, int r) const { return zn ? 0 : (r > l - d + 1 ? r : l - d + 1); }
   int cmax(int l, int r) const { return zn ? zn - 1 : (l < r + d - 1 ? l : r + d - 1); }
+  // the middle charges of a pair (l, r), ascending, into out[MPS_MAX_D]; returns their count
+  int mids(int l, int r, int* out) const {
+    int n = 0;
+    if (multi) {
+      for (int i = d - 1; i >= 0; --i)
+        if (phys(l - q[i], r) >= 0) out[n++] = l - q[i];
+      return n;
+    }
+    for (int c = cmin(l, r); c <= cmax(l, r); ++c) out[n++] = c;
+    return n;
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -85,9 +136,23 @@ void layout_site(const BondTable& left, const BondTable& right, const ChargeRule
 // ---------------------------------------------------------------------------
 struct SectorPlanEntry {
   int c;             // candidate middle charge
-  int l0, l1;        // row sectors: indices [l0, l1) of the left bond table
-  int r0, r1;        // column sectors: indices [r0, r1) of the right bond table
+  int l0, l1;        // row sectors: indices [l0, l1) of the left bond table (U(1), Z_n)
+  int r0, r1;        // column sectors: indices [r0, r1) of the right bond table (U(1), Z_n)
   int rows, cols;    // Theta(c) size
+  // the row / column sectors in order with their offsets inside Theta(c) (every rule; for
+  // U(1) and Z_n the runs above); contiguous == the rows are one run of the left table
+  std::vector<int> li, loff, ri, coff;
+  bool contiguous = true;
+  int row_off(int i) const {        // offset of left sector i, or -1
+    for (size_t a = 0; a < li.size(); ++a)
+      if (li[a] == i) return loff[a];
+    return -1;
+  }
+  int col_off(int j) const {
+    for (size_t a = 0; a < ri.size(); ++a)
+      if (ri[a] == j) return coff[a];
+    return -1;
+  }
 };
 struct UpdatePlan {
   std::vector<SectorPlanEntry> sectors;                 // c ascending

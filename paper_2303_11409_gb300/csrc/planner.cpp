@@ -70,6 +70,42 @@ void plan_update(const BondTable& left, const BondTable& mid, const BondTable& r
   plan_update(left, mid, right, u1, plan);
 }
 
+void ChargeRule::init_multi() {
+  std::vector<int> tot;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) tot.push_back(q[i] + q[j]);
+  std::sort(tot.begin(), tot.end());
+  tot.erase(std::unique(tot.begin(), tot.end()), tot.end());
+  nb2 = (int)tot.size();
+  int64_t off = 0;
+  for (int k = 0; k < nb2; ++k) {
+    q2[k] = tot[k];
+    int n = 0;
+    for (int i = 0; i < d; ++i) {
+      pos2[k][i] = -1;
+      for (int j = 0; j < d; ++j)
+        if (q[i] + q[j] == tot[k]) { pos2[k][i] = (signed char)n++; break; }
+    }
+    sn2[k] = n;
+    off2[k] = off;
+    off += (int64_t)n * n;
+  }
+  off2[nb2] = off;
+}
+
+static void fill_lists(const BondTable& left, const BondTable& right, SectorPlanEntry& e) {
+  e.loff.clear();
+  e.coff.clear();
+  int o = 0;
+  for (int i : e.li) { e.loff.push_back(o); o += left.dim[i]; }
+  e.rows = o;
+  o = 0;
+  for (int j : e.ri) { e.coff.push_back(o); o += right.dim[j]; }
+  e.cols = o;
+  e.contiguous = true;
+  for (size_t a = 1; a < e.li.size(); ++a) e.contiguous = e.contiguous && e.li[a] == e.li[a - 1] + 1;
+}
+
 void plan_update(const BondTable& left, const BondTable& mid, const BondTable& right, const ChargeRule& rule,
                  UpdatePlan& plan) {
   const int d = rule.d;
@@ -84,14 +120,41 @@ void plan_update(const BondTable& left, const BondTable& mid, const BondTable& r
       }
     }
   if (left.size() == 0 || right.size() == 0) return;
+  if (rule.multi) {
+    // several U(1) charges: every middle charge some (l, r) pair reaches, with the left sectors
+    // l - c and the right sectors c - r among the physical charges as rows and columns
+    std::vector<int> cands;
+    int buf[MPS_MAX_D];
+    for (int i = 0; i < left.size(); ++i)
+      for (int k = 0; k < right.size(); ++k) {
+        const int n = rule.mids(left.charge[i], right.charge[k], buf);
+        cands.insert(cands.end(), buf, buf + n);
+      }
+    std::sort(cands.begin(), cands.end());
+    cands.erase(std::unique(cands.begin(), cands.end()), cands.end());
+    for (int c : cands) {
+      SectorPlanEntry e;
+      e.c = c; e.l0 = e.l1 = e.r0 = e.r1 = -1;
+      for (int i = 0; i < left.size(); ++i)
+        if (rule.phys(left.charge[i], c) >= 0) e.li.push_back(i);
+      for (int k = 0; k < right.size(); ++k)
+        if (rule.phys(c, right.charge[k]) >= 0) e.ri.push_back(k);
+      if (e.li.empty() || e.ri.empty()) continue;
+      fill_lists(left, right, e);
+      if (e.contiguous) { e.l0 = e.li.front(); e.l1 = e.li.back() + 1; }
+      plan.sectors.push_back(e);
+    }
+    return;
+  }
   if (rule.zn) {
     // Z_n with d = n: every middle charge c has all left sectors as rows (i' = (l - c) mod n)
     // and all right sectors as columns (j' = (c - r) mod n)
     for (int c = 0; c < rule.zn; ++c) {
       SectorPlanEntry e;
       e.c = c; e.l0 = 0; e.l1 = left.size(); e.r0 = 0; e.r1 = right.size();
-      e.rows = left.total();
-      e.cols = right.total();
+      for (int i = e.l0; i < e.l1; ++i) e.li.push_back(i);
+      for (int k = e.r0; k < e.r1; ++k) e.ri.push_back(k);
+      fill_lists(left, right, e);
       plan.sectors.push_back(e);
     }
     return;
@@ -108,8 +171,9 @@ void plan_update(const BondTable& left, const BondTable& mid, const BondTable& r
     if (l0 >= l1 || r0 >= r1) continue;
     SectorPlanEntry e;
     e.c = c; e.l0 = l0; e.l1 = l1; e.r0 = r0; e.r1 = r1;
-    e.rows = left.off[l1] - left.off[l0];
-    e.cols = right.off[r1] - right.off[r0];
+    for (int i = l0; i < l1; ++i) e.li.push_back(i);
+    for (int k = r0; k < r1; ++k) e.ri.push_back(k);
+    fill_lists(left, right, e);
     plan.sectors.push_back(e);
   }
 }
