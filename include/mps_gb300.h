@@ -587,6 +587,12 @@ MPS_API int mps_svd_mixed_min_k(int min_k);
 /* mps_svd_mixed_sweeps - the limit of those FP32 sweeps (1..40, default 8: on the chi = 2048 layer 6-10
  * FP32 sweeps minimise the time; the FP64 sweeps finish either way); MPS_EINVAL outside. */
 MPS_API int mps_svd_mixed_sweeps(int max_sweeps);
+/* mps_svd_cluster_min_k - sectors with min(m, n) >= min_k run on the cluster SVD kernels even when
+ * they fit in one CTA's shared memory (spreading a batch of few sectors over more SMs); 0 (the
+ * default): only sectors that do not fit.  A process setting read when mps_svd_sectors or an
+ * update call lays out its scratch; mps_dmrg picks its own threshold per step.  MPS_EINVAL for
+ * 0 < min_k < 16 or min_k < 0. */
+MPS_API int mps_svd_cluster_min_k(int min_k);
 
 /*
  * mps_svd_sectors_noalloc - the batched sector SVD of mps_svd_sectors for callers

@@ -11,7 +11,7 @@ from ._binding import (EXPORTED, LIB_PATH, MPS, MPS_BF16X3, MPS_EINVAL, MPS_ECHA
                        svd_sectors, svd_work_bytes)
 from ._binding import MPS_NOALLOC_SCRATCH_BYTES, svd_sectors_noalloc  # noqa: F401
 from ._binding import Executor, footprint_bytes, fp64_peak_probe, zgemm_tc  # noqa: F401
-from ._binding import tc_inject_stall, svd_mixed_min_k, svd_mixed_sweeps  # noqa: F401
+from ._binding import tc_inject_stall, svd_mixed_min_k, svd_mixed_sweeps, svd_cluster_min_k  # noqa: F401
 from ._binding import (autotune_clear, autotune_force, autotune_freeze, autotune_min_flops,  # noqa: F401
                        autotune_stats, autotune_table)
 from . import models, tebd, serve  # noqa: F401

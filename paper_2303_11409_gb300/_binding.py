@@ -124,6 +124,7 @@ _SIGS = {
     "mps_create_multi": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p,
                                         ctypes.c_int, ctypes.c_int, _vp]),
     "mps_charge_radix": (ctypes.c_int, [_h, _intp, _i32p]),
+    "mps_svd_cluster_min_k": (ctypes.c_int, [ctypes.c_int]),
 }
 DMRG_KINDS = ("heff", "env", "lanczos", "svd", "other")
 for _name, (_res, _args) in _SIGS.items():
@@ -610,6 +611,13 @@ def svd_mixed_min_k(min_k: int) -> None:
     rc = lib.mps_svd_mixed_min_k(int(min_k))
     if rc != MPS_OK:
         raise MPSError(rc, "mps_svd_mixed_min_k")
+
+
+def svd_cluster_min_k(min_k: int) -> None:
+    """Sectors with min(m, n) >= min_k use the cluster SVD kernels (0: only those that do not fit one CTA)."""
+    rc = lib.mps_svd_cluster_min_k(int(min_k))
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_svd_cluster_min_k")
 
 
 def svd_mixed_sweeps(max_sweeps: int) -> None:

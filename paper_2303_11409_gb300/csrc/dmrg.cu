@@ -465,6 +465,18 @@ struct SPBuild {
     flops += 8.0 * t.M * t.N * K;
     bytes += 16.0 * ((double)t.M * K + (double)K * t.N);
   }
+  // longest-processing-time order: the tiles with the most work start first, so that the
+  // tail of a launch with more tiles than resident CTAs is made of the short ones
+  void order_tiles() {
+    std::vector<double> w(tasks.size(), 0.0);
+    for (size_t t = 0; t < tasks.size(); ++t)
+      for (int q = tasks[t].t0; q < tasks[t].t1; ++q) w[t] += (terms[q].flags & kNoB) ? 1.0 : (double)terms[q].K;
+    auto cost = [&](const SPTile& x) {
+      const SPTask& t = tasks[x.task];
+      return w[x.task] * std::min(kT, t.M - x.ti * kT) * std::min(kT, t.N - x.tj * kT);
+    };
+    std::stable_sort(tiles.begin(), tiles.end(), [&](const SPTile& a, const SPTile& b) { return cost(a) > cost(b); });
+  }
   void copy(int64_t a, int sar, int sac, cplx coef, int flags) {
     if (coef == 0.0) return;
     SPTask& t = tasks.back();
@@ -884,6 +896,7 @@ struct Dmrg {
         }
       }
     }
+    mv.order_tiles();
     if (reserve_desc(desc_bytes(mv) + desc_bytes(th)) != cudaSuccess) return fail(MPS_ENOMEM, "DMRG descriptors");
     int64_t cur = 0;
     Up umv, uth;
@@ -985,8 +998,11 @@ struct Dmrg {
       sm[k] = right_moving ? E.cols : E.rows;
       sn[k] = right_moving ? E.rows : E.cols;
     }
+    // a step has few sectors: when one CTA each would leave most SMs idle, the sectors from
+    // min(m, n) >= 48 run on 8-CTA clusters instead
+    const bool spread = ns * 8 <= 152;
     SvdScratchLayout JL;
-    if (!svd_layout(ns, sm.data(), sn.data(), JL)) return fail(MPS_EINVAL, "DMRG SVD layout");
+    if (!svd_layout(ns, sm.data(), sn.data(), JL, spread ? 48 : -1)) return fail(MPS_EINVAL, "DMRG SVD layout");
     int64_t so = 0;
     std::vector<int64_t> o_mat(ns), o_y(ns), o_sig(ns);
     for (int k = 0; k < ns; ++k) {
@@ -1032,6 +1048,7 @@ struct Dmrg {
     }
     std::vector<SvdGroup> groups;
     SvdTune tune;
+    if (spread) tune.cl_min = 8;
     svd_forced_tune(tune);
     e = svd_group(secs, groups, tune);
     if (e != cudaSuccess) return fail(MPS_ECUDA, "DMRG SVD grouping");
@@ -1197,7 +1214,9 @@ struct Dmrg {
       }
       const int ns = (int)which.size();
       SvdScratchLayout JL;
-      if (!last && !svd_layout(ns, sm.data(), snn.data(), JL)) return fail(MPS_EINVAL, "DMRG SVD layout");
+      const bool spread = ns * 8 <= 152;
+      if (!last && !svd_layout(ns, sm.data(), snn.data(), JL, spread ? 48 : -1))
+        return fail(MPS_EINVAL, "DMRG SVD layout");
       std::vector<int64_t> o_y(ns), o_sig(ns);
       int64_t ysz = 0;
       for (int k = 0; k < ns && !last; ++k) {
@@ -1271,6 +1290,7 @@ struct Dmrg {
       }
       std::vector<SvdGroup> groups;
       SvdTune tune;
+      if (spread) tune.cl_min = 8;
       svd_forced_tune(tune);
       if (svd_group(secs, groups, tune) != cudaSuccess) return fail(MPS_ECUDA, "DMRG SVD grouping");
       SelectTask task{0, ns, 1 << 30, 0.0};

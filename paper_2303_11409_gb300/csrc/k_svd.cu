@@ -1708,7 +1708,8 @@ cudaError_t launch_svd_groups(const SvdSector* d_secs, const std::vector<SvdGrou
   return cudaSuccess;
 }
 
-bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L) {
+bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L, int cluster_min_k) {
+  if (cluster_min_k < 0) cluster_min_k = svd_cluster_min_k();
   L.mode.assign(ns, kSvdSmem);
   L.work_off.assign(ns, -1);
   L.v_off.assign(ns, -1);
@@ -1727,7 +1728,7 @@ bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L) {
   for (int k = 0; k < ns; ++k) {
     if (m[k] < 1 || n[k] < 1) return false;
     const int64_t need = svd_smem_need(m[k], n[k]);
-    if (need <= kSvdSmemMax) {
+    if (need <= kSvdSmemMax && std::min(m[k], n[k]) < cluster_min_k) {
       L.smem = std::max<int>(L.smem, (int)need);
       continue;
     }
@@ -1787,8 +1788,10 @@ void svd_fill_scratch(SvdSector& S, const SvdScratchLayout& L, int k, char* base
 namespace {
 std::atomic<int> g_mixed_min_k{192};
 std::atomic<int> g_mixed_sweeps{8};
+std::atomic<int> g_cluster_min_k{1 << 30};
 }
 int svd_mixed_min_k() { return g_mixed_min_k.load(); }
+int svd_cluster_min_k() { return g_cluster_min_k.load(); }
 int svd_mixed_sweeps() { return g_mixed_sweeps.load(); }
 
 }  // namespace mps
@@ -1796,6 +1799,12 @@ int svd_mixed_sweeps() { return g_mixed_sweeps.load(); }
 extern "C" int mps_svd_mixed_min_k(int min_k) {
   if (min_k < 0) return MPS_EINVAL;
   mps::g_mixed_min_k.store(min_k);
+  return MPS_OK;
+}
+
+extern "C" int mps_svd_cluster_min_k(int min_k) {
+  if (min_k != 0 && min_k < 16) return MPS_EINVAL;
+  mps::g_cluster_min_k.store(min_k == 0 ? (1 << 30) : min_k);
   return MPS_OK;
 }
 

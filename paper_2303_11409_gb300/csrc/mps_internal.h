@@ -225,7 +225,11 @@ struct SvdScratchLayout {
   int smem = 0;               // dynamic shared memory of the one-CTA kernel
   int64_t total = 0;
 };
-bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L);
+// Sectors that fit in shared memory run on the one-CTA kernel unless min(m, n) >= cluster_min_k
+// (a cluster kernel then spreads them over several SMs; -1: the process setting
+// mps_svd_cluster_min_k, off by default).
+bool svd_layout(int ns, const int* m, const int* n, SvdScratchLayout& L, int cluster_min_k = -1);
+int svd_cluster_min_k();
 // Cluster sectors with min(m, n) >= this run FP32 Jacobi sweeps first and finish in FP64
 // (0: every sector FP64 only); mps_svd_mixed_min_k sets it.
 int svd_mixed_min_k();

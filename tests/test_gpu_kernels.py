@@ -120,3 +120,27 @@ def test_zgemm_tc_rejects_bad_arguments(gpu_lib):
     A = np.ones((4, 4), np.complex128)
     with pytest.raises(gpu_lib.MPSError):
         gpu_lib.zgemm_tc(A, A, precision=gpu_lib.MPS_FP64)
+
+
+def test_cluster_kernels_on_sectors_that_fit_one_cta(gpu_lib):
+    """mps_svd_cluster_min_k puts small and medium sectors on the cluster kernels (how mps_dmrg
+    spreads a step's few sectors over the GPU): same accuracy as the one-CTA kernel, graded rows
+    included."""
+    rng = np.random.default_rng(5)
+    shapes = [(16, 16), (17, 40), (48, 48), (64, 31), (85, 85), (90, 120), (130, 70)]
+    mats = [W.random_complex(s, rng) for s in shapes]
+    scales = [np.logspace(0, -10, s[0]) for s in shapes]
+    try:
+        gpu_lib.svd_cluster_min_k(16)
+        out = gpu_lib.svd_sectors(mats, rowscales=scales)
+    finally:
+        gpu_lib.svd_cluster_min_k(0)
+    for M, r, (sig, Y, sw) in zip(mats, scales, out):
+        Ms = r[:, None] * M
+        ref = np.linalg.svd(Ms, compute_uv=False)
+        assert np.max(np.abs(sig - ref[:len(sig)])) <= 1e-12 * ref[0] * 4
+        assert sw >= 0
+        good = sig > 1e-8 * ref[0]
+        Yg = Y[:, good]
+        assert np.max(np.abs(Yg.conj().T @ Yg - np.eye(Yg.shape[1]))) < 1e-10
+        assert np.max(np.abs(np.linalg.norm(Ms @ Yg, axis=0) - sig[good])) <= 1e-12 * ref[0] * np.sqrt(M.shape[1])
