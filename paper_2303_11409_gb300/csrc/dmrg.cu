@@ -465,18 +465,6 @@ struct SPBuild {
     flops += 8.0 * t.M * t.N * K;
     bytes += 16.0 * ((double)t.M * K + (double)K * t.N);
   }
-  // longest-processing-time order: the tiles with the most work start first, so that the
-  // tail of a launch with more tiles than resident CTAs is made of the short ones
-  void order_tiles() {
-    std::vector<double> w(tasks.size(), 0.0);
-    for (size_t t = 0; t < tasks.size(); ++t)
-      for (int q = tasks[t].t0; q < tasks[t].t1; ++q) w[t] += (terms[q].flags & kNoB) ? 1.0 : (double)terms[q].K;
-    auto cost = [&](const SPTile& x) {
-      const SPTask& t = tasks[x.task];
-      return w[x.task] * std::min(kT, t.M - x.ti * kT) * std::min(kT, t.N - x.tj * kT);
-    };
-    std::stable_sort(tiles.begin(), tiles.end(), [&](const SPTile& a, const SPTile& b) { return cost(a) > cost(b); });
-  }
   void copy(int64_t a, int sar, int sac, cplx coef, int flags) {
     if (coef == 0.0) return;
     SPTask& t = tasks.back();
@@ -896,7 +884,6 @@ struct Dmrg {
         }
       }
     }
-    mv.order_tiles();
     if (reserve_desc(desc_bytes(mv) + desc_bytes(th)) != cudaSuccess) return fail(MPS_ENOMEM, "DMRG descriptors");
     int64_t cur = 0;
     Up umv, uth;
