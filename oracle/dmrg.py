@@ -30,6 +30,11 @@ Readings (the paper gives no DMRG schedule; the CUDA path follows the same):
     S_kept / |S_kept| (the TEBD truncation and noise floor, u1mps.select_kept);
   * the local ground state: the lowest eigenvector of H_eff (dense eigh for
     dim <= DENSE_MAX, else ARPACK's Lanczos with tol 1e-13 from the current Psi);
+  * two-site TDVP (tdvp_step): the same steps with the ground-state solve replaced by
+    exp(-i dt/2 H_eff) of the pair, and after every split but the turn the new centre site
+    evolved backward by exp(+i dt/2 H_eff^(1)) (its one-site effective Hamiltonian); a step
+    of length dt is a right-moving then a left-moving pass of dt/2 each; exponentials by dense
+    expm, or scipy's expm_multiply for large dimensions;
   * after the last sweep the state is brought back to the TEBD storage form
     (right-canonical B with every lambda the Schmidt values) by one inverse-free
     left-to-right pass: B'(l, m) = W(l) B(l, m), M(m) = diag(lambda_l) B'(., m)
@@ -320,12 +325,14 @@ class DMRG:
         return float(w[0]), v[:, 0]
 
     # -- one local step --------------------------------------------------------
-    def step(self, s: int, chi: int, cutoff: float, right_moving: bool) -> dict:
+    def step(self, s: int, chi: int, cutoff: float, right_moving: bool, local=None) -> dict:
+        """One two-site step; `local(s, lay, dim, X0)` -> (value, new vector) replaces the
+        ground-state solve (TDVP passes its forward exponential)."""
         st = self.st
         left, right = st.bond[s], st.bond[s + 2]
         lay, dim = self._layout(s)
         X0 = self._theta(s, lay)
-        E, v = self.local_ground_state(s, lay, dim, X0)
+        E, v = (local or self.local_ground_state)(s, lay, dim, X0)
         Psi = self._unflat(lay, v)
         svals, us, vhs = {}, {}, {}
         for e in lay:
@@ -355,8 +362,86 @@ class DMRG:
             self._left_env(s)
         else:
             self._right_env(s + 1)
-        self.energies.append(E)
+        if E is not None:
+            self.energies.append(E)
         return dict(energy=E, dim=dim, kept=dict(new_mid), trunc_err=info["trunc_err"], sigmas=svals)
+
+    # -- TDVP -------------------------------------------------------------------
+    def _apply1(self, j: int, C: dict) -> dict:
+        """One-site H_eff on the blocks C[(l, m)] of site j (left environment at bond j,
+        right environment at bond j+1)."""
+        st, d = self.st, self.d
+        EH, ET, RH, RT = self.EH[j], self.ET[j], self.RH[j + 1], self.RT[j + 1]
+        lcross = self.terms[j - 1] if j >= 1 else []
+        rcross = self.terms[j] if j <= st.L - 2 else []
+        out = {}
+        for (l, m), x in C.items():
+            i = l - m
+            y = EH[l] @ x + x @ RH[m]
+            for t, (delta, _O, P) in enumerate(lcross):
+                i2 = i + delta
+                if 0 <= i2 < d and (l + delta, m) in C and l in ET[t] and P[i, i2] != 0:
+                    y = y + P[i, i2] * (ET[t][l] @ C[(l + delta, m)])
+            for t, (delta, O, _P) in enumerate(rcross):
+                i3 = i - delta
+                if 0 <= i3 < d and (l, m + delta) in C and m in RT[t] and O[i, i3] != 0:
+                    y = y + O[i, i3] * (C[(l, m + delta)] @ RT[t][m])
+            out[(l, m)] = y
+        return out
+
+    @staticmethod
+    def _expm_apply(apply, v0: np.ndarray, t: complex) -> np.ndarray:
+        """exp(t H) v0 for the Hermitian H that `apply` multiplies by (dense expm for small
+        dimensions, else scipy's expm_multiply)."""
+        dim = v0.size
+        if dim <= DENSE_MAX:
+            H = np.zeros((dim, dim), dtype=np.complex128)
+            for k in range(dim):
+                e = np.zeros(dim, dtype=np.complex128)
+                e[k] = 1.0
+                H[:, k] = apply(e)
+            H = 0.5 * (H + H.conj().T)
+            return scipy.linalg.expm(t * H) @ v0
+        op = spla.LinearOperator((dim, dim), dtype=np.complex128, matvec=lambda v: t * apply(v))
+        return spla.expm_multiply(op, v0, traceA=0.0)
+
+    def _backward(self, j: int, tau: float) -> None:
+        """Site j (the centre) <- exp(+i tau H_eff^(1)) site j."""
+        keys = sorted(self.st.B[j])
+        shapes = [self.st.B[j][k].shape for k in keys]
+        sizes = [a * b for a, b in shapes]
+        offs = np.cumsum([0] + sizes)
+
+        def unflat(v):
+            return {k: v[offs[n]:offs[n + 1]].reshape(shapes[n]) for n, k in enumerate(keys)}
+
+        def flat(C):
+            return np.concatenate([C[k].reshape(-1) for k in keys])
+
+        v = self._expm_apply(lambda x: flat(self._apply1(j, unflat(x))), flat(self.st.B[j]), 1j * tau)
+        self.st.B[j] = {k: b.copy() for k, b in unflat(v).items()}
+
+    def tdvp_step(self, dt: float, chi: int, cutoff: float) -> list:
+        """One second-order two-site TDVP step of length dt: a right-moving and a left-moving
+        pass of dt/2 each; every pair is evolved forward by exp(-i dt/2 H_eff^(2)), split, and
+        the new centre site evolved backward by exp(+i dt/2 H_eff^(1)) except at the turn."""
+        L = self.st.L
+        half = 0.5 * dt
+
+        def forward(s, lay, dim, X0):
+            v0 = self._flat(lay, X0)
+            return None, self._expm_apply(lambda x: self._flat(lay, self._apply(s, lay, self._unflat(lay, x))),
+                                          v0, -1j * half)
+        out = []
+        for s in range(0, L - 1):
+            out.append(self.step(s, chi, cutoff, True, local=forward))
+            if s < L - 2:
+                self._backward(s + 1, half)
+        for s in range(L - 2, -1, -1):
+            out.append(self.step(s, chi, cutoff, False, local=forward))
+            if s > 0:
+                self._backward(s, half)
+        return out
 
     def sweep(self, chi: int, cutoff: float) -> list:
         L = self.st.L
@@ -404,6 +489,16 @@ class DMRG:
             st.B[s], st.bond[s + 1], st.lam[s + 1] = newB, bond, lam
             W = newW
         st.lam[st.L] = {0: np.ones(1)}
+
+
+def run_tdvp(state: U1MPS, h_bonds, n_steps: int, dt: float, chi: int, cutoff: float):
+    """n_steps second-order two-site TDVP steps of length dt, then the canonical form."""
+    dm = DMRG(state, h_bonds)
+    infos = []
+    for _ in range(n_steps):
+        infos += dm.tdvp_step(dt, chi, cutoff)
+    dm.canonicalize()
+    return infos
 
 
 def run_dmrg(state: U1MPS, h_bonds, n_sweeps: int, chi: int, cutoff: float):
