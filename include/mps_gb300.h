@@ -534,6 +534,21 @@ MPS_API int mps_charge_radix(mps_t h, int* ncomp, int32_t* radix);
 MPS_API int mps_dmrg(mps_t h, const double* const* bond_terms, int n_sweeps, int chi, double cutoff,
                      int lanczos_dim, double tol, double* energies, int energies_cap, int* n_energies);
 MPS_API int mps_dmrg_stats(mps_t h, int kind, int64_t* launches, double* ms, double* flops);
+/*
+ * mps_tdvp - second-order two-site TDVP (time-dependent variational principle) time steps on
+ * the state of h, the real-time counterpart of mps_dmrg on the same environments and H_eff:
+ * a step of length dt is a right-moving and a left-moving pass of dt/2; each pair is evolved
+ * by exp(-i dt/2 H_eff) (a Krylov exponential on the device: Lanczos basis of krylov_dim
+ * vectors, 2..40, the tridiagonal's eigenpairs by Jacobi rotations; the step is split into
+ * substeps until the error estimate |beta y_last| <= tol), split per middle charge with the
+ * truncation of mps_apply_gate2, and the new centre site evolved backward by exp(+i dt/2
+ * H_eff^(1)) with its one-site effective Hamiltonian, except at the turn.  Arguments, the
+ * storage form on entry and exit, and the errors are those of mps_dmrg; energies receives
+ * <psi|H_eff|psi> of the pair before each of the 2 (L-1) n_steps forward evolutions; mps_dmrg_stats
+ * reports the call's work (kind 0 counts both the two-site and the one-site H_eff products).
+ */
+MPS_API int mps_tdvp(mps_t h, const double* const* bond_terms, int n_steps, double dt, int chi, double cutoff,
+                     int krylov_dim, double tol, double* energies, int energies_cap, int* n_energies);
 MPS_API int mps_dmrg_counts(mps_t h, int64_t* matvecs, int64_t* restarts);
 
 /*

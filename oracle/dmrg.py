@@ -402,7 +402,8 @@ class DMRG:
                 H[:, k] = apply(e)
             H = 0.5 * (H + H.conj().T)
             return scipy.linalg.expm(t * H) @ v0
-        op = spla.LinearOperator((dim, dim), dtype=np.complex128, matvec=lambda v: t * apply(v))
+        op = spla.LinearOperator((dim, dim), dtype=np.complex128, matvec=lambda v: t * apply(v),
+                                 rmatvec=lambda v: np.conj(t) * apply(v))
         return spla.expm_multiply(op, v0, traceA=0.0)
 
     def _backward(self, j: int, tau: float) -> None:

@@ -125,6 +125,8 @@ _SIGS = {
                                         ctypes.c_int, ctypes.c_int, _vp]),
     "mps_charge_radix": (ctypes.c_int, [_h, _intp, _i32p]),
     "mps_svd_cluster_min_k": (ctypes.c_int, [ctypes.c_int]),
+    "mps_tdvp": (ctypes.c_int, [_h, ctypes.POINTER(_dblp), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                ctypes.c_double, ctypes.c_int, ctypes.c_double, _dblp, ctypes.c_int, _intp]),
 }
 DMRG_KINDS = ("heff", "env", "lanczos", "svd", "other")
 for _name, (_res, _args) in _SIGS.items():
@@ -484,6 +486,24 @@ class MPS:
         rc = lib.mps_dmrg(self._h, arr, n_sweeps, chi, cutoff, lanczos_dim, tol, _ptr(en, _dblp), cap,
                           ctypes.byref(n))
         self._check(rc, "mps_dmrg")
+        return en[:n.value].copy()
+
+    def tdvp(self, bond_terms, n_steps: int, dt: float, chi: int, cutoff: float, krylov_dim: int = 24,
+             tol: float = 1e-12) -> np.ndarray:
+        """Second-order two-site TDVP steps of length dt (mps_tdvp); returns <H_eff> before each
+        forward evolution of a pair."""
+        hs = [_c128_flat(h) for h in bond_terms]
+        if len(hs) != self.L - 1:
+            raise ValueError("one bond term per bond (L - 1)")
+        if any(h.size != gate_length(self.d) for h in hs):
+            raise ValueError("a bond term has the wrong number of entries")
+        arr = (_dblp * len(hs))(*[h.ctypes.data_as(_dblp) for h in hs])
+        cap = n_steps * 2 * (self.L - 1)
+        en = np.zeros(max(cap, 1))
+        n = ctypes.c_int(0)
+        rc = lib.mps_tdvp(self._h, arr, n_steps, dt, chi, cutoff, krylov_dim, tol, _ptr(en, _dblp), cap,
+                          ctypes.byref(n))
+        self._check(rc, "mps_tdvp")
         return en[:n.value].copy()
 
     def dmrg_stats(self) -> dict:

@@ -368,6 +368,114 @@ __global__ void tridiag_kernel(const double* __restrict__ alpha, const double* _
   res[2] = (double)m;
 }
 
+// exp(-i tau T) e_1 for the Lanczos tridiagonal T (alpha on the diagonal, beta next to it),
+// one warp: T's eigenpairs by cyclic Jacobi rotations (the symmetric Schur decomposition, each
+// rotation zeroing one off-diagonal pair, sweeps until the off-diagonal part is below 1e-15 of
+// the matrix), then y_j = sum_k Z[j][k] exp(-i tau lambda_k) Z[0][k].  The basis ends at the
+// first beta below 1e-13 of the matrix scale, as for the ground state.  res[0] = alpha_0
+// (<v0|H|v0>), res[1] = |beta_{m-1} y_{m-1}| (the estimate of the Krylov error), res[2] = m.
+constexpr int kExpMax = 40;
+__global__ void expm_tridiag_kernel(const double* __restrict__ alpha, const double* __restrict__ beta, int n,
+                                    double tau, double2* __restrict__ y, double* __restrict__ res) {
+  __shared__ double A[kExpMax][kExpMax + 1];
+  __shared__ double Z[kExpMax][kExpMax + 1];
+  const int lane = threadIdx.x;
+  if (blockIdx.x != 0 || lane >= 32) return;
+  double scale = 0.0;
+  for (int k = 0; k < n; ++k) scale = fmax(scale, fabs(alpha[k]) + (k + 1 < n ? fabs(beta[k]) : 0.0));
+  scale = fmax(scale, 1e-300);
+  int m = n;
+  for (int k = 0; k + 1 < n; ++k)
+    if (beta[k] <= 1e-13 * scale) { m = k + 1; break; }
+  for (int k = lane; k < m; k += 32)
+    for (int j = 0; j < m; ++j) {
+      A[k][j] = (j == k) ? alpha[k] : (j == k + 1 ? beta[k] : (j + 1 == k ? beta[j] : 0.0));
+      Z[k][j] = (j == k) ? 1.0 : 0.0;
+    }
+  __syncwarp();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, fro = 0.0;
+    for (int k = 0; k < m; ++k)
+      for (int j = 0; j < m; ++j) {
+        const double v = A[k][j] * A[k][j];
+        fro += v;
+        if (j != k) off += v;
+      }
+    if (off <= 1e-30 * fro) break;
+    for (int p = 0; p + 1 < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[p][q];
+        if (fabs(apq) < 1e-300) continue;
+        const double t0 = (A[q][q] - A[p][p]) / (2.0 * apq);
+        const double t = t0 >= 0.0 ? 1.0 / (t0 + sqrt(1.0 + t0 * t0)) : -1.0 / (-t0 + sqrt(1.0 + t0 * t0));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+        __syncwarp();
+        for (int k = lane; k < m; k += 32) {      // A <- A J
+          const double ap = A[k][p], aq = A[k][q];
+          A[k][p] = c * ap - sn * aq;
+          A[k][q] = sn * ap + c * aq;
+        }
+        __syncwarp();
+        for (int k = lane; k < m; k += 32) {      // A <- J^T A, Z <- Z J
+          const double ap = A[p][k], aq = A[q][k];
+          A[p][k] = c * ap - sn * aq;
+          A[q][k] = sn * ap + c * aq;
+          const double zp = Z[k][p], zq = Z[k][q];
+          Z[k][p] = c * zp - sn * zq;
+          Z[k][q] = sn * zp + c * zq;
+        }
+        __syncwarp();
+      }
+  }
+  for (int j = lane; j < n; j += 32) {
+    double2 acc = make_double2(0.0, 0.0);
+    if (j < m)
+      for (int k = 0; k < m; ++k) {
+        double sv, cv;
+        sincos(-tau * A[k][k], &sv, &cv);
+        const double w = Z[j][k] * Z[0][k];
+        acc.x = fma(w, cv, acc.x);
+        acc.y = fma(w, sv, acc.y);
+      }
+    y[j] = acc;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    res[0] = alpha[0];
+    const double2 yl = y[m - 1];
+    res[1] = m < n ? 0.0 : fabs(beta[m - 1]) * sqrt(yl.x * yl.x + yl.y * yl.y);
+    res[2] = (double)m;
+  }
+}
+
+// out[e] = f[0] * sum_k y[k] V_k[e] (y complex)
+__global__ void __launch_bounds__(kVecThreads) combine_c_kernel(double2* __restrict__ out, const double2* __restrict__ V,
+                                                                int64_t ldv, int nk, const double2* __restrict__ y,
+                                                                const double* __restrict__ f, int64_t n) {
+  __shared__ double2 ys[kExpMax];
+  for (int k = threadIdx.x; k < nk; k += kVecThreads) ys[k] = y[k];
+  __syncthreads();
+  const double a = f[0];
+  for (int64_t e = (int64_t)blockIdx.x * kVecThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kVecThreads) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < nk; ++k) {
+      const double2 v = V[(int64_t)k * ldv + e], c = ys[k];
+      acc.x = fma(c.x, v.x, fma(-c.y, v.y, acc.x));
+      acc.y = fma(c.x, v.y, fma(c.y, v.x, acc.y));
+    }
+    out[e] = make_double2(a * acc.x, a * acc.y);
+  }
+}
+
+// out[0] = |x| from out-of-place dot <x, x>
+__global__ void fill_kernel(double* __restrict__ p, double v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) p[0] = v;
+}
+
+__global__ void norm_kernel(const double2* __restrict__ nrm2, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = sqrt(fmax(nrm2[0].x, 0.0));
+}
+
 int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(kDotBlocks * 2, (n + kVecThreads - 1) / kVecThreads)); }
 
 // ---------------------------------------------------------------------------
@@ -778,8 +886,211 @@ struct Dmrg {
     return MPS_OK;
   }
 
+  // ---- Krylov work (Lanczos ground state, or the exponential of TDVP) on one vector ----------
+  struct KBuf {
+    int64_t dim = 0, ldv = 0;
+    int K = 0, nb = 1, vb = 1;
+    double2 *V = nullptr, *w = nullptr, *tv = nullptr, *part = nullptr, *hdots = nullptr, *gdots = nullptr,
+            *nrm = nullptr, *yc = nullptr;
+    double *alpha = nullptr, *beta = nullptr, *inv = nullptr, *yv = nullptr, *res = nullptr, *scl = nullptr,
+           *one = nullptr;
+  };
+  // Lays out the basis (K + 1 vectors), the product w, a scratch vector tv (the caller's start
+  // vector), the dot partials and the scalars in lz, zeroed.
+  int kbuf(int64_t dim, int kmax, KBuf& b) {
+    b.dim = dim;
+    b.K = (int)std::min<int64_t>(kmax, dim);
+    b.ldv = (dim + 31) / 32 * 32;
+    b.nb = std::max(1, std::min(kDotBlocks, (int)((dim + kVecThreads - 1) / kVecThreads)));
+    b.vb = vec_blocks(dim);
+    const int64_t o_w = (int64_t)(b.K + 1) * b.ldv, o_t = o_w + b.ldv, o_part = o_t + b.ldv;
+    const int64_t o_sc = o_part + (int64_t)(b.K + 1) * b.nb;
+    const int64_t nsc = 4 * 72 + 64 + 64;
+    if (lz.reserve((size_t)(o_sc + nsc) * 16) != cudaSuccess) return fail(MPS_ENOMEM, "DMRG Krylov vectors");
+    b.V = reinterpret_cast<double2*>(lz.p);
+    b.w = b.V + o_w;
+    b.tv = b.V + o_t;
+    b.part = b.V + o_part;
+    b.hdots = b.V + o_sc;            // 72
+    b.gdots = b.hdots + 72;          // 72
+    b.nrm = b.gdots + 72;            // 4
+    b.yc = b.nrm + 4;                // 64 complex
+    b.alpha = reinterpret_cast<double*>(b.yc + 64);   // 64
+    b.beta = b.alpha + 64;           // 64
+    b.inv = b.beta + 64;             // 8
+    b.yv = b.inv + 8;                // 64
+    b.res = b.yv + 64;               // 4
+    b.scl = b.res + 4;               // 2
+    b.one = b.scl + 2;               // 2
+    if (cudaMemsetAsync(b.V, 0, (size_t)(o_sc + nsc) * 16, st) != cudaSuccess) return fail(MPS_ECUDA, "DMRG memset");
+    return MPS_OK;
+  }
+
+  // mode 0: the lowest eigenpair of H by Lanczos with full reorthogonalisation, restarted from
+  //         the Ritz vector until |H v - E v| <= tol max(1, |E|): V[0] = the normalised vector,
+  //         *value = E.
+  // mode 1: exp(-i tau H) of the start vector: Krylov substeps of tau / n (n doubling until every
+  //         error estimate is <= tol), V[0] = the result with the start vector's norm,
+  //         *value = <v|H|v> of the normalised start vector.
+  // The start vector is in b.tv; mv(x, y) enqueues y = H x (mv_flops of work).
+  template <class MV>
+  int krylov(KBuf& b, MV&& mv, double mv_flops, int mode, double tau, double* value, bool* converged) {
+    const int K = b.K;
+    const int64_t dim = b.dim, ldv = b.ldv;
+    double2* V = b.V;
+    auto dots = [&](const double2* Vb, int nk, const double2* x, double2* out) -> cudaError_t {
+      count_launch();
+      dots_kernel<<<dim3(b.nb, nk), kVecThreads, 0, st>>>(Vb, ldv, x, dim, b.part);
+      cudaError_t e2 = cudaGetLastError();
+      if (e2 != cudaSuccess) return e2;
+      count_launch();
+      dots_reduce_kernel<<<nk, kVecThreads, 0, st>>>(b.part, b.nb, out);
+      return cudaGetLastError();
+    };
+    auto normalise_into = [&](double2* dst, const double2* src) -> cudaError_t {
+      cudaError_t e2 = dots(src, 1, src, b.nrm);
+      if (e2 != cudaSuccess) return e2;
+      count_launch();
+      inv_norm_kernel<<<1, 32, 0, st>>>(b.nrm, b.inv);
+      e2 = cudaGetLastError();
+      if (e2 != cudaSuccess) return e2;
+      count_launch();
+      scale_kernel<<<b.vb, kVecThreads, 0, st>>>(dst, src, b.inv, dim);
+      return cudaGetLastError();
+    };
+    auto lanczos = [&]() -> cudaError_t {       // K iterations from V[0]
+      cudaError_t e = cudaSuccess;
+      for (int j = 0; j < K && e == cudaSuccess; ++j) {
+        double2* vj = V + (int64_t)j * ldv;
+        e = timed(0, mv_flops, [&] { return mv(vj, b.w); });
+        matvecs++;
+        if (e != cudaSuccess) break;
+        e = timed(2, 16.0 * dim * (j + 1) * 4, [&] {
+          cudaError_t e2 = dots(V, j + 1, b.w, b.hdots);
+          if (e2 == cudaSuccess) {
+            count_launch();
+            subtract_kernel<<<b.vb, kVecThreads, 0, st>>>(b.w, V, ldv, j + 1, b.hdots, dim);
+            e2 = cudaGetLastError();
+          }
+          if (e2 == cudaSuccess) e2 = dots(V, j + 1, b.w, b.gdots);
+          if (e2 == cudaSuccess) {
+            count_launch();
+            subtract_kernel<<<b.vb, kVecThreads, 0, st>>>(b.w, V, ldv, j + 1, b.gdots, dim);
+            e2 = cudaGetLastError();
+          }
+          if (e2 == cudaSuccess) e2 = dots(b.w, 1, b.w, b.nrm);
+          if (e2 == cudaSuccess) {
+            count_launch();
+            lanczos_scalars_kernel<<<1, 32, 0, st>>>(j, b.hdots, b.gdots, b.nrm, b.alpha, b.beta, b.inv);
+            e2 = cudaGetLastError();
+          }
+          if (e2 == cudaSuccess) {
+            count_launch();
+            scale_kernel<<<b.vb, kVecThreads, 0, st>>>(V + (int64_t)(j + 1) * ldv, b.w, b.inv, dim);
+            e2 = cudaGetLastError();
+          }
+          return e2;
+        });
+      }
+      return e;
+    };
+    auto readback = [&](double* r) -> cudaError_t {
+      cudaError_t e = cudaMemcpyAsync(rb.p, b.res, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      resolve();
+      restarts++;
+      if (e == cudaSuccess) std::memcpy(r, rb.p, 4 * sizeof(double));
+      return e;
+    };
+    cudaError_t e = cudaSuccess;
+    *converged = false;
+    if (mode == 0) {
+      e = timed(2, 0.0, [&] { return normalise_into(V, b.tv); });
+      double E0 = 0.0, resid = 1e300;
+      for (int it = 0; e == cudaSuccess && it < max_restarts; ++it) {
+        e = lanczos();
+        if (e != cudaSuccess) break;
+        e = timed(2, 8.0 * dim * K, [&] {
+          count_launch();
+          tridiag_kernel<<<1, 32, 0, st>>>(b.alpha, b.beta, K, b.yv, b.res);
+          cudaError_t e2 = cudaGetLastError();
+          if (e2 == cudaSuccess) {
+            count_launch();
+            combine_kernel<<<b.vb, kVecThreads, 0, st>>>(b.tv, V, ldv, K, b.yv, dim);
+            e2 = cudaGetLastError();
+          }
+          if (e2 == cudaSuccess) e2 = normalise_into(V, b.tv);
+          return e2;
+        });
+        double r[4];
+        if (e == cudaSuccess) e = readback(r);
+        if (e != cudaSuccess) break;
+        E0 = r[0];
+        resid = r[1];
+        if (!(resid == resid)) return fail(MPS_ECUDA, "DMRG: Lanczos produced NaN");
+        if (resid <= tol * std::max(1.0, std::fabs(E0))) break;
+      }
+      if (e != cudaSuccess) return fail(MPS_ECUDA, std::string("DMRG Lanczos: ") + cudaGetErrorString(e));
+      *value = E0;
+      *converged = resid <= tol * std::max(1.0, std::fabs(E0));
+      return MPS_OK;
+    }
+    // mode 1: the exponential; the start vector stays in tv until every substep passed
+    e = timed(2, 0.0, [&] {
+      cudaError_t e2 = dots(b.tv, 1, b.tv, b.nrm);
+      if (e2 == cudaSuccess) {
+        count_launch();
+        norm_kernel<<<1, 32, 0, st>>>(b.nrm, b.scl);
+        e2 = cudaGetLastError();
+      }
+      if (e2 == cudaSuccess) {
+        count_launch();
+        fill_kernel<<<1, 32, 0, st>>>(b.one, 1.0);
+        e2 = cudaGetLastError();
+      }
+      return e2;
+    });
+    bool first_value = true;
+    for (int nsub = 1; e == cudaSuccess && nsub <= 64; nsub *= 2) {
+      bool ok = true;
+      e = timed(2, 0.0, [&] { return normalise_into(V, b.tv); });
+      for (int sub = 0; e == cudaSuccess && sub < nsub; ++sub) {
+        e = lanczos();
+        if (e != cudaSuccess) break;
+        e = timed(2, 8.0 * dim * K, [&] {
+          count_launch();
+          expm_tridiag_kernel<<<1, 32, 0, st>>>(b.alpha, b.beta, K, tau / nsub, b.yc, b.res);
+          cudaError_t e2 = cudaGetLastError();
+          if (e2 == cudaSuccess) {
+            count_launch();
+            combine_c_kernel<<<b.vb, kVecThreads, 0, st>>>(b.w, V, ldv, K, b.yc, b.one, dim);
+            e2 = cudaGetLastError();
+          }
+          if (e2 == cudaSuccess && sub + 1 < nsub) e2 = normalise_into(V, b.w);
+          if (e2 == cudaSuccess && sub + 1 == nsub) {
+            count_launch();
+            scale_kernel<<<b.vb, kVecThreads, 0, st>>>(V, b.w, b.scl, dim);
+            e2 = cudaGetLastError();
+          }
+          return e2;
+        });
+        double r[4];
+        if (e == cudaSuccess) e = readback(r);
+        if (e != cudaSuccess) break;
+        if (first_value) { *value = r[0]; first_value = false; }
+        if (!(r[1] == r[1])) return fail(MPS_ECUDA, "TDVP: Krylov exponential produced NaN");
+        if (r[1] > tol) { ok = false; break; }
+      }
+      if (e != cudaSuccess) break;
+      if (ok) { *converged = true; break; }
+    }
+    if (e != cudaSuccess) return fail(MPS_ECUDA, std::string("TDVP Krylov: ") + cudaGetErrorString(e));
+    return MPS_OK;
+  }
+
   // ---- one local step ------------------------------------------------------------------
-  int step(int s, int chi, double cutoff, bool right_moving, double* energy) {
+  // mode 0: DMRG (the local ground state); mode 1: TDVP (the pair evolved by exp(-i tau H_eff))
+  int step(int s, int chi, double cutoff, bool right_moving, double* energy, int mode = 0, double tau = 0.0) {
     const BondTable &Lb = h->bonds[s], &Mb = h->bonds[s + 1], &Rb = h->bonds[s + 2];
     const SiteTable &SL = h->sites[s], &SR = h->sites[s + 1];
     const double2* slotL = h->slot_ptr(s, h->cur[s]);
@@ -796,26 +1107,9 @@ struct Dmrg {
         if (P.sectors[k].c == c) return k;
       return -1;
     };
-    const int K = (int)std::min<int64_t>(kdim, dim);
-    // Lanczos buffer: K + 1 basis vectors, w, scratch vector, dot partials and scalars
-    const int64_t ldv = (dim + 31) / 32 * 32;
-    const int nb = std::max(1, std::min(kDotBlocks, (int)((dim + kVecThreads - 1) / kVecThreads)));
-    const int64_t o_w = (int64_t)(K + 1) * ldv, o_t = o_w + ldv, o_part = o_t + ldv;
-    const int64_t o_sc = o_part + (int64_t)(K + 1) * nb;     // complex scalars from here
-    const int64_t nsc = 4 * 72 + 64;
-    if (lz.reserve((size_t)(o_sc + nsc) * 16) != cudaSuccess) return fail(MPS_ENOMEM, "DMRG Lanczos vectors");
-    double2* V = reinterpret_cast<double2*>(lz.p);
-    double2* w = V + o_w;
-    double2* tv = V + o_t;
-    double2* part = V + o_part;
-    double2* hdots = V + o_sc;           // 72
-    double2* gdots = hdots + 72;         // 72
-    double2* nrm = gdots + 72;           // 1
-    double* alpha = reinterpret_cast<double*>(nrm + 4);    // 64
-    double* beta = alpha + 64;           // 64
-    double* inv = beta + 64;             // 1
-    double* yv = inv + 8;                // 64
-    double* res = yv + 64;               // 4
+    KBuf kb;
+    if (int rc0 = kbuf(dim, mode ? std::min(kdim, kExpMax) : kdim, kb)) return rc0;
+    double2* tv = kb.tv;
 
     // ---- H_eff descriptors (X = the vector being multiplied, Y = the product) and Theta ----
     SPBuild mv, th;
@@ -889,93 +1183,16 @@ struct Dmrg {
     Up umv, uth;
     cudaError_t e = upload(mv, cur, umv);
     if (e == cudaSuccess) e = upload(th, cur, uth);
-    if (e == cudaSuccess) e = cudaMemsetAsync(V, 0, (size_t)(o_sc + nsc) * 16, st);
-    // v0 = Theta / |Theta|
+    // the start vector Theta, then the local ground state or the forward exponential
     if (e == cudaSuccess) e = timed(4, th.flops, [&] { return launch(uth, nullptr, tv); });
-    auto dots = [&](const double2* Vb, int nk, const double2* x, double2* out) -> cudaError_t {
-      count_launch();
-      dots_kernel<<<dim3(nb, nk), kVecThreads, 0, st>>>(Vb, ldv, x, dim, part);
-      cudaError_t e2 = cudaGetLastError();
-      if (e2 != cudaSuccess) return e2;
-      count_launch();
-      dots_reduce_kernel<<<nk, kVecThreads, 0, st>>>(part, nb, out);
-      return cudaGetLastError();
-    };
-    const int vb = vec_blocks(dim);
-    auto normalise_into = [&](double2* dst, const double2* src) -> cudaError_t {
-      cudaError_t e2 = dots(src, 1, src, nrm);
-      if (e2 != cudaSuccess) return e2;
-      count_launch();
-      inv_norm_kernel<<<1, 32, 0, st>>>(nrm, inv);
-      e2 = cudaGetLastError();
-      if (e2 != cudaSuccess) return e2;
-      count_launch();
-      scale_kernel<<<vb, kVecThreads, 0, st>>>(dst, src, inv, dim);
-      return cudaGetLastError();
-    };
-    if (e == cudaSuccess) e = timed(2, 0.0, [&] { return normalise_into(V, tv); });
-    double E0 = 0.0, resid = 1e300;
-    int it_restart = 0;
-    for (; e == cudaSuccess && it_restart < max_restarts; ++it_restart) {
-      for (int j = 0; j < K && e == cudaSuccess; ++j) {
-        double2* vj = V + (int64_t)j * ldv;
-        e = timed(0, mv.flops, [&] { return launch(umv, vj, w); });
-        matvecs++;
-        if (e != cudaSuccess) break;
-        e = timed(2, 16.0 * dim * (j + 1) * 4, [&] {
-          cudaError_t e2 = dots(V, j + 1, w, hdots);
-          if (e2 == cudaSuccess) {
-            count_launch();
-            subtract_kernel<<<vb, kVecThreads, 0, st>>>(w, V, ldv, j + 1, hdots, dim);
-            e2 = cudaGetLastError();
-          }
-          if (e2 == cudaSuccess) e2 = dots(V, j + 1, w, gdots);
-          if (e2 == cudaSuccess) {
-            count_launch();
-            subtract_kernel<<<vb, kVecThreads, 0, st>>>(w, V, ldv, j + 1, gdots, dim);
-            e2 = cudaGetLastError();
-          }
-          if (e2 == cudaSuccess) e2 = dots(w, 1, w, nrm);
-          if (e2 == cudaSuccess) {
-            count_launch();
-            lanczos_scalars_kernel<<<1, 32, 0, st>>>(j, hdots, gdots, nrm, alpha, beta, inv);
-            e2 = cudaGetLastError();
-          }
-          if (e2 == cudaSuccess) {
-            count_launch();
-            scale_kernel<<<vb, kVecThreads, 0, st>>>(V + (int64_t)(j + 1) * ldv, w, inv, dim);
-            e2 = cudaGetLastError();
-          }
-          return e2;
-        });
-      }
-      if (e != cudaSuccess) break;
-      e = timed(2, 8.0 * dim * K, [&] {
-        count_launch();
-        tridiag_kernel<<<1, 32, 0, st>>>(alpha, beta, K, yv, res);
-        cudaError_t e2 = cudaGetLastError();
-        if (e2 == cudaSuccess) {
-          count_launch();
-          combine_kernel<<<vb, kVecThreads, 0, st>>>(tv, V, ldv, K, yv, dim);
-          e2 = cudaGetLastError();
-        }
-        if (e2 == cudaSuccess) e2 = normalise_into(V, tv);
-        return e2;
-      });
-      if (e == cudaSuccess) e = cudaMemcpyAsync(rb.p, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      resolve();
-      restarts++;
-      if (e != cudaSuccess) break;
-      const double* r = (const double*)rb.p;
-      E0 = r[0];
-      resid = r[1];
-      if (!(resid == resid)) return fail(MPS_ECUDA, "DMRG: Lanczos produced NaN");
-      if (resid <= tol * std::max(1.0, std::fabs(E0))) break;
-    }
-    if (e != cudaSuccess) return fail(MPS_ECUDA, std::string("DMRG Lanczos: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(MPS_ECUDA, std::string("DMRG: ") + cudaGetErrorString(e));
+    bool converged = false;
+    double E0 = 0.0;
+    const int rck = krylov(kb, [&](const double2* x, double2* y) { return launch(umv, x, y); }, mv.flops, mode, tau,
+                           &E0, &converged);
+    if (rck != MPS_OK) return rck;
     *energy = E0;
-    const bool converged = resid <= tol * std::max(1.0, std::fabs(E0));
+    double2* V = kb.V;
     const double2* psi = V;        // the normalised ground state, Theta layout
 
     // ---- per-sector SVD (of Psi(c)^dag when moving right: its right vectors are U) ----
@@ -1151,8 +1368,72 @@ struct Dmrg {
     h->cur[s + 1] ^= 1;
     int rc2 = right_moving ? build_left(s) : build_right(s + 1);
     if (rc2 != MPS_OK) return rc2;
-    if (!converged) { h->err = "Lanczos did not reach its tolerance; state updated with the last Ritz vector"; return MPS_ENOCONV; }
+    if (!converged) {
+      h->err = mode ? "TDVP Krylov exponential did not reach its tolerance"
+                    : "Lanczos did not reach its tolerance; state updated with the last Ritz vector";
+      return MPS_ENOCONV;
+    }
     if (noconv) { h->err = "Jacobi SVD hit its sweep limit; state updated with the last iterate"; return MPS_ENOCONV; }
+    return MPS_OK;
+  }
+
+  // ---- TDVP: the centre site j evolved backward, site j <- exp(+i tau H_eff^(1)) site j -------
+  // One-site H_eff on the blocks C(l, m) of site j (left environment at bond j, right at j+1):
+  //   EH(l) C(l, m) + C(l, m) RH(m) + sum_t P_t[i, i+delta] ET_t(l) C(l+delta, m)
+  //   + sum_t O_t[i, i-delta] C(l, m+delta) RT_t(m),   i = l - m.
+  // The site's slot is the vector (its blocks in (l, m) order); the result goes back in place.
+  int backward(int j, double tau, double* energy) {
+    const SiteTable& S = h->sites[j];
+    double2* slot = h->slot_ptr(j, h->cur[j]);
+    const Env &EL = envL[j], &ER = envR[j + 1];
+    const std::vector<OpPair>* lcr = bond_ops(j - 1);
+    const std::vector<OpPair>* rcr = bond_ops(j);
+    SPBuild m1;
+    for (const SiteBlock& b : S.blocks) {
+      const int i = b.l - b.m;
+      m1.out(b.off, b.Dm, b.Dl, b.Dm, kCY);
+      m1.gemm(addr(EL.at(0, b.il)), b.Dl, 1, b.off, b.Dm, 1, b.Dl, 1.0, kBX);
+      m1.gemm(b.off, b.Dm, 1, addr(ER.at(0, b.im)), b.Dm, 1, b.Dm, 1.0, kAX);
+      if (lcr)
+        for (int t = 0; t < (int)lcr->size(); ++t) {
+          const int delta = (*lcr)[t].delta, i2 = i + delta;
+          if (i2 < 0 || i2 >= d) continue;
+          const int b2 = S.find(b.l + delta, b.m);
+          const double2* env = EL.at(t + 1, b.il);
+          const cplx p = (*lcr)[t].P[i * d + i2];
+          if (b2 < 0 || !env || p == 0.0) continue;
+          const SiteBlock& B2 = S.blocks[b2];
+          m1.gemm(addr(env), B2.Dl, 1, B2.off, B2.Dm, 1, B2.Dl, p, kBX);
+        }
+      if (rcr)
+        for (int t = 0; t < (int)rcr->size(); ++t) {
+          const int delta = (*rcr)[t].delta, i3 = i - delta;
+          if (i3 < 0 || i3 >= d) continue;
+          const int b3 = S.find(b.l, b.m + delta);
+          const double2* env = ER.at(t + 1, b.im);
+          const cplx o = (*rcr)[t].O[i * d + i3];
+          if (b3 < 0 || !env || o == 0.0) continue;
+          const SiteBlock& B3 = S.blocks[b3];
+          m1.gemm(B3.off, B3.Dm, 1, addr(env), b.Dm, 1, B3.Dm, o, kAX);
+        }
+    }
+    const int64_t dim = S.nnz;
+    KBuf kb;
+    if (int rc0 = kbuf(dim, std::min(kdim, kExpMax), kb)) return rc0;
+    if (reserve_desc(desc_bytes(m1)) != cudaSuccess) return fail(MPS_ENOMEM, "TDVP descriptors");
+    int64_t cur = 0;
+    Up u;
+    cudaError_t e = upload(m1, cur, u);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(kb.tv, slot, sizeof(double2) * dim, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return fail(MPS_ECUDA, "TDVP backward step");
+    bool converged = false;
+    const int rck = krylov(kb, [&](const double2* x, double2* y) { return launch(u, x, y); }, m1.flops, 1, -tau,
+                           energy, &converged);
+    if (rck != MPS_OK) return rck;
+    e = cudaMemcpyAsync(slot, kb.V, sizeof(double2) * dim, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(MPS_ECUDA, "TDVP backward step");
+    if (!converged) { h->err = "TDVP Krylov exponential did not reach its tolerance"; return MPS_ENOCONV; }
     return MPS_OK;
   }
 
@@ -1434,6 +1715,82 @@ int mps_dmrg(mps_t h, const double* const* bond_terms, int n_sweeps, int chi, do
   if (rc == MPS_ENOCONV) status = MPS_ENOCONV;
   for (auto& c : h->cut_est) c = 0.0;
   // per-kind device time and work of this call, read by mps_dmrg_stats
+  h->dmrg_last.matvecs = D.matvecs;
+  h->dmrg_last.restarts = D.restarts;
+  for (int k = 0; k < 5; ++k) {
+    h->dmrg_last.ms[k] = D.ms[k];
+    h->dmrg_last.flops[k] = D.flops[k];
+    h->dmrg_last.launches[k] = D.launches[k];
+  }
+  return status;
+}
+
+int mps_tdvp(mps_t h, const double* const* bond_terms, int n_steps, double dt, int chi, double cutoff,
+             int krylov_dim, double tol, double* energies, int energies_cap, int* n_energies) {
+  if (!h || !bond_terms || n_steps < 0 || chi < 1 || !(cutoff >= 0.0) || !n_energies || !(dt == dt)) return MPS_EINVAL;
+  *n_energies = 0;
+  if (h->precision != MPS_FP64) { h->err = "TDVP runs on FP64 handles"; return MPS_EINVAL; }
+  if (h->rule.zn || h->rule.multi) { h->err = "TDVP is built for single U(1) charges"; return MPS_EINVAL; }
+  if (krylov_dim < 2 || krylov_dim > kExpMax || !(tol > 0.0)) return MPS_EINVAL;
+  const int L = h->L;
+  for (int k = 0; k < L - 1; ++k)
+    if (!bond_terms[k]) return MPS_EINVAL;
+  for (int s = 0; s < L; ++s)
+    if (h->dirty[s]) { h->err = "site " + std::to_string(s) + " needs mps_set_site"; return MPS_EINVAL; }
+  const int64_t need = (int64_t)n_steps * 2 * (L - 1);
+  if (energies && energies_cap < need) return MPS_EINVAL;
+  Dmrg D;
+  D.h = h;
+  D.st = h->stream;
+  D.L = L;
+  D.d = h->d;
+  D.kdim = krylov_dim;
+  D.tol = tol;
+  D.profiling = h->profiling;
+  D.hb.assign(bond_terms, bond_terms + (L - 1));
+  for (int k = 0; k < L - 1; ++k) D.ops.push_back(split_bond(bond_terms[k], h->rule));
+  D.envL.resize(L + 1);
+  D.envR.resize(L + 1);
+  if (D.rb.reserve(4096) != cudaSuccess) return MPS_ENOMEM;
+  if (cudaStreamSynchronize(D.st) != cudaSuccess) return MPS_ECUDA;
+  if (D.layout_env(D.envL[0], h->bonds[0], nullptr) != cudaSuccess) return MPS_ENOMEM;
+  if (D.layout_env(D.envR[L], h->bonds[L], nullptr) != cudaSuccess) return MPS_ENOMEM;
+  for (int s = L - 1; s >= 2; --s) {
+    const int rc = D.build_right(s);
+    if (rc != MPS_OK) return rc;
+  }
+  const double half = 0.5 * dt;
+  int status = MPS_OK;
+  int64_t ne = 0;
+  auto note = [&](int rc) { if (rc == MPS_ENOCONV) status = MPS_ENOCONV; return rc == MPS_OK || rc == MPS_ENOCONV; };
+  for (int step = 0; step < n_steps; ++step) {
+    for (int s = 0; s < L - 1; ++s) {             // right-moving pass, dt/2
+      double E = 0.0, Eb = 0.0;
+      int rc = D.step(s, chi, cutoff, true, &E, 1, half);
+      if (!note(rc)) return rc;
+      if (energies) energies[ne] = E;
+      ++ne;
+      if (s < L - 2) {
+        rc = D.backward(s + 1, half, &Eb);
+        if (!note(rc)) return rc;
+      }
+    }
+    for (int s = L - 2; s >= 0; --s) {            // left-moving pass, dt/2
+      double E = 0.0, Eb = 0.0;
+      int rc = D.step(s, chi, cutoff, false, &E, 1, half);
+      if (!note(rc)) return rc;
+      if (energies) energies[ne] = E;
+      ++ne;
+      if (s > 0) {
+        rc = D.backward(s, half, &Eb);
+        if (!note(rc)) return rc;
+      }
+    }
+  }
+  *n_energies = (int)ne;
+  const int rc = D.canonicalize();
+  if (!note(rc)) return rc;
+  for (auto& c : h->cut_est) c = 0.0;
   h->dmrg_last.matvecs = D.matvecs;
   h->dmrg_last.restarts = D.restarts;
   for (int k = 0; k < 5; ++k) {
