@@ -59,6 +59,10 @@ CASES = {
     # is one sweep (126 two-site updates) through mps_dmrg, after warm-up sweeps from the Mott state
     "dmrg": dict(L=64, N=64, CHI=256, precision="fp64", start="dmrg",
                  workload="dmrg_bose_hubbard_L64_nmax4_N64_J1_U2_chi256_cutoff1e-10"),
+    # two-site TDVP quench: the chi<=256 DMRG ground state of U=2 evolved with U=4, dt=0.02; one
+    # step is one TDVP time step (two passes, 126 two-site updates and 124 one-site backward steps)
+    "tdvp": dict(L=64, N=64, CHI=256, precision="fp64", start="dmrg",
+                 workload="tdvp_bose_hubbard_L64_nmax4_N64_J1_U2to4_dt0.02_chi256_cutoff1e-10"),
     # the same at L=24, chi<=128, for profiler captures
     "dmrg_small": dict(L=24, N=24, CHI=128, precision="fp64", start="dmrg",
                        workload="dmrg_bose_hubbard_L24_nmax4_N24_J1_U2_chi128_cutoff1e-10"),
@@ -429,26 +433,41 @@ def build_workload(args, m, W, stream, prec):
     return psi, step, prep
 
 
-def oracle_dmrg_sample(cfg, seconds: float):
+def oracle_dmrg_sample(cfg, seconds: float, tdvp: bool = False):
     """The oracle's DMRG on the same chain and schedule from the Mott state, timed for about
     `seconds` of local steps.  Its bonds are still below chi during the sample, so the rate is
-    an upper bound on the oracle's rate at saturation."""
+    an upper bound on the oracle's rate at saturation.  For TDVP the sample is the oracle's TDVP
+    (forward steps and the backward site steps between them) on the same quench, from the Mott
+    state."""
     from oracle import U1MPS, dmrg as odmrg
     import workloads as W
     L, CHI = cfg["L"], cfg["CHI"]
-    dm = odmrg.DMRG(U1MPS.product(D, W.mott_occupations(L)), odmrg.bh_bonds(L, D, J, U))
+    dm = odmrg.DMRG(U1MPS.product(D, W.mott_occupations(L)), odmrg.bh_bonds(L, D, J, 2.0 * U if tdvp else U))
     order = [(s_, True) for s_ in range(L - 1)] + [(s_, False) for s_ in range(L - 2, -1, -1)]
     t0 = time.perf_counter()
     n = 0
+    half = 0.5 * DT
+
+    def forward(s_, lay, dim, X0):
+        v0 = dm._flat(lay, X0)
+        return None, dm._expm_apply(lambda x: dm._flat(lay, dm._apply(s_, lay, dm._unflat(lay, x))), v0, -1j * half)
     while time.perf_counter() - t0 < seconds:
         s_, right = order[n % len(order)]
-        dm.step(s_, CHI, CUTOFF, right)
+        if tdvp:
+            dm.step(s_, CHI, CUTOFF, right, local=forward)
+            if right and s_ < L - 2:
+                dm._backward(s_ + 1, half)
+            elif not right and s_ > 0:
+                dm._backward(s_, half)
+        else:
+            dm.step(s_, CHI, CUTOFF, right)
         n += 1
     el = time.perf_counter() - t0
     largest = max(sum(b.values()) for b in dm.st.bond)
     return {"value": n / el, "unit": "updates/s", "cores": blas_threads(), "kind": "oracle",
-            "sample": (f"the first {n} local steps ({el:.1f} s) of the oracle's DMRG on the same chain from the Mott "
-                       f"state (largest bond reached {largest} < chi: an upper bound on its rate at saturation)")}
+            "sample": (f"the first {n} local steps ({el:.1f} s) of the oracle's {'TDVP' if tdvp else 'DMRG'} on the same "
+                       f"chain from the Mott state (largest bond reached {largest} < chi: an upper bound on its rate "
+                       f"at saturation)")}
 
 
 def run_dmrg_case(args, world, rank, local):
@@ -467,6 +486,8 @@ def run_dmrg_case(args, world, rank, local):
     torch.cuda.set_stream(stream)
     fp64_measured = m.fp64_peak_probe(stream.cuda_stream)
     terms = m.models.chain_bond_terms("bh", L, D, J=J, U=U)
+    tdvp = args.case == "tdvp"
+    quench = m.models.chain_bond_terms("bh", L, D, J=J, U=2.0 * U) if tdvp else None
     psi = m.MPS(D, W.mott_occupations(L), CHI, stream=stream.cuda_stream)
     t0 = time.perf_counter()
     for _ in range(args.warmup):
@@ -483,7 +504,7 @@ def run_dmrg_case(args, world, rank, local):
     with ClockSampler(local) as clk:
         for k in range(args.steps):
             ev[k][0].record(stream)
-            e = psi.dmrg(terms, 1, CHI, CUTOFF)
+            e = psi.tdvp(quench, 1, DT, CHI, CUTOFF) if tdvp else psi.dmrg(terms, 1, CHI, CUTOFF)
             ev[k][1].record(stream)
             n_upd += 2 * (L - 1)
             energies.append(float(e[-1]))
@@ -515,25 +536,33 @@ def run_dmrg_case(args, world, rank, local):
     # e2e: the same call with host-resident bond terms and energies (mps_dmrg is host-in,
     # host-out), timed on the host clock
     t0 = time.perf_counter()
-    psi.dmrg(terms, 1, CHI, CUTOFF)
+    if tdvp:
+        psi.tdvp(quench, 1, DT, CHI, CUTOFF)
+    else:
+        psi.dmrg(terms, 1, CHI, CUTOFF)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     glen = m.gate_length(D)
     e2e = {"value": world * 2 * (L - 1) / e2e_s, "unit": "updates/s", "steps": 1,
            "h2d_bytes_per_step": int((L - 1) * glen * 16), "d2h_bytes_per_step": int(2 * (L - 1) * 8),
-           "what": "one sweep through MPS.dmrg (mps_dmrg) with host bond terms, energies read back"}
+           "what": ("one time step through MPS.tdvp (mps_tdvp)" if tdvp else "one sweep through MPS.dmrg (mps_dmrg)")
+                   + " with host bond terms, energies read back"}
     psi.close()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_dmrg_sample(cfg, args.cpu_seconds)
+        cpu = oracle_dmrg_sample(cfg, args.cpu_seconds, tdvp)
     if rank == 0:
-        line = {"metric": "two-site DMRG updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
+        line = {"metric": "two-site TDVP updates/s" if tdvp else "two-site DMRG updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
                 "config": {"workload": cfg["workload"], "model": "bose_hubbard", "L": L, "d": D, "N": cfg["N"],
                            "J": J, "U": U, "chi": CHI, "cutoff": CUTOFF,
-                           "step": f"one mps_dmrg call of one sweep ({2 * (L - 1)} two-site updates, then the canonical form)",
-                           "lanczos": "Krylov 24, residual tolerance 1e-12 |E|", "largest_bond_dim": largest,
+                           "step": (f"one mps_tdvp call of one time step dt={DT} of the U={2.0 * U} quench ({2 * (L - 1)} "
+                                    f"two-site and {2 * (L - 2)} one-site updates, then the canonical form)" if tdvp else
+                                    f"one mps_dmrg call of one sweep ({2 * (L - 1)} two-site updates, then the canonical form)"),
+                           "lanczos": ("Krylov 24, exponential error estimate 1e-12" if tdvp else
+                                       "Krylov 24, residual tolerance 1e-12 |E|"),
+                           "largest_bond_dim": largest,
                            "l2": "no flush (one sweep streams the environments and Krylov vectors of 63 bonds)"},
                 "energy_per_site": energies[-1] / L, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "step_ms": [round(x, 3) for x in step_ms]}
@@ -819,7 +848,7 @@ def main():
         run_serving(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
-    elif args.case in ("dmrg", "dmrg_small"):
+    elif args.case in ("dmrg", "dmrg_small", "tdvp"):
         run_dmrg_case(args, world, rank, local)
     else:
         precisions = args.precision.split(",")
