@@ -887,7 +887,12 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
       for (const SvdSector& S : svd_sorted[c_used]) {
         if (!redo_upd[upd_of[S.status - status0]]) continue;
         SvdSector T = S;
-        T.floor_abs = 0.0;
+        // when chi set the first pass's cut, that cut bounds the redo's from below (resolving
+        // more values can only raise the chi-th largest candidate), so values under kChiGuard
+        // times it stay unresolved within the same guard; otherwise everything is resolved
+        const int uu = upd_of[S.status - status0];
+        const SelectResult& R1 = res[uu];
+        T.floor_abs = (R1.n_candidates > reqs[uu].chi && R1.norm_all > 0.0) ? kChiGuard * R1.cut / R1.norm_all : 0.0;
         sub.push_back(T);
         const double a = std::max(S.m, S.n), b = std::min(S.m, S.n);
         sub_flops += 4.0 * (6.0 * a * b * b + 20.0 * b * b * b);
