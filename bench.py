@@ -117,6 +117,8 @@ def parse():
     p.add_argument("--serve", action="store_true",
                    help="serving workload instead: continuous batching vs the plain one-request-at-a-time form")
     p.add_argument("--serve-requests", type=int, default=48)
+    p.add_argument("--serve-lanes", type=int, default=2, choices=(1, 2),
+                   help="serving executors run concurrently from two host threads, each on its own stream")
     p.add_argument("--serve-seconds", type=float, default=25.0,
                    help="wall-time bound of the serving sub-measurement of the main line (0: none)")
     p.add_argument("--graphs", type=int, default=1, help="capture each update call's launch phases in CUDA graphs")
@@ -730,7 +732,7 @@ def serving_sample(args, m, W, stream, prec):
     reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=0.0)
             for r in raw]
     srv = m.serve.Server(budget_bytes=64 << 30, max_slots=64, stream=stream.cuda_stream, precision=prec,
-                         graphs=bool(args.graphs))
+                         graphs=bool(args.graphs), lanes=args.serve_lanes)
     t0 = time.perf_counter()
     res = srv.run(reqs)
     cap_s = time.perf_counter() - t0
@@ -742,7 +744,7 @@ def serving_sample(args, m, W, stream, prec):
     reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=r["arrival"])
             for r in raw]
     srv = m.serve.Server(budget_bytes=64 << 30, max_slots=64, stream=stream.cuda_stream, precision=prec,
-                         graphs=bool(args.graphs))
+                         graphs=bool(args.graphs), lanes=args.serve_lanes)
     t0 = time.perf_counter()
     res = srv.run(reqs)
     wall = time.perf_counter() - t0
@@ -750,7 +752,7 @@ def serving_sample(args, m, W, stream, prec):
     s = m.serve.summarize(res, wall)
     return {"p50_latency_s": s["p50_latency_s"], "p99_latency_s": s["p99_latency_s"], "requests": s["requests"],
             "updates_per_s_under_load": s["updates_per_s"], "capacity_updates_per_s": capacity,
-            "arrival_rate_hz": rate,
+            "arrival_rate_hz": rate, "lanes": args.serve_lanes,
             "mix": {k: list(v) for k, v in SERVE_MIX.items()}, "precision": args.precision,
             "what": "scaled serving mix (xxz / bose-hubbard quenches), Poisson arrivals at 0.8 x capacity"}
 
@@ -796,7 +798,7 @@ def run_serving(args, world, rank, local):
     plain_s = time.perf_counter() - t0
     plain_rate = plain_updates / plain_s
     srv = m.serve.Server(budget_bytes=budget, max_slots=64, stream=stream.cuda_stream, precision=prec,
-                         graphs=graphs)
+                         graphs=graphs, lanes=args.serve_lanes)
     t0 = time.perf_counter()
     res = srv.run(reqs)
     torch.cuda.synchronize()
@@ -809,7 +811,7 @@ def run_serving(args, world, rank, local):
     reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=r["arrival"])
             for r in raw]
     srv = m.serve.Server(budget_bytes=budget, max_slots=64, stream=stream.cuda_stream, precision=prec,
-                         graphs=graphs)
+                         graphs=graphs, lanes=args.serve_lanes)
     launches0 = m.launch_count()
     t0 = time.perf_counter()
     res = srv.run(reqs)
@@ -837,6 +839,7 @@ def run_serving(args, world, rank, local):
                            "latency": "Poisson arrivals at 0.8 x the served capacity",
                            "plain": "FP64, each request alone, one after another, direct launches",
                            "served_precision": prec_name, "cuda_graphs": graphs, "budget_bytes": budget,
+                           "lanes": args.serve_lanes,
                            "max_slots": 64}}
         print(json.dumps(line), flush=True)
 

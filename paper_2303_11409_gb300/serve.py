@@ -9,10 +9,17 @@ parallel, arXiv:2303.11409 Sec. II).  Admission is by device-memory footprint
 both computed from the per-bond sector-size bounds) against a budget, and by a
 slot count; a request admitted mid-run joins the next tick.  Completed requests
 report observables and free their memory at once, which admits waiting ones.
+
+With lanes = 2 the active requests are dealt to two executors, each with its own
+CUDA stream and workspace, and every tick runs both executor calls at once from two
+host threads (the library releases the interpreter lock): one lane's host planning
+and kept-count round trip overlap the other lane's kernels, and the two lanes'
+kernels overlap each other.  A request stays on the lane that admitted it.
 """
 from __future__ import annotations
 
 import time
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -44,6 +51,7 @@ class Job:
     layers: list
     bytes: int
     admitted: float
+    lane: int = 0
     next_layer: int = 0
     updates: int = 0
     trunc: float = 0.0
@@ -101,11 +109,24 @@ class Server:
     clock: object = time.perf_counter
     precision: int = MPS_FP64      # sector-GEMM precision of every admitted request's MPS
     graphs: bool = False           # capture the merged update calls in CUDA graphs
+    lanes: int = 1                 # executors run concurrently, each on its own stream
     executor: Executor = field(init=False)
 
     def __post_init__(self):
-        self.executor = Executor(self.stream)
-        self.executor.set_graphs(self.graphs)
+        if self.lanes not in (1, 2):
+            raise ValueError("lanes must be 1 or 2")
+        streams = [self.stream]
+        if self.lanes == 2:
+            import torch
+            self._lane_stream = torch.cuda.Stream()     # kept alive with the server
+            streams.append(self._lane_stream.cuda_stream)
+        self.executors = []
+        for st in streams:
+            ex = Executor(st)
+            ex.set_graphs(self.graphs)
+            self.executors.append(ex)
+        self.executor = self.executors[0]
+        self._pool = ThreadPoolExecutor(max_workers=self.lanes) if self.lanes > 1 else None
         self.max_active_seen = 0
         self.max_bytes_seen = 0
 
@@ -126,9 +147,12 @@ class Server:
                     break
                 req = pending.pop(0)
                 d, occ, gates = _setup(req)
-                psi = MPS(d, occ, req.chi, precision=self.precision, stream=self.executor.stream)
+                # the lane with the least work per tick (sum of L chi^2 of its requests)
+                load = [sum(j.req.L * j.req.chi ** 2 for j in active if j.lane == k) for k in range(self.lanes)]
+                lane = int(min(range(self.lanes), key=lambda k: load[k]))
+                psi = MPS(d, occ, req.chi, precision=self.precision, stream=self.executors[lane].stream)
                 layers = [lay for _ in range(req.steps) for lay in strang_layers(req.L)]
-                active.append(Job(req, psi, gates, layers, need, now))
+                active.append(Job(req, psi, gates, layers, need, now, lane))
                 used += need
             self.max_active_seen = max(self.max_active_seen, len(active))
             self.max_bytes_seen = max(self.max_bytes_seen, used)
@@ -136,17 +160,23 @@ class Server:
                 if pending:                       # idle until the next arrival
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
                 continue
-            # one tick: the next layer of every active request, merged into one call
-            items, owners = [], []
+            # one tick: the next layer of every active request, merged into one call per lane
+            items = [[] for _ in range(self.lanes)]
+            owners = [[] for _ in range(self.lanes)]
             for job in active:
                 sites, f = job.layers[job.next_layer]
                 for s in sites:
-                    items.append((job.psi, s, job.gates(s, f), job.req.chi, job.req.cutoff))
-                    owners.append(job)
-            te, _ = self.executor.apply(items)
-            for job, e in zip(owners, te):
-                job.updates += 1
-                job.trunc += float(e)
+                    items[job.lane].append((job.psi, s, job.gates(s, f), job.req.chi, job.req.cutoff))
+                    owners[job.lane].append(job)
+            if self._pool is None:
+                outs = [self.executor.apply(items[0])]
+            else:
+                futs = [self._pool.submit(self.executors[k].apply, items[k]) for k in range(self.lanes)]
+                outs = [f.result() for f in futs]
+            for k in range(self.lanes):
+                for job, e in zip(owners[k], outs[k][0]):
+                    job.updates += 1
+                    job.trunc += float(e)
             finished = []
             for job in active:
                 job.next_layer += 1
@@ -164,7 +194,10 @@ class Server:
         return sorted(done, key=lambda r: r.id)
 
     def close(self):
-        self.executor.close()
+        for ex in self.executors:
+            ex.close()
+        if self._pool is not None:
+            self._pool.shutdown()
 
 
 def summarize(results: list[Result], wall: float) -> dict:

@@ -25,10 +25,13 @@ def _requests(m):
     ]
 
 
-def test_mix_equals_alone(gpu_lib):
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_mix_equals_alone(gpu_lib, lanes):
+    """With one executor, and with two executor lanes on their own streams running each tick's
+    calls from two host threads at once."""
     m = gpu_lib
     reqs = _requests(m)
-    srv = m.serve.Server(budget_bytes=8 << 30, max_slots=3)
+    srv = m.serve.Server(budget_bytes=8 << 30, max_slots=3, lanes=lanes)
     mixed = {r.id: r for r in srv.run(reqs)}
     assert srv.max_active_seen <= 3
     for req in reqs:
