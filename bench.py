@@ -640,6 +640,7 @@ def run_ours(args, world, rank, local):
     roofline = {"kernel": dom, "bound": KERNEL_BOUND[dom], "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": None,
                 "traffic_note": "null: no ncu DRAM capture of this kernel at this configuration's current build",
+                "traffic_small_case": None,
                 "per_launch": {"flops" if unit == "GFLOP/s" else "bytes":
                                (kd["flops"] if unit == "GFLOP/s" else kd["bytes"]) / max(kd["launches"], 1),
                                "ms": per_launch_ms},
@@ -647,6 +648,18 @@ def run_ours(args, world, rank, local):
                 "frac_of_measured_fp64": achieved / fp64_measured if unit == "GFLOP/s" else None,
                 "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "share": v["ms"] / tot_ms}
                             for k, v in ks.items() if v["launches"]}}
+    if dom == "svd":
+        # ncu DRAM bytes of the cluster SVD on the saturated L=24, chi<=1024 chain (bench.py --case
+        # small_tf32; profiles/svd_block_jacobi_kernel_bose_hubbard_L24_chi1024.md): 9.05 + 28.21 GB
+        # for a launch of 3.21e11 nominal flops.  The write-back of staged column blocks grows with
+        # the sweep work, so the figure is scaled to this launch by its nominal flops.
+        small_bytes, small_flops = 9.05e9 + 28.21e9, 3.2139e11
+        flops_launch = kd["flops"] / max(kd["launches"], 1)
+        roofline["traffic"] = small_bytes * flops_launch / small_flops
+        roofline["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of the small-case capture "
+                                    "(L=24, chi<=1024), scaled to this launch by nominal flops; the column "
+                                    "blocks written back after every block round, about 1% of the DRAM bandwidth")
+        roofline["traffic_small_case"] = {"bytes": small_bytes, "nominal_flops": small_flops}
     if args.precision != "fp64":
         # the tensor-core sector GEMMs (the products of the Theta' build and of the reassembly,
         # one TMA-fed kernel) against the format's peak, and against the HBM roofline of their
