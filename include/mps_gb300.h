@@ -7,7 +7,11 @@
  * c^[k] = sum_{j>k} i_j, the Kronecker deltas of the U(1) amplitude formula force
  * c^[k-1] - c^[k] = i_k with c^[0] = N and c^[M] = 0, so a site tensor is a block
  * matrix without an explicit physical index, and a two-site update needs only
- * block-sparse SVDs of the submatrices Theta(c), each at most chi x chi.
+ * block-sparse SVDs of the submatrices Theta(c), each at most chi x chi.  On the
+ * same sector machinery it runs two-site DMRG and TDVP (mps_dmrg, mps_tdvp), samples
+ * occupation patterns (mps_sample), and supports Z_n charges (mps_create_zn),
+ * several U(1) charges at once (mps_create_multi) and chain segments for multi-rank
+ * runs (mps_create_segment).
  *
  * Conventions used by every entry point
  *   - Sites are 0-based, s = 0..L-1.  Bond b (b = 0..L) sits left of site b, so

@@ -1,12 +1,13 @@
-// Two-site DMRG on the U(1) block-sparse MPS (the ground-state method Sec. I of
-// arXiv:2303.11409 names; the block structure is that of Sec. II).
+// Two-site DMRG and two-site TDVP on the U(1) block-sparse MPS (the variational methods
+// Sec. I of arXiv:2303.11409 names beside TEBD; the block structure is that of Sec. II).
 //
 // The two-site wave function of sites (s, s+1) is the set of matrices Psi(c) over the
 // middle charge c, in the layout of the TEBD update's Theta(c): rows are the left-bond
 // sectors l = c .. c+d-1 (physical index i = l - c), columns the right-bond sectors
 // r = c-d+1 .. c (j = c - r).  One local step
-//   Psi = B^[s] B^[s+1]  ->  Lanczos on H_eff  ->  per-sector SVD  ->  global top-chi
-//   -> new sites (left- or right-canonical)  ->  environment of the new bond
+//   Psi = B^[s] B^[s+1]  ->  Lanczos on H_eff (DMRG: the ground state; TDVP: exp(-i tau H_eff))
+//   -> per-sector SVD  ->  global top-chi  ->  new sites (left- or right-canonical)
+//   -> environment of the new bond  (TDVP: the centre site evolved back by its one-site H_eff)
 // runs in these kernels, with one host round trip per Lanczos restart and one for the
 // kept counts:
 //   sumprod_kernel   every block contraction (H_eff Psi, environment updates, the centre
@@ -17,6 +18,9 @@
 //                    basis stays orthonormal to rounding), deterministic two-pass sums;
 //   tridiag_kernel   the lowest Ritz pair of the Lanczos tridiagonal (Sturm bisection,
 //                    then inverse iteration with a shift just below it);
+//   expm_tridiag_kernel / combine_c_kernel   TDVP's Krylov exponential exp(-i tau T) e_1
+//                    (the tridiagonal's eigenpairs by cyclic Jacobi rotations in one warp)
+//                    and the complex Ritz combination;
 //   the SVD, selection and lambda kernels of the TEBD update (k_svd.cu, k_select.cu).
 // H = sum_k h_{k,k+1}: each bond term (given by its charge blocks in the gate layout) is
 // split on the host into operator pairs sum_t O_t (x) P_t with O_t raising the left site's
