@@ -117,6 +117,10 @@ def parse():
     p.add_argument("--serve", action="store_true",
                    help="serving workload instead: continuous batching vs the plain one-request-at-a-time form")
     p.add_argument("--serve-requests", type=int, default=48)
+    p.add_argument("--serve-mix", default="scaled", choices=("scaled", "full"),
+                   help="full: the 512-request configuration (L in {32,64,128}, chi in {64,256,1024}, 50-500 steps) "
+                        "at --serve-rate requests/s, served for --serve-seconds of wall time")
+    p.add_argument("--serve-rate", type=float, default=4.0)
     p.add_argument("--serve-lanes", type=int, default=2, choices=(1, 2),
                    help="serving executors run concurrently from two host threads, each on its own stream")
     p.add_argument("--serve-seconds", type=float, default=25.0,
@@ -770,6 +774,53 @@ def serving_sample(args, m, W, stream, prec):
             "what": "scaled serving mix (xxz / bose-hubbard quenches), Poisson arrivals at 0.8 x capacity"}
 
 
+def run_serving_full(args, world, rank, local):
+    """The full serving configuration, bounded in wall time: 512 requests (XXZ or Bose-Hubbard
+    quenches, L in {32, 64, 128}, chi in {64, 256, 1024}, 50-500 Trotter steps) arriving as a
+    Poisson process of --serve-rate requests/s, served by continuous batching (two lanes) for
+    --serve-seconds.  Completed requests give p50 / p99 latency (the short ones complete first,
+    so these describe the completed part of the mix); all requests' updates give the served
+    throughput under load."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    import paper_2303_11409_gb300 as m
+    import workloads as W
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    prec_name = args.precision.split(",")[0]
+    prec = {"fp64": m.MPS_FP64, "tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[prec_name]
+    raw = W.serving_requests(512, seed=rank, rate_hz=args.serve_rate)
+    reqs = [m.serve.Request(r["id"], r["model"], r["L"], r["chi"], r["steps"], r["param"], arrival=r["arrival"])
+            for r in raw]
+    budget = 120 << 30
+    srv = m.serve.Server(budget_bytes=budget, max_slots=64, stream=stream.cuda_stream, precision=prec,
+                         graphs=bool(args.graphs), lanes=args.serve_lanes)
+    launches0 = m.launch_count()
+    t0 = time.perf_counter()
+    res = srv.run(reqs, deadline=args.serve_seconds)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    srv.close()
+    ups = sum(r.updates for r in res) + srv.unfinished_updates
+    lat = np.array([r.latency for r in res]) if res else np.zeros(1)
+    if rank == 0:
+        line = {"metric": "serving two-site updates/s (full request mix, bounded run)", "value": ups / wall,
+                "unit": "updates/s", "n_gpus": world, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if prec_name == "fp64" else f"{prec_name}+f64",
+                "data": "synthetic", "wall_s": wall, "requests_arrived": sum(1 for r in raw if r["arrival"] <= wall),
+                "requests_completed": len(res), "requests_unfinished": srv.unfinished,
+                "p50_latency_completed_s": float(np.percentile(lat, 50)),
+                "p99_latency_completed_s": float(np.percentile(lat, 99)),
+                "max_active": srv.max_active_seen, "max_bytes": srv.max_bytes_seen,
+                "gpu_launches": m.launch_count() - launches0,
+                "config": {"workload": "serving_mix_full_512", "rate_hz": args.serve_rate,
+                           "seconds": args.serve_seconds, "lanes": args.serve_lanes, "budget_bytes": budget,
+                           "max_slots": 64, "served_precision": prec_name, "cuda_graphs": bool(args.graphs),
+                           "latency": "arrival to result, requests completed within the bounded run"}}
+        print(json.dumps(line), flush=True)
+
+
 def run_serving(args, world, rank, local):
     """Serving: Poisson arrivals of mixed XXZ / Bose-Hubbard quenches through the
     continuous-batching server, next to the plain form (each request alone, in turn).
@@ -860,7 +911,9 @@ def run_serving(args, world, rank, local):
 def main():
     args = parse()
     world, rank, local = dist_setup()
-    if args.serve:
+    if args.serve and args.serve_mix == "full":
+        run_serving_full(args, world, rank, local)
+    elif args.serve:
         run_serving(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)

@@ -130,16 +130,27 @@ class Server:
         self.max_active_seen = 0
         self.max_bytes_seen = 0
 
-    def run(self, requests: list[Request]) -> list[Result]:
-        """Serve every request to completion; arrivals follow req.arrival on the wall clock."""
+    def run(self, requests: list[Request], deadline: float | None = None) -> list[Result]:
+        """Serve every request to completion; arrivals follow req.arrival on the wall clock.
+        With a deadline (seconds) the run stops at the first tick boundary after it: requests
+        not finished by then are dropped (their handles freed) and counted in self.unfinished,
+        their updates so far in self.unfinished_updates."""
         pending = sorted(requests, key=lambda r: (r.arrival, r.id))
         check_admissible(pending, self.budget_bytes)
         active: list[Job] = []
         done: list[Result] = []
         used = 0
+        self.unfinished = 0
+        self.unfinished_updates = 0
         t0 = self.clock()
         while pending or active:
             now = self.clock() - t0
+            if deadline is not None and now >= deadline:
+                self.unfinished = len(active) + len(pending)
+                self.unfinished_updates = sum(j.updates for j in active)
+                for job in active:
+                    job.psi.close()
+                break
             # admit arrived requests, in arrival order, while slots and memory allow
             while pending and pending[0].arrival <= now and len(active) < self.max_slots:
                 need = footprint(pending[0])
