@@ -63,6 +63,10 @@ CASES = {
     # step is one TDVP time step (two passes, 126 two-site updates and 124 one-site backward steps)
     "tdvp": dict(L=64, N=64, CHI=256, precision="fp64", start="dmrg",
                  workload="tdvp_bose_hubbard_L64_nmax4_N64_J1_U2to4_dt0.02_chi256_cutoff1e-10"),
+    # a short chain whose bonds saturate at chi<=256 within three sweeps, for profiler captures of
+    # the H_eff products at the benchmark's sector sizes
+    "dmrg_mid": dict(L=12, N=12, CHI=256, precision="fp64", start="dmrg",
+                     workload="dmrg_bose_hubbard_L12_nmax4_N12_J1_U2_chi256_cutoff1e-10"),
     # the same at L=24, chi<=128, for profiler captures
     "dmrg_small": dict(L=24, N=24, CHI=128, precision="fp64", start="dmrg",
                        workload="dmrg_bose_hubbard_L24_nmax4_N24_J1_U2_chi128_cutoff1e-10"),
@@ -917,7 +921,7 @@ def main():
         run_serving(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
-    elif args.case in ("dmrg", "dmrg_small", "tdvp"):
+    elif args.case in ("dmrg", "dmrg_small", "dmrg_mid", "tdvp"):
         run_dmrg_case(args, world, rank, local)
     else:
         precisions = args.precision.split(",")

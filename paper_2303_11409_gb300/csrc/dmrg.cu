@@ -81,6 +81,84 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// A block of at most 1024 outputs (one tile): its outputs are dealt to the threads in order,
+// up to four per thread, so that every warp's lanes hold real outputs (the 16 x 16 thread grid
+// of the general path would spend most FP64 issue slots of a block of 17-30 rows and columns
+// on padding; this part issues 2 FP64 FMA per clock per SM, so only dense warps pay).
+__device__ __forceinline__ void small_block(const SPTask& T, const SPTerm* __restrict__ terms,
+                                            const double2* __restrict__ X, double2* __restrict__ Y, SPSmem& sm) {
+  const int tid = threadIdx.x;
+  const int MN = T.M * T.N, nq = (MN + kThr - 1) / kThr;
+  int rr[4], cc[4];
+  bool ok[4];
+  double2 acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int o = tid + kThr * q;
+    ok[q] = o < MN;
+    rr[q] = ok[q] ? o / T.N : 0;
+    cc[q] = ok[q] ? o % T.N : 0;
+    acc[q] = make_double2(0.0, 0.0);
+  }
+  for (int t = T.t0; t < T.t1; ++t) {
+    const SPTerm P = terms[t];
+    const double2* A = (P.flags & kAX) ? X + P.a : reinterpret_cast<const double2*>(P.a);
+    const bool ca = (P.flags & kConjA) != 0;
+    if (P.flags & kNoB) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (q < nq && ok[q]) {
+          double2 v = A[(int64_t)rr[q] * P.sar + (int64_t)cc[q] * P.sac];
+          if (ca) v.y = -v.y;
+          cfma(acc[q], P.coef, v);
+        }
+      }
+      continue;
+    }
+    const double2* B = (P.flags & kBX) ? X + P.b : reinterpret_cast<const double2*>(P.b);
+    const bool cb = (P.flags & kConjB) != 0;
+    for (int k0 = 0; k0 < P.K; k0 += kKc) {
+      const int kc = min(kKc, P.K - k0);
+      for (int e = tid; e < T.M * kc; e += kThr) {
+        int r, k;
+        if (P.sac == 1) { r = e / kc; k = e % kc; } else { k = e / T.M; r = e % T.M; }
+        double2 v = A[(int64_t)r * P.sar + (int64_t)(k0 + k) * P.sac];
+        if (ca) v.y = -v.y;
+        sm.A[r][k] = cmul(P.coef, v);
+      }
+      for (int e = tid; e < T.N * kc; e += kThr) {
+        int k, c;
+        if (P.sbc == 1) { k = e / T.N; c = e % T.N; } else { c = e / kc; k = e % kc; }
+        double2 v = B[(int64_t)(k0 + k) * P.sbr + (int64_t)c * P.sbc];
+        if (cb) v.y = -v.y;
+        sm.B[k][c] = v;
+      }
+      __syncthreads();
+      for (int kk = 0; kk < kc; ++kk) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nq) cfma(acc[q], sm.A[rr[q]][kk], sm.B[kk][cc[q]]);
+      }
+      __syncthreads();
+    }
+  }
+  double2* C = (T.flags & kCY) ? Y + T.c : reinterpret_cast<double2*>(T.c);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q < nq && ok[q]) {
+      double2& o = C[(int64_t)rr[q] * T.ldc + cc[q]];
+      if (T.flags & kAccum) {
+        double2 v = o;
+        v.x += acc[q].x;
+        v.y += acc[q].y;
+        o = v;
+      } else {
+        o = acc[q];
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThr, 2) sumprod_kernel(const SPTask* __restrict__ tasks,
                                                        const SPTerm* __restrict__ terms,
                                                        const SPTile* __restrict__ tiles,
@@ -88,6 +166,10 @@ __global__ void __launch_bounds__(kThr, 2) sumprod_kernel(const SPTask* __restri
   __shared__ SPSmem sm;
   const SPTile tr = tiles[blockIdx.x];
   const SPTask T = tasks[tr.task];
+  if (T.M <= kT && T.N <= kT && T.M * T.N <= 4 * kThr) {
+    small_block(T, terms, X, Y, sm);
+    return;
+  }
   const int row0 = tr.ti * kT, col0 = tr.tj * kT;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   double2 acc[4][4];
@@ -125,36 +207,34 @@ __global__ void __launch_bounds__(kThr, 2) sumprod_kernel(const SPTask* __restri
     for (int i = 0; i < 4; ++i) ni += (row0 + warp_ty + 16 * i < T.M);
 #pragma unroll
     for (int j = 0; j < 4; ++j) nj += (col0 + 16 * j < T.N);
+    // only the block's own rows / columns are staged and read: the accumulators of padding rows
+    // and columns see stale shared memory and are never stored
+    const int mr = min(kT, T.M - row0), ncl = min(kT, T.N - col0);
     for (int k0 = 0; k0 < P.K; k0 += kKc) {
       const int kc = min(kKc, P.K - k0);
-      for (int e = tid; e < kT * kKc; e += kThr) {
+      for (int e = tid; e < mr * kc; e += kThr) {
         int r, k;
-        if (P.sac == 1) { r = e / kKc; k = e % kKc; } else { k = e / kT; r = e % kT; }
-        double2 v = make_double2(0.0, 0.0);
-        if (row0 + r < T.M && k < kc) {
-          v = A[(int64_t)(row0 + r) * P.sar + (int64_t)(k0 + k) * P.sac];
-          if (ca) v.y = -v.y;
-          v = cmul(P.coef, v);
-        }
-        sm.A[r][k] = v;
+        if (P.sac == 1) { r = e / kc; k = e % kc; } else { k = e / mr; r = e % mr; }
+        double2 v = A[(int64_t)(row0 + r) * P.sar + (int64_t)(k0 + k) * P.sac];
+        if (ca) v.y = -v.y;
+        sm.A[r][k] = cmul(P.coef, v);
       }
-      for (int e = tid; e < kT * kKc; e += kThr) {
+      for (int e = tid; e < ncl * kc; e += kThr) {
         int k, c;
-        if (P.sbc == 1) { k = e / kT; c = e % kT; } else { c = e / kKc; k = e % kKc; }
-        double2 v = make_double2(0.0, 0.0);
-        if (col0 + c < T.N && k < kc) {
-          v = B[(int64_t)(k0 + k) * P.sbr + (int64_t)(col0 + c) * P.sbc];
-          if (cb) v.y = -v.y;
-        }
+        if (P.sbc == 1) { k = e / ncl; c = e % ncl; } else { c = e / kc; k = e % kc; }
+        double2 v = B[(int64_t)(k0 + k) * P.sbr + (int64_t)(col0 + c) * P.sbc];
+        if (cb) v.y = -v.y;
         sm.B[k][c] = v;
       }
       __syncthreads();
       for (int kk = 0; kk < kc; ++kk) {
         double2 a[4], b[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = sm.A[ty + 16 * i][kk];
+        for (int i = 0; i < 4; ++i)
+          if (i < ni) a[i] = sm.A[ty + 16 * i][kk];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) b[j] = sm.B[kk][tx + 16 * j];
+        for (int j = 0; j < 4; ++j)
+          if (j < nj) b[j] = sm.B[kk][tx + 16 * j];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           if (i < ni) {
