@@ -658,9 +658,9 @@ def run_ours(args, world, rank, local):
                             for k, v in ks.items() if v["launches"]}}
     if dom == "svd":
         # ncu DRAM bytes of the cluster SVD on the saturated L=24, chi<=1024 chain (bench.py --case
-        # small_tf32; profiles/svd_block_jacobi_kernel_bose_hubbard_L24_chi1024.md): 9.05 + 28.21 GB
-        # for a launch of 3.21e11 nominal flops.  The write-back of staged column blocks grows with
-        # the sweep work, so the figure is scaled to this launch by its nominal flops.
+        # small_tf32, the first cluster-SVD launch of the layer): 9.05 + 28.21 GB for a launch of
+        # 3.21e11 nominal flops.  The write-back of staged column blocks grows with the sweep work,
+        # so the figure is scaled to this launch by its nominal flops.
         small_bytes, small_flops = 9.05e9 + 28.21e9, 3.2139e11
         flops_launch = kd["flops"] / max(kd["launches"], 1)
         roofline["traffic"] = small_bytes * flops_launch / small_flops
