@@ -134,7 +134,8 @@ def parse():
                    help="SVD tile shape chosen per sector-size histogram (tuning runs happen before the timed steps)")
     p.add_argument("--chi-deflation", type=float, default=3e-4,
                    help="second SVD deflation level: values below this fraction of a bond's previous chi cut are "
-                        "left unresolved (the update is redone if its cut falls below level / 6e-4 of it); 0: off")
+                        "left unresolved (level / 30 when the cut is older than the previous layer; the update is redone if its cut "
+                        "falls below that level / 6e-4 of it); 0: off")
     p.add_argument("--svd-mixed-min-k", type=int, default=192,
                    help="cluster SVD sectors with min(m, n) >= this start with FP32 Jacobi sweeps (0: FP64 only)")
     p.add_argument("--svd-candidate", type=int, default=-1,

@@ -141,9 +141,10 @@ MPS_API int mps_info(mps_t h, int* L, int* d, int* N, int* chi_max, int* precisi
  * singular values below 0.01 * cutoff * |M(c)|_F (at least 100x under the cutoff
  * threshold cutoff * |sigma|_2, so discarded in any case), nor, when chi set the cut
  * of the previous update of the same bond, below 3e-4 times that relative cut
- * (smallest kept value / |sigma|_2; the level is set by mps_set_chi_deflation): their
- * columns are not rotated and they count as zero.  When the new cut falls under
- * level / 6e-4 of that previous one (half of it at the default level), the call redoes
+ * (smallest kept value / |sigma|_2; the level is set by mps_set_chi_deflation) when that
+ * cut was recorded by the previous update call on the handle, 30x lower when it is older:
+ * their columns are not rotated and they count as zero.  When the new cut falls under
+ * the applied level / 6e-4 of that previous one (half of it at 3e-4), the call redoes
  * that update's SVDs and the selection without the second level, so an unresolved value
  * always lies >= 1600x under the kept ones.
  * mps_deflation_stats counts updates that used the second level and those redone.
@@ -302,8 +303,10 @@ MPS_API int mps_last_update_stats(mps_t h, int* n_sectors, int* n_triples, int* 
 /*
  * mps_set_chi_deflation - the second deflation level of the updates of h (see
  * mps_apply_gate2): singular values below level x the previous relative chi cut of the bond
- * are left unresolved, and an update whose new cut falls below level / 6e-4 of that estimate
- * is redone without it, so an unresolved value always lies at least 1600x under the kept ones.
+ * (level / 30 when the previous update call on h did not record that cut) are left
+ * unresolved, and an update whose new cut falls below the applied level / 6e-4 of that
+ * estimate is redone without it, so an unresolved value always lies at least 1600x under the
+ * kept ones.
  * level 0 turns the second level off; the default is 3e-4 (a redo when the cut halves); a
  * smaller level deflates less but redoes only after larger drops of the cut.  It applies to
  * the updates of h whichever handle's call (or executor) runs them.  MPS_EINVAL outside

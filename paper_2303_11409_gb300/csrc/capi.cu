@@ -294,6 +294,14 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
   cudaStream_t st = owner->stream;
   const int nreq = (int)reqs.size();
   std::vector<UpdWork> W(nreq);
+  {   // one more update call on every handle of the batch
+    std::vector<mps_s*> seen;
+    for (const Req& r : reqs)
+      if (std::find(seen.begin(), seen.end(), r.h) == seen.end()) {
+        seen.push_back(r.h);
+        r.h->calls++;
+      }
+  }
 
   Range batch_range("mps.update_call");
   // ---- K0: plan every update and size the workspace --------------------------------
@@ -314,7 +322,12 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     plan_update(h->bonds[s], h->bonds[s + 1], h->bonds[s + 2], h->rule, W[u].plan);
     if (h->chi_deflate > 0.0 && (int)h->cut_est.size() == h->L + 1) {
       W[u].cut_est = h->cut_est[s + 1];
-      W[u].chi_level = h->chi_deflate;
+      // a cut recorded by the previous update call on this handle (the same layer kind in a row,
+      // as the two odd half-step layers of consecutive Strang steps) is a close estimate; an
+      // older one has seen the neighbouring bonds change in between, so its level is 30x lower
+      // (a redo then needs a 30x larger drop of the cut)
+      const bool fresh = (int)h->cut_call.size() == h->L + 1 && h->calls - h->cut_call[s + 1] <= 1;
+      W[u].chi_level = fresh ? h->chi_deflate : h->chi_deflate / 30.0;
     }
     max_tri = std::max<int>(max_tri, (int)W[u].plan.triple_l.size());
     n_sec_total += (int)W[u].plan.sectors.size();
@@ -1155,9 +1168,11 @@ int run_batch(std::vector<Req>& reqs, mps_s* owner) {
     h->sites[s + 1] = newR[u];
     // the next update of this bond deflates from this cut when chi set it (more candidates
     // than kept); a cut set by the cutoff lies under the cutoff deflation level anyway
-    if ((int)h->cut_est.size() == h->L + 1)
+    if ((int)h->cut_est.size() == h->L + 1) {
       h->cut_est[s + 1] = (res[u].n_candidates > reqs[u].chi && res[u].norm_all > 0.0)
                               ? res[u].cut / res[u].norm_all : 0.0;
+      if ((int)h->cut_call.size() == h->L + 1) h->cut_call[s + 1] = h->calls;
+    }
     h->cur[s] ^= 1;
     h->cur[s + 1] ^= 1;
   }
@@ -1307,6 +1322,7 @@ static int create_handle(mps_t* out, int L, int d, const int32_t* site_charges, 
   h->sites.resize(L);
   h->cur.assign(L, 0);
   h->cut_est.assign(L + 1, 0.0);
+  h->cut_call.assign(L + 1, 0);
   h->dirty.assign(L, 0);
   h->site_cap.resize(L);
   h->site_base.resize(L);

@@ -332,6 +332,8 @@ struct mps_s {
   std::vector<cudaEvent_t> event_pool;
   int* tc_flag = nullptr;                 // set by a tensor-core GEMM whose bounded wait expired
   std::vector<double> cut_est;            // per bond: smallest kept sigma of its last update (0: none)
+  std::vector<int64_t> cut_call;          // per bond: the update call that recorded cut_est
+  int64_t calls = 0;                      // update calls on this handle so far
   int sweep_limit = 40;                   // Jacobi sweep limit of this handle's update calls
   double chi_deflate = 3e-4;              // level of the deflation from a bond's previous chi cut (0: off)
   // CUDA graphs: the two launch phases of an update call are captured and replayed
