@@ -575,6 +575,34 @@ MPS_API int mps_plan_sectors(int d, int nl, const int32_t* lc, const int32_t* ld
                      int32_t* sectors, int cap_sectors, int* n_sectors);
 
 /*
+ * mps_plan_sectors_rule - the sector planner of mps_plan_sectors for every charge rule a handle
+ * can have (host code, no GPU needed): U(1) (zn = 0, ncomp = 0, as mps_plan_sectors), Z_n
+ * (zn = n = d, as mps_create_zn) and several U(1) charges (ncomp >= 1, as mps_create_multi).
+ * Sec. II's Kronecker deltas give the blocks: (l, m) is a site block iff l - m is the charge of
+ * a physical index (taken mod n for Z_n, as a vector for several charges), and Theta(c) has as
+ * rows the left sectors l with l - c such a charge and as columns the right sectors r with
+ * c - r one.
+ *   phys_charges  (ncomp >= 1) d x ncomp row-major charge vectors, ascending, components >= 0
+ *   radix         (ncomp >= 1) the mixed radix of the encoded bond charges (first component
+ *                 most significant; mps_charge_radix of a handle gives it); every component of a
+ *                 physical or bond charge must lie below radix / 2, else MPS_ECHARGE
+ *   lc, mc, rc    ascending bond charges (residues in [0, n-1] for Z_n, encoded for ncomp >= 1)
+ *   triples       out, 3 ints per (l, m, r), lexicographic in the tables' order
+ *   sectors       out, 5 ints per candidate middle charge: (c, rows, cols, row sectors,
+ *                 column sectors), c ascending
+ *   lists         out, per sector its row sector charges then its column sector charges
+ *   n_triples, n_sectors, n_lists  sizes written; MPS_EINVAL if a capacity is too small, for
+ *                 zn != d, or for zn and ncomp both set
+ */
+MPS_API int mps_plan_sectors_rule(int d, int zn, int ncomp, const int32_t* phys_charges, const int32_t* radix,
+                     int nl, const int32_t* lc, const int32_t* ld,
+                     int nm, const int32_t* mc, const int32_t* md,
+                     int nr, const int32_t* rc, const int32_t* rd,
+                     int32_t* triples, int cap_triples, int* n_triples,
+                     int32_t* sectors, int cap_sectors, int* n_sectors,
+                     int32_t* lists, int cap_lists, int* n_lists);
+
+/*
  * mps_svd_sectors - the batched per-sector SVD kernel alone, on device memory
  * (one-sided Jacobi in FP64; Sec. II: the local update needs one SVD per charge block).
  * For each sector k it decomposes M_k = diag(rowscale_k) A_k, A_k being the

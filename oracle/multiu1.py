@@ -25,7 +25,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.linalg
 
-from .u1mps import NOISE_REL, select_kept
+from .u1mps import NOISE_REL, SectorPlan, select_kept
 
 
 def _add(a, b):
@@ -45,6 +45,37 @@ def pair_blocks(q):
             tot.setdefault(_add(q[i], q[j]), []).append((i, j))
     keys = sorted(tot)
     return keys, {Q: sorted(tot[Q]) for Q in keys}
+
+
+def phys_index(q, l, m) -> int:
+    """The physical index i with q_i = l - m (the vector Kronecker delta of Sec. II), or -1."""
+    dq = _sub(l, m)
+    for i, x in enumerate(q):
+        if x == dq:
+            return i
+    return -1
+
+
+def plan_update(left: dict, mid: dict, right: dict, q) -> SectorPlan:
+    """The sector structure of a two-site update with charge vectors q_i, by looping over charges.
+
+    triples: (l, m, r) with l - m and m - r physical charges, lexicographic; sectors: every middle
+    charge c = l - q_i that some right r reaches with c - r a physical charge; rows of Theta(c):
+    the left l with l - c a physical charge, columns: the right r with c - r one, ascending.
+    """
+    triples = [(l, m, r) for l in sorted(left) for m in sorted(mid) if phys_index(q, l, m) >= 0
+               for r in sorted(right) if phys_index(q, m, r) >= 0]
+    cands = set()
+    for l in left:
+        for r in right:
+            for x in q:
+                c = _sub(l, x)
+                if phys_index(q, c, r) >= 0:
+                    cands.add(c)
+    sectors = sorted(cands)
+    rows = {c: [l for l in sorted(left) if phys_index(q, l, c) >= 0] for c in sectors}
+    cols = {c: [r for r in sorted(right) if phys_index(q, c, r) >= 0] for c in sectors}
+    return SectorPlan(triples, sectors, rows, cols)
 
 
 @dataclass
@@ -75,27 +106,15 @@ class MultiU1MPS:
         return st
 
     def phys(self, l, m):
-        dq = _sub(l, m)
-        for i, x in enumerate(self.q):
-            if x == dq:
-                return i
-        return -1
+        return phys_index(self.q, l, m)
 
     def apply_gate2(self, s: int, G: dict, chi: int, cutoff: float) -> dict:
         """G[Q]: the gate block of total charge Q over pair_blocks(q)[1][Q]."""
         left, mid, right = self.bond[s], self.bond[s + 1], self.bond[s + 2]
         BL, BR = self.B[s], self.B[s + 1]
         _, pairs = pair_blocks(self.q)
-        cands = set()
-        for l in left:
-            for r in right:
-                for x in self.q:
-                    c = _sub(l, x)
-                    if self.phys(c, r) >= 0:
-                        cands.add(c)
-        sectors = sorted(cands)
-        rows = {c: [l for l in sorted(left) if self.phys(l, c) >= 0] for c in sectors}
-        cols = {c: [r for r in sorted(right) if self.phys(c, r) >= 0] for c in sectors}
+        plan = plan_update(left, mid, right, self.q)
+        sectors, rows, cols = plan.sectors, plan.rows, plan.cols
         theta = {}
         for c in sectors:
             T = np.zeros((sum(left[l] for l in rows[c]), sum(right[r] for r in cols[c])), dtype=np.complex128)

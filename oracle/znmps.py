@@ -28,12 +28,23 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.linalg
 
-from .u1mps import NOISE_REL, select_kept
+from .u1mps import NOISE_REL, SectorPlan, select_kept
 
 
 def zn_blocks_of(n: int, q: int) -> list[tuple[int, int]]:
     """Basis of the two-site gate block of total charge q: (i, (q - i) mod n), i ascending."""
     return [(i, (q - i) % n) for i in range(n)]
+
+
+def plan_update(left: dict, mid: dict, right: dict, n: int) -> SectorPlan:
+    """The sector structure of a Z_n two-site update (d = n): every (l, m, r) is a triple (each
+    residue difference is a physical index), every residue c = 0..n-1 a middle charge, and
+    Theta(c) has all left sectors as rows and all right sectors as columns, ascending."""
+    triples = [(l, m, r) for l in sorted(left) for m in sorted(mid) for r in sorted(right)]
+    sectors = list(range(n))
+    rows = {c: sorted(left) for c in sectors}
+    cols = {c: sorted(right) for c in sectors}
+    return SectorPlan(triples, sectors, rows, cols)
 
 
 @dataclass
@@ -72,8 +83,9 @@ class ZnMPS:
         n = self.n
         left, mid, right = self.bond[s], self.bond[s + 1], self.bond[s + 2]
         BL, BR = self.B[s], self.B[s + 1]
-        rows = sorted(left)
-        cols = sorted(right)
+        plan = plan_update(left, mid, right, n)
+        rows = plan.rows[0]
+        cols = plan.cols[0]
         m_rows = sum(left[l] for l in rows)
         n_cols = sum(right[r] for r in cols)
         theta = {}

@@ -87,6 +87,10 @@ _SIGS = {
     "mps_plan_sectors": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.c_int, _i32p, _i32p,
                                         ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_int, _intp, _i32p,
                                         ctypes.c_int, _intp]),
+    "mps_plan_sectors_rule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p,
+                                             ctypes.c_int, _i32p, _i32p, ctypes.c_int, _i32p, _i32p,
+                                             ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_int, _intp, _i32p,
+                                             ctypes.c_int, _intp, _i32p, ctypes.c_int, _intp]),
     "mps_last_batch_sweeps": (ctypes.c_int, [_h, _intp, _i64p, _intp]),
     "mps_set_profiling": (ctypes.c_int, [_h, ctypes.c_int]),
     "mps_kernel_stats": (ctypes.c_int, [_h, ctypes.c_int, _i64p, _dblp, _dblp, _dblp]),
@@ -737,6 +741,64 @@ def plan_sectors(d: int, left: dict, mid: dict, right: dict):
     if rcode != MPS_OK:
         raise MPSError(rcode, "mps_plan_sectors")
     return tri[:3 * nt.value].reshape(-1, 3), sec[:3 * ns.value].reshape(-1, 3)
+
+
+def plan_sectors_rule(d: int, left: dict, mid: dict, right: dict, zn: int = 0, charges=None, radix=None):
+    """The library's sector planner under any charge rule (mps_plan_sectors_rule).
+
+    zn: n of a Z_n rule (d = n).  charges: d charge vectors of a several-U(1) rule, with the
+    tables keyed by charge tuples and radix the mixed radix of their encoding (default: each
+    component's radix 2 * (largest table value) + 3).  Returns (triples, sectors) with
+    triples a list of (l, m, r) and sectors a list of (c, rows, cols, row charges, column
+    charges), charges as tuples for a several-U(1) rule.
+    """
+    ncomp = 0 if charges is None else len(charges[0])
+    if ncomp:
+        if radix is None:
+            top = [max([0] + [int(k[j]) for t in (left, mid, right) for k in t]) for j in range(ncomp)]
+            radix = [2 * t + 3 for t in top]
+        weights = [int(np.prod(radix[j + 1:])) for j in range(ncomp)]
+        enc = lambda c: int(sum(int(x) * w for x, w in zip(c, weights)))
+
+        def dec(v):
+            out = []
+            for w in weights:
+                out.append(int(v) // w)
+                v = int(v) - out[-1] * w
+            return tuple(out)
+        q = _i32([x for vec in charges for x in vec])
+        rad = _i32(radix)
+    else:
+        enc = dec = int
+        q = rad = None
+
+    def tab(t):
+        ks = sorted(t, key=enc)
+        return _i32([enc(k) for k in ks]), _i32([t[k] for k in ks])
+    (lc, ld), (mc, md), (rc, rd) = tab(left), tab(mid), tab(right)
+    cap_t = max(1, len(lc) * len(mc) * len(rc))
+    cap_s = max(1, len(lc) * len(rc) * d + 2 * d)
+    cap_l = max(1, cap_s * (len(lc) + len(rc)))
+    tri = np.zeros(3 * cap_t, np.int32)
+    sec = np.zeros(5 * cap_s, np.int32)
+    lst = np.zeros(cap_l, np.int32)
+    nt, ns, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rcode = lib.mps_plan_sectors_rule(d, zn, ncomp, None if q is None else _ptr(q, _i32p),
+                                      None if rad is None else _ptr(rad, _i32p),
+                                      len(lc), _ptr(lc, _i32p), _ptr(ld, _i32p), len(mc), _ptr(mc, _i32p),
+                                      _ptr(md, _i32p), len(rc), _ptr(rc, _i32p), _ptr(rd, _i32p),
+                                      _ptr(tri, _i32p), cap_t, ctypes.byref(nt), _ptr(sec, _i32p), cap_s,
+                                      ctypes.byref(ns), _ptr(lst, _i32p), cap_l, ctypes.byref(nl))
+    if rcode != MPS_OK:
+        raise MPSError(rcode, "mps_plan_sectors_rule")
+    triples = [tuple(dec(x) for x in t) for t in tri[:3 * nt.value].reshape(-1, 3).tolist()]
+    sectors, o = [], 0
+    for c, rows, cols, nr_, nc_ in sec[:5 * ns.value].reshape(-1, 5).tolist():
+        rl = [dec(x) for x in lst[o:o + nr_]]
+        cl = [dec(x) for x in lst[o + nr_:o + nr_ + nc_]]
+        o += nr_ + nc_
+        sectors.append((dec(c), rows, cols, rl, cl))
+    return triples, sectors
 
 
 def svd_work_bytes(ms, ns) -> int:

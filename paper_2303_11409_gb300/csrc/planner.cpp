@@ -221,3 +221,85 @@ extern "C" int mps_plan_sectors(int d, int nl, const int32_t* lc, const int32_t*
   }
   return MPS_OK;
 }
+
+extern "C" int mps_plan_sectors_rule(int d, int zn, int ncomp, const int32_t* phys_charges, const int32_t* radix,
+                                     int nl, const int32_t* lc, const int32_t* ld,
+                                     int nm, const int32_t* mc, const int32_t* md,
+                                     int nr, const int32_t* rc, const int32_t* rd,
+                                     int32_t* triples, int cap_triples, int* n_triples,
+                                     int32_t* sectors, int cap_sectors, int* n_sectors,
+                                     int32_t* lists, int cap_lists, int* n_lists) {
+  if (d < 2 || d > MPS_MAX_D || !n_triples || !n_sectors || !n_lists) return MPS_EINVAL;
+  if (zn < 0 || ncomp < 0 || ncomp > 4 || (zn && ncomp)) return MPS_EINVAL;
+  if (zn && zn != d) return MPS_EINVAL;                    // Z_n is built for d = n
+  ChargeRule rule;
+  rule.d = d;
+  rule.zn = zn;
+  if (ncomp) {
+    if (!phys_charges || !radix) return MPS_EINVAL;
+    rule.multi = 1;
+    rule.ncomp = ncomp;
+    int64_t w = 1;
+    int64_t weight[4];
+    for (int k = ncomp - 1; k >= 0; --k) {
+      if (radix[k] < 2) return MPS_EINVAL;
+      rule.radix[k] = radix[k];
+      weight[k] = w;
+      w *= radix[k];
+      if (w > (int64_t)1 << 30) return MPS_EINVAL;
+    }
+    for (int i = 0; i < d; ++i) {
+      int64_t e = 0;
+      for (int k = 0; k < ncomp; ++k) {
+        const int v = phys_charges[i * ncomp + k];
+        if (v < 0 || 2 * (int64_t)v >= radix[k]) return MPS_ECHARGE;
+        e += v * weight[k];
+      }
+      rule.q[i] = (int)e;
+      if (i && rule.q[i] <= rule.q[i - 1]) return MPS_ECHARGE;
+    }
+    rule.init_multi();
+  }
+  BondTable L, M, R;
+  if (!make_table(nl, lc, ld, L) || !make_table(nm, mc, md, M) || !make_table(nr, rc, rd, R))
+    return MPS_EINVAL;
+  for (const BondTable* t : {&L, &M, &R})
+    for (int c : t->charge) {
+      if (zn && (c < 0 || c >= zn)) return MPS_ECHARGE;
+      if (ncomp) {   // every component in [0, radix / 2): differences then decode uniquely
+        int64_t v = c;
+        for (int k = ncomp - 1; k >= 0; --k) {
+          const int64_t x = v % rule.radix[k];
+          if (v < 0 || 2 * x >= rule.radix[k]) return MPS_ECHARGE;
+          v /= rule.radix[k];
+        }
+        if (v != 0) return MPS_ECHARGE;
+      }
+    }
+  UpdatePlan p;
+  plan_update(L, M, R, rule, p);
+  int64_t nlist = 0;
+  for (const SectorPlanEntry& e : p.sectors) nlist += (int64_t)e.li.size() + (int64_t)e.ri.size();
+  *n_triples = (int)p.triple_l.size();
+  *n_sectors = (int)p.sectors.size();
+  *n_lists = (int)nlist;
+  if (*n_triples > cap_triples || *n_sectors > cap_sectors || nlist > cap_lists) return MPS_EINVAL;
+  if ((*n_triples && !triples) || (*n_sectors && !sectors) || (nlist && !lists)) return MPS_EINVAL;
+  for (int t = 0; t < *n_triples; ++t) {
+    triples[3 * t + 0] = L.charge[p.triple_l[t]];
+    triples[3 * t + 1] = M.charge[p.triple_m[t]];
+    triples[3 * t + 2] = R.charge[p.triple_r[t]];
+  }
+  int64_t o = 0;
+  for (int s = 0; s < *n_sectors; ++s) {
+    const SectorPlanEntry& e = p.sectors[s];
+    sectors[5 * s + 0] = e.c;
+    sectors[5 * s + 1] = e.rows;
+    sectors[5 * s + 2] = e.cols;
+    sectors[5 * s + 3] = (int)e.li.size();
+    sectors[5 * s + 4] = (int)e.ri.size();
+    for (int i : e.li) lists[o++] = L.charge[i];
+    for (int k : e.ri) lists[o++] = R.charge[k];
+  }
+  return MPS_OK;
+}

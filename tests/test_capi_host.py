@@ -102,3 +102,84 @@ def test_load_rejects_impossible_headers_without_touching_the_gpu(built, tmp_pat
         rc = m.lib.mps_load(ctypes.byref(h), str(p).encode(), None)
         assert rc == m.MPS_EINVAL, (name, rc)
         assert not h.value
+
+
+def _check_rule_plan(got, p, left, right):
+    triples, sectors = got
+    assert triples == p.triples
+    assert [s[0] for s in sectors] == p.sectors
+    for c, rows, cols, rl, cl in sectors:
+        assert rl == p.rows[c] and cl == p.cols[c]
+        assert rows == sum(left[l] for l in rl)
+        assert cols == sum(right[r] for r in cl)
+
+
+@pytest.mark.parametrize("d", [2, 3, 5])
+def test_rule_planner_u1_equals_the_u1_planner(built, d):
+    import paper_2303_11409_gb300 as m
+    from oracle import plan_update
+    rng = np.random.default_rng(300 + d)
+    for _ in range(20):
+        base = int(rng.integers(0, 9))
+        left = _rand_table(rng, base + 2 * (d - 1), base + 4 * (d - 1))
+        mid = _rand_table(rng, base + (d - 1), base + 3 * (d - 1))
+        right = _rand_table(rng, base, base + 2 * (d - 1))
+        _check_rule_plan(m.plan_sectors_rule(d, left, mid, right), plan_update(left, mid, right, d), left, right)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 7])
+def test_rule_planner_matches_the_zn_oracle(built, n):
+    """Z_n, d = n (oracle/znmps.py): all triples, every residue a sector, all rows and columns."""
+    import paper_2303_11409_gb300 as m
+    from oracle import znmps
+    rng = np.random.default_rng(400 + n)
+    for _ in range(20):
+        left, mid, right = (_rand_table(rng, 0, n - 1) for _ in range(3))
+        got = m.plan_sectors_rule(n, left, mid, right, zn=n)
+        _check_rule_plan(got, znmps.plan_update(left, mid, right, n), left, right)
+
+
+def _rand_tuple_table(rng, lo, hi, k):
+    """A random set of charge vectors with components in [lo_j, hi_j] and random dims."""
+    pts = {tuple(int(rng.integers(lo[j], hi[j] + 1)) for j in range(len(lo))) for _ in range(k)}
+    return {c: int(rng.integers(1, 30)) for c in pts}
+
+
+@pytest.mark.parametrize("q", [
+    [(0, 0), (0, 1), (1, 0), (1, 1)],                         # two boson species, at most one each
+    [(0, 0, 0), (0, 0, 1), (0, 1, 0), (1, 0, 0), (1, 1, 0)],  # three species, one pair allowed
+    [(0,), (2,), (3,)],                                        # one charge with gaps (listed rows)
+])
+def test_rule_planner_matches_the_several_u1_oracle(built, q):
+    """Several U(1) charges (oracle/multiu1.py): listed rows and columns, encoded charges."""
+    import paper_2303_11409_gb300 as m
+    from oracle import multiu1
+    rng = np.random.default_rng(500 + len(q))
+    nc = len(q[0])
+    top = [max(x[j] for x in q) for j in range(nc)]
+    for _ in range(25):
+        base = [int(rng.integers(0, 4)) for _ in range(nc)]
+        right = _rand_tuple_table(rng, base, [b + 2 * t for b, t in zip(base, top)], 8)
+        mid = _rand_tuple_table(rng, base, [b + 3 * t for b, t in zip(base, top)], 10)
+        left = _rand_tuple_table(rng, base, [b + 4 * t for b, t in zip(base, top)], 12)
+        got = m.plan_sectors_rule(len(q), left, mid, right, charges=q)
+        p = multiu1.plan_update(left, mid, right, q)
+        assert p.sectors, "no sector: the random tables do not couple"
+        _check_rule_plan(got, p, left, right)
+
+
+def test_rule_planner_rejects_bad_rules(built):
+    import paper_2303_11409_gb300 as m
+    t = {0: 1, 1: 2}
+    with pytest.raises(m.MPSError):
+        m.plan_sectors_rule(3, t, t, t, zn=4)                  # Z_n only for d = n
+    with pytest.raises(m.MPSError):
+        m.plan_sectors_rule(3, {0: 1, 3: 1}, t, t, zn=3)       # residue outside [0, n-1]
+    q = [(0, 0), (0, 1), (1, 0), (1, 1)]
+    tt = {(0, 0): 1, (1, 1): 2}
+    with pytest.raises(m.MPSError):                            # a component beyond radix / 2
+        m.plan_sectors_rule(4, {(3, 0): 1}, tt, tt, charges=q, radix=[5, 5])
+    with pytest.raises(m.MPSError):                            # physical charges not ascending
+        m.plan_sectors_rule(4, tt, tt, tt, charges=[(0, 1), (0, 0), (1, 0), (1, 1)])
+    with pytest.raises(m.MPSError):                            # radix below 2
+        m.plan_sectors_rule(4, tt, tt, tt, charges=q, radix=[1, 5])
