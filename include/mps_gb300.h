@@ -490,7 +490,8 @@ MPS_API int mps_fp64_peak_probe(double* gflops, void* cuda_stream);
  *   ncomp         1..4 charge components; every component >= 0; the vectors distinct and in
  *                 ascending lexicographic order of i
  *   site_indices  L physical indices in [0, d-1]: the initial product state
- *   precision     MPS_FP64 only (other values: MPS_EINVAL)
+ *   precision     MPS_FP64, MPS_TF32 or MPS_BF16X3 (the sector GEMMs on the tensor cores, as
+ *                 for mps_create; the listed rows and columns change no kernel)
  * Bond charges are the vector sums to the right of each bond, encoded as one int32 in mixed
  * radix (first component most significant; mps_charge_radix gives the radices, each more than
  * twice the largest bond value, so differences decode uniquely and the integer order is the
@@ -498,8 +499,8 @@ MPS_API int mps_fp64_peak_probe(double* gflops, void* cuda_stream);
  * Theta(c) are the left sectors l with l - c a physical charge (in general not one contiguous
  * run of the bond table; their lambdas are gathered before the SVD).  Gate and bond-term blocks
  * are the distinct pair totals q_i + q_j in ascending order, each over its pairs (i, j), i
- * ascending (rows outputs).  Every update, measurement and sampling call applies; mps_dmrg,
- * mps_save and the tensor-core precisions are for single-U(1) handles.  Errors: MPS_EINVAL,
+ * ascending (rows outputs).  Every update, measurement and sampling call applies; mps_dmrg
+ * and mps_save are for single-U(1) handles.  Errors: MPS_EINVAL,
  * MPS_ECHARGE (a negative component, vectors not ascending, or encoded charges beyond int32),
  * MPS_ENOMEM.
  * mps_charge_radix - *ncomp and the radix of each component (radix may be NULL); 1 and 0 for

@@ -189,7 +189,7 @@ def multi_pair_blocks(charges):
 class MPS:
     """A U(1)-symmetric MPS living on the GPU (one handle of the C library); zn = n >= 2 makes it
     Z_n-symmetric instead (mps_create_zn, d = n); charges = [q_0, ..., q_{d-1}] (tuples, ascending)
-    gives physical index i the several-U(1) charge q_i (mps_create_multi, FP64): bond charges and
+    gives physical index i the several-U(1) charge q_i (mps_create_multi): bond charges and
     gate blocks are then keyed by tuples."""
 
     charges = None          # several-U(1) charge vectors (None: a single U(1) or Z_n charge)

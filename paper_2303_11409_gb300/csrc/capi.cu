@@ -1241,7 +1241,6 @@ int mps_create_multi(mps_t* out, int L, int d, int ncomp, const int32_t* phys_ch
                      int precision, int chi_max, void* cuda_stream) {
   if (out) *out = nullptr;
   if (!out || L < 2 || d < 2 || d > MPS_MAX_D || ncomp < 1 || ncomp > 4 || !phys_charges) return MPS_EINVAL;
-  if (precision != MPS_FP64) return MPS_EINVAL;
   ChargeRule r;
   r.d = d;
   r.multi = 1;

@@ -19,8 +19,11 @@ pytestmark = pytest.mark.gpu
 Q = multiu1.TWO_SPECIES_Q
 
 
-def _run(m, L, occ, J, U, dt, steps, chi, cutoff):
-    g = m.MPS(4, occ, chi, charges=Q)
+def _run(m, L, occ, J, U, dt, steps, chi, cutoff, precision=None):
+    """Both evolutions; in FP64 every bond table equals the oracle's after every layer; with
+    reduced-precision GEMMs the number of (layer, bond) tables that differ is returned."""
+    g = m.MPS(4, occ, chi, charges=Q, precision=m.MPS_FP64 if precision is None else precision)
+    differ = 0
     st = multiu1.MultiU1MPS.product(Q, occ)
     for _ in range(steps):
         for sites, f in tebd.strang_layers(L):
@@ -29,8 +32,11 @@ def _run(m, L, occ, J, U, dt, steps, chi, cutoff):
             for s, G in zip(sites, gates):
                 st.apply_gate2(s, G, chi, cutoff)
             for b in range(L + 1):
-                assert g.bond_dims(b) == st.bond[b], (b, g.bond_dims(b), st.bond[b])
-    return g, st
+                if precision is None:
+                    assert g.bond_dims(b) == st.bond[b], (b, g.bond_dims(b), st.bond[b])
+                else:
+                    differ += g.bond_dims(b) != st.bond[b]
+    return (g, st) if precision is None else (g, st, differ)
 
 
 @pytest.mark.parametrize("L,chi,steps", [(10, 24, 8), (16, 64, 10)])
@@ -67,9 +73,41 @@ def test_two_species_bosons_match_the_oracle(gpu_lib, L, chi, steps):
     g.close()
 
 
-def test_multi_handle_rejects_reduced_precision_and_bad_charges(gpu_lib):
+# stated accuracy of the reduced-precision modes against the FP64 oracle (the densities' and
+# entropies' tolerances of the single-U(1) precision tests, whose runs are of this length)
+TOL = {"tf32": dict(obs=5e-3, ent=5e-3), "bf16x3": dict(obs=8e-5, ent=1e-4)}
+
+
+@pytest.mark.parametrize("name", ["tf32", "bf16x3"])
+def test_two_species_bosons_with_tensor_core_gemms(gpu_lib, name):
+    """The sector GEMMs of a several-U(1) handle on the tensor cores (listed rows and columns
+    in the tensor-core Theta' build and reassembly); the SVD and truncation stay FP64."""
+    m = gpu_lib
+    L, chi, steps = 10, 24, 8
+    rng = np.random.default_rng(L)
+    occ = [int(x) for x in rng.integers(0, 4, L)]
+    prec = {"tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[name]
+    g, st, differ = _run(m, L, occ, 1.0, 2.0, 0.05, steps, chi, 1e-10, precision=prec)
+    t = TOL[name]
+    for b in range(L + 1):   # the truncation's invariants hold whatever the GEMM precision
+        lam = g.bond(b)
+        assert sum(len(v) for v in lam.values()) <= chi
+        assert abs(sum(float(v @ v) for v in lam.values()) - 1.0) <= 1e-12
+    nu = np.array([q[0] for q in Q], float)
+    nd = np.array([q[1] for q in Q], float)
+    dn = max(max(abs(g.expect(s, nu) - st.expect_local(s, nu)), abs(g.expect(s, nd) - st.expect_local(s, nd)))
+             for s in range(L))
+    dS = max(abs(g.entropy(b) - st.entropy(b)) for b in range(1, L))
+    print(f"two species, {name}: densities {dn:.2e}, entropies {dS:.2e}, {differ} bond tables "
+          f"(layer, bond) differing from the oracle's")
+    assert dn <= t["obs"], dn
+    assert dS <= t["ent"], dS
+    g.close()
+
+
+def test_multi_handle_rejects_bad_charges(gpu_lib):
     m = gpu_lib
     with pytest.raises(m.MPSError):
-        m.MPS(4, [0, 1, 2, 3], 8, precision=m.MPS_TF32, charges=Q)
+        m.MPS(4, [0, 1, 2, 3], 8, precision=7, charges=Q)
     with pytest.raises(m.MPSError):
         m.MPS(4, [0, 1, 2, 3], 8, charges=[(0, 0), (1, 0), (0, 1), (1, 1)])   # not ascending

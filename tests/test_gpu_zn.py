@@ -57,6 +57,34 @@ def test_zn_tebd_matches_the_oracle(gpu_lib, n, L, occ, J, f, chi, steps):
     gpu.close()
 
 
+@pytest.mark.parametrize("name,tol", [("tf32", 5e-3), ("bf16x3", 8e-5)])
+def test_zn_tensor_core_gemms_against_the_fp64_oracle(gpu_lib, name, tol):
+    """The Z_3 clock chain with the sector GEMMs on the tensor cores: <X + X^dag> within the
+    stated accuracy of the reduced-precision modes (5e-3 TF32, 8e-5 BF16x3, of the observable's
+    scale 2), unit-norm lambda and at most chi states on every bond."""
+    m = gpu_lib
+    n, L, occ, J, f, chi, steps = 3, 9, [0, 1, 2, 0, 1, 2, 0, 1, 2], 1.0, 0.6, 24, 5
+    dt, cutoff = 0.1, 1e-10
+    prec = {"tf32": m.MPS_TF32, "bf16x3": m.MPS_BF16X3}[name]
+    gpu = m.MPS(n, occ, chi, zn=n, precision=prec)
+    ref = ZnMPS.product(n, occ)
+    table = m.tebd.GateTable("clock", L, n, dt, J=J, f=f)
+    for _ in range(steps):
+        for sites, frac in m.tebd.strang_layers(L):
+            gpu.apply_layer(sites, [table(s, frac) for s in sites], chi, cutoff)
+            for s in sites:
+                ref.apply_gate2(s, ogates.clock_gate(L, s, n, J, f, frac * dt), chi, cutoff)
+    xs = 2.0 * np.cos(2.0 * np.pi * np.arange(n) / n)
+    dx = max(abs(gpu.expect(s, xs) - ref.expect_local(s, xs)) for s in range(L))
+    print(f"Z_3 clock chain, {name}: <X + X^dag> {dx:.2e}")
+    assert dx <= tol * 2.0, dx
+    for b in range(L + 1):
+        lam = gpu.bond(b)
+        assert sum(len(v) for v in lam.values()) <= chi
+        assert abs(sum(float(v @ v) for v in lam.values()) - 1.0) <= 1e-12
+    gpu.close()
+
+
 def test_zn_handle_rejects_bad_arguments(gpu_lib):
     m = gpu_lib
     with pytest.raises(m.MPSError):
