@@ -5,20 +5,25 @@ baseline may import it; the library never does, and it imports nothing from the 
 
 arXiv:2303.11409, Sec. II builds the block-sparse MPS for U(1); Sec. I and the outlook
 name more general Abelian symmetries.  This is the same construction for the cyclic
-group Z_n with local dimension d = n, the physical index i carrying charge i (mod n):
+group Z_n with local dimension d <= n, the physical index i = 0..d-1 carrying charge
+i (mod n):
   * bond b carries the right-charge c^[b] = (sum_{j >= b} i_j) mod n, c^[L] = 0;
-  * block (l, m) of site s carries the physical index i = (l - m) mod n; since d = n,
-    every pair (l, m) of charges occurs;
+  * block (l, m) of site s exists iff i = (l - m) mod n is a physical index (i < d); for
+    d = n every pair (l, m) of charges occurs;
   * the two-site gate is block diagonal in the total charge q = (i + j) mod n; block q
-    acts on the pairs (i, (q - i) mod n), i = 0..n-1 ascending (rows outputs, columns
-    inputs);
-  * Theta of an update splits by its middle charge c: rows are all left sectors l (with
-    i' = (l - c) mod n), columns all right sectors r (with j' = (c - r) mod n), and
+    acts on the pairs (i, (q - i) mod n) with both entries below d, i ascending (rows
+    outputs, columns inputs); for d < n one block can join pairs whose plain sums i + j
+    differ by n;
+  * Theta of an update splits by its middle charge c: rows are the left sectors l with
+    i' = (l - c) mod n < d, columns the right sectors r with j' = (c - r) mod n < d
+    (all of them for d = n), and
       Theta'(c)[l, r] = sum_m G_q[i', i] B^[s][l, m] B^[s+1][m, r],
       q = (l - r) mod n,  i = (l - m) mod n,
     one SVD per c, the global top-chi truncation, the inverse-free reassembly and the
     renormalisation exactly as in the U(1) oracle (same readings, same tie rule).
-Charge sectors are listed in ascending order of their residue.
+Charge sectors are listed in ascending order of their residue.  A U(1)-conserving model
+also conserves the particle number mod n, so for d < n the same evolution runs in the
+coarser Z_n blocks: each Theta(c) is a direct sum of the U(1) blocks of charges c + kn.
 """
 from __future__ import annotations
 
@@ -31,19 +36,59 @@ import scipy.linalg
 from .u1mps import NOISE_REL, SectorPlan, select_kept
 
 
-def zn_blocks_of(n: int, q: int) -> list[tuple[int, int]]:
-    """Basis of the two-site gate block of total charge q: (i, (q - i) mod n), i ascending."""
-    return [(i, (q - i) % n) for i in range(n)]
+def zn_blocks_of(n: int, q: int, d: int | None = None) -> list[tuple[int, int]]:
+    """Basis of the two-site gate block of total charge q: the pairs (i, (q - i) mod n) with
+    both entries below d (default n), i ascending."""
+    d = n if d is None else d
+    return [(i, (q - i) % n) for i in range(d) if (q - i) % n < d]
 
 
-def plan_update(left: dict, mid: dict, right: dict, n: int) -> SectorPlan:
-    """The sector structure of a Z_n two-site update (d = n): every (l, m, r) is a triple (each
-    residue difference is a physical index), every residue c = 0..n-1 a middle charge, and
-    Theta(c) has all left sectors as rows and all right sectors as columns, ascending."""
-    triples = [(l, m, r) for l in sorted(left) for m in sorted(mid) for r in sorted(right)]
-    sectors = list(range(n))
-    rows = {c: sorted(left) for c in sectors}
-    cols = {c: sorted(right) for c in sectors}
+def zn_charges(n: int, d: int | None = None) -> list[int]:
+    """The total charges q whose gate block is not empty, ascending (all of 0..n-1 for d = n)."""
+    return [q for q in range(n) if zn_blocks_of(n, q, d)]
+
+
+def gate_blocks_from_dense(G: np.ndarray, n: int, d: int) -> dict:
+    """The Z_n blocks of a two-site operator given as a d^2 x d^2 matrix on |i j>."""
+    out = {}
+    for q in zn_charges(n, d):
+        idx = [i * d + j for i, j in zn_blocks_of(n, q, d)]
+        out[q] = np.ascontiguousarray(G[np.ix_(idx, idx)], dtype=np.complex128)
+    return out
+
+
+def gate_blocks_from_u1(u1_blocks, n: int, d: int) -> dict:
+    """The Z_n blocks of a U(1)-conserving gate given by its U(1) blocks (block t over the pairs
+    (i, t - i), i ascending): a U(1) gate conserves the particle number mod n too, so block q
+    joins the U(1) blocks of totals t = q, q + n, ..., with zeros between different totals."""
+    out = {}
+    for q in zn_charges(n, d):
+        pairs = zn_blocks_of(n, q, d)
+        G = np.zeros((len(pairs), len(pairs)), dtype=np.complex128)
+        for a, (i, j) in enumerate(pairs):
+            for b, (k, l) in enumerate(pairs):
+                if i + j == k + l:
+                    base = max(0, i + j - d + 1)       # first left index of U(1) block i + j
+                    G[a, b] = u1_blocks[i + j][i - base, k - base]
+        out[q] = G
+    return out
+
+
+def plan_update(left: dict, mid: dict, right: dict, n: int, d: int | None = None) -> SectorPlan:
+    """The sector structure of a Z_n two-site update, by looping over charges: the triples
+    (l, m, r) with (l - m) mod n and (m - r) mod n below d (every triple for d = n), the
+    residues c with a row and a column, and for each the left sectors l with (l - c) mod n < d
+    as rows and the right sectors r with (c - r) mod n < d as columns, ascending."""
+    d = n if d is None else d
+    triples = [(l, m, r) for l in sorted(left) for m in sorted(mid) if (l - m) % n < d
+               for r in sorted(right) if (m - r) % n < d]
+    rows, cols, sectors = {}, {}, []
+    for c in range(n):
+        rl = [l for l in sorted(left) if (l - c) % n < d]
+        cl = [r for r in sorted(right) if (c - r) % n < d]
+        if rl and cl:
+            sectors.append(c)
+            rows[c], cols[c] = rl, cl
     return SectorPlan(triples, sectors, rows, cols)
 
 
@@ -60,38 +105,41 @@ class ZnMPS:
     bond: list = field(default_factory=list)
     lam: list = field(default_factory=list)
     B: list = field(default_factory=list)
+    d_local: int = 0          # local dimension d <= n (0: d = n)
 
     @property
     def d(self) -> int:
-        return self.n
+        return self.d_local or self.n
 
     @classmethod
-    def product(cls, n: int, occupations) -> "ZnMPS":
+    def product(cls, n: int, occupations, d: int | None = None) -> "ZnMPS":
+        d = n if d is None else int(d)
+        if not 2 <= d <= n:
+            raise ValueError("local dimension outside [2, n]")
         occ = [int(x) for x in occupations]
-        if any(not 0 <= x <= n - 1 for x in occ):
-            raise ValueError("occupation outside [0, n-1]")
+        if any(not 0 <= x <= d - 1 for x in occ):
+            raise ValueError("occupation outside [0, d-1]")
         L = len(occ)
         c = [sum(occ[b:]) % n for b in range(L + 1)]
-        st = cls(L, n, c[0])
+        st = cls(L, n, c[0], d_local=d)
         st.bond = [{c[b]: 1} for b in range(L + 1)]
         st.lam = [{c[b]: np.ones(1)} for b in range(L + 1)]
         st.B = [{(c[s], c[s + 1]): np.ones((1, 1), dtype=np.complex128)} for s in range(L)]
         return st
 
     def apply_gate2(self, s: int, G, chi: int, cutoff: float) -> dict:
-        """G[q] (q = 0..n-1): the gate on total charge q over zn_blocks_of(n, q)."""
-        n = self.n
+        """G[q] (q in zn_charges(n, d)): the gate on total charge q over zn_blocks_of(n, q, d)."""
+        n, d = self.n, self.d
         left, mid, right = self.bond[s], self.bond[s + 1], self.bond[s + 2]
         BL, BR = self.B[s], self.B[s + 1]
-        plan = plan_update(left, mid, right, n)
-        rows = plan.rows[0]
-        cols = plan.cols[0]
-        m_rows = sum(left[l] for l in rows)
-        n_cols = sum(right[r] for r in cols)
+        plan = plan_update(left, mid, right, n, d)
+        # position of the left index i inside gate block q (i itself for d = n)
+        pos = {q: {i: k for k, (i, _) in enumerate(zn_blocks_of(n, q, d))} for q in zn_charges(n, d)}
         theta = {}
         # loop over the middle charges and build Theta'(c) block by block
-        for c in range(n):
-            T = np.zeros((m_rows, n_cols), dtype=np.complex128)
+        for c in plan.sectors:
+            rows, cols = plan.rows[c], plan.cols[c]
+            T = np.zeros((sum(left[l] for l in rows), sum(right[r] for r in cols)), dtype=np.complex128)
             ro = 0
             for l in rows:
                 co = 0
@@ -102,15 +150,15 @@ class ZnMPS:
                     for m in sorted(mid):
                         if (l, m) in BL and (m, r) in BR:
                             i = (l - m) % n
-                            g = G[q][ip, i]
+                            g = G[q][pos[q][ip], pos[q][i]]
                             if g != 0:
                                 block += g * (BL[(l, m)] @ BR[(m, r)])
                     co += right[r]
                 ro += left[l]
             theta[c] = T
-        lam_rows = np.concatenate([self.lam[s][l] for l in rows])
         svals, vecs = {}, {}
-        for c in range(n):
+        for c in plan.sectors:
+            lam_rows = np.concatenate([self.lam[s][l] for l in plan.rows[c]])
             M = lam_rows[:, None] * theta[c]
             _, S, Yh = scipy.linalg.svd(M, full_matrices=False, lapack_driver="gesvd")
             S = np.where(S <= NOISE_REL * math.sqrt(float(np.sum(S * S))), 0.0, S)
@@ -118,7 +166,7 @@ class ZnMPS:
         kept, info = select_kept(svals, chi, cutoff)
         norm_kept = info["kept_norm"]
         new_mid, new_lam, new_BL, new_BR = {}, {}, {}, {}
-        for c in range(n):
+        for c in plan.sectors:
             k = kept[c]
             if k == 0:
                 continue
@@ -127,11 +175,11 @@ class ZnMPS:
             Yh = vecs[c][:k, :]
             left_part = (theta[c] @ Yh.conj().T) / norm_kept
             ro = 0
-            for l in rows:
+            for l in plan.rows[c]:
                 new_BL[(l, c)] = left_part[ro:ro + left[l], :].copy()
                 ro += left[l]
             co = 0
-            for r in cols:
+            for r in plan.cols[c]:
                 new_BR[(c, r)] = Yh[:, co:co + right[r]].copy()
                 co += right[r]
         self.bond[s + 1] = new_mid

@@ -103,3 +103,121 @@ def test_planted_sign_mistake_in_the_physical_index_is_caught():
                                                                  frac * 0.2))
     err = max(abs(st.amplitude(c) - psi[tuple(c)]) for c in np.ndindex(*psi.shape))
     assert err > 1e-3
+
+
+# ---- Z_n with d < n: a U(1) model also conserves its particle number mod n ---------------
+
+def _bh_dense_gate(L, s, d, J, U, tau):
+    wl, wr = gates.bh_weights(L, s)
+    return dense.gate_from_h(dense.bh_two_site(d, J, U, wl, wr), tau)
+
+
+def test_cyclic_gate_blocks_join_the_u1_totals_of_one_residue():
+    """d = 3, n = 4: residue 0 joins the pairs (0, 0) and (2, 2) (totals 0 and 4), residue 1 the
+    pairs (0, 1), (1, 0) and residue 3 (1, 2), (2, 1); the dense gate has no entry between
+    different totals, and each block equals the dense gate on its pairs."""
+    from oracle.znmps import gate_blocks_from_dense, gate_blocks_from_u1, zn_blocks_of, zn_charges
+    d, n, L = 3, 4, 6
+    G = _bh_dense_gate(L, 2, d, 1.0, 2.0, 0.07)
+    assert zn_charges(n, d) == [0, 1, 2, 3]
+    assert zn_blocks_of(n, 0, d) == [(0, 0), (2, 2)]
+    assert zn_blocks_of(n, 2, d) == [(0, 2), (1, 1), (2, 0)]
+    blocks = gate_blocks_from_dense(G, n, d)
+    assert blocks[0][0, 1] == 0 and blocks[0][1, 0] == 0
+    assert blocks[0][0, 0] == G[0, 0] and blocks[0][1, 1] == G[8, 8]
+    # the same blocks from the U(1) gate (eigh per total) agree to rounding
+    u1 = gates.bh_gate(L, 2, d, 1.0, 2.0, 0.07)
+    for q, b in gate_blocks_from_u1(u1, n, d).items():
+        assert np.max(np.abs(b - blocks[q])) < 1e-13
+
+
+@pytest.mark.parametrize("d,n,L,occ", [
+    (3, 4, 6, [1, 0, 2, 1, 0, 1]),
+    (3, 5, 6, [2, 0, 2, 1, 2, 0]),
+    (2, 3, 8, [1, 0, 1, 1, 0, 0, 1, 0]),
+])
+def test_untruncated_zn_with_d_below_n_equals_dense_evolution(d, n, L, occ):
+    from oracle.znmps import gate_blocks_from_dense
+    J, U, dt, steps = 1.0, 2.0, 0.1, 3
+    st = ZnMPS.product(n, occ, d=d)
+    psi = dense.product_state(d, occ)
+    for _ in range(steps):
+        for sites, frac in _schedule(L):
+            for s in sites:
+                G = _bh_dense_gate(L, s, d, J, U, frac * dt)
+                st.apply_gate2(s, gate_blocks_from_dense(G, n, d), 10 ** 6, 0.0)
+                psi = dense.apply_two_site(psi, s, G)
+    nop = np.arange(d, dtype=float)
+    for s in range(L):
+        assert abs(st.expect_local(s, nop) - dense.mean_op(psi, s, nop)) < 1e-11
+    for b in range(1, L):
+        assert abs(st.entropy(b) - dense.bond_entropy(psi, b)) < 1e-10
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        cfg = rng.integers(0, d, size=L)
+        assert abs(st.amplitude(cfg) - psi[tuple(cfg)]) < 1e-12
+    # some bond carries more U(1) charges (particles right of it, with weight) than Z_n sectors:
+    # charges c and c + n share one Z_n sector there
+    occ_idx = np.indices(psi.shape)
+    p = np.abs(psi) ** 2
+    merged = False
+    for b in range(1, L):
+        right = occ_idx[b:].sum(axis=0)
+        charges = {int(c) for c in np.unique(right) if p[right == c].sum() > 1e-20}
+        merged = merged or len(charges) > len(st.bond[b])
+    assert merged
+
+
+def test_truncated_zn_with_d_below_n_equals_the_u1_run():
+    """With truncation the Z_n run of a Bose-Hubbard chain is the U(1) run in coarser blocks:
+    each Theta(c) of the Z_n update is a direct sum of the U(1) blocks of charges c + kn, so
+    the pooled singular values, the kept set and the state are the same (no ties at the cuts
+    of this asymmetric start): per bond the sorted Schmidt values agree to 1e-12, the Z_n
+    dimensions are the U(1) ones summed per residue, densities and entropies agree."""
+    from oracle import U1MPS
+    from oracle.znmps import gate_blocks_from_u1
+    d, n, L, chi, steps = 3, 4, 10, 12, 4
+    occ = [2, 0, 1, 1, 0, 2, 1, 1, 0, 1]
+    J, U, dt = 1.0, 2.0, 0.1
+    zs = ZnMPS.product(n, occ, d=d)
+    us = U1MPS.product(d, occ)
+    cut_seen = False
+    for _ in range(steps):
+        for sites, frac in _schedule(L):
+            for s in sites:
+                u1 = gates.bh_gate(L, s, d, J, U, frac * dt)
+                us.apply_gate2(s, u1, chi, 1e-10)
+                zs.apply_gate2(s, gate_blocks_from_u1(u1, n, d), chi, 1e-10)
+            for b in range(L + 1):
+                merged = {}
+                for c, k in us.bond[b].items():
+                    merged[c % n] = merged.get(c % n, 0) + k
+                assert zs.bond[b] == merged, (b, zs.bond[b], us.bond[b])
+                lz = np.sort(np.concatenate(list(zs.lam[b].values())))
+                lu = np.sort(np.concatenate(list(us.lam[b].values())))
+                assert np.max(np.abs(lz - lu)) < 1e-12
+                cut_seen = cut_seen or sum(us.bond[b].values()) == chi
+    assert cut_seen, "the chi cut never became active"
+    nop = np.arange(d, dtype=float)
+    for s in range(L):
+        assert abs(zs.expect_local(s, nop) - us.expect_local(s, nop)) < 1e-10
+    for b in range(1, L):
+        assert abs(zs.entropy(b) - us.entropy(b)) < 1e-10
+
+
+def test_planted_wrong_residue_block_fails_the_dense_pin():
+    """Swapping the two pairs of residue 0 (a wrong gate position for d < n) breaks the pin."""
+    from oracle.znmps import gate_blocks_from_dense
+    d, n, L, occ = 3, 4, 6, [1, 0, 2, 1, 0, 1]
+    st = ZnMPS.product(n, occ, d=d)
+    psi = dense.product_state(d, occ)
+    for sites, frac in _schedule(L):
+        for s in sites:
+            G = _bh_dense_gate(L, s, d, 1.0, 2.0, frac * 0.1)
+            blocks = gate_blocks_from_dense(G, n, d)
+            blocks[0] = blocks[0][::-1, ::-1].copy()
+            st.apply_gate2(s, blocks, 10 ** 6, 0.0)
+            psi = dense.apply_two_site(psi, s, G)
+    rng = np.random.default_rng(5)
+    cfgs = [rng.integers(0, d, size=L) for _ in range(200)]
+    assert max(abs(st.amplitude(c) - psi[tuple(c)]) for c in cfgs) > 1e-6
