@@ -119,6 +119,22 @@ MPS_API int mps_create_segment(mps_t* out, int L, int d, const int32_t* site_cha
 MPS_API int mps_create_zn(mps_t* out, int L, int n, const int32_t* site_charges, int precision, int chi_max,
                           void* cuda_stream);
 
+/*
+ * mps_create_cyclic - a Z_n handle whose local dimension d may be below n (2 <= d <= n <=
+ * 2^20; d = n is mps_create_zn).  The physical index i = 0..d-1 carries charge i mod n, bond
+ * b the residue of the occupations right of it, and a site block (l, m) exists iff
+ * (l - m) mod n < d; a Theta(c) then has as rows the left sectors l with (l - c) mod n < d,
+ * in general not one run of the bond table (the update lists them and gathers their lambda).
+ * Gate blocks are the residues q = (i + j) mod n reached by some pair, ascending, each over
+ * its pairs (i, (q - i) mod n) with both entries below d, i ascending (rows outputs, columns
+ * inputs), concatenated row-major.  A U(1)-conserving model (for example Bose-Hubbard with
+ * n_max = d - 1) also conserves the particle number mod n; its U(1) gate blocks of totals
+ * t = q, q + n, ... then sit in block q.  Calls as for mps_create_zn handles.  Errors:
+ * MPS_EINVAL (d or n out of range), as mps_create otherwise.
+ */
+MPS_API int mps_create_cyclic(mps_t* out, int L, int d, int n, const int32_t* site_charges, int precision,
+                              int chi_max, void* cuda_stream);
+
 MPS_API int mps_destroy(mps_t h);
 
 /* mps_last_error - message of the last failing call on h ("" if none); owned by h. */
@@ -578,7 +594,8 @@ MPS_API int mps_plan_sectors(int d, int nl, const int32_t* lc, const int32_t* ld
 /*
  * mps_plan_sectors_rule - the sector planner of mps_plan_sectors for every charge rule a handle
  * can have (host code, no GPU needed): U(1) (zn = 0, ncomp = 0, as mps_plan_sectors), Z_n
- * (zn = n = d, as mps_create_zn) and several U(1) charges (ncomp >= 1, as mps_create_multi).
+ * (zn = n >= d, as mps_create_zn and mps_create_cyclic) and several U(1) charges (ncomp >= 1,
+ * as mps_create_multi).
  * Sec. II's Kronecker deltas give the blocks: (l, m) is a site block iff l - m is the charge of
  * a physical index (taken mod n for Z_n, as a vector for several charges), and Theta(c) has as
  * rows the left sectors l with l - c such a charge and as columns the right sectors r with
@@ -593,7 +610,7 @@ MPS_API int mps_plan_sectors(int d, int nl, const int32_t* lc, const int32_t* ld
  *                 column sectors), c ascending
  *   lists         out, per sector its row sector charges then its column sector charges
  *   n_triples, n_sectors, n_lists  sizes written; MPS_EINVAL if a capacity is too small, for
- *                 zn != d, or for zn and ncomp both set
+ *                 zn < d or zn > 2^20, or for zn and ncomp both set
  */
 MPS_API int mps_plan_sectors_rule(int d, int zn, int ncomp, const int32_t* phys_charges, const int32_t* radix,
                      int nl, const int32_t* lc, const int32_t* ld,

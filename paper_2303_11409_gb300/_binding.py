@@ -118,6 +118,8 @@ _SIGS = {
     "mps_set_chi_deflation": (ctypes.c_int, [_h, ctypes.c_double]),
     "mps_create_zn": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int,
                                      ctypes.c_int, _vp]),
+    "mps_create_cyclic": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p,
+                                         ctypes.c_int, ctypes.c_int, _vp]),
     "mps_zgemm_tc_work_bytes": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mps_svd_mixed_min_k": (ctypes.c_int, [ctypes.c_int]),
     "mps_svd_mixed_sweeps": (ctypes.c_int, [ctypes.c_int]),
@@ -186,9 +188,20 @@ def multi_pair_blocks(charges):
     return {Q: sorted(tot[Q]) for Q in sorted(tot)}
 
 
+def cyclic_pair_blocks(n: int, d: int):
+    """Two-site gate layout of a Z_n handle with local dimension d <= n: the residues q = (i + j)
+    mod n that some pair reaches, ascending, each with its pairs (i, (q - i) mod n), i ascending."""
+    out = {}
+    for q in range(n):
+        pairs = [(i, (q - i) % n) for i in range(d) if (q - i) % n < d]
+        if pairs:
+            out[q] = pairs
+    return out
+
+
 class MPS:
-    """A U(1)-symmetric MPS living on the GPU (one handle of the C library); zn = n >= 2 makes it
-    Z_n-symmetric instead (mps_create_zn, d = n); charges = [q_0, ..., q_{d-1}] (tuples, ascending)
+    """A U(1)-symmetric MPS living on the GPU (one handle of the C library); zn = n >= d makes it
+    Z_n-symmetric instead (mps_create_zn for d = n, mps_create_cyclic for d < n); charges = [q_0, ..., q_{d-1}] (tuples, ascending)
     gives physical index i the several-U(1) charge q_i (mps_create_multi): bond charges and
     gate blocks are then keyed by tuples."""
 
@@ -222,10 +235,14 @@ class MPS:
             self.N = tuple(sum(self.charges[i][k] for i in occ) for k in range(nc))
             return
         if self.zn:
-            if self.zn != self.d:
-                raise ValueError("a Z_n handle has d = n")
-            rc = lib.mps_create_zn(ctypes.byref(h), self.L, self.zn, _ptr(occ, _i32p), precision, self.chi_max,
-                                   self.stream)
+            if self.zn < self.d:
+                raise ValueError("a Z_n handle has d <= n")
+            if self.zn == self.d:
+                rc = lib.mps_create_zn(ctypes.byref(h), self.L, self.zn, _ptr(occ, _i32p), precision,
+                                       self.chi_max, self.stream)
+            else:
+                rc = lib.mps_create_cyclic(ctypes.byref(h), self.L, self.d, self.zn, _ptr(occ, _i32p), precision,
+                                           self.chi_max, self.stream)
         else:
             rc = lib.mps_create(ctypes.byref(h), self.L, self.d, _ptr(occ, _i32p), precision, self.chi_max,
                                 self.stream)
@@ -253,8 +270,11 @@ class MPS:
         return _c128_flat(gate)
 
     def gate_length(self) -> int:
+        """Complex numbers in one flattened gate of this handle's charge rule."""
         if self.charges is not None:
             return sum(len(p) ** 2 for p in self._pairs.values())
+        if getattr(self, "zn", 0):
+            return sum(len(p) ** 2 for p in cyclic_pair_blocks(self.zn, self.d).values())
         return gate_length(self.d)
 
     # -- checkpoint -------------------------------------------------------------
@@ -323,6 +343,8 @@ class MPS:
         gs = [self._gate_flat(g) for g in gates]
         if len(gs) != len(sites):
             raise ValueError("one gate per site")
+        if any(g.size != self.gate_length() for g in gs):
+            raise ValueError("a gate has the wrong number of entries")
         arr = (_dblp * len(gs))(*[g.ctypes.data_as(_dblp) for g in gs])
         te = np.zeros(len(gs))
         rc = lib.mps_apply_layer(self._h, len(gs), _ptr(sites, _intp), arr, chi, cutoff, _ptr(te, _dblp))
@@ -574,6 +596,8 @@ class Executor:
         hs = (_h * n)(*[it[0].handle for it in items])
         sites = np.array([it[1] for it in items], dtype=np.intc)
         gs = [_c128_flat(it[2]) for it in items]
+        if any(g.size != it[0].gate_length() for g, it in zip(gs, items)):
+            raise ValueError("a gate has the wrong number of entries")
         garr = (_dblp * n)(*[g.ctypes.data_as(_dblp) for g in gs])
         chis = np.array([it[3] for it in items], dtype=np.intc)
         cuts = np.array([it[4] for it in items], dtype=np.float64)
@@ -711,7 +735,9 @@ def apply_gate2_batch(items, stream_owner: MPS | None = None):
     n = len(items)
     hs = (_h * n)(*[it[0].handle for it in items])
     sites = np.array([it[1] for it in items], dtype=np.intc)
-    gs = [_c128_flat(it[2]) for it in items]
+    gs = [it[0]._gate_flat(it[2]) for it in items]
+    if any(g.size != it[0].gate_length() for g, it in zip(gs, items)):
+        raise ValueError("a gate has the wrong number of entries")
     garr = (_dblp * n)(*[g.ctypes.data_as(_dblp) for g in gs])
     chis = np.array([it[3] for it in items], dtype=np.intc)
     cuts = np.array([it[4] for it in items], dtype=np.float64)
@@ -746,7 +772,7 @@ def plan_sectors(d: int, left: dict, mid: dict, right: dict):
 def plan_sectors_rule(d: int, left: dict, mid: dict, right: dict, zn: int = 0, charges=None, radix=None):
     """The library's sector planner under any charge rule (mps_plan_sectors_rule).
 
-    zn: n of a Z_n rule (d = n).  charges: d charge vectors of a several-U(1) rule, with the
+    zn: n of a Z_n rule (d <= n).  charges: d charge vectors of a several-U(1) rule, with the
     tables keyed by charge tuples and radix the mixed radix of their encoding (default: each
     component's radix 2 * (largest table value) + 3).  Returns (triples, sectors) with
     triples a list of (l, m, r) and sectors a list of (c, rows, cols, row charges, column

@@ -1237,6 +1237,18 @@ int mps_create_zn(mps_t* out, int L, int n, const int32_t* site_charges, int pre
   return create_handle(out, L, n, site_charges, 0, L, precision, chi_max, cuda_stream, n);
 }
 
+int mps_create_cyclic(mps_t* out, int L, int d, int n, const int32_t* site_charges, int precision, int chi_max,
+                      void* cuda_stream) {
+  if (out) *out = nullptr;
+  if (!out || d < 2 || d > MPS_MAX_D || n < d || n > kMaxZn) return MPS_EINVAL;
+  if (n == d) return create_handle(out, L, n, site_charges, 0, L, precision, chi_max, cuda_stream, n);
+  ChargeRule r;
+  r.d = d;
+  r.zn = n;
+  r.init_zn();
+  return create_handle(out, L, d, site_charges, 0, L, precision, chi_max, cuda_stream, n, &r);
+}
+
 int mps_create_multi(mps_t* out, int L, int d, int ncomp, const int32_t* phys_charges, const int32_t* site_indices,
                      int precision, int chi_max, void* cuda_stream) {
   if (out) *out = nullptr;

@@ -22,6 +22,8 @@ constexpr int kSvdSideStreams = 4;      // side streams for concurrent SVD kerne
 // block's rows and columns are contiguous runs of the sorted bond tables (for Z_n with
 // d = n: all sectors).
 // ---------------------------------------------------------------------------
+constexpr int kMaxZn = 1 << 20;   // largest n of a Z_n handle (bond charges are residues)
+
 struct ChargeRule {
   int d = 2;
   int zn = 0;
@@ -34,6 +36,11 @@ struct ChargeRule {
   // Two-site gate blocks are the distinct totals q[i] + q[j], ascending, each over its pairs
   // (i, j) with i ascending.
   int multi = 0;
+  // Z_n with d < n (ztab = 1): physical index i = 0..d-1 carries charge i mod n; a block (l, m)
+  // exists iff (l - m) mod n < d, and the two-site gate blocks are the residues q = (i + j) mod n
+  // that some pair reaches, ascending, each over its pairs (i, (q - i) mod n), i ascending (the
+  // tables below, filled by init_zn; for d = n every residue has all n pairs and no table is used)
+  int ztab = 0;
   int q[MPS_MAX_D] = {};
   int ncomp = 1;
   int radix[4] = {1, 1, 1, 1};
@@ -43,6 +50,8 @@ struct ChargeRule {
   int64_t off2[MPS_MAX_D * MPS_MAX_D + 1] = {};
   signed char pos2[MPS_MAX_D * MPS_MAX_D][MPS_MAX_D] = {};
   void init_multi();                       // fills the two-site block tables from q[]
+  void init_zn();                          // fills them for Z_n with d < n (sets ztab)
+  bool tabled() const { return multi || ztab; }
   int wrap(int c) const { return zn ? ((c % zn) + zn) % zn : c; }
   int phys(int l, int m) const {           // physical index of block (l, m), or -1
     if (multi) {
@@ -56,8 +65,8 @@ struct ChargeRule {
   }
   int charge_of(int i) const { return multi ? q[i] : i; }   // (encoded) charge of physical index i
   int pair(int l, int r) const {           // two-site gate block of (l, r), or -1
-    if (multi) {
-      const int x = l - r;
+    if (tabled()) {
+      const int x = ztab ? wrap(l - r) : l - r;
       int lo = 0, hi = nb2 - 1;
       while (lo <= hi) {
         const int mid = (lo + hi) / 2;
@@ -70,15 +79,15 @@ struct ChargeRule {
     const int q_ = l - r;
     return (q_ >= 0 && q_ <= 2 * (d - 1)) ? q_ : -1;
   }
-  int nblocks() const { return multi ? nb2 : (zn ? zn : 2 * d - 1); }
+  int nblocks() const { return tabled() ? nb2 : (zn ? zn : 2 * d - 1); }
   int base(int q_) const { return zn ? 0 : (q_ - d + 1 > 0 ? q_ - d + 1 : 0); }   // first left index of block q (U(1))
   int sn(int k) const {
-    if (multi) return sn2[k];
+    if (tabled()) return sn2[k];
     return zn ? zn : (k < d - 1 ? k : d - 1) - base(k) + 1;
   }
-  int gpos(int k, int i) const { return multi ? pos2[k][i] : i - base(k); }   // row of left index i in block k
+  int gpos(int k, int i) const { return tabled() ? pos2[k][i] : i - base(k); }   // row of left index i in block k
   int64_t block_off(int k) const {
-    if (multi) return off2[k];
+    if (tabled()) return off2[k];
     int64_t t = 0;
     for (int j = 0; j < k; ++j) t += (int64_t)sn(j) * sn(j);
     return t;
@@ -93,6 +102,16 @@ struct ChargeRule {
     if (multi) {
       for (int i = d - 1; i >= 0; --i)
         if (phys(l - q[i], r) >= 0) out[n++] = l - q[i];
+      return n;
+    }
+    if (ztab) {   // c = (l - i) mod n for a physical i, with (c - r) mod n < d; ascending
+      for (int i = 0; i < d; ++i) {
+        const int c = wrap(l - i);
+        if (phys(c, r) < 0) continue;
+        int k = n++;
+        for (; k > 0 && out[k - 1] > c; --k) out[k] = out[k - 1];
+        out[k] = c;
+      }
       return n;
     }
     for (int c = cmin(l, r); c <= cmax(l, r); ++c) out[n++] = c;

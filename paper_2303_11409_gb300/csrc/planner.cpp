@@ -93,6 +93,26 @@ void ChargeRule::init_multi() {
   off2[nb2] = off;
 }
 
+void ChargeRule::init_zn() {
+  ztab = 1;
+  nb2 = 0;
+  int64_t off = 0;
+  for (int t = 0; t < zn; ++t) {
+    int n = 0;
+    for (int i = 0; i < d; ++i) {
+      pos2[nb2][i] = -1;
+      if (wrap(t - i) < d) pos2[nb2][i] = (signed char)n++;
+    }
+    if (n == 0) continue;
+    q2[nb2] = t;
+    sn2[nb2] = n;
+    off2[nb2] = off;
+    off += (int64_t)n * n;
+    ++nb2;
+  }
+  off2[nb2] = off;
+}
+
 static void fill_lists(const BondTable& left, const BondTable& right, SectorPlanEntry& e) {
   e.loff.clear();
   e.coff.clear();
@@ -120,9 +140,10 @@ void plan_update(const BondTable& left, const BondTable& mid, const BondTable& r
       }
     }
   if (left.size() == 0 || right.size() == 0) return;
-  if (rule.multi) {
-    // several U(1) charges: every middle charge some (l, r) pair reaches, with the left sectors
-    // l - c and the right sectors c - r among the physical charges as rows and columns
+  if (rule.tabled()) {
+    // several U(1) charges, or Z_n with d < n: every middle charge some (l, r) pair reaches,
+    // with the left sectors l - c and the right sectors c - r among the physical charges (mod n
+    // for Z_n) as rows and columns
     std::vector<int> cands;
     int buf[MPS_MAX_D];
     for (int i = 0; i < left.size(); ++i)
@@ -231,10 +252,11 @@ extern "C" int mps_plan_sectors_rule(int d, int zn, int ncomp, const int32_t* ph
                                      int32_t* lists, int cap_lists, int* n_lists) {
   if (d < 2 || d > MPS_MAX_D || !n_triples || !n_sectors || !n_lists) return MPS_EINVAL;
   if (zn < 0 || ncomp < 0 || ncomp > 4 || (zn && ncomp)) return MPS_EINVAL;
-  if (zn && zn != d) return MPS_EINVAL;                    // Z_n is built for d = n
+  if (zn && (zn < d || zn > kMaxZn)) return MPS_EINVAL;   // Z_n with d <= n
   ChargeRule rule;
   rule.d = d;
   rule.zn = zn;
+  if (zn && d < zn) rule.init_zn();
   if (ncomp) {
     if (!phys_charges || !radix) return MPS_EINVAL;
     rule.multi = 1;

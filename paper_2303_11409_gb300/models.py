@@ -6,7 +6,8 @@ blocks G_n over the basis (i, n - i), i ascending (the layout of the C ABI).
 Models: XXZ chain, Bose-Hubbard chain, boson-sampling beam splitter (the U(1)
 examples of arXiv:2303.11409, Sec. I), and the Z_n clock chain for the cyclic-group
 handles (mps_create_zn; n = 2 is the transverse-field Ising chain): its gates have the n
-blocks q = (i + j) mod n over the pairs (i, (q - i) mod n), i ascending.
+blocks q = (i + j) mod n over the pairs (i, (q - i) mod n), i ascending.  cyclic_blocks
+regroups a U(1) gate for a Z_n handle with d < n (mps_create_cyclic).
 """
 from __future__ import annotations
 
@@ -103,6 +104,28 @@ def clock_gate(n: int, J: float, f: float, tau: float, w_left: float, w_right: f
             h[(a + 1) % n, a] += -J        # Z1 Z2^dag
             h[(a - 1) % n, a] += -J        # its adjoint
         out.append(scipy.linalg.expm(-1j * tau * h))
+    return out
+
+
+def cyclic_blocks(u1_blocks, d: int, n: int) -> list[np.ndarray]:
+    """The gate of a U(1)-conserving model in the layout of a Z_n handle with local dimension
+    d <= n (mps_create_cyclic): the particle number mod n is conserved too, so the Z_n block of
+    residue q holds the U(1) blocks of the totals t = q, q + n, ... (zero between different t),
+    over the pairs (i, (q - i) mod n) with both entries below d, i ascending; residues that no
+    pair reaches are left out."""
+    out = []
+    for q in range(n):
+        pairs = [(i, (q - i) % n) for i in range(d) if (q - i) % n < d]
+        if not pairs:
+            continue
+        G = np.zeros((len(pairs), len(pairs)), dtype=np.complex128)
+        for a, (i, j) in enumerate(pairs):
+            for b, (k, l) in enumerate(pairs):
+                t = i + j
+                if k + l == t:
+                    lo = max(0, t - d + 1)
+                    G[a, b] = u1_blocks[t][i - lo, k - lo]
+        out.append(G)
     return out
 
 

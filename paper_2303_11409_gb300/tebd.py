@@ -44,6 +44,8 @@ class GateTable:
                 blocks = models.bose_hubbard_gate(self.d, self.p.get("J", 1.0), self.p["U"], tau, wl, wr)
             else:
                 raise ValueError(self.model)
+            if self.p.get("zn") and self.model != "clock":   # a U(1) model on a Z_n handle (d < n)
+                blocks = models.cyclic_blocks(blocks, self.d, int(self.p["zn"]))
             g = models.flatten(blocks)
             self._cache[key] = g
         return g

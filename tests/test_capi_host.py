@@ -127,16 +127,18 @@ def test_rule_planner_u1_equals_the_u1_planner(built, d):
         _check_rule_plan(m.plan_sectors_rule(d, left, mid, right), plan_update(left, mid, right, d), left, right)
 
 
-@pytest.mark.parametrize("n", [2, 3, 4, 7])
-def test_rule_planner_matches_the_zn_oracle(built, n):
-    """Z_n, d = n (oracle/znmps.py): all triples, every residue a sector, all rows and columns."""
+@pytest.mark.parametrize("n,d", [(2, 2), (3, 3), (4, 4), (7, 7), (3, 2), (4, 3), (5, 3), (7, 4), (9, 5)])
+def test_rule_planner_matches_the_zn_oracle(built, n, d):
+    """Z_n (oracle/znmps.py): for d = n all triples, every residue a sector, all rows and
+    columns; for d < n the triples, sectors, rows and columns whose residue differences are
+    physical indices (listed, in general not one run of the table)."""
     import paper_2303_11409_gb300 as m
     from oracle import znmps
-    rng = np.random.default_rng(400 + n)
+    rng = np.random.default_rng(400 + 10 * n + d)
     for _ in range(20):
         left, mid, right = (_rand_table(rng, 0, n - 1) for _ in range(3))
-        got = m.plan_sectors_rule(n, left, mid, right, zn=n)
-        _check_rule_plan(got, znmps.plan_update(left, mid, right, n), left, right)
+        got = m.plan_sectors_rule(d, left, mid, right, zn=n)
+        _check_rule_plan(got, znmps.plan_update(left, mid, right, n, d), left, right)
 
 
 def _rand_tuple_table(rng, lo, hi, k):
@@ -172,7 +174,7 @@ def test_rule_planner_rejects_bad_rules(built):
     import paper_2303_11409_gb300 as m
     t = {0: 1, 1: 2}
     with pytest.raises(m.MPSError):
-        m.plan_sectors_rule(3, t, t, t, zn=4)                  # Z_n only for d = n
+        m.plan_sectors_rule(3, t, t, t, zn=2)                  # Z_n only for d <= n
     with pytest.raises(m.MPSError):
         m.plan_sectors_rule(3, {0: 1, 3: 1}, t, t, zn=3)       # residue outside [0, n-1]
     q = [(0, 0), (0, 1), (1, 0), (1, 1)]
