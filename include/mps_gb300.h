@@ -113,7 +113,7 @@ MPS_API int mps_create_segment(mps_t* out, int L, int d, const int32_t* site_cha
  * a site block (l, m) with i = (l - m) mod n.  Gate blocks for such a handle are the n blocks
  * q = 0..n-1 of the total charge (i + j) mod n, each n x n over the pairs (i, (q - i) mod n),
  * i ascending (rows outputs, columns inputs), concatenated row-major.  Every update, batch,
- * observable and amplitude call works on it; mps_save / mps_load, mps_create_segment and
+ * observable, amplitude and checkpoint call works on it; mps_create_segment and
  * mps_footprint_bytes are for U(1) handles only.  Errors as mps_create.
  */
 MPS_API int mps_create_zn(mps_t* out, int L, int n, const int32_t* site_charges, int precision, int chi_max,
@@ -455,18 +455,19 @@ MPS_API int mps_autotune_min_flops(double flops);
 MPS_API int mps_last_batch_sweeps(mps_t h, int* n_sectors, int64_t* sweeps_sum, int* sweeps_max);
 
 /*
- * mps_save - writes the current state of h (bond charge tables and Schmidt values,
- * site blocks) to the file `path` (created or truncated).  The file holds the
+ * mps_save - writes the current state of h (its charge rule: U(1), Z_n or several U(1)
+ * charges; bond charge tables and Schmidt values, site blocks, and each bond's deflation
+ * history) to the file `path` (created or truncated).  The file holds the
  * right-canonical B = Gamma lambda form the updates keep (Sec. II), so a handle
  * loaded from it continues the evolution bit for bit.  Synchronises h's stream.
  * Errors: MPS_EINVAL (NULL arguments, a site awaiting mps_set_site, I/O failure;
  * mps_last_error says which), MPS_ECUDA.
  *
  * mps_load - a new handle with the state stored by mps_save, on cuda_stream (as in
- * mps_create).  The stored L, d, N, chi_max and precision are reused.  The library
- * owns the handle; free it with mps_destroy.  Errors: MPS_EINVAL (unreadable,
+ * mps_create).  The stored charge rule, L, d, N, chi_max and precision are reused.  The
+ * library owns the handle; free it with mps_destroy.  Errors: MPS_EINVAL (unreadable,
  * truncated or foreign file), MPS_ECHARGE (charge tables or blocks that violate the
- * U(1) structure), MPS_ENOMEM, MPS_ECUDA; *out is NULL on error.
+ * charge structure), MPS_ENOMEM, MPS_ECUDA; *out is NULL on error.
  * The paper describes no checkpoint; this pair exists for long runs and serving.
  */
 MPS_API int mps_save(mps_t h, const char* path);
@@ -515,8 +516,8 @@ MPS_API int mps_fp64_peak_probe(double* gflops, void* cuda_stream);
  * Theta(c) are the left sectors l with l - c a physical charge (in general not one contiguous
  * run of the bond table; their lambdas are gathered before the SVD).  Gate and bond-term blocks
  * are the distinct pair totals q_i + q_j in ascending order, each over its pairs (i, j), i
- * ascending (rows outputs).  Every update, measurement and sampling call applies; mps_dmrg
- * and mps_save are for single-U(1) handles.  Errors: MPS_EINVAL,
+ * ascending (rows outputs).  Every update, measurement, sampling and checkpoint call applies;
+ * mps_dmrg and mps_tdvp are for single-U(1) handles.  Errors: MPS_EINVAL,
  * MPS_ECHARGE (a negative component, vectors not ascending, or encoded charges beyond int32),
  * MPS_ENOMEM.
  * mps_charge_radix - *ncomp and the radix of each component (radix may be NULL); 1 and 0 for
@@ -525,6 +526,15 @@ MPS_API int mps_fp64_peak_probe(double* gflops, void* cuda_stream);
 MPS_API int mps_create_multi(mps_t* out, int L, int d, int ncomp, const int32_t* phys_charges,
                              const int32_t* site_indices, int precision, int chi_max, void* cuda_stream);
 MPS_API int mps_charge_radix(mps_t h, int* ncomp, int32_t* radix);
+
+/*
+ * mps_charge_rule - the charge rule of a handle: *zn = n for a Z_n handle (0 otherwise),
+ * *ncomp = the number of charge components of a several-U(1) handle (0 otherwise), and for
+ * such a handle its d charge vectors into phys_charges (d x ncomp row-major, as passed to
+ * mps_create_multi).  Any pointer may be NULL.  A handle from mps_load reports the rule it
+ * was saved with.
+ */
+MPS_API int mps_charge_rule(mps_t h, int* zn, int* ncomp, int32_t* phys_charges);
 
 /*
  * mps_dmrg - two-site DMRG sweeps on the state of h (ground states of the U(1) chains the

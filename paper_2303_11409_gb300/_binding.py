@@ -130,6 +130,7 @@ _SIGS = {
     "mps_create_multi": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p,
                                         ctypes.c_int, ctypes.c_int, _vp]),
     "mps_charge_radix": (ctypes.c_int, [_h, _intp, _i32p]),
+    "mps_charge_rule": (ctypes.c_int, [_h, _intp, _intp, _i32p]),
     "mps_svd_cluster_min_k": (ctypes.c_int, [ctypes.c_int]),
     "mps_tdvp": (ctypes.c_int, [_h, ctypes.POINTER(_dblp), ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                 ctypes.c_double, ctypes.c_int, ctypes.c_double, _dblp, ctypes.c_int, _intp]),
@@ -223,15 +224,7 @@ class MPS:
             if rc != MPS_OK:
                 raise MPSError(rc, "mps_create_multi failed")
             self._h = h
-            ncomp = ctypes.c_int(0)
-            rad = np.zeros(4, np.int32)
-            lib.mps_charge_radix(h, ctypes.byref(ncomp), _ptr(rad, _i32p))
-            w, self._weights = 1, [0] * nc
-            for k in range(nc - 1, -1, -1):
-                self._weights[k] = w
-                w *= int(rad[k])
-            self._radix = [int(x) for x in rad[:nc]]
-            self._pairs = multi_pair_blocks(self.charges)
+            self._set_multi_keys()
             self.N = tuple(sum(self.charges[i][k] for i in occ) for k in range(nc))
             return
         if self.zn:
@@ -252,6 +245,19 @@ class MPS:
         self.N = int(occ.sum()) % self.zn if self.zn else int(occ.sum())
 
     # -- several-U(1) charge keys -------------------------------------------------
+    def _set_multi_keys(self):
+        """The encoding weights, radices and gate layout of a several-U(1) handle."""
+        nc = len(self.charges[0])
+        ncomp = ctypes.c_int(0)
+        rad = np.zeros(4, np.int32)
+        lib.mps_charge_radix(self._h, ctypes.byref(ncomp), _ptr(rad, _i32p))
+        w, self._weights = 1, [0] * nc
+        for k in range(nc - 1, -1, -1):
+            self._weights[k] = w
+            w *= int(rad[k])
+        self._radix = [int(x) for x in rad[:nc]]
+        self._pairs = multi_pair_blocks(self.charges)
+
     def _enc(self, c):
         return int(sum(x * w for x, w in zip(c, self._weights))) if self.charges is not None else int(c)
 
@@ -295,6 +301,14 @@ class MPS:
         L, d, N, chi, prec = (ctypes.c_int() for _ in range(5))
         lib.mps_info(h, ctypes.byref(L), ctypes.byref(d), ctypes.byref(N), ctypes.byref(chi), ctypes.byref(prec))
         obj.L, obj.d, obj.N, obj.chi_max = L.value, d.value, N.value, chi.value
+        zn, nc = ctypes.c_int(0), ctypes.c_int(0)
+        q = np.zeros(4 * MPS_MAX_D, np.int32)
+        lib.mps_charge_rule(h, ctypes.byref(zn), ctypes.byref(nc), _ptr(q, _i32p))
+        obj.zn = zn.value
+        if nc.value:
+            obj.charges = [tuple(int(x) for x in q[i * nc.value:(i + 1) * nc.value]) for i in range(obj.d)]
+            obj._set_multi_keys()
+            obj.N = obj._dec(obj.N)
         return obj
 
     # -- lifetime ---------------------------------------------------------------

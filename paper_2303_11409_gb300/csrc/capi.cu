@@ -1283,6 +1283,22 @@ int mps_create_multi(mps_t* out, int L, int d, int ncomp, const int32_t* phys_ch
   return create_handle(out, L, d, site_indices, 0, L, precision, chi_max, cuda_stream, 0, &r);
 }
 
+int mps_charge_rule(mps_t h, int* zn, int* ncomp, int32_t* phys_charges) {
+  if (!h) return MPS_EINVAL;
+  const ChargeRule& R = h->rule;
+  if (zn) *zn = R.zn;
+  if (ncomp) *ncomp = R.multi ? R.ncomp : 0;
+  if (phys_charges && R.multi)
+    for (int i = 0; i < h->d; ++i) {   // decode q_i, first component most significant
+      int64_t v = R.q[i];
+      for (int k = R.ncomp - 1; k >= 0; --k) {
+        phys_charges[i * R.ncomp + k] = (int32_t)(v % R.radix[k]);
+        v /= R.radix[k];
+      }
+    }
+  return MPS_OK;
+}
+
 int mps_charge_radix(mps_t h, int* ncomp, int32_t* radix) {
   if (!h || !ncomp) return MPS_EINVAL;
   *ncomp = h->rule.multi ? h->rule.ncomp : 1;

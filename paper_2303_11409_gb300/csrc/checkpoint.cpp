@@ -1,19 +1,24 @@
-// Checkpoint of a U(1) MPS handle: mps_save writes the charge tables, the Schmidt
-// values and the site blocks of the current state to a file, mps_load rebuilds a
+// Checkpoint of an MPS handle: mps_save writes the charge rule, the charge tables, the
+// Schmidt values and the site blocks of the current state to a file, mps_load rebuilds a
 // handle from it.  The state is the right-canonical form the update keeps
 // (B = Gamma lambda per site, lambda per bond; Sec. II), so a loaded handle
 // continues an evolution exactly where the saved one stopped.
 //
 // File layout (little-endian, all integers int32 unless noted):
 //   "U1MPSCK1"                                   8-byte magic
-//   version (2), L, d, N, chi_max, precision
+//   version (3), L, d, N, chi_max, precision     (N encoded for several U(1) charges)
+//   rule (version 3 only): kind (0 U(1), 1 Z_n, 2 several U(1)); Z_n: n; several U(1):
+//                        ncomp, radix[ncomp], phys_charges[d * ncomp]
 //   per bond b = 0..L:  n, charge[n], dim[n], lambda[sum dim] (float64)
 //   per site s = 0..L-1: n_blocks (int32), nnz (int64), block (l, m) pairs
 //                        [2 n_blocks], data[2 nnz] (float64, interleaved complex)
 //   cut[L + 1] (float64): per bond, the relative cut of its last update, which
-//                        sets the next update's SVD deflation level (version 2 only)
+//                        sets the next update's SVD deflation level (versions 2, 3)
+//   age[L + 1] (version 3 only): per bond, the update calls on the handle since that cut
+//                        was recorded (the deflation level depends on it)
 //   "U1MPSEND"                                   8-byte trailer
-// Version 1 files (without the cut record) load with no deflation history.
+// Version 1 files (without the cut record) load with no deflation history, version 2 files
+// with every cut one call old; both hold U(1) handles.
 // The block order is the library's (l ascending, then m ascending), which the
 // loader checks against the order the bond tables imply.
 #include <cstdint>
@@ -54,6 +59,37 @@ int64_t remaining(FILE* f) {
 }
 
 constexpr int64_t kMaxSites = int64_t(1) << 24;   // far above any chain a handle can hold
+constexpr int32_t kAgeCap = 1 << 30;               // ages beyond this read as "long ago"
+constexpr int64_t kCallBase = int64_t(1) << 40;    // call count of a loaded handle
+
+// The charge rule of a version-3 file, read and checked before anything is created.
+struct RuleRecord {
+  int kind = 0, zn = 0, ncomp = 0;
+  int32_t radix[4] = {};
+  std::vector<int32_t> phys;   // d x ncomp
+};
+
+bool read_rule(FILE* f, int d, RuleRecord& r) {
+  int32_t kind = -1;
+  if (!get(f, &kind, 1)) return false;
+  r.kind = kind;
+  if (kind == 0) return true;
+  if (kind == 1) {
+    int32_t n = 0;
+    if (!get(f, &n, 1) || n < d || n > mps::kMaxZn) return false;
+    r.zn = n;
+    return true;
+  }
+  if (kind != 2) return false;
+  int32_t nc = 0;
+  if (!get(f, &nc, 1) || nc < 1 || nc > 4) return false;
+  r.ncomp = nc;
+  if (!get(f, r.radix, nc)) return false;
+  for (int k = 0; k < nc; ++k)
+    if (r.radix[k] < 2) return false;
+  r.phys.resize((size_t)d * nc);
+  return get(f, r.phys.data(), r.phys.size());
+}
 
 int save_fail(mps_t h, const std::string& msg) {
   h->err = msg;
@@ -67,14 +103,30 @@ extern "C" {
 int mps_save(mps_t h, const char* path) {
   if (!h) return MPS_EINVAL;
   if (!path) return save_fail(h, "path is NULL");
-  if (h->rule.zn || h->rule.multi) return save_fail(h, "checkpoints hold U(1) handles only");
   for (int s = 0; s < h->L; ++s)
     if (h->dirty[s]) return save_fail(h, "site " + std::to_string(s) + " needs mps_set_site before saving");
   File out;
   out.f = std::fopen(path, "wb");
   if (!out.f) return save_fail(h, std::string("cannot open ") + path + " for writing");
-  const int32_t hdr[6] = {2, h->L, h->d, h->N, h->chi_max, h->precision};
+  const int32_t hdr[6] = {3, h->L, h->d, h->N, h->chi_max, h->precision};
   bool ok = put(out.f, kMagic, 8) && put(out.f, hdr, 6);
+  const mps::ChargeRule& R = h->rule;
+  std::vector<int32_t> rule;
+  if (R.multi) {
+    rule = {2, R.ncomp};
+    for (int k = 0; k < R.ncomp; ++k) rule.push_back(R.radix[k]);
+    for (int i = 0; i < h->d; ++i) {   // decode q_i: first component most significant
+      int64_t v = R.q[i];
+      std::vector<int32_t> comp(R.ncomp);
+      for (int k = R.ncomp - 1; k >= 0; --k) { comp[k] = (int32_t)(v % R.radix[k]); v /= R.radix[k]; }
+      rule.insert(rule.end(), comp.begin(), comp.end());
+    }
+  } else if (R.zn) {
+    rule = {1, R.zn};
+  } else {
+    rule = {0};
+  }
+  ok = ok && put(out.f, rule.data(), rule.size());
   std::vector<int32_t> ch, dm;
   std::vector<double> lam;
   for (int b = 0; ok && b <= h->L; ++b) {
@@ -109,7 +161,10 @@ int mps_save(mps_t h, const char* path) {
   }
   std::vector<double> cut(h->L + 1, 0.0);
   if ((int)h->cut_est.size() == h->L + 1) cut = h->cut_est;
-  ok = ok && put(out.f, cut.data(), cut.size()) && put(out.f, kTrailer, 8);
+  std::vector<int32_t> age(h->L + 1, kAgeCap);
+  if ((int)h->cut_call.size() == h->L + 1)
+    for (int b = 0; b <= h->L; ++b) age[b] = (int32_t)std::min<int64_t>(kAgeCap, h->calls - h->cut_call[b]);
+  ok = ok && put(out.f, cut.data(), cut.size()) && put(out.f, age.data(), age.size()) && put(out.f, kTrailer, 8);
   if (!ok) return save_fail(h, std::string("write to ") + path + " failed");
   if (std::fclose(out.f) != 0) {
     out.f = nullptr;
@@ -142,27 +197,45 @@ static int load_body(mps_t* out, const char* path, void* cuda_stream) {
   char magic[8];
   int32_t hdr[6];
   if (!get(in.f, magic, 8) || std::memcmp(magic, kMagic, 8) != 0 || !get(in.f, hdr, 6) ||
-      (hdr[0] != 1 && hdr[0] != 2))
+      hdr[0] < 1 || hdr[0] > 3)
     return MPS_EINVAL;
   const int version = hdr[0];
   const int L = hdr[1], d = hdr[2], N = hdr[3], chi_max = hdr[4], precision = hdr[5];
-  if (L < 2 || (int64_t)L > kMaxSites || d < 2 || d > MPS_MAX_D || N < 0 || (int64_t)N > (int64_t)L * (d - 1) ||
-      chi_max < 1)
-    return MPS_EINVAL;
+  if (L < 2 || (int64_t)L > kMaxSites || d < 2 || d > MPS_MAX_D || N < 0 || chi_max < 1) return MPS_EINVAL;
+  RuleRecord rule;
+  if (version >= 3 && !read_rule(in.f, d, rule)) return MPS_EINVAL;
+  // the total charge: a particle number (U(1)), a residue (Z_n) or an encoded vector
+  if (rule.kind == 0 && (int64_t)N > (int64_t)L * (d - 1)) return MPS_EINVAL;
+  if (rule.kind == 1 && (N >= rule.zn || (int64_t)N > (int64_t)L * (d - 1))) return MPS_EINVAL;
   // every bond record holds at least an int32 count, a charge, a dimension and one lambda
   if (remaining(in.f) < (int64_t)(L + 1) * 20) return MPS_EINVAL;
-  // a product state with the same total charge; every bond and site is then overwritten
+  // a product state of the same charge rule and total charge; every bond and site is then
+  // overwritten (for several U(1) charges the left boundary charge is set afterwards)
   std::vector<int32_t> occ(L, 0);
-  for (int s = 0, left = N; s < L; ++s) { occ[s] = left < d - 1 ? left : d - 1; left -= occ[s]; }
+  if (rule.kind != 2)
+    for (int s = 0, left = N; s < L; ++s) { occ[s] = left < d - 1 ? left : d - 1; left -= occ[s]; }
   mps_t h = nullptr;
-  int rc = mps_create(&h, L, d, occ.data(), precision, chi_max, cuda_stream);
-  if (rc != MPS_OK) return rc;
+  int rc = MPS_OK;
+  if (rule.kind == 0)
+    rc = mps_create(&h, L, d, occ.data(), precision, chi_max, cuda_stream);
+  else if (rule.kind == 1)
+    rc = mps_create_cyclic(&h, L, d, rule.zn, occ.data(), precision, chi_max, cuda_stream);
+  else
+    rc = mps_create_multi(&h, L, d, rule.ncomp, rule.phys.data(), occ.data(), precision, chi_max, cuda_stream);
+  if (rc != MPS_OK) return rc == MPS_ECHARGE ? MPS_EINVAL : rc;
   std::unique_ptr<mps_s, int (*)(mps_t)> guard(h, mps_destroy);
+  if (rule.kind == 2) {
+    for (int k = 0; k < rule.ncomp; ++k)
+      if (h->rule.radix[k] != rule.radix[k]) return MPS_EINVAL;   // not the encoding of this rule
+    h->bonds[0].charge[0] = N;
+    h->N = N;
+  }
+  const int max_sectors = rule.kind == 0 ? N + 1 : chi_max;
   std::vector<int32_t> ch, dm;
   std::vector<double> lam;
   for (int b = 0; b <= L; ++b) {
     int32_t n = 0;
-    if (!get(in.f, &n, 1) || n < 1 || n > N + 1 || (int64_t)n * 8 > remaining(in.f)) return MPS_EINVAL;
+    if (!get(in.f, &n, 1) || n < 1 || n > max_sectors || (int64_t)n * 8 > remaining(in.f)) return MPS_EINVAL;
     ch.resize(n);
     dm.resize(n);
     if (!get(in.f, ch.data(), n) || !get(in.f, dm.data(), n)) return MPS_EINVAL;
@@ -196,7 +269,7 @@ static int load_body(mps_t* out, const char* path, void* cuda_stream) {
     mc.resize(nb);
     for (int i = 0; i < nb; ++i) { lc[i] = pairs[2 * i]; mc[i] = pairs[2 * i + 1]; }
     mps::SiteTable t;
-    mps::layout_site(h->bonds[s], h->bonds[s + 1], d, t);
+    mps::layout_site(h->bonds[s], h->bonds[s + 1], h->rule, t);
     if (t.nnz != nnz) return MPS_ECHARGE;   // the blocks do not fit the bond tables
     rc = mps_set_site(h, s, nb, lc.data(), mc.data(), data.data());
     if (rc != MPS_OK) return rc;
@@ -207,9 +280,18 @@ static int load_body(mps_t* out, const char* path, void* cuda_stream) {
     for (double c : cut)
       if (!(c >= 0.0 && c <= 1.0)) return MPS_EINVAL;
   }
+  std::vector<int32_t> age(L + 1, 0);   // older files: every cut recorded by the last call
+  if (version >= 3) {
+    if (!get(in.f, age.data(), age.size())) return MPS_EINVAL;
+    for (int32_t a : age)
+      if (a < 0 || a > kAgeCap) return MPS_EINVAL;
+  }
   char trailer[8];
   if (!get(in.f, trailer, 8) || std::memcmp(trailer, kTrailer, 8) != 0) return MPS_EINVAL;
   h->cut_est = cut;   // after every mps_set_bond / mps_set_site, which clear it
+  h->calls = kCallBase;
+  h->cut_call.assign(L + 1, 0);
+  for (int b = 0; b <= L; ++b) h->cut_call[b] = kCallBase - age[b];
   *out = guard.release();
   return MPS_OK;
 }

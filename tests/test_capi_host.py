@@ -185,3 +185,29 @@ def test_rule_planner_rejects_bad_rules(built):
         m.plan_sectors_rule(4, tt, tt, tt, charges=[(0, 1), (0, 0), (1, 0), (1, 1)])
     with pytest.raises(m.MPSError):                            # radix below 2
         m.plan_sectors_rule(4, tt, tt, tt, charges=q, radix=[1, 5])
+
+
+def test_load_rejects_bad_rule_records_without_touching_the_gpu(built, tmp_path):
+    """Version-3 checkpoints carry the charge rule after the header; an unknown kind, a Z_n
+    with n below d, a residue total charge at or above n, or a bad several-U(1) record is
+    refused before any handle exists."""
+    import ctypes
+    import struct
+    import paper_2303_11409_gb300 as m
+    h = ctypes.c_void_p()
+    head = lambda N: struct.pack("<8s6i", b"U1MPSCK1", 3, 8, 3, N, 16, 0)
+    pad = b"\0" * 4096
+    cases = {
+        "unknown_kind": head(2) + struct.pack("<i", 7) + pad,
+        "zn_below_d": head(1) + struct.pack("<2i", 1, 2) + pad,
+        "residue_too_large": head(5) + struct.pack("<2i", 1, 4) + pad,
+        "no_components": head(0) + struct.pack("<2i", 2, 0) + pad,
+        "radix_below_two": head(0) + struct.pack("<4i", 2, 2, 1, 9) + pad,
+        "version_4": struct.pack("<8s6i", b"U1MPSCK1", 4, 8, 3, 2, 16, 0) + pad,
+    }
+    for name, blob in cases.items():
+        p = tmp_path / f"{name}.u1mps"
+        p.write_bytes(blob)
+        rc = m.lib.mps_load(ctypes.byref(h), str(p).encode(), None)
+        assert rc == m.MPS_EINVAL, (name, rc)
+        assert not h.value

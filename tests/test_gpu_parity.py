@@ -245,6 +245,56 @@ def test_save_load_round_trip_continues_bit_for_bit(gpu_lib, tmp_path):
         assert sa.keys() == sb.keys() and all(np.array_equal(sa[k], sb[k]) for k in sa)
 
 
+def _round_trip(m, a, layers, gate_of, chi, tmp_path, name):
+    """Save a, load it back, continue both by the same layers: identical bonds and blocks."""
+    path = tmp_path / f"{name}.u1mps"
+    a.save(path)
+    b = m.MPS.load(path)
+    assert (b.L, b.d, b.N, b.chi_max, b.zn, b.charges) == (a.L, a.d, a.N, a.chi_max, a.zn, a.charges)
+    for bond in range(a.L + 1):
+        ba, bb = a.bond(bond), b.bond(bond)
+        assert ba.keys() == bb.keys() and all(np.array_equal(ba[c], bb[c]) for c in ba)
+    for sites, f in layers:
+        a.apply_layer(sites, [gate_of(s, f) for s in sites], chi, 1e-10)
+        b.apply_layer(sites, [gate_of(s, f) for s in sites], chi, 1e-10)
+    for s in range(a.L):
+        sa, sb = a.site(s), b.site(s)
+        assert sa.keys() == sb.keys() and all(np.array_equal(sa[k], sb[k]) for k in sa)
+    b.close()
+
+
+def test_round_trip_of_every_charge_rule_and_of_the_deflation_ages(gpu_lib, tmp_path):
+    """Checkpoints of Z_n (d = n and d < n) and several-U(1) handles; and a U(1) handle saved
+    after an even layer and continued by an odd one: the odd bonds' cuts are two update calls
+    old there, on the loaded handle as on the saved one (their deflation level depends on it)."""
+    m = gpu_lib
+    from oracle import multiu1
+    from oracle.gates import bh_weights
+    L = 10
+    layers = tebd.strang_layers(L)
+    # U(1), saved after an even layer
+    gate_of = tebd.bh_gates(L, 3, 1.0, 2.0, 0.05)
+    a = _gpu(m, 3, W.mott_occupations(L), 24)
+    for sites, f in layers * 2 + layers[:2]:
+        a.apply_layer(sites, [gate_of(s, f) for s in sites], 24, 1e-10)
+    _round_trip(m, a, layers, gate_of, 24, tmp_path, "u1")
+    # Z_3 clock chain (d = n) and Bose-Hubbard on Z_4 (d = 3 < n)
+    for d, n, model, p in ((3, 3, "clock", dict(J=1.0, f=0.6)), (3, 4, "bh", dict(J=1.0, U=2.0, zn=4))):
+        table = m.tebd.GateTable(model, L, d, 0.1, **p)
+        a = m.MPS(d, [(2 * s) % d for s in range(L)], 16, zn=n)
+        for sites, f in layers * 2:
+            a.apply_layer(sites, [table(s, f) for s in sites], 16, 1e-10)
+        _round_trip(m, a, layers, table, 16, tmp_path, f"z{n}_{d}")
+    # two species of hard-core bosons
+    Q = multiu1.TWO_SPECIES_Q
+    a = m.MPS(4, [s % 4 for s in range(L)], 16, charges=Q)
+    gq = lambda s, f: multiu1.two_species_gate(1.0, 2.0, *bh_weights(L, s), f * 0.05)
+    for sites, f in layers * 2:
+        a.apply_layer(sites, [gq(s, f) for s in sites], 16, 1e-10)
+    _round_trip(m, a, layers, gq, 16, tmp_path, "two_species")
+    a.close()
+
+
 def test_load_rejects_missing_and_damaged_files(gpu_lib, tmp_path):
     m = gpu_lib
     with pytest.raises(m.MPSError):
@@ -263,7 +313,8 @@ def test_load_rejects_missing_and_damaged_files(gpu_lib, tmp_path):
             m.MPS.load(p)
     # a charge table with a charge outside the bond's range is refused
     import struct
-    hdr = struct.calcsize("<8s6i")
+    hdr = struct.calcsize("<8s6i") + 4   # magic, header, the rule record of a U(1) handle (kind 0)
+    assert struct.unpack_from("<i", raw, 8)[0] == 3 and struct.unpack_from("<i", raw, hdr - 4)[0] == 0
     L = 8
     off = hdr
     for b in range(L + 1):   # walk to bond 1's first charge

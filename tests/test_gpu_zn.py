@@ -145,6 +145,4 @@ def test_zn_handle_rejects_bad_arguments(gpu_lib):
     g = m.MPS(2, [0, 1, 1, 0], 8, zn=2)
     assert g.bond_dims(0) == {0: 1}               # (0 + 1 + 1 + 0) mod 2
     assert g.bond_dims(1) == {0: 1} and g.bond_dims(2) == {1: 1} and g.bond_dims(3) == {0: 1}
-    with pytest.raises(m.MPSError):
-        g.save("/dev/null")                       # checkpoints hold U(1) handles only
     g.close()
