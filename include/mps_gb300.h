@@ -108,8 +108,9 @@ MPS_API int mps_create_segment(mps_t* out, int L, int d, const int32_t* site_cha
 /*
  * mps_create_zn - like mps_create, for the cyclic group Z_n instead of U(1) (Sec. I names
  * more general Abelian symmetries; the block construction of Sec. II carries over): local
- * dimension d = n (2..MPS_MAX_D), the physical index i carries charge i mod n, bond b the
- * right-charge (sum of the occupations right of it) mod n, and every pair of charges forms
+ * dimension d = n (2..MPS_MAX_D; mps_create_cyclic takes d < n), the physical index i
+ * carries charge i mod n, bond b the right-charge (sum of the occupations right of it)
+ * mod n, and every pair of charges forms
  * a site block (l, m) with i = (l - m) mod n.  Gate blocks for such a handle are the n blocks
  * q = 0..n-1 of the total charge (i + j) mod n, each n x n over the pairs (i, (q - i) mod n),
  * i ascending (rows outputs, columns inputs), concatenated row-major.  Every update, batch,

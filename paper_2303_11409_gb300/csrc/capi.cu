@@ -1,5 +1,5 @@
-// C ABI of the GB300 U(1) MPS library: handles, the device arena, and the
-// batched two-site update executor.
+// C ABI of the GB300 symmetric-MPS library (U(1), Z_n and several U(1) charges): handles,
+// the device arena, and the batched two-site update executor.
 //
 // One update (Sec. II of arXiv:2303.11409) runs as
 //   host planner (K0) -> theta_kernel (K1: Theta'(c) for all middle charges)

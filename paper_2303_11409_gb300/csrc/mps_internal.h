@@ -16,11 +16,12 @@ constexpr int kSvdSideStreams = 4;      // side streams for concurrent SVD kerne
 // ---------------------------------------------------------------------------
 // Charge arithmetic.  U(1) (zn = 0, Sec. II): block (l, m) of a site carries the physical
 // index i = l - m and exists for 0 <= i <= d - 1; the two-site gate has blocks q = l - r in
-// [0, 2(d-1)] over the pairs (i, q - i).  Z_n (zn = n = d, the "more general Abelian" case of
-// Sec. I): charges are residues mod n, i = (l - m) mod n, every pair of charges occurs, and
-// gate block q in [0, n) acts on the n pairs (i, (q - i) mod n).  Either way a Theta(c)
-// block's rows and columns are contiguous runs of the sorted bond tables (for Z_n with
-// d = n: all sectors).
+// [0, 2(d-1)] over the pairs (i, q - i).  Z_n (zn = n >= d, the "more general Abelian" case
+// of Sec. I): charges are residues mod n, i = (l - m) mod n must lie below d; for d = n every
+// pair of charges occurs and gate block q in [0, n) acts on the n pairs (i, (q - i) mod n), and
+// for d < n the gate blocks come from tables (ztab).  For U(1) and for Z_n with d = n a
+// Theta(c) block's rows and columns are contiguous runs of the sorted bond tables (for Z_n:
+// all sectors); for Z_n with d < n and for several U(1) charges (multi) they are listed.
 // ---------------------------------------------------------------------------
 constexpr int kMaxZn = 1 << 20;   // largest n of a Z_n handle (bond charges are residues)
 
