@@ -10,6 +10,7 @@
 // columns of every Theta(c) are contiguous ranges of the left and right tables
 // (the "charge-sorted memory alignment" of Sec. II).
 #include <algorithm>
+#include <new>
 #include <cstring>
 
 #include "mps_internal.h"
@@ -215,7 +216,7 @@ static bool make_table(int n, const int32_t* c, const int32_t* dims, BondTable& 
   return true;
 }
 
-extern "C" int mps_plan_sectors(int d, int nl, const int32_t* lc, const int32_t* ld,
+static int plan_sectors_body(int d, int nl, const int32_t* lc, const int32_t* ld,
                                 int nm, const int32_t* mc, const int32_t* md,
                                 int nr, const int32_t* rc, const int32_t* rd,
                                 int32_t* triples, int cap_triples, int* n_triples,
@@ -243,7 +244,7 @@ extern "C" int mps_plan_sectors(int d, int nl, const int32_t* lc, const int32_t*
   return MPS_OK;
 }
 
-extern "C" int mps_plan_sectors_rule(int d, int zn, int ncomp, const int32_t* phys_charges, const int32_t* radix,
+static int plan_sectors_rule_body(int d, int zn, int ncomp, const int32_t* phys_charges, const int32_t* radix,
                                      int nl, const int32_t* lc, const int32_t* ld,
                                      int nm, const int32_t* mc, const int32_t* md,
                                      int nr, const int32_t* rc, const int32_t* rd,
@@ -324,4 +325,37 @@ extern "C" int mps_plan_sectors_rule(int d, int zn, int ncomp, const int32_t* ph
     for (int k : e.ri) lists[o++] = R.charge[k];
   }
   return MPS_OK;
+}
+
+// The C entry points: no exception of the host containers crosses the C boundary.
+extern "C" int mps_plan_sectors(int d, int nl, const int32_t* lc, const int32_t* ld,
+                                int nm, const int32_t* mc, const int32_t* md,
+                                int nr, const int32_t* rc, const int32_t* rd,
+                                int32_t* triples, int cap_triples, int* n_triples,
+                                int32_t* sectors, int cap_sectors, int* n_sectors) {
+  try {
+    return plan_sectors_body(d, nl, lc, ld, nm, mc, md, nr, rc, rd, triples, cap_triples, n_triples, sectors,
+                             cap_sectors, n_sectors);
+  } catch (const std::bad_alloc&) {
+    return MPS_ENOMEM;
+  } catch (...) {
+    return MPS_EINVAL;
+  }
+}
+
+extern "C" int mps_plan_sectors_rule(int d, int zn, int ncomp, const int32_t* phys_charges, const int32_t* radix,
+                                     int nl, const int32_t* lc, const int32_t* ld,
+                                     int nm, const int32_t* mc, const int32_t* md,
+                                     int nr, const int32_t* rc, const int32_t* rd,
+                                     int32_t* triples, int cap_triples, int* n_triples,
+                                     int32_t* sectors, int cap_sectors, int* n_sectors,
+                                     int32_t* lists, int cap_lists, int* n_lists) {
+  try {
+    return plan_sectors_rule_body(d, zn, ncomp, phys_charges, radix, nl, lc, ld, nm, mc, md, nr, rc, rd, triples,
+                                  cap_triples, n_triples, sectors, cap_sectors, n_sectors, lists, cap_lists, n_lists);
+  } catch (const std::bad_alloc&) {
+    return MPS_ENOMEM;
+  } catch (...) {
+    return MPS_EINVAL;
+  }
 }
