@@ -9,9 +9,10 @@
  * matrix without an explicit physical index, and a two-site update needs only
  * block-sparse SVDs of the submatrices Theta(c), each at most chi x chi.  On the
  * same sector machinery it runs two-site DMRG and TDVP (mps_dmrg, mps_tdvp), samples
- * occupation patterns (mps_sample), and supports Z_n charges (mps_create_zn),
- * several U(1) charges at once (mps_create_multi) and chain segments for multi-rank
- * runs (mps_create_segment).
+ * occupation patterns (mps_sample), and supports Z_n charges (mps_create_zn,
+ * mps_create_cyclic), several U(1) charges at once (mps_create_multi) and chain segments
+ * for multi-rank runs (mps_create_segment).  Entry points that serve bookkeeping,
+ * diagnostics or tuning say that the paper has no counterpart.
  *
  * Conventions used by every entry point
  *   - Sites are 0-based, s = 0..L-1.  Bond b (b = 0..L) sits left of site b, so
@@ -104,7 +105,6 @@ MPS_API int mps_create(mps_t* out, int L, int d, const int32_t* site_charges,
 MPS_API int mps_create_segment(mps_t* out, int L, int d, const int32_t* site_charges, int site_lo,
                                int site_hi, int precision, int chi_max, void* cuda_stream);
 
-/* mps_destroy - frees the handle and its device memory (after its stream drains). */
 /*
  * mps_create_zn - like mps_create, for the cyclic group Z_n instead of U(1) (Sec. I names
  * more general Abelian symmetries; the block construction of Sec. II carries over): local
@@ -130,18 +130,23 @@ MPS_API int mps_create_zn(mps_t* out, int L, int n, const int32_t* site_charges,
  * its pairs (i, (q - i) mod n) with both entries below d, i ascending (rows outputs, columns
  * inputs), concatenated row-major.  A U(1)-conserving model (for example Bose-Hubbard with
  * n_max = d - 1) also conserves the particle number mod n; its U(1) gate blocks of totals
- * t = q, q + n, ... then sit in block q.  Calls as for mps_create_zn handles.  Errors:
+ * t = q, q + n, ... then sit in block q.  Calls as for mps_create_zn handles (Sec. I's
+ * "more general Abelian" symmetries on the block construction of Sec. II).  Errors:
  * MPS_EINVAL (d or n out of range), as mps_create otherwise.
  */
 MPS_API int mps_create_cyclic(mps_t* out, int L, int d, int n, const int32_t* site_charges, int precision,
                               int chi_max, void* cuda_stream);
 
+/* mps_destroy - frees the handle and its device memory (after its stream drains); resource
+ * management, no counterpart in the paper. */
 MPS_API int mps_destroy(mps_t h);
 
-/* mps_last_error - message of the last failing call on h ("" if none); owned by h. */
+/* mps_last_error - message of the last failing call on h ("" if none); owned by h.  No
+ * counterpart in the paper. */
 MPS_API const char* mps_last_error(mps_t h);
 
-/* mps_info - L, d, N, chi_max and precision of a handle (any pointer may be NULL). */
+/* mps_info - L, d, N, chi_max and precision of a handle (any pointer may be NULL); N is the
+ * boundary charge c^[0] of Sec. II. */
 MPS_API int mps_info(mps_t h, int* L, int* d, int* N, int* chi_max, int* precision);
 
 /*
@@ -186,7 +191,8 @@ MPS_API int mps_apply_layer(mps_t h, int n, const int* sites, const double* cons
  * one handle must touch disjoint site pairs.  All handles must live on the current
  * device; work runs on hs[0]'s stream (the others' streams are joined first).
  * status_out[k] receives the per-item status; the return value is the first
- * non-OK item status, or MPS_OK.
+ * non-OK item status, or MPS_OK.  Sec. II: two-site updates on disjoint pairs, here also
+ * of different states, are independent and run as one batch.
  */
 MPS_API int mps_apply_gate2_batch(int n, mps_t* hs, const int* sites, const double* const* gates,
                           const int* chis, const double* cutoffs, double* trunc_err_out,
@@ -212,7 +218,9 @@ MPS_API int mps_exec_apply(mps_exec_t ex, int n, mps_t* hs, const int* sites, co
  * mps_create allocates: per bond min(chi_max, Hilbert bound) lambdas, two slots per
  * site of bond_cap(s) * bond_cap(s+1) complex numbers) and an upper bound of the
  * update workspace one of its Trotter layers needs (about 64 d chi^2 bytes per
- * update).  Host-only; used for admission by HBM footprint.
+ * update).  Host-only; used for admission by HBM footprint.  It follows the memory count
+ * of Sec. II (every block at most chi x chi, bounded per bond by the charge-resolved
+ * Hilbert dimension).
  */
 MPS_API int mps_footprint_bytes(int L, int d, int N, int chi_max, int64_t* arena_bytes,
                                 int64_t* layer_workspace_bytes);
@@ -235,7 +243,8 @@ MPS_API int mps_expect(mps_t h, int site, const double* diag_op, double* out);
  */
 MPS_API int mps_amplitude(mps_t h, const int32_t* config, double out_complex[2]);
 
-/* mps_amplitude_batch - n amplitudes; configs is n x L row-major, out is n x 2. */
+/* mps_amplitude_batch - n amplitudes (the U(1) amplitude formula of Sec. II, one CTA per
+ * configuration); configs is n x L row-major, out is n x 2. */
 MPS_API int mps_amplitude_batch(mps_t h, int n, const int32_t* configs, double* out);
 
 /*
@@ -264,7 +273,8 @@ MPS_API int mps_sample(mps_t h, int n, const double* uniforms, int32_t* configs_
 
 /*
  * mps_bond_spectrum - the sectors of bond b (0..L): charges and dims ascending by
- * charge, and lambda values sector by sector (each sector descending).
+ * charge, and lambda values sector by sector (each sector descending): the Schmidt values
+ * of Sec. II's canonical form, split by the bond charge.
  *   cap    capacity of charges/dims (sectors); lambda must hold the bond dimension
  *   n_out  number of sectors; if cap is too small nothing else is written and
  *          MPS_EINVAL is returned with n_out set
@@ -282,7 +292,8 @@ MPS_API int mps_bond_spectrum(mps_t h, int bond, int32_t* charges, int32_t* dims
 MPS_API int mps_bond_entropy(mps_t h, int bond, double* out);
 
 /*
- * mps_get_site - the blocks of site s in (l ascending, m ascending) order.
+ * mps_get_site - the blocks B^[s][l, m] of site s (Sec. II's block matrix without an
+ * explicit physical index) in (l ascending, m ascending) order.
  *   lcharges, mcharges  block labels (capacity cap_blocks)
  *   data                complex128 interleaved, blocks concatenated, each row-major
  *                       D_l x D_m (capacity cap_values complex numbers)
@@ -301,7 +312,7 @@ MPS_API int mps_get_site(mps_t h, int site, int32_t* lcharges, int32_t* mcharges
  * a segmented chain); set every bond first, then every site whose neighbouring bonds
  * changed.  mps_set_bond clears the deflation history of that bond only (the previous
  * cut an update of the bond would deflate from, see mps_apply_gate2); mps_set_site
- * keeps every bond's history.
+ * keeps every bond's history.  The tables and blocks are those of Sec. II's block form.
  */
 MPS_API int mps_set_bond(mps_t h, int bond, int n_sectors, const int32_t* charges, const int32_t* dims,
                  const double* lambda);
@@ -312,7 +323,7 @@ MPS_API int mps_set_site(mps_t h, int site, int n_blocks, const int32_t* lcharge
  * mps_last_update_stats - diagnostics of the last update on h: counts of sectors,
  * (l,m,r) triples, Jacobi sweeps (max over sectors), ties resolved at the chi cut,
  * and the pre-renormalisation norm |S_all| and kept norm |S_kept|.
- * Any pointer may be NULL.
+ * Any pointer may be NULL.  Diagnostics; no counterpart in the paper.
  */
 MPS_API int mps_last_update_stats(mps_t h, int* n_sectors, int* n_triples, int* max_sweeps,
                           int* tie_band, double* norm_all, double* norm_kept);
@@ -327,14 +338,15 @@ MPS_API int mps_last_update_stats(mps_t h, int* n_sectors, int* n_triples, int* 
  * level 0 turns the second level off; the default is 3e-4 (a redo when the cut halves); a
  * smaller level deflates less but redoes only after larger drops of the cut.  It applies to
  * the updates of h whichever handle's call (or executor) runs them.  MPS_EINVAL outside
- * [0, 6e-4].
+ * [0, 6e-4].  A tuning of the SVD of Sec. II's update; no counterpart in the paper.
  */
 MPS_API int mps_set_chi_deflation(mps_t h, double level);
 
 /*
  * mps_deflation_stats - updates on h (cumulative) whose SVDs used the previous cut of
  * their bond as a deflation level, and how many of those were redone without it
- * (see mps_apply_gate2).  Either pointer may be NULL.
+ * (see mps_apply_gate2).  Either pointer may be NULL.  Diagnostics; no counterpart in the
+ * paper.
  */
 MPS_API int mps_deflation_stats(mps_t h, int64_t* deflated_updates, int64_t* redos);
 
@@ -375,6 +387,7 @@ MPS_API int mps_deflation_stats(mps_t h, int64_t* deflated_updates, int64_t* red
  * (compulsory reads + writes).  Synchronises h's stream.
  * mps_reset_kernel_stats - zeroes the counters of h.
  * mps_launch_count - kernels launched by this library in this process so far.
+ * Measurement support; no counterpart in the paper.
  */
 MPS_API int mps_set_profiling(mps_t h, int on);
 MPS_API int mps_kernel_stats(mps_t h, int kind, int64_t* launches, double* ms, double* flops, double* bytes);
@@ -440,6 +453,7 @@ MPS_API int mps_graph_stats(mps_t h, int64_t* launches, int64_t* updates, int64_
  *   from 2 << (k >> 2); 8 and 9: width 6 from 2 CTAs, 16-CTA clusters from min(m, n) =
  *   512 and 256; 10 and 11: the sectors from min(m, n) = 512 and 256 on the round-robin
  *   cluster kernel instead of the block-Jacobi one.  MPS_EINVAL for any other value.
+ * Launch tuning of the per-sector SVDs of Sec. II; no counterpart in the paper.
  */
 MPS_API int mps_set_autotune(mps_t h, int on);
 MPS_API int mps_autotune_stats(int64_t* keys, int64_t* tuning_runs, int64_t* hits);
@@ -452,6 +466,7 @@ MPS_API int mps_autotune_min_flops(double flops);
 /*
  * mps_last_batch_sweeps - Jacobi sweeps of the last update call on h over all of its
  * sectors: sector count, summed sweeps and the largest sweep count (any may be NULL).
+ * Diagnostics of the per-sector SVDs of Sec. II; no counterpart in the paper.
  */
 MPS_API int mps_last_batch_sweeps(mps_t h, int* n_sectors, int64_t* sweeps_sum, int* sweeps_max);
 
@@ -522,7 +537,7 @@ MPS_API int mps_fp64_peak_probe(double* gflops, void* cuda_stream);
  * MPS_ECHARGE (a negative component, vectors not ascending, or encoded charges beyond int32),
  * MPS_ENOMEM.
  * mps_charge_radix - *ncomp and the radix of each component (radix may be NULL); 1 and 0 for
- * single-charge handles.
+ * single-charge handles (the encoding of the vector charges above).
  */
 MPS_API int mps_create_multi(mps_t* out, int L, int d, int ncomp, const int32_t* phys_charges,
                              const int32_t* site_indices, int precision, int chi_max, void* cuda_stream);
@@ -533,7 +548,7 @@ MPS_API int mps_charge_radix(mps_t h, int* ncomp, int32_t* radix);
  * *ncomp = the number of charge components of a several-U(1) handle (0 otherwise), and for
  * such a handle its d charge vectors into phys_charges (d x ncomp row-major, as passed to
  * mps_create_multi).  Any pointer may be NULL.  A handle from mps_load reports the rule it
- * was saved with.
+ * was saved with.  (Sec. I's symmetry groups: U(1), Z_n, products of U(1).)
  */
 MPS_API int mps_charge_rule(mps_t h, int* zn, int* ncomp, int32_t* phys_charges);
 
@@ -544,8 +559,9 @@ MPS_API int mps_charge_rule(mps_t h, int* zn, int* ncomp, int32_t* phys_charges)
  * SVD, truncated globally as mps_apply_gate2 does).
  *   bond_terms   L-1 host pointers; bond_terms[k] is the Hermitian two-site term h_{k,k+1}
  *                of H = sum_k h_{k,k+1} as charge blocks in the gate layout (block n over the
- *                pairs (i, n - i), i ascending, rows outputs; interleaved complex128,
- *                mps_gate_length(d) complex numbers); read during the call only
+ *                pairs (i, n - i), i ascending, rows outputs; interleaved complex128, the
+ *                sum over n of s_n^2 complex numbers, s_n the size of block n); read
+ *                during the call only
  *   n_sweeps     sweeps; a sweep is a right-moving pass over the pairs (0,1) .. (L-2,L-1)
  *                and a left-moving pass back (2 (L-1) local steps)
  *   chi, cutoff  the truncation of every local step (the rule of mps_apply_gate2)
@@ -564,14 +580,15 @@ MPS_API int mps_charge_rule(mps_t h, int* zn, int* ncomp, int32_t* phys_charges)
  * mps_dmrg_stats reports, for the last call, per kind (0: H_eff products, 1: environment
  * updates, 2: Krylov vector work, 3: SVD, 4: other block contractions) the launches, the
  * device milliseconds (with mps_set_profiling on) and the algorithmic flops; mps_dmrg_counts
- * the H_eff products and Lanczos cycles.
+ * the H_eff products and Lanczos cycles (diagnostics, no counterpart in the paper).
  */
 MPS_API int mps_dmrg(mps_t h, const double* const* bond_terms, int n_sweeps, int chi, double cutoff,
                      int lanczos_dim, double tol, double* energies, int energies_cap, int* n_energies);
 MPS_API int mps_dmrg_stats(mps_t h, int kind, int64_t* launches, double* ms, double* flops);
 /*
  * mps_tdvp - second-order two-site TDVP (time-dependent variational principle) time steps on
- * the state of h, the real-time counterpart of mps_dmrg on the same environments and H_eff:
+ * the state of h, the real-time counterpart of mps_dmrg on the same environments and H_eff (the
+ * paper names no time-evolution scheme beyond TEBD, Sec. I; this is the standard two-site one):
  * a step of length dt is a right-moving and a left-moving pass of dt/2; each pair is evolved
  * by exp(-i dt/2 H_eff) (a Krylov exponential on the device: Lanczos basis of krylov_dim
  * vectors, 2..40, the tridiagonal's eigenpairs by Jacobi rotations; the step is split into
@@ -658,19 +675,21 @@ MPS_API int mps_svd_sectors(int n_sectors, const int* m, const int* n,
  * 0: none) first run one-sided Jacobi sweeps in FP32 on the Jacobi matrix stacked on the
  * identity, which accumulates the rotations V; V is then made unitary in FP64 (one Cholesky
  * QR) and the FP64 sweeps start from the Jacobi matrix times V, converging in 2-3 sweeps.
- * Results meet the same FP64 accuracy; FP32 runs at 64x the FP64 rate on this part.  A process
+ * Results meet the same FP64 accuracy; FP32 runs at 61x the FP64 rate on this part.  A process
  * setting, read when an update call or mps_svd_sectors lays out its scratch (more scratch per
- * such sector: about 8 (jlen + K) K + 48 K^2 bytes).  MPS_EINVAL for min_k < 0.
+ * such sector: about 8 (jlen + K) K + 48 K^2 bytes).  MPS_EINVAL for min_k < 0.  A tuning of
+ * the per-sector SVDs of Sec. II; no counterpart in the paper.
  */
 MPS_API int mps_svd_mixed_min_k(int min_k);
 /* mps_svd_mixed_sweeps - the limit of those FP32 sweeps (1..40, default 8: on the chi = 2048 layer 6-10
- * FP32 sweeps minimise the time; the FP64 sweeps finish either way); MPS_EINVAL outside. */
+ * FP32 sweeps minimise the time; the FP64 sweeps finish either way); MPS_EINVAL outside.  Tuning;
+ * no counterpart in the paper. */
 MPS_API int mps_svd_mixed_sweeps(int max_sweeps);
 /* mps_svd_cluster_min_k - sectors with min(m, n) >= min_k run on the cluster SVD kernels even when
  * they fit in one CTA's shared memory (spreading a batch of few sectors over more SMs); 0 (the
  * default): only sectors that do not fit.  A process setting read when mps_svd_sectors or an
  * update call lays out its scratch; mps_dmrg picks its own threshold per step.  MPS_EINVAL for
- * 0 < min_k < 16 or min_k < 0. */
+ * 0 < min_k < 16 or min_k < 0.  Tuning; no counterpart in the paper. */
 MPS_API int mps_svd_cluster_min_k(int min_k);
 
 /*
