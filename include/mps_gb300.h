@@ -649,6 +649,20 @@ MPS_API int mps_plan_sectors_rule(int d, int zn, int ncomp, const int32_t* phys_
                      int32_t* lists, int cap_lists, int* n_lists);
 
 /*
+ * mps_gate_layout - the two-site gate (and bond-term) layout of a charge rule (host code, no
+ * GPU needed): the sizes s_k of its blocks in layout order into sizes (capacity cap; may be
+ * NULL), their number *n_blocks and the flattened length sum_k s_k^2 in complex numbers that
+ * every gate passed to an update of such a handle holds.  U(1) (zn = 0, ncomp = 0): blocks
+ * n = 0..2(d-1) over (i, n - i); Z_n (zn = n >= d): the residues q = (i + j) mod n some pair
+ * reaches; several U(1) charges (ncomp >= 1, phys_charges as for mps_create_multi): the distinct
+ * totals q_i + q_j, lexicographic.  The charge of a pair is the sum of Sec. II's local charges.
+ * Errors: MPS_EINVAL (bad arguments, cap too small), MPS_ECHARGE (charge vectors negative or
+ * not ascending).
+ */
+MPS_API int mps_gate_layout(int d, int zn, int ncomp, const int32_t* phys_charges, int32_t* sizes, int cap,
+                            int* n_blocks, int64_t* length);
+
+/*
  * mps_svd_sectors - the batched per-sector SVD kernel alone, on device memory
  * (one-sided Jacobi in FP64; Sec. II: the local update needs one SVD per charge block).
  * For each sector k it decomposes M_k = diag(rowscale_k) A_k, A_k being the

@@ -7,7 +7,7 @@ set-up.  Importing it fails if the library has not been built.
 from ._binding import (EXPORTED, LIB_PATH, MPS, MPS_BF16X3, MPS_EINVAL, MPS_ECHARGE, MPS_ENOCONV,  # noqa: F401
                        MPS_ENOMEM, MPS_ECUDA, MPS_ETIMEOUT, MPS_FP64, MPS_MAX_D, MPS_OK, MPS_TF32,
                        JacobiNotConverged, KERNEL_KINDS, MPSError, apply_gate2_batch, gate_length, launch_count, lib,
-                       plan_sectors, plan_sectors_rule,
+                       plan_sectors, plan_sectors_rule, gate_layout,
                        svd_sectors, svd_work_bytes)
 from ._binding import MPS_NOALLOC_SCRATCH_BYTES, svd_sectors_noalloc  # noqa: F401
 from ._binding import Executor, footprint_bytes, fp64_peak_probe, zgemm_tc  # noqa: F401

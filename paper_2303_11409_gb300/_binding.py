@@ -91,6 +91,8 @@ _SIGS = {
                                              ctypes.c_int, _i32p, _i32p, ctypes.c_int, _i32p, _i32p,
                                              ctypes.c_int, _i32p, _i32p, _i32p, ctypes.c_int, _intp, _i32p,
                                              ctypes.c_int, _intp, _i32p, ctypes.c_int, _intp]),
+    "mps_gate_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p, ctypes.c_int,
+                                       _intp, _i64p]),
     "mps_last_batch_sweeps": (ctypes.c_int, [_h, _intp, _i64p, _intp]),
     "mps_set_profiling": (ctypes.c_int, [_h, ctypes.c_int]),
     "mps_kernel_stats": (ctypes.c_int, [_h, ctypes.c_int, _i64p, _dblp, _dblp, _dblp]),
@@ -839,6 +841,19 @@ def plan_sectors_rule(d: int, left: dict, mid: dict, right: dict, zn: int = 0, c
         o += nr_ + nc_
         sectors.append((dec(c), rows, cols, rl, cl))
     return triples, sectors
+
+
+def gate_layout(d: int, zn: int = 0, charges=None):
+    """The library's gate layout of a charge rule (mps_gate_layout): (block sizes, length)."""
+    nc = 0 if charges is None else len(charges[0])
+    q = None if charges is None else _i32([x for vec in charges for x in vec])
+    sizes = np.zeros(4 * MPS_MAX_D * MPS_MAX_D, np.int32)
+    nb, ln = ctypes.c_int(0), ctypes.c_int64(0)
+    rc = lib.mps_gate_layout(d, zn, nc, None if q is None else _ptr(q, _i32p), _ptr(sizes, _i32p), len(sizes),
+                             ctypes.byref(nb), ctypes.byref(ln))
+    if rc != MPS_OK:
+        raise MPSError(rc, "mps_gate_layout")
+    return [int(x) for x in sizes[:nb.value]], int(ln.value)
 
 
 def svd_work_bytes(ms, ns) -> int:

@@ -359,3 +359,70 @@ extern "C" int mps_plan_sectors_rule(int d, int zn, int ncomp, const int32_t* ph
     return MPS_EINVAL;
   }
 }
+
+// Two-site gate layout of a charge rule: the block sizes in layout order and the flattened
+// length (host code).  U(1): blocks n = 0..2(d-1) over (i, n - i); Z_n: the residues that some
+// pair reaches; several U(1): the distinct vector totals q_i + q_j, lexicographic.
+static int gate_layout_body(int d, int zn, int ncomp, const int32_t* phys_charges, int32_t* sizes, int cap,
+                            int* n_blocks, int64_t* length) {
+  if (d < 2 || d > MPS_MAX_D || zn < 0 || ncomp < 0 || ncomp > 4 || (zn && ncomp) || !n_blocks || !length)
+    return MPS_EINVAL;
+  if (zn && (zn < d || zn > kMaxZn)) return MPS_EINVAL;
+  std::vector<int> sz;
+  if (ncomp) {
+    if (!phys_charges) return MPS_EINVAL;
+    std::vector<std::vector<int64_t>> tot;
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        std::vector<int64_t> t(ncomp);
+        for (int k = 0; k < ncomp; ++k) {
+          const int32_t a = phys_charges[i * ncomp + k], b = phys_charges[j * ncomp + k];
+          if (a < 0 || b < 0) return MPS_ECHARGE;
+          t[k] = (int64_t)a + b;
+        }
+        tot.push_back(t);
+      }
+    std::sort(tot.begin(), tot.end());
+    for (size_t a = 0; a < tot.size();) {
+      size_t b = a;
+      while (b < tot.size() && tot[b] == tot[a]) ++b;
+      const int pairs = (int)(b - a);
+      // pairs (i, j) with the same total; each i appears at most once when the charges are
+      // distinct, so the block size is the pair count
+      sz.push_back(pairs);
+      a = b;
+    }
+    for (int i = 1; i < d; ++i)   // distinct charge vectors, ascending
+      if (!std::lexicographical_compare(phys_charges + (i - 1) * ncomp, phys_charges + i * ncomp,
+                                        phys_charges + i * ncomp, phys_charges + (i + 1) * ncomp))
+        return MPS_ECHARGE;
+  } else if (zn) {
+    for (int t = 0; t < zn; ++t) {
+      int n = 0;
+      for (int i = 0; i < d; ++i) n += ((t - i) % zn + zn) % zn < d;
+      if (n) sz.push_back(n);
+    }
+  } else {
+    for (int n = 0; n <= 2 * (d - 1); ++n) sz.push_back(std::min(d - 1, n) - std::max(0, n - d + 1) + 1);
+  }
+  *n_blocks = (int)sz.size();
+  int64_t len = 0;
+  for (int v : sz) len += (int64_t)v * v;
+  *length = len;
+  if (sizes) {
+    if (cap < *n_blocks) return MPS_EINVAL;
+    for (int k = 0; k < *n_blocks; ++k) sizes[k] = sz[k];
+  }
+  return MPS_OK;
+}
+
+extern "C" int mps_gate_layout(int d, int zn, int ncomp, const int32_t* phys_charges, int32_t* sizes, int cap,
+                               int* n_blocks, int64_t* length) {
+  try {
+    return gate_layout_body(d, zn, ncomp, phys_charges, sizes, cap, n_blocks, length);
+  } catch (const std::bad_alloc&) {
+    return MPS_ENOMEM;
+  } catch (...) {
+    return MPS_EINVAL;
+  }
+}

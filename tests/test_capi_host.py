@@ -211,3 +211,35 @@ def test_load_rejects_bad_rule_records_without_touching_the_gpu(built, tmp_path)
         rc = m.lib.mps_load(ctypes.byref(h), str(p).encode(), None)
         assert rc == m.MPS_EINVAL, (name, rc)
         assert not h.value
+
+
+def test_gate_layout_matches_the_oracles_gate_bases(built):
+    """mps_gate_layout against the oracle's gate bases: U(1) blocks over (i, n - i)
+    (oracle.gate_basis), Z_n blocks over (i, (q - i) mod n) with both entries below d
+    (oracle.znmps.zn_blocks_of), several U(1) charges over the pairs of each vector total
+    (oracle.multiu1.pair_blocks); the binding checks every gate against this length."""
+    import paper_2303_11409_gb300 as m
+    from oracle import gate_basis
+    from oracle.multiu1 import pair_blocks
+    from oracle.znmps import zn_blocks_of, zn_charges
+    for d in range(2, 9):
+        sizes, length = m.gate_layout(d)
+        want = [len(gate_basis(n, d)) for n in range(2 * d - 1)]
+        assert sizes == want and length == sum(k * k for k in want)
+        assert length == m.gate_length(d)
+        for n in (d, d + 1, d + 3, 2 * d + 1):
+            sizes, length = m.gate_layout(d, zn=n)
+            want = [len(zn_blocks_of(n, q, d)) for q in zn_charges(n, d)]
+            assert sizes == want and length == sum(k * k for k in want)
+            assert length == sum(len(p) ** 2 for p in m._binding.cyclic_pair_blocks(n, d).values())
+    for q in ([(0, 0), (0, 1), (1, 0), (1, 1)], [(0,), (2,), (3,)],
+              [(0, 0, 0), (0, 0, 1), (0, 1, 0), (1, 0, 0), (1, 1, 0)]):
+        sizes, length = m.gate_layout(len(q), charges=q)
+        keys, pairs = pair_blocks(q)
+        want = [len(pairs[k]) for k in keys]
+        assert sizes == want and length == sum(k * k for k in want)
+        assert length == sum(len(p) ** 2 for p in m._binding.multi_pair_blocks(q).values())
+    with pytest.raises(m.MPSError):
+        m.gate_layout(3, zn=2)                                     # Z_n needs d <= n
+    with pytest.raises(m.MPSError):
+        m.gate_layout(2, charges=[(1, 0), (0, 1)])                 # not ascending
